@@ -1,0 +1,195 @@
+/*
+ * sgm.h -- C ABI of the GB300 (sm_103a) Semi-Global Matching hot path.
+ *
+ * Method: Hernandez-Juarez et al., "Embedded real-time stereo estimation via
+ * Semi-Global Matching on the GPU", arXiv 1610.04121.  The library computes,
+ * for a rectified pair (base = left image, match = right image):
+ *   1. the 9x7 center-symmetric Census feature of every pixel (Eq. 1);
+ *   2. the matching cost MC(x,y,d) = bitcount(F_base(x,y) XOR F_match(x-d,y))
+ *      for d in [0, D) (Eq. 2);
+ *   3. the aggregated cost L_r along 2, 4 or 8 path directions (Eq. 3);
+ *   4. the summed cost S = sum_r L_r and the winner-take-all disparity
+ *      argmin_d S, lowest d on ties (Eq. 4);
+ *   5. a 3x3 median filter of that disparity (Section 2, stage 4).
+ * The problem statement is "two rectified images in, one disparity image out"
+ * (Section 2, Fig. 2).  All arithmetic is integer and the output is exact.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  Images   uint8, row-major, pitch = W bytes, H rows.
+ *  Output   uint8 disparity, row-major, pitch = W (values 0 .. D-1).
+ *  W, H     >= 1.
+ *  D        one of 32, 64, 96, 128, 160, 192, 224, 256.
+ *  P1, P2   penalties of Eq. 3, each in [0, 224] (keeps every L_r <= 255).
+ *  n_paths  2 (left-to-right, top-to-bottom), 4 (adds right-to-left and
+ *           bottom-to-top) or 8 (adds the four diagonals) (Section 4).
+ *  Borders  the feature is 0 where the 9x7 window leaves the image, and a
+ *           match column x-d < 0 uses the feature 0; the first pixel of each
+ *           path takes L_r = MC; the median copies the one-pixel border ring.
+ *  Pointers "host or device": the library asks the CUDA runtime which kind a
+ *           pointer is.  Host memory may be pageable or pinned (pinned is
+ *           faster).  Device pointers must be on the context's device.
+ *  Ownership the caller owns every buffer it passes; the library never frees
+ *           or keeps a caller pointer beyond the call, except for
+ *           sgm_submit (see there).  The library owns its context, its device
+ *           work arena and its CUDA graphs.
+ *  Errors   every function returns an sgm_status; nothing is thrown across
+ *           the ABI.  sgm_last_error(ctx) gives a human-readable reason for
+ *           the last failure on that context (thread-local to the context).
+ *  Threads  one context must not be used by two threads at once, except that
+ *           sgm_submit / sgm_poll may be called from any thread.
+ */
+#ifndef SGM_GB300_H
+#define SGM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sgm_ctx sgm_ctx;
+
+typedef enum sgm_status {
+    SGM_OK = 0,
+    SGM_EAGAIN = 1,      /* sgm_poll: the request is still running */
+    SGM_EINVAL = -1,     /* bad argument (sizes, D, penalties, paths, null pointer, unknown ticket) */
+    SGM_ENOMEM = -2,     /* device memory (or the context's memory cap) exhausted */
+    SGM_ECUDA = -3,      /* a CUDA runtime call failed; see sgm_last_error */
+    SGM_ETIMEDOUT = -4,  /* sgm_poll: the timeout elapsed */
+    SGM_ECANCELED = -5,  /* the request was cancelled by sgm_destroy */
+    SGM_EDEVICE = -6     /* a kernel reported an error through the device status word */
+} sgm_status;
+
+/* Limits checked by every entry point. */
+#define SGM_MAX_D 256
+#define SGM_MAX_PENALTY 224
+
+/* One pair of a batch (sgm_compute_batch).  Pointers as described above. */
+typedef struct sgm_pair {
+    const uint8_t *left;
+    const uint8_t *right;
+    uint8_t *disp_out;
+    int32_t W, H, D, P1, P2, n_paths;
+} sgm_pair;
+
+/*
+ * Create a context on CUDA device `device` (makes it current for the calling
+ * thread).  `mem_cap_bytes` caps the device memory the context may hold for
+ * its work arena and served requests (0 = no cap beyond the device's free
+ * memory).  `flags` must be 0.  On success *out receives the context.
+ * Errors: SGM_EINVAL (null out, bad device, flags != 0), SGM_ECUDA.
+ */
+int sgm_create(sgm_ctx **out, int device, size_t mem_cap_bytes, unsigned flags);
+
+/*
+ * Destroy a context: requests submitted and not yet finished are cancelled
+ * (their tickets then poll as SGM_ECANCELED is no longer observable, since
+ * the context is gone); the call waits for work already on the GPU to end,
+ * then frees every device and host resource.  NULL is accepted (no-op).
+ */
+int sgm_destroy(sgm_ctx *ctx);
+
+/* Text of the last error on this context ("" if none); valid until the next
+ * call on the context.  Accepts NULL (returns a static message). */
+const char *sgm_last_error(const sgm_ctx *ctx);
+
+/*
+ * Make the context enqueue its work on `cuda_stream` (a cudaStream_t of the
+ * context's device, or NULL for the context's own stream).  The caller keeps
+ * the stream alive while the context uses it.
+ */
+int sgm_set_stream(sgm_ctx *ctx, void *cuda_stream);
+
+/*
+ * Blocking disparity computation (Section 2, stages 1-5): copies host
+ * inputs in if needed, runs the whole path on the GPU, copies the result out
+ * if `disp_out` is host memory, and returns when `disp_out` holds the
+ * median-filtered disparity.  Uses the context's arena (grown on demand).
+ * Errors: SGM_EINVAL, SGM_ENOMEM, SGM_ECUDA, SGM_EDEVICE.
+ */
+int sgm_compute(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
+                int n_paths, uint8_t *disp_out);
+
+/*
+ * Non-blocking form for device pointers only: enqueues the whole path on the
+ * context's stream and returns at once.  `left`, `right` and `disp_out` must
+ * be device memory; the caller synchronises the stream before reading
+ * `disp_out`.  The launch sequence for one (W, H, D, P1, P2, n_paths) and one
+ * set of pointers is captured once into a CUDA graph and replayed.
+ * Errors: SGM_EINVAL (including host pointers), SGM_ENOMEM, SGM_ECUDA.
+ */
+int sgm_compute_async(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
+                      int n_paths, uint8_t *disp_out);
+
+/*
+ * Batched computation of `n` independent pairs of possibly different sizes,
+ * D, penalties and path counts (the paper's scaling argument, Section 4,
+ * applied to many pairs at once).  Each stage runs as one launch over a
+ * device work list covering every pair.  Pointers of each pair as in
+ * sgm_compute (all host or all device per pair).  Blocking.
+ * Each pair's result is bit-identical to sgm_compute of that pair alone.
+ * Errors: SGM_EINVAL (n < 0, null pairs, any invalid pair), SGM_ENOMEM,
+ * SGM_ECUDA, SGM_EDEVICE.
+ */
+int sgm_compute_batch(sgm_ctx *ctx, int n, const sgm_pair *pairs);
+
+/*
+ * Served form: queue one pair and return a ticket at once.  A scheduler
+ * thread owned by the context admits queued requests while device memory
+ * (within mem_cap_bytes) allows, batches whatever is admitted into one
+ * launch sequence, and keeps up to two batches in flight on the GPU.
+ * The caller keeps left/right/disp_out alive and unmodified until sgm_poll
+ * returns something other than SGM_EAGAIN for the ticket.
+ * Errors: SGM_EINVAL (bad pair or null ticket), SGM_ENOMEM (the pair alone
+ * exceeds the memory cap).
+ */
+int sgm_submit(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
+               int n_paths, uint8_t *disp_out, uint64_t *ticket);
+
+/*
+ * Wait up to `timeout_us` microseconds (0 = just test, < 0 = wait forever)
+ * for a submitted request.  Returns SGM_OK once `disp_out` holds the result
+ * (the ticket is then retired), SGM_EAGAIN if timeout_us == 0 and it is not
+ * done, SGM_ETIMEDOUT if the wait elapsed, SGM_EINVAL for an unknown ticket,
+ * or the request's own error status.
+ */
+int sgm_poll(sgm_ctx *ctx, uint64_t ticket, int64_t timeout_us);
+
+/*
+ * Served-request latency statistics since the context was created:
+ * out[0] = completed requests, out[1] = p50 latency (us), out[2] = p99
+ * latency (us), out[3] = max latency (us); latency = poll-visible completion
+ * time minus submit time.  `n_out` must be >= 4.
+ */
+int sgm_served_stats(sgm_ctx *ctx, double *out, int n_out);
+
+/*
+ * Debug form of sgm_compute for localising a mismatch stage by stage.  All
+ * pointers are host pointers; each optional output may be NULL:
+ *   Fb, Fm   uint32 [H][W]    Census features of left and right (Eq. 1)
+ *   MC       uint8  [H][W][D] matching cost (Eq. 2), d fastest
+ *   S        uint16 [H][W][D] summed aggregated cost (Eq. 4's sum)
+ *   raw      uint8  [H][W]    winner-take-all disparity before the median
+ *   disp     uint8  [H][W]    final disparity
+ * Errors as sgm_compute.
+ */
+int sgm_debug_stages(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
+                     int n_paths, uint32_t *Fb, uint32_t *Fm, uint8_t *MC, uint16_t *S, uint8_t *raw, uint8_t *disp);
+
+/*
+ * Kernel launches issued by this context so far (every launch of this
+ * library's kernels, counted on the host when enqueued; a replayed graph
+ * adds the launches it contains).
+ */
+uint64_t sgm_kernel_launches(const sgm_ctx *ctx);
+
+/* Library version string. */
+const char *sgm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGM_GB300_H */

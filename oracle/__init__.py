@@ -1,0 +1,21 @@
+"""CPU oracle for the SGM hot path (test infrastructure only).
+
+The oracle is the plain C program in ``sgm_oracle.c``.  Only the tests, the
+smoke check and the benchmark's CPU-baseline leg may use it; the product path
+never imports it.  Build it with ``build()`` (gcc, no GPU needed).
+"""
+from .oracle import (  # noqa: F401
+    build,
+    load,
+    csct,
+    csct_at,
+    bitcount,
+    cost,
+    aggregate,
+    directions,
+    wta,
+    median3x3,
+    sgm,
+    pixel,
+    disp_at,
+)

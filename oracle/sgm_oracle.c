@@ -1,0 +1,300 @@
+/*
+ * CPU oracle for the SGM hot path of Hernandez-Juarez et al., "Embedded
+ * real-time stereo estimation via Semi-Global Matching on the GPU"
+ * (arXiv 1610.04121).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain, obviously-correct
+ * statement of what the GPU path must compute.  Only the test-suite, the
+ * smoke check and the benchmark's CPU-baseline leg may load it.  It shares no
+ * code, header, table or helper with the CUDA library, and the CUDA library
+ * never calls it.
+ *
+ * Every quantity is an int32 and every loop follows the paper's definitions
+ * in the paper's order; there is no blocking, fusion or vectorisation.
+ *
+ * Readings where the paper is silent (each is also listed in the design notes):
+ *  - s(u, v) = 1 if u >= v, else 0 (Section 3.1, Eq. 1).
+ *  - Bit k of the CSCT feature is the k-th comparison of Eq. 1 in its printed
+ *    order: i = 1..4 (outer), j = -3..3 (inner), then the three i = 0 pairs
+ *    j = 1..3; bit 0 is the least significant bit.
+ *  - The feature is 0 wherever the 9x7 window leaves the image
+ *    (4 <= x <= W-5 and 3 <= y <= H-4 are the valid centres).
+ *  - In Eq. 2 a match column x-d < 0 uses the feature 0.
+ *  - Eq. 3 at the first pixel of a path (p - r outside the image) is
+ *    L_r(p, d) = MC(p, d); disparities d-1 < 0 and d+1 >= D drop out of
+ *    the minimum.
+ *  - Eq. 4 breaks ties toward the lowest d.
+ *  - The 3x3 median (Section 2, stage 4) takes the 5th of the 9 sorted
+ *    values in the interior and copies the raw disparity on the one-pixel
+ *    border ring (and everywhere when W < 3 or H < 3).
+ *  - Path sets: 2 paths = left-to-right and top-to-bottom; 4 paths adds
+ *    right-to-left and bottom-to-top; 8 paths adds the four diagonals
+ *    (Section 4).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_EXPORT __attribute__((visibility("default")))
+
+/* s(u, v) of Eq. 1. */
+static int census_s(int u, int v) { return u >= v ? 1 : 0; }
+
+static int pixel(const uint8_t *I, int W, int x, int y) { return (int)I[(size_t)y * W + x]; }
+
+/*
+ * Eq. 1 (Section 3.1): the 9x7 center-symmetric Census transform of pixel
+ * (x, y); 0 when the window leaves the image.
+ */
+ORACLE_EXPORT uint32_t oracle_csct_at(const uint8_t *I, int W, int H, int x, int y) {
+    uint32_t f = 0;
+    int inside = (x - 4 >= 0) && (x + 4 <= W - 1) && (y - 3 >= 0) && (y + 3 <= H - 1);
+    if (!inside) return 0;
+    int k = 0;
+    for (int i = 1; i <= 4; ++i) {
+        for (int j = -3; j <= 3; ++j) {
+            int bit = census_s(pixel(I, W, x + i, y + j), pixel(I, W, x - i, y - j));
+            f |= (uint32_t)bit << k;
+            ++k;
+        }
+    }
+    for (int j = 1; j <= 3; ++j) {
+        int bit = census_s(pixel(I, W, x, y + j), pixel(I, W, x, y - j));
+        f |= (uint32_t)bit << k;
+        ++k;
+    }
+    return f;
+}
+
+/* Eq. 1 over the whole image: F[y*W + x] = CSCT(I, x, y). */
+ORACLE_EXPORT void oracle_csct(const uint8_t *I, int W, int H, uint32_t *F) {
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) F[(size_t)y * W + x] = oracle_csct_at(I, W, H, x, y);
+}
+
+/* bitcount of Eq. 2, written as a plain loop over the 32 bit positions. */
+ORACLE_EXPORT int oracle_bitcount(uint32_t v) {
+    int c = 0;
+    for (int b = 0; b < 32; ++b) c += (int)((v >> b) & 1u);
+    return c;
+}
+
+/* Match feature used by Eq. 2: zero left of the image. */
+static uint32_t match_feature(const uint32_t *Fm, int W, int x, int y) {
+    if (x < 0) return 0;
+    return Fm[(size_t)y * W + x];
+}
+
+/*
+ * Eq. 2 (Section 3.1): MC(x, y, d) = bitcount(F_base(x, y) XOR F_match(x-d, y)).
+ * Output layout MC[y][x][d], d fastest (Section 3.1, layout discussion).
+ */
+ORACLE_EXPORT void oracle_cost(const uint32_t *Fb, const uint32_t *Fm, int W, int H, int D, uint8_t *MC) {
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x)
+            for (int d = 0; d < D; ++d) {
+                uint32_t v = Fb[(size_t)y * W + x] ^ match_feature(Fm, W, x - d, y);
+                MC[((size_t)y * W + x) * D + d] = (uint8_t)oracle_bitcount(v);
+            }
+}
+
+/*
+ * Eq. 3 (Section 3.2) along one direction r = (rx, ry), rx, ry in {-1, 0, 1}.
+ * The predecessor of p = (x, y) is q = (x - rx, y - ry).  Pixels are visited
+ * so that q is always finished before p.  L[y][x][d] (int32) receives L_r.
+ */
+ORACLE_EXPORT void oracle_aggregate(const uint8_t *MC, int W, int H, int D, int P1, int P2, int rx, int ry,
+                                    int32_t *L) {
+    int y0 = (ry >= 0) ? 0 : H - 1, y1 = (ry >= 0) ? H : -1, sy = (ry >= 0) ? 1 : -1;
+    int x0 = (rx >= 0) ? 0 : W - 1, x1 = (rx >= 0) ? W : -1, sx = (rx >= 0) ? 1 : -1;
+    for (int y = y0; y != y1; y += sy) {
+        for (int x = x0; x != x1; x += sx) {
+            const uint8_t *mc = MC + ((size_t)y * W + x) * D;
+            int32_t *out = L + ((size_t)y * W + x) * D;
+            int qx = x - rx, qy = y - ry;
+            if (qx < 0 || qx >= W || qy < 0 || qy >= H) {
+                for (int d = 0; d < D; ++d) out[d] = mc[d];
+                continue;
+            }
+            const int32_t *prev = L + ((size_t)qy * W + qx) * D;
+            int32_t mprev = prev[0];
+            for (int k = 1; k < D; ++k)
+                if (prev[k] < mprev) mprev = prev[k];
+            for (int d = 0; d < D; ++d) {
+                int32_t best = prev[d];
+                if (d - 1 >= 0 && prev[d - 1] + P1 < best) best = prev[d - 1] + P1;
+                if (d + 1 < D && prev[d + 1] + P1 < best) best = prev[d + 1] + P1;
+                if (mprev + P2 < best) best = mprev + P2;
+                out[d] = (int32_t)mc[d] + best - mprev;
+            }
+        }
+    }
+}
+
+/* The direction set for n_paths in {2, 4, 8}; returns the count, or 0. */
+ORACLE_EXPORT int oracle_directions(int n_paths, int *rx, int *ry) {
+    static const int dx[8] = {1, 0, -1, 0, 1, -1, 1, -1};
+    static const int dy[8] = {0, 1, 0, -1, 1, 1, -1, -1};
+    if (n_paths != 2 && n_paths != 4 && n_paths != 8) return 0;
+    for (int i = 0; i < n_paths; ++i) {
+        rx[i] = dx[i];
+        ry[i] = dy[i];
+    }
+    return n_paths;
+}
+
+/* Eq. 4 (Section 3.2): disparity = the lowest d minimising S(p, d). */
+ORACLE_EXPORT void oracle_wta(const int32_t *S, int W, int H, int D, uint8_t *disp) {
+    for (size_t p = 0; p < (size_t)W * H; ++p) {
+        const int32_t *s = S + p * D;
+        int best = 0;
+        for (int d = 1; d < D; ++d)
+            if (s[d] < s[best]) best = d;
+        disp[p] = (uint8_t)best;
+    }
+}
+
+/* 3x3 median of stage 4 (Section 2). */
+ORACLE_EXPORT void oracle_median3x3(const uint8_t *in, int W, int H, uint8_t *out) {
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            size_t p = (size_t)y * W + x;
+            if (x == 0 || y == 0 || x == W - 1 || y == H - 1) {
+                out[p] = in[p];
+                continue;
+            }
+            int v[9], n = 0;
+            for (int j = -1; j <= 1; ++j)
+                for (int i = -1; i <= 1; ++i) v[n++] = in[(size_t)(y + j) * W + (x + i)];
+            /* insertion sort */
+            for (int a = 1; a < 9; ++a) {
+                int t = v[a], b = a - 1;
+                while (b >= 0 && v[b] > t) {
+                    v[b + 1] = v[b];
+                    --b;
+                }
+                v[b + 1] = t;
+            }
+            out[p] = (uint8_t)v[4];
+        }
+    }
+}
+
+/*
+ * The whole path of Section 2, stages 2-4: features, matching cost, the
+ * aggregated paths, S, the winner-take-all disparity and the 3x3 median.
+ * Optional debug outputs (NULL to skip): Fb/Fm features (uint32 [H][W]),
+ * S (int32 [H][W][D]), raw disparity (uint8 [H][W]).
+ * Returns 0, or -1 on bad arguments, -2 if memory runs out.
+ */
+ORACLE_EXPORT int oracle_sgm(const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
+                             int n_paths, uint8_t *disp_out, uint8_t *raw_out, uint32_t *Fb_out, uint32_t *Fm_out,
+                             int32_t *S_out) {
+    int rx[8], ry[8];
+    if (W < 1 || H < 1 || D < 1 || D > 256 || !left || !right || !disp_out) return -1;
+    int npaths = oracle_directions(n_paths, rx, ry);
+    if (npaths == 0) return -1;
+    size_t n = (size_t)W * H;
+    uint32_t *Fb = (uint32_t *)malloc(n * sizeof(uint32_t));
+    uint32_t *Fm = (uint32_t *)malloc(n * sizeof(uint32_t));
+    uint8_t *MC = (uint8_t *)malloc(n * D);
+    int32_t *L = (int32_t *)malloc(n * D * sizeof(int32_t));
+    int32_t *S = (int32_t *)calloc(n * D, sizeof(int32_t));
+    uint8_t *raw = (uint8_t *)malloc(n);
+    int rc = 0;
+    if (!Fb || !Fm || !MC || !L || !S || !raw) {
+        rc = -2;
+        goto done;
+    }
+    oracle_csct(left, W, H, Fb);
+    oracle_csct(right, W, H, Fm);
+    oracle_cost(Fb, Fm, W, H, D, MC);
+    for (int r = 0; r < npaths; ++r) {
+        oracle_aggregate(MC, W, H, D, P1, P2, rx[r], ry[r], L);
+        for (size_t i = 0; i < n * D; ++i) S[i] += L[i];
+    }
+    oracle_wta(S, W, H, D, raw);
+    if (W < 3 || H < 3)
+        memcpy(disp_out, raw, n);
+    else
+        oracle_median3x3(raw, W, H, disp_out);
+    if (raw_out) memcpy(raw_out, raw, n);
+    if (Fb_out) memcpy(Fb_out, Fb, n * sizeof(uint32_t));
+    if (Fm_out) memcpy(Fm_out, Fm, n * sizeof(uint32_t));
+    if (S_out) memcpy(S_out, S, n * D * sizeof(int32_t));
+done:
+    free(Fb);
+    free(Fm);
+    free(MC);
+    free(L);
+    free(S);
+    free(raw);
+    return rc;
+}
+
+/*
+ * The same quantities at one pixel only, for checks on images too large for
+ * oracle_sgm: S(p, .) at p = (px, py) (int32 [D]) and its raw disparity.
+ * For each direction r, Eq. 3 is evaluated along the single path that ends
+ * at p, starting from the first pixel of that path inside the image; the
+ * costs along the path come from Eq. 1 and Eq. 2 evaluated at each pixel.
+ * Returns the raw disparity, or -1 on bad arguments, -2 if memory runs out.
+ */
+ORACLE_EXPORT int oracle_pixel(const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
+                               int n_paths, int px, int py, int32_t *S_out) {
+    int rx[8], ry[8];
+    if (W < 1 || H < 1 || D < 1 || D > 256 || px < 0 || px >= W || py < 0 || py >= H) return -1;
+    int npaths = oracle_directions(n_paths, rx, ry);
+    if (npaths == 0) return -1;
+    int32_t *S = (int32_t *)calloc((size_t)D, sizeof(int32_t));
+    int32_t *Lprev = (int32_t *)malloc((size_t)D * sizeof(int32_t));
+    int32_t *Lcur = (int32_t *)malloc((size_t)D * sizeof(int32_t));
+    int result = -2;
+    if (!S || !Lprev || !Lcur) goto done;
+    for (int r = 0; r < npaths; ++r) {
+        /* walk back from p to the first pixel of the path inside the image */
+        int x = px, y = py, len = 1;
+        while (x - rx[r] >= 0 && x - rx[r] < W && y - ry[r] >= 0 && y - ry[r] < H) {
+            x -= rx[r];
+            y -= ry[r];
+            ++len;
+        }
+        for (int step = 0; step < len; ++step) {
+            uint32_t fb = oracle_csct_at(left, W, H, x, y);
+            int32_t mprev = 0;
+            if (step > 0) {
+                mprev = Lprev[0];
+                for (int k = 1; k < D; ++k)
+                    if (Lprev[k] < mprev) mprev = Lprev[k];
+            }
+            for (int d = 0; d < D; ++d) {
+                uint32_t fm = (x - d >= 0) ? oracle_csct_at(right, W, H, x - d, y) : 0u;
+                int mc = oracle_bitcount(fb ^ fm);
+                if (step == 0) {
+                    Lcur[d] = mc;
+                } else {
+                    int32_t best = Lprev[d];
+                    if (d - 1 >= 0 && Lprev[d - 1] + P1 < best) best = Lprev[d - 1] + P1;
+                    if (d + 1 < D && Lprev[d + 1] + P1 < best) best = Lprev[d + 1] + P1;
+                    if (mprev + P2 < best) best = mprev + P2;
+                    Lcur[d] = mc + best - mprev;
+                }
+            }
+            int32_t *t = Lprev;
+            Lprev = Lcur;
+            Lcur = t;
+            x += rx[r];
+            y += ry[r];
+        }
+        for (int d = 0; d < D; ++d) S[d] += Lprev[d];
+    }
+    result = 0;
+    for (int d = 1; d < D; ++d)
+        if (S[d] < S[result]) result = d;
+    if (S_out) memcpy(S_out, S, (size_t)D * sizeof(int32_t));
+done:
+    free(S);
+    free(Lprev);
+    free(Lcur);
+    return result;
+}
