@@ -1,0 +1,310 @@
+"""Benchmark of the SGM hot path (arXiv 1610.04121) on GB300.
+
+One step = the whole path (Census, matching cost, path aggregation, sum,
+winner-take-all, 3x3 median) over one synthetic stereo pair already resident
+in HBM.  Default workload: 640x480, D = 128, 4 paths, P1 = 7, P2 = 84 (the
+paper's headline shape, Section 4).  The metric is MDE/s = W*H*D per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun (N > 1) every rank processes its own pairs (replicas: pairs are
+independent and one pair does not shard), so per-GPU work is fixed and the
+scaling is weak.  ``--impl reference`` times the CPU oracle on the host cores
+instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import stereo_synth as synth  # noqa: E402
+
+DEFAULT_WORKLOAD = "sgm_640x480_d128_p4"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+SM_COUNT_GB300 = 152
+SM_MAX_MHZ_GB300 = 2070.0
+# Algorithmic integer operations per disparity evaluation (DE) and path of
+# Eq. 3: two "+P1", three minima, "+MC", "-m" and one minimum of the
+# reduction over d; the winner-take-all adds one add per extra term and one
+# minimum.  Packed u16x2 arithmetic does two of them per lane instruction.
+OPS_PER_DE_PATH = 8
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": SM_MAX_MHZ_GB300}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].strip()
+                                                         .replace('.', '', 1).isdigit()) if rows else None}
+
+
+def oracle_mdes(w, max_seconds: float, rows: int = 0):
+    """Time the CPU oracle (single thread, as it stands) on the workload."""
+    import oracle
+
+    oracle.build()
+    pair = synth.workload_pair(w.name)
+    left, right = pair.left, pair.right
+    if rows:
+        left, right = left[:rows].copy(), right[:rows].copy()
+    H, W = left.shape
+    n, t0 = 0, time.perf_counter()
+    while True:
+        oracle.sgm(left, right, w.spec.D, w.P1, w.P2, w.n_paths)
+        n += 1
+        if time.perf_counter() - t0 >= max_seconds:
+            break
+    dt = time.perf_counter() - t0
+    return W * H * w.spec.D * n / dt / 1e6, n, (W, H)
+
+
+def run_reference(args, w, ws, rank):
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    pair = synth.workload_pair(w.name)
+    # each step is a bounded sample: a band of rows of the frame, sized so the
+    # whole run stays within a few minutes
+    rows = min(w.spec.H, max(16, int(96 * 200 / max(args.steps + args.warmup, 1))))
+    left, right = pair.left[:rows].copy(), pair.right[:rows].copy()
+    for _ in range(args.warmup):
+        oracle.sgm(left, right, w.spec.D, w.P1, w.P2, w.n_paths)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sgm(left, right, w.spec.D, w.P1, w.P2, w.n_paths)
+    dt = time.perf_counter() - t0
+    de = w.spec.W * rows * w.spec.D
+    value = de * args.steps / dt / 1e6
+    sample = f"{w.spec.W}x{rows} band (rows 0..{rows - 1}) of the {w.spec.W}x{w.spec.H} D={w.spec.D} frame per step"
+    line = {
+        "impl": "reference", "metric": "MDE/s", "value": value, "unit": "MDE/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded stereo_synth pair)",
+        "config": workload_config(w),
+        "cpu_baseline": {"value": value, "unit": "MDE/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "MDE/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(w):
+    return {"workload": w.name, "W": w.spec.W, "H": w.spec.H, "D": w.spec.D, "P1": w.P1, "P2": w.P2,
+            "n_paths": w.n_paths, "pairs_per_step": 1}
+
+
+def main():
+    args = parse()
+    w = synth.WORKLOADS[args.workload]
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, w, ws, rank)
+
+    import torch
+
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        pg = dist
+    torch.cuda.set_device(local)
+    from paper_1610_04121_gb300 import sgm
+
+    W, H, D = w.spec.W, w.spec.H, w.spec.D
+    pair = synth.make_pair(w.spec, synth.BASE_SEED + synth.WORKLOAD_INDEX[w.name] + 7919 * rank)
+    dev = torch.device("cuda", local)
+    L = torch.from_numpy(pair.left).to(dev)
+    R = torch.from_numpy(pair.right).to(dev)
+    out = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = sgm.Context(local, flags=sgm.SGM_FLAG_STAGE_TIMING)
+    sgm.sgm_set_stream(ctx.handle, stream)
+
+    def step():
+        sgm.sgm_compute_async(ctx.handle, L, R, W, H, D, w.P1, w.P2, w.n_paths, out)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage_ms = {}
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = ctx.launches
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)  # evict the previous step's data from L2
+            ev0[k].record(stream)
+            step()
+            ev1[k].record(stream)
+            for name, ms in sgm.sgm_stage_times(ctx.handle).items():  # waits for this step
+                stage_ms.setdefault(name, []).append(ms)
+        torch.cuda.synchronize(dev)
+        if pg:
+            pg.barrier()
+    launches = ctx.launches - launches0
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    total_ms = sum(step_ms)
+    if pg:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    de = W * H * D
+    value = ws * args.steps * de / (total_ms / 1e3) / 1e6
+
+    # dominant kernel and its roofline (integer ALU: packed u16x2 lanes)
+    peaks, peak_kind = load_peaks()
+    clocks = clk.summary()
+    mean_stage = {k: statistics.mean(v) for k, v in stage_ms.items()}
+    dom = max(mean_stage, key=mean_stage.get)
+    paths_in = {"sweep_h": 2 if w.n_paths >= 4 else 1, "sweep_v": 2 if w.n_paths >= 4 else 1,
+                "sweep_diag+": 2, "sweep_diag-": 2}
+    roofline = None
+    if dom in paths_in:
+        ops = de * (OPS_PER_DE_PATH * paths_in[dom] + (3 if dom == "sweep_v" else 1))
+        sm_mhz = float(peaks.get("sm_max_mhz", SM_MAX_MHZ_GB300))
+        peak_tops = SM_COUNT_GB300 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        achieved = ops / (mean_stage[dom] / 1e3) / 1e12
+        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                    "frac": achieved / peak_tops, "traffic": None,
+                    "peak_source": f"152 SMs x 128 lanes x 2 (u16x2) x {sm_mhz:.0f} MHz (recipe unit counts, "
+                                   f"max clock)", "ops_per_launch": ops}
+    frame_bytes = 2 * W * H + W * H + 4 * de
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    frame_gbs = frame_bytes / (ms_per_step / 1e3) / 1e9
+    frame_roofline = {"bound": "hbm", "achieved": frame_gbs, "peak": hbm, "unit": "GB/s", "frac": frame_gbs / hbm,
+                      "algorithmic_bytes_per_frame": frame_bytes, "peak_source": f"{peak_kind} hbm_gbs"}
+
+    # end to end through the public C call with pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        Lh = torch.from_numpy(pair.left).pin_memory()
+        Rh = torch.from_numpy(pair.right).pin_memory()
+        Oh = torch.empty((H, W), dtype=torch.uint8).pin_memory()
+        ctx2 = sgm.Context(local)
+        for _ in range(3):
+            sgm.sgm_compute(ctx2.handle, Lh, Rh, W, H, D, w.P1, w.P2, w.n_paths, Oh)
+        if pg:
+            pg.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            sgm.sgm_compute(ctx2.handle, Lh, Rh, W, H, D, w.P1, w.P2, w.n_paths, Oh)
+        dt = time.perf_counter() - t0
+        if pg:
+            t = torch.tensor([dt], device=dev, dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": ws * args.e2e_steps * de / dt / 1e6, "unit": "MDE/s", "h2d_bytes_per_step": 2 * W * H,
+               "d2h_bytes_per_step": W * H, "ms_per_step": dt / args.e2e_steps * 1e3, "api": "sgm_compute"}
+        ctx2.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, n, (bw, bh) = oracle_mdes(w, max_seconds=10.0)
+        cpu = {"value": v, "unit": "MDE/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n} full {bw}x{bh} D={D} {w.n_paths}-path frames, single thread, ~10 s"}
+
+    if rank == 0:
+        line = {
+            "metric": "MDE/s", "value": value, "unit": "MDE/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u16", "data": "synthetic (seeded stereo_synth pair, resident in HBM)",
+            "config": dict(workload_config(w), parallelism=f"replicas x{ws}",
+                           l2="flushed between timed steps (256 MiB write)", fps=1e3 / ms_per_step),
+            "roofline": roofline, "frame_roofline": frame_roofline,
+            "stage_ms": {k: round(v, 5) for k, v in mean_stage.items()},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

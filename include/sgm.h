@@ -45,6 +45,12 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define SGM_API __attribute__((visibility("default")))
+#else
+#define SGM_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -62,6 +68,9 @@ typedef enum sgm_status {
     SGM_EDEVICE = -6     /* a kernel reported an error through the device status word */
 } sgm_status;
 
+/* sgm_create flags. */
+#define SGM_FLAG_STAGE_TIMING 1u /* record a CUDA event between the kernels of every path (sgm_stage_times) */
+
 /* Limits checked by every entry point. */
 #define SGM_MAX_D 256
 #define SGM_MAX_PENALTY 224
@@ -78,10 +87,11 @@ typedef struct sgm_pair {
  * Create a context on CUDA device `device` (makes it current for the calling
  * thread).  `mem_cap_bytes` caps the device memory the context may hold for
  * its work arena and served requests (0 = no cap beyond the device's free
- * memory).  `flags` must be 0.  On success *out receives the context.
- * Errors: SGM_EINVAL (null out, bad device, flags != 0), SGM_ECUDA.
+ * memory).  `flags` is 0 or SGM_FLAG_STAGE_TIMING.  On success *out
+ * receives the context.
+ * Errors: SGM_EINVAL (null out, bad device, unknown flag), SGM_ECUDA.
  */
-int sgm_create(sgm_ctx **out, int device, size_t mem_cap_bytes, unsigned flags);
+SGM_API int sgm_create(sgm_ctx **out, int device, size_t mem_cap_bytes, unsigned flags);
 
 /*
  * Destroy a context: requests submitted and not yet finished are cancelled
@@ -89,18 +99,18 @@ int sgm_create(sgm_ctx **out, int device, size_t mem_cap_bytes, unsigned flags);
  * the context is gone); the call waits for work already on the GPU to end,
  * then frees every device and host resource.  NULL is accepted (no-op).
  */
-int sgm_destroy(sgm_ctx *ctx);
+SGM_API int sgm_destroy(sgm_ctx *ctx);
 
 /* Text of the last error on this context ("" if none); valid until the next
  * call on the context.  Accepts NULL (returns a static message). */
-const char *sgm_last_error(const sgm_ctx *ctx);
+SGM_API const char *sgm_last_error(const sgm_ctx *ctx);
 
 /*
  * Make the context enqueue its work on `cuda_stream` (a cudaStream_t of the
  * context's device, or NULL for the context's own stream).  The caller keeps
  * the stream alive while the context uses it.
  */
-int sgm_set_stream(sgm_ctx *ctx, void *cuda_stream);
+SGM_API int sgm_set_stream(sgm_ctx *ctx, void *cuda_stream);
 
 /*
  * Blocking disparity computation (Section 2, stages 1-5): copies host
@@ -109,7 +119,7 @@ int sgm_set_stream(sgm_ctx *ctx, void *cuda_stream);
  * median-filtered disparity.  Uses the context's arena (grown on demand).
  * Errors: SGM_EINVAL, SGM_ENOMEM, SGM_ECUDA, SGM_EDEVICE.
  */
-int sgm_compute(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
+SGM_API int sgm_compute(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
                 int n_paths, uint8_t *disp_out);
 
 /*
@@ -120,7 +130,7 @@ int sgm_compute(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, int W, 
  * set of pointers is captured once into a CUDA graph and replayed.
  * Errors: SGM_EINVAL (including host pointers), SGM_ENOMEM, SGM_ECUDA.
  */
-int sgm_compute_async(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
+SGM_API int sgm_compute_async(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
                       int n_paths, uint8_t *disp_out);
 
 /*
@@ -133,7 +143,7 @@ int sgm_compute_async(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, i
  * Errors: SGM_EINVAL (n < 0, null pairs, any invalid pair), SGM_ENOMEM,
  * SGM_ECUDA, SGM_EDEVICE.
  */
-int sgm_compute_batch(sgm_ctx *ctx, int n, const sgm_pair *pairs);
+SGM_API int sgm_compute_batch(sgm_ctx *ctx, int n, const sgm_pair *pairs);
 
 /*
  * Served form: queue one pair and return a ticket at once.  A scheduler
@@ -145,7 +155,7 @@ int sgm_compute_batch(sgm_ctx *ctx, int n, const sgm_pair *pairs);
  * Errors: SGM_EINVAL (bad pair or null ticket), SGM_ENOMEM (the pair alone
  * exceeds the memory cap).
  */
-int sgm_submit(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
+SGM_API int sgm_submit(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
                int n_paths, uint8_t *disp_out, uint64_t *ticket);
 
 /*
@@ -155,7 +165,7 @@ int sgm_submit(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, int W, i
  * done, SGM_ETIMEDOUT if the wait elapsed, SGM_EINVAL for an unknown ticket,
  * or the request's own error status.
  */
-int sgm_poll(sgm_ctx *ctx, uint64_t ticket, int64_t timeout_us);
+SGM_API int sgm_poll(sgm_ctx *ctx, uint64_t ticket, int64_t timeout_us);
 
 /*
  * Served-request latency statistics since the context was created:
@@ -163,7 +173,7 @@ int sgm_poll(sgm_ctx *ctx, uint64_t ticket, int64_t timeout_us);
  * latency (us), out[3] = max latency (us); latency = poll-visible completion
  * time minus submit time.  `n_out` must be >= 4.
  */
-int sgm_served_stats(sgm_ctx *ctx, double *out, int n_out);
+SGM_API int sgm_served_stats(sgm_ctx *ctx, double *out, int n_out);
 
 /*
  * Debug form of sgm_compute for localising a mismatch stage by stage.  All
@@ -175,18 +185,32 @@ int sgm_served_stats(sgm_ctx *ctx, double *out, int n_out);
  *   disp     uint8  [H][W]    final disparity
  * Errors as sgm_compute.
  */
-int sgm_debug_stages(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
+SGM_API int sgm_debug_stages(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
                      int n_paths, uint32_t *Fb, uint32_t *Fm, uint8_t *MC, uint16_t *S, uint8_t *raw, uint8_t *disp);
+
+/*
+ * Per-kernel device times (milliseconds) of the most recent path this context
+ * enqueued through sgm_compute / sgm_compute_async, in launch order; needs a
+ * context created with SGM_FLAG_STAGE_TIMING.  Waits for that path to finish.
+ * Writes min(n, stages) values to ms_out and returns the number of stages
+ * (5 for 2 or 4 paths, 7 for 8 paths), or a negative sgm_status.
+ * Stage names, in order: census, cost, sweep_h, [sweep_diag+, sweep_diag-,]
+ * sweep_v, median (sgm_stage_name).
+ */
+SGM_API int sgm_stage_times(sgm_ctx *ctx, float *ms_out, int n);
+
+/* Name of stage i of a path with n_paths directions, or NULL. */
+SGM_API const char *sgm_stage_name(int n_paths, int i);
 
 /*
  * Kernel launches issued by this context so far (every launch of this
  * library's kernels, counted on the host when enqueued; a replayed graph
  * adds the launches it contains).
  */
-uint64_t sgm_kernel_launches(const sgm_ctx *ctx);
+SGM_API uint64_t sgm_kernel_launches(const sgm_ctx *ctx);
 
 /* Library version string. */
-const char *sgm_version(void);
+SGM_API const char *sgm_version(void);
 
 #ifdef __cplusplus
 }

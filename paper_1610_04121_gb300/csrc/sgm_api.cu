@@ -1,0 +1,583 @@
+// C ABI of the SGM path (include/sgm.h): context, device work arena, launch
+// sequence and CUDA-graph cache, batched and served execution.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "sgm.h"
+#include "sgm_internal.h"
+
+using namespace sgm;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// Offsets of one pair's buffers inside a work arena.
+struct Layout {
+    size_t Fb, Fm, MC, Lx, S, raw, in_left, in_right, out, total;
+};
+
+Layout layout_for(int W, int H, int D) {
+    const size_t wh = static_cast<size_t>(W) * H;
+    Layout l{};
+    size_t o = 0;
+    l.Fb = o;
+    o = align_up(o + 4 * wh);
+    l.Fm = o;
+    o = align_up(o + 4 * wh);
+    l.MC = o;
+    o = align_up(o + wh * D);
+    l.Lx = o;
+    o = align_up(o + wh * D);
+    l.S = o;
+    o = align_up(o + 2 * wh * D);
+    l.raw = o;
+    o = align_up(o + wh);
+    l.in_left = o;
+    o = align_up(o + wh);
+    l.in_right = o;
+    o = align_up(o + wh);
+    l.out = o;
+    o = align_up(o + wh);
+    l.total = o;
+    return l;
+}
+
+struct Problem {
+    int W, H, D, P1, P2, n_paths;
+};
+
+bool valid_problem(const Problem& p, std::string* why) {
+    char buf[160];
+    if (p.W < 1 || p.H < 1) {
+        snprintf(buf, sizeof buf, "W and H must be >= 1 (got %d x %d)", p.W, p.H);
+    } else if (!supported_D(p.D)) {
+        snprintf(buf, sizeof buf, "D must be a multiple of 32 in [32, %d] (got %d)", SGM_MAX_D, p.D);
+    } else if (p.P1 < 0 || p.P1 > SGM_MAX_PENALTY || p.P2 < 0 || p.P2 > SGM_MAX_PENALTY) {
+        snprintf(buf, sizeof buf, "P1 and P2 must lie in [0, %d] (got %d, %d)", SGM_MAX_PENALTY, p.P1, p.P2);
+    } else if (p.n_paths != 2 && p.n_paths != 4 && p.n_paths != 8) {
+        snprintf(buf, sizeof buf, "n_paths must be 2, 4 or 8 (got %d)", p.n_paths);
+    } else if (static_cast<double>(p.W) * p.H * p.D > 8.0e9) {
+        snprintf(buf, sizeof buf, "W*H*D too large (%d x %d x %d)", p.W, p.H, p.D);
+    } else {
+        return true;
+    }
+    *why = buf;
+    return false;
+}
+
+struct GraphKey {
+    Problem p;
+    const void *left, *right, *out, *arena;
+    bool operator<(const GraphKey& o) const {
+        return std::tie(p.W, p.H, p.D, p.P1, p.P2, p.n_paths, left, right, out, arena) <
+               std::tie(o.p.W, o.p.H, o.p.D, o.p.P1, o.p.P2, o.p.n_paths, o.left, o.right, o.out, o.arena);
+    }
+};
+
+struct Request {
+    uint64_t ticket;
+    Problem p;
+    const uint8_t *left, *right;
+    uint8_t* out;
+    std::chrono::steady_clock::time_point t_submit;
+};
+
+}  // namespace
+
+struct sgm_ctx {
+    int device = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    size_t mem_cap = 0;
+    uint8_t* arena = nullptr;
+    size_t arena_bytes = 0;
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::string err;
+    std::atomic<uint64_t> launches{0};
+    bool stage_timing = false;
+    cudaEvent_t stage_ev[8] = {};
+    int last_stages = 0;
+
+    // served requests
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request> queue;
+    std::unordered_map<uint64_t, int> done;  // ticket -> status, finished and not yet polled
+    std::unordered_set<uint64_t> outstanding;  // submitted and not yet retired by sgm_poll
+    std::vector<double> latencies_us;
+    uint64_t next_ticket = 1;
+    size_t pending = 0;
+    bool stop = false;
+    bool worker_started = false;
+    std::thread worker;
+    cudaStream_t serve_stream = nullptr;
+    uint8_t* serve_arena = nullptr;
+    size_t serve_arena_bytes = 0;
+};
+
+static thread_local std::string g_noctx_err;
+
+static int fail(sgm_ctx* ctx, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx)
+        ctx->err = buf;
+    else
+        g_noctx_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                                                   \
+    do {                                                                                                      \
+        cudaError_t e_ = (call);                                                                              \
+        if (e_ != cudaSuccess)                                                                                \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? SGM_ENOMEM : SGM_ECUDA, "%s: %s (%s:%d)", #call, \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                                          \
+    } while (0)
+
+static int ensure_arena(sgm_ctx* ctx, uint8_t** arena, size_t* bytes, size_t need, bool clear_graphs) {
+    if (*bytes >= need) return SGM_OK;
+    const size_t used_elsewhere = (arena == &ctx->arena) ? ctx->serve_arena_bytes : ctx->arena_bytes;
+    if (ctx->mem_cap && need + used_elsewhere > ctx->mem_cap)
+        return fail(ctx, SGM_ENOMEM, "work arena of %zu bytes exceeds the context's memory cap of %zu bytes", need,
+                    ctx->mem_cap);
+    if (*arena) {
+        cudaError_t e = cudaFree(*arena);
+        *arena = nullptr;
+        *bytes = 0;
+        if (e != cudaSuccess) return fail(ctx, SGM_ECUDA, "cudaFree: %s", cudaGetErrorString(e));
+    }
+    if (clear_graphs) {
+        for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+        ctx->graphs.clear();
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, need);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, SGM_ENOMEM, "cudaMalloc(%zu) for the work arena: %s", need, cudaGetErrorString(e));
+    }
+    *arena = static_cast<uint8_t*>(p);
+    *bytes = need;
+    return SGM_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static int launches_per_path(const Problem& p) { return p.n_paths == 8 ? 7 : 5; }
+
+// Enqueue the whole path (Section 2, stages 2-4) for one pair whose inputs
+// and output are device pointers.  Returns a cudaError_t.
+static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const uint8_t* left,
+                                const uint8_t* right, uint8_t* disp, uint16_t* Sdbg, cudaStream_t s, bool timed) {
+    const Layout l = layout_for(p.W, p.H, p.D);
+    uint32_t* Fb = reinterpret_cast<uint32_t*>(arena + l.Fb);
+    uint32_t* Fm = reinterpret_cast<uint32_t*>(arena + l.Fm);
+    uint8_t* MC = arena + l.MC;
+    cudaError_t e;
+    int stage = 0;
+    // with stage timing, event k is recorded before kernel k and after the last
+    auto mark = [&]() -> cudaError_t {
+        if (!timed) return cudaSuccess;
+        return cudaEventRecord(ctx->stage_ev[stage++], s);
+    };
+    if ((e = mark()) != cudaSuccess) return e;
+    if ((e = launch_census(left, right, Fb, Fm, p.W, p.H, s)) != cudaSuccess) return e;
+    if ((e = mark()) != cudaSuccess) return e;
+    if ((e = launch_cost(Fb, Fm, MC, p.W, p.H, p.D, s)) != cudaSuccess) return e;
+    if ((e = mark()) != cudaSuccess) return e;
+    SweepArgs a{};
+    a.MC = MC;
+    a.Lx = arena + l.Lx;
+    a.S = reinterpret_cast<uint32_t*>(arena + l.S);
+    a.raw = arena + l.raw;
+    a.Sdbg = Sdbg;
+    a.W = p.W;
+    a.H = p.H;
+    a.D = p.D;
+    a.P1x2 = static_cast<uint32_t>(p.P1) * 0x10001u;
+    a.P2x2 = static_cast<uint32_t>(p.P2) * 0x10001u;
+    a.pair = p.n_paths >= 4;
+    a.rx = 0;
+    a.wta = 0;
+    if ((e = launch_sweep_h(a, s)) != cudaSuccess) return e;
+    if ((e = mark()) != cudaSuccess) return e;
+    if (p.n_paths == 8) {
+        a.rx = 1;
+        if ((e = launch_sweep_v(a, s)) != cudaSuccess) return e;
+        if ((e = mark()) != cudaSuccess) return e;
+        a.rx = -1;
+        if ((e = launch_sweep_v(a, s)) != cudaSuccess) return e;
+        if ((e = mark()) != cudaSuccess) return e;
+    }
+    a.rx = 0;
+    a.wta = 1;
+    if ((e = launch_sweep_v(a, s)) != cudaSuccess) return e;
+    if ((e = mark()) != cudaSuccess) return e;
+    if ((e = launch_median(a.raw, disp, p.W, p.H, s)) != cudaSuccess) return e;
+    if ((e = mark()) != cudaSuccess) return e;
+    ctx->launches += launches_per_path(p);
+    return cudaSuccess;
+}
+
+// Enqueue through a cached CUDA graph for this problem and these pointers.
+static int enqueue_graph(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const uint8_t* left, const uint8_t* right,
+                         uint8_t* disp, cudaStream_t s) {
+    GraphKey key{p, left, right, disp, arena};
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) {
+        if (ctx->graphs.size() >= 64) {
+            for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+            ctx->graphs.clear();
+        }
+        cudaGraph_t g = nullptr;
+        CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+        const uint64_t before = ctx->launches.load();
+        cudaError_t e = enqueue_path(ctx, p, arena, left, right, disp, nullptr, ctx->capture_stream, ctx->stage_timing);
+        ctx->launches = before;  // captured, not launched
+        cudaError_t e2 = cudaStreamEndCapture(ctx->capture_stream, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return fail(ctx, SGM_ECUDA, "graph capture failed: %s / %s", cudaGetErrorString(e),
+                        cudaGetErrorString(e2));
+        }
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(ctx, SGM_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        it = ctx->graphs.emplace(key, exec).first;
+    }
+    CUDA_TRY(ctx, cudaGraphLaunch(it->second, s));
+    ctx->launches += launches_per_path(p);
+    ctx->last_stages = ctx->stage_timing ? launches_per_path(p) : 0;
+    return SGM_OK;
+}
+
+// Copy-in / path / copy-out for one pair into `arena` (already large enough).
+static int enqueue_pair(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const uint8_t* left, const uint8_t* right,
+                        uint8_t* disp, cudaStream_t s, bool use_graph) {
+    const Layout l = layout_for(p.W, p.H, p.D);
+    const size_t wh = static_cast<size_t>(p.W) * p.H;
+    const uint8_t* dl = left;
+    const uint8_t* dr = right;
+    uint8_t* dout = disp;
+    if (!is_device_ptr(left)) {
+        CUDA_TRY(ctx, cudaMemcpyAsync(arena + l.in_left, left, wh, cudaMemcpyHostToDevice, s));
+        dl = arena + l.in_left;
+    }
+    if (!is_device_ptr(right)) {
+        CUDA_TRY(ctx, cudaMemcpyAsync(arena + l.in_right, right, wh, cudaMemcpyHostToDevice, s));
+        dr = arena + l.in_right;
+    }
+    const bool out_host = !is_device_ptr(disp);
+    if (out_host) dout = arena + l.out;
+    if (use_graph) {
+        int rc = enqueue_graph(ctx, p, arena, dl, dr, dout, s);
+        if (rc != SGM_OK) return rc;
+    } else {
+        CUDA_TRY(ctx, enqueue_path(ctx, p, arena, dl, dr, dout, nullptr, s, false));
+    }
+    if (out_host) CUDA_TRY(ctx, cudaMemcpyAsync(disp, dout, wh, cudaMemcpyDeviceToHost, s));
+    return SGM_OK;
+}
+
+static int check_args(sgm_ctx* ctx, const Problem& p, const void* left, const void* right, const void* out) {
+    if (!ctx) return fail(nullptr, SGM_EINVAL, "null context");
+    if (!left || !right || !out) return fail(ctx, SGM_EINVAL, "null image or output pointer");
+    std::string why;
+    if (!valid_problem(p, &why)) return fail(ctx, SGM_EINVAL, "%s", why.c_str());
+    return SGM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Served requests: a worker thread runs queued pairs in submission order on
+// its own stream and arena and records each ticket's status.
+// ---------------------------------------------------------------------------
+static void serve_loop(sgm_ctx* ctx) {
+    cudaSetDevice(ctx->device);
+    for (;;) {
+        Request r;
+        {
+            std::unique_lock<std::mutex> lk(ctx->mu);
+            ctx->cv_work.wait(lk, [&] { return ctx->stop || !ctx->queue.empty(); });
+            if (ctx->queue.empty()) return;  // stop requested and nothing queued
+            r = ctx->queue.front();
+            ctx->queue.pop_front();
+        }
+        int rc;
+        if (ctx->stop) {
+            rc = SGM_ECANCELED;
+        } else {
+            const Layout l = layout_for(r.p.W, r.p.H, r.p.D);
+            rc = ensure_arena(ctx, &ctx->serve_arena, &ctx->serve_arena_bytes, l.total, false);
+            if (rc == SGM_OK)
+                rc = enqueue_pair(ctx, r.p, ctx->serve_arena, r.left, r.right, r.out, ctx->serve_stream, false);
+            if (rc == SGM_OK) {
+                cudaError_t e = cudaStreamSynchronize(ctx->serve_stream);
+                if (e != cudaSuccess) rc = fail(ctx, SGM_ECUDA, "served request: %s", cudaGetErrorString(e));
+            }
+        }
+        const double us =
+            std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - r.t_submit).count();
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            ctx->done[r.ticket] = rc;
+            if (rc == SGM_OK) ctx->latencies_us.push_back(us);
+            --ctx->pending;
+        }
+        ctx->cv_done.notify_all();
+    }
+}
+
+extern "C" {
+
+int sgm_create(sgm_ctx** out, int device, size_t mem_cap_bytes, unsigned flags) {
+    if (!out) return fail(nullptr, SGM_EINVAL, "null output pointer");
+    *out = nullptr;
+    if (flags & ~SGM_FLAG_STAGE_TIMING) return fail(nullptr, SGM_EINVAL, "unknown flags %#x", flags);
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return fail(nullptr, SGM_ECUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+    if (device < 0 || device >= n) return fail(nullptr, SGM_EINVAL, "device %d out of range [0, %d)", device, n);
+    if ((e = cudaSetDevice(device)) != cudaSuccess)
+        return fail(nullptr, SGM_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    sgm_ctx* ctx = new sgm_ctx();
+    ctx->device = device;
+    ctx->mem_cap = mem_cap_bytes;
+    if ((e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&ctx->serve_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        sgm_destroy(ctx);
+        return fail(nullptr, SGM_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    }
+    ctx->stream = ctx->own_stream;
+    ctx->stage_timing = (flags & SGM_FLAG_STAGE_TIMING) != 0;
+    if (ctx->stage_timing) {
+        for (auto& ev : ctx->stage_ev) {
+            if ((e = cudaEventCreate(&ev)) != cudaSuccess) {
+                sgm_destroy(ctx);
+                return fail(nullptr, SGM_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
+            }
+        }
+    }
+    *out = ctx;
+    return SGM_OK;
+}
+
+int sgm_destroy(sgm_ctx* ctx) {
+    if (!ctx) return SGM_OK;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->stop = true;
+    }
+    ctx->cv_work.notify_all();
+    if (ctx->worker.joinable()) ctx->worker.join();
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    if (ctx->arena) cudaFree(ctx->arena);
+    if (ctx->serve_arena) cudaFree(ctx->serve_arena);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    if (ctx->serve_stream) cudaStreamDestroy(ctx->serve_stream);
+    for (auto& ev : ctx->stage_ev)
+        if (ev) cudaEventDestroy(ev);
+    delete ctx;
+    return SGM_OK;
+}
+
+const char* sgm_last_error(const sgm_ctx* ctx) { return ctx ? ctx->err.c_str() : g_noctx_err.c_str(); }
+
+int sgm_set_stream(sgm_ctx* ctx, void* cuda_stream) {
+    if (!ctx) return fail(nullptr, SGM_EINVAL, "null context");
+    ctx->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->own_stream;
+    return SGM_OK;
+}
+
+int sgm_compute(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H, int D, int P1, int P2,
+                int n_paths, uint8_t* disp_out) {
+    const Problem p{W, H, D, P1, P2, n_paths};
+    int rc = check_args(ctx, p, left, right, disp_out);
+    if (rc != SGM_OK) return rc;
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, layout_for(W, H, D).total, true);
+    if (rc != SGM_OK) return rc;
+    rc = enqueue_pair(ctx, p, ctx->arena, left, right, disp_out, ctx->stream, true);
+    if (rc != SGM_OK) return rc;
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return SGM_OK;
+}
+
+int sgm_compute_async(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H, int D, int P1, int P2,
+                      int n_paths, uint8_t* disp_out) {
+    const Problem p{W, H, D, P1, P2, n_paths};
+    int rc = check_args(ctx, p, left, right, disp_out);
+    if (rc != SGM_OK) return rc;
+    if (!is_device_ptr(left) || !is_device_ptr(right) || !is_device_ptr(disp_out))
+        return fail(ctx, SGM_EINVAL, "sgm_compute_async takes device pointers only");
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, layout_for(W, H, D).total, true);
+    if (rc != SGM_OK) return rc;
+    return enqueue_graph(ctx, p, ctx->arena, left, right, disp_out, ctx->stream);
+}
+
+int sgm_compute_batch(sgm_ctx* ctx, int n, const sgm_pair* pairs) {
+    if (!ctx) return fail(nullptr, SGM_EINVAL, "null context");
+    if (n < 0 || (n > 0 && !pairs)) return fail(ctx, SGM_EINVAL, "bad batch (n=%d, pairs=%p)", n, (const void*)pairs);
+    size_t need = 0;
+    for (int i = 0; i < n; ++i) {
+        const sgm_pair& q = pairs[i];
+        const Problem p{q.W, q.H, q.D, q.P1, q.P2, q.n_paths};
+        int rc = check_args(ctx, p, q.left, q.right, q.disp_out);
+        if (rc != SGM_OK) return fail(ctx, rc, "pair %d: %s", i, ctx->err.c_str());
+        need = std::max(need, layout_for(q.W, q.H, q.D).total);
+    }
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    int rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, need, true);
+    if (rc != SGM_OK) return rc;
+    for (int i = 0; i < n; ++i) {
+        const sgm_pair& q = pairs[i];
+        const Problem p{q.W, q.H, q.D, q.P1, q.P2, q.n_paths};
+        rc = enqueue_pair(ctx, p, ctx->arena, q.left, q.right, q.disp_out, ctx->stream, false);
+        if (rc != SGM_OK) return rc;
+    }
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return SGM_OK;
+}
+
+int sgm_submit(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H, int D, int P1, int P2,
+               int n_paths, uint8_t* disp_out, uint64_t* ticket) {
+    const Problem p{W, H, D, P1, P2, n_paths};
+    int rc = check_args(ctx, p, left, right, disp_out);
+    if (rc != SGM_OK) return rc;
+    if (!ticket) return fail(ctx, SGM_EINVAL, "null ticket pointer");
+    if (ctx->mem_cap && layout_for(W, H, D).total + ctx->arena_bytes > ctx->mem_cap)
+        return fail(ctx, SGM_ENOMEM, "pair %dx%d D=%d needs more than the context's memory cap", W, H, D);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->worker_started) {
+        ctx->worker = std::thread(serve_loop, ctx);
+        ctx->worker_started = true;
+    }
+    Request r{ctx->next_ticket++, p, left, right, disp_out, std::chrono::steady_clock::now()};
+    *ticket = r.ticket;
+    ctx->queue.push_back(r);
+    ctx->outstanding.insert(r.ticket);
+    ++ctx->pending;
+    ctx->cv_work.notify_one();
+    return SGM_OK;
+}
+
+int sgm_poll(sgm_ctx* ctx, uint64_t ticket, int64_t timeout_us) {
+    if (!ctx) return fail(nullptr, SGM_EINVAL, "null context");
+    std::unique_lock<std::mutex> lk(ctx->mu);
+    if (!ctx->outstanding.count(ticket))
+        return fail(ctx, SGM_EINVAL, "unknown or already retired ticket %llu", (unsigned long long)ticket);
+    auto ready = [&] { return ctx->done.count(ticket) != 0; };
+    if (!ready()) {
+        if (timeout_us == 0) return SGM_EAGAIN;
+        if (timeout_us < 0) {
+            ctx->cv_done.wait(lk, ready);
+        } else if (!ctx->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) {
+            return SGM_ETIMEDOUT;
+        }
+    }
+    const int rc = ctx->done[ticket];
+    ctx->done.erase(ticket);
+    ctx->outstanding.erase(ticket);
+    return rc;
+}
+
+int sgm_served_stats(sgm_ctx* ctx, double* out, int n_out) {
+    if (!ctx || !out || n_out < 4) return fail(ctx, SGM_EINVAL, "sgm_served_stats needs a context and 4 outputs");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    std::vector<double> v = ctx->latencies_us;
+    std::sort(v.begin(), v.end());
+    auto q = [&](double f) { return v.empty() ? 0.0 : v[std::min(v.size() - 1, static_cast<size_t>(f * v.size()))]; };
+    out[0] = static_cast<double>(v.size());
+    out[1] = q(0.50);
+    out[2] = q(0.99);
+    out[3] = v.empty() ? 0.0 : v.back();
+    return SGM_OK;
+}
+
+int sgm_debug_stages(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H, int D, int P1, int P2,
+                     int n_paths, uint32_t* Fb, uint32_t* Fm, uint8_t* MC, uint16_t* S, uint8_t* raw, uint8_t* disp) {
+    const Problem p{W, H, D, P1, P2, n_paths};
+    int rc = check_args(ctx, p, left, right, left);
+    if (rc != SGM_OK) return rc;
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const Layout l = layout_for(W, H, D);
+    const size_t wh = static_cast<size_t>(W) * H;
+    const size_t extra = align_up(wh * D * 2) + align_up(wh * D);
+    rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, l.total + extra, true);
+    if (rc != SGM_OK) return rc;
+    uint8_t* a = ctx->arena;
+    uint16_t* Sdev = reinterpret_cast<uint16_t*>(a + l.total);
+    uint8_t* MCnat = a + l.total + align_up(wh * D * 2);
+    cudaStream_t s = ctx->stream;
+    CUDA_TRY(ctx, cudaMemcpyAsync(a + l.in_left, left, wh, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(ctx, cudaMemcpyAsync(a + l.in_right, right, wh, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(ctx, enqueue_path(ctx, p, a, a + l.in_left, a + l.in_right, a + l.out, S ? Sdev : nullptr, s, false));
+    if (Fb) CUDA_TRY(ctx, cudaMemcpyAsync(Fb, a + l.Fb, 4 * wh, cudaMemcpyDeviceToHost, s));
+    if (Fm) CUDA_TRY(ctx, cudaMemcpyAsync(Fm, a + l.Fm, 4 * wh, cudaMemcpyDeviceToHost, s));
+    if (MC) {
+        CUDA_TRY(ctx, launch_unpair_cost(a + l.MC, MCnat, W, H, D, s));
+        CUDA_TRY(ctx, cudaMemcpyAsync(MC, MCnat, wh * D, cudaMemcpyDeviceToHost, s));
+    }
+    if (S) CUDA_TRY(ctx, cudaMemcpyAsync(S, Sdev, 2 * wh * D, cudaMemcpyDeviceToHost, s));
+    if (raw) CUDA_TRY(ctx, cudaMemcpyAsync(raw, a + l.raw, wh, cudaMemcpyDeviceToHost, s));
+    if (disp) CUDA_TRY(ctx, cudaMemcpyAsync(disp, a + l.out, wh, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    return SGM_OK;
+}
+
+int sgm_stage_times(sgm_ctx* ctx, float* ms_out, int n) {
+    if (!ctx) return fail(nullptr, SGM_EINVAL, "null context");
+    if (!ctx->stage_timing) return fail(ctx, SGM_EINVAL, "context was created without SGM_FLAG_STAGE_TIMING");
+    const int k = ctx->last_stages;
+    if (k == 0) return fail(ctx, SGM_EINVAL, "no path has been enqueued yet");
+    CUDA_TRY(ctx, cudaEventSynchronize(ctx->stage_ev[k]));
+    for (int i = 0; i < k && i < n; ++i) CUDA_TRY(ctx, cudaEventElapsedTime(&ms_out[i], ctx->stage_ev[i], ctx->stage_ev[i + 1]));
+    return k;
+}
+
+const char* sgm_stage_name(int n_paths, int i) {
+    static const char* four[] = {"census", "cost", "sweep_h", "sweep_v", "median"};
+    static const char* eight[] = {"census", "cost", "sweep_h", "sweep_diag+", "sweep_diag-", "sweep_v", "median"};
+    if (n_paths == 8) return (i >= 0 && i < 7) ? eight[i] : nullptr;
+    if (n_paths == 2 || n_paths == 4) return (i >= 0 && i < 5) ? four[i] : nullptr;
+    return nullptr;
+}
+
+uint64_t sgm_kernel_launches(const sgm_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
+
+const char* sgm_version(void) { return "sgm-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

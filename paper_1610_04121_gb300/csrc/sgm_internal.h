@@ -1,0 +1,36 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sgm {
+
+// Arguments of the aggregation sweeps (Eq. 3) over one pair.
+struct SweepArgs {
+    const uint8_t* MC;  // paired costs [H][W][D]
+    uint8_t* Lx;        // scratch: one direction's path costs, paired [H][W][D]
+    uint32_t* S;        // packed sums [H][W][D/2]
+    uint8_t* raw;       // winner-take-all disparity [H][W] (final vertical sweep)
+    uint16_t* Sdbg;     // optional natural-order S [H][W][D] (debug)
+    int W, H, D;
+    uint32_t P1x2, P2x2;  // penalties replicated in both u16 halves
+    int rx;               // vertical-type sweeps: 0 (vertical), +1 / -1 (diagonals)
+    int pair;             // 1: both opposite directions, 0: the forward one only
+    int wta;              // vertical-type sweeps: 1 = finish with Eq. 4, 0 = add into S
+};
+
+// Each launcher enqueues one kernel on `stream` and returns the launch error.
+cudaError_t launch_census(const uint8_t* left, const uint8_t* right, uint32_t* Fb, uint32_t* Fm, int W, int H,
+                          cudaStream_t stream);
+cudaError_t launch_cost(const uint32_t* Fb, const uint32_t* Fm, uint8_t* MC, int W, int H, int D,
+                        cudaStream_t stream);
+cudaError_t launch_sweep_h(const SweepArgs& a, cudaStream_t stream);
+cudaError_t launch_sweep_v(const SweepArgs& a, cudaStream_t stream);
+cudaError_t launch_median(const uint8_t* raw, uint8_t* disp, int W, int H, cudaStream_t stream);
+// Debug: paired costs -> natural order [H][W][D].
+cudaError_t launch_unpair_cost(const uint8_t* MC, uint8_t* out, int W, int H, int D, cudaStream_t stream);
+
+bool supported_D(int D);
+
+}  // namespace sgm

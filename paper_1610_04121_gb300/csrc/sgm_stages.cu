@@ -1,0 +1,166 @@
+// Census (Eq. 1), matching cost (Eq. 2) and the 3x3 median (Section 2,
+// stage 4) of the SGM path in arXiv 1610.04121, for sm_103a.
+#include "sgm_device.cuh"
+#include "sgm_internal.h"
+
+namespace sgm {
+
+// ---------------------------------------------------------------------------
+// Eq. 1: 9x7 center-symmetric Census transform.  A CTA computes a 32x16 tile
+// of features from a (32+8)x(16+6) byte tile staged in shared memory (the
+// read-cooperative 2D tiling of Section 3.1); blockIdx.z picks the image.
+// The feature is 0 where the 9x7 window leaves the image.
+// Bit k follows the printed order of Eq. 1: i = 1..4, j = -3..3 give bit
+// (i-1)*7 + j+3; the i = 0 pairs j = 1..3 give bits 28..30; s(u,v) = u >= v.
+// ---------------------------------------------------------------------------
+constexpr int kCtW = 32, kCtH = 16;
+
+__global__ void __launch_bounds__(256) census_kernel(const uint8_t* __restrict__ left,
+                                                     const uint8_t* __restrict__ right, uint32_t* __restrict__ Fb,
+                                                     uint32_t* __restrict__ Fm, int W, int H) {
+    __shared__ uint8_t tile[kCtH + 6][kCtW + 8];
+    const uint8_t* img = blockIdx.z ? right : left;
+    uint32_t* F = blockIdx.z ? Fm : Fb;
+    const int x0 = blockIdx.x * kCtW, y0 = blockIdx.y * kCtH;
+    const int t = threadIdx.y * 32 + threadIdx.x;
+    for (int i = t; i < (kCtH + 6) * (kCtW + 8); i += 256) {
+        const int ty = i / (kCtW + 8), tx = i % (kCtW + 8);
+        const int gx = x0 - 4 + tx, gy = y0 - 3 + ty;
+        tile[ty][tx] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? img[(size_t)gy * W + gx] : 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kCtH / 8; ++r) {
+        const int lx = threadIdx.x, ly = threadIdx.y + 8 * r;
+        const int x = x0 + lx, y = y0 + ly;
+        if (x >= W || y >= H) continue;
+        uint32_t f = 0;
+        if (x >= 4 && x <= W - 5 && y >= 3 && y <= H - 4) {
+            const int cx = lx + 4, cy = ly + 3;
+            int k = 0;
+#pragma unroll
+            for (int i = 1; i <= 4; ++i)
+#pragma unroll
+                for (int j = -3; j <= 3; ++j, ++k)
+                    f |= static_cast<uint32_t>(tile[cy + j][cx + i] >= tile[cy - j][cx - i]) << k;
+#pragma unroll
+            for (int j = 1; j <= 3; ++j, ++k) f |= static_cast<uint32_t>(tile[cy + j][cx] >= tile[cy - j][cx]) << k;
+        }
+        F[(size_t)y * W + x] = f;
+    }
+}
+
+cudaError_t launch_census(const uint8_t* left, const uint8_t* right, uint32_t* Fb, uint32_t* Fm, int W, int H,
+                          cudaStream_t stream) {
+    dim3 grid((W + kCtW - 1) / kCtW, (H + kCtH - 1) / kCtH, 2);
+    census_kernel<<<grid, dim3(32, 8), 0, stream>>>(left, right, Fb, Fm, W, H);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 2: MC(x, y, d) = bitcount(F_base(x, y) XOR F_match(x - d, y)), with the
+// match feature 0 left of the image.  A CTA covers 32 pixels of one row; the
+// match features x0-D+1 .. x0+31 are staged in shared memory (the 1D tiling
+// of Section 3.1) and every thread writes one 32-bit word = two paired words.
+// ---------------------------------------------------------------------------
+constexpr int kMcSeg = 32;
+
+__global__ void __launch_bounds__(256) cost_kernel(const uint32_t* __restrict__ Fb, const uint32_t* __restrict__ Fm,
+                                                   uint8_t* __restrict__ MC, int W, int H, int D) {
+    extern __shared__ uint32_t smem[];
+    uint32_t* fm = smem;                      // D - 1 + kMcSeg match features
+    uint32_t* fb = smem + (D - 1 + kMcSeg);   // kMcSeg base features
+    const int y = blockIdx.y, x0 = blockIdx.x * kMcSeg;
+    const uint32_t* fmrow = Fm + (size_t)y * W;
+    for (int i = threadIdx.x; i < D - 1 + kMcSeg; i += blockDim.x) {
+        const int gx = x0 - (D - 1) + i;
+        fm[i] = (gx >= 0 && gx < W) ? fmrow[gx] : 0u;
+    }
+    for (int i = threadIdx.x; i < kMcSeg; i += blockDim.x) fb[i] = (x0 + i < W) ? Fb[(size_t)y * W + x0 + i] : 0u;
+    __syncthreads();
+    const int Q = D / 4, half = D / 2;
+    const int npx = min(kMcSeg, W - x0);
+    uint32_t* out = reinterpret_cast<uint32_t*>(MC + ((size_t)y * W + x0) * D);
+    for (int t = threadIdx.x; t < npx * Q; t += blockDim.x) {
+        const int px = t / Q, i0 = 2 * (t % Q);
+        const uint32_t b = fb[px];
+        const int base = px + D - 1;  // fm[base - d] = F_match(x - d)
+        const uint32_t c0 = __popc(b ^ fm[base - i0]);
+        const uint32_t c1 = __popc(b ^ fm[base - i0 - half]);
+        const uint32_t c2 = __popc(b ^ fm[base - i0 - 1]);
+        const uint32_t c3 = __popc(b ^ fm[base - i0 - 1 - half]);
+        out[t] = c0 | (c1 << 8) | (c2 << 16) | (c3 << 24);
+    }
+}
+
+cudaError_t launch_cost(const uint32_t* Fb, const uint32_t* Fm, uint8_t* MC, int W, int H, int D,
+                        cudaStream_t stream) {
+    dim3 grid((W + kMcSeg - 1) / kMcSeg, H);
+    const size_t smem = (size_t)(D - 1 + 2 * kMcSeg) * sizeof(uint32_t);
+    cost_kernel<<<grid, 256, smem, stream>>>(Fb, Fm, MC, W, H, D);
+    return cudaGetLastError();
+}
+
+// Paired order -> natural order (debug only).
+__global__ void unpair_kernel(const uint8_t* __restrict__ MC, uint8_t* __restrict__ out, size_t npix, int D) {
+    const size_t n = npix * D;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t p = t / D;
+        const int d = static_cast<int>(t % D);
+        const int half = D / 2;
+        const int src = (d < half) ? 2 * d : 2 * (d - half) + 1;
+        out[t] = MC[p * D + src];
+    }
+}
+
+cudaError_t launch_unpair_cost(const uint8_t* MC, uint8_t* out, int W, int H, int D, cudaStream_t stream) {
+    unpair_kernel<<<1024, 256, 0, stream>>>(MC, out, (size_t)W * H, D);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// 3x3 median of the winner-take-all disparity (Section 2, stage 4).  The
+// one-pixel border ring copies the raw value.  With each row of the window
+// sorted (lo <= mid <= hi), the median of the nine values is the median of
+// {max of the lows, median of the mids, min of the highs}.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void sort3(int& a, int& b, int& c) {
+    const int lo = min(a, b), hi = max(a, b);
+    a = min(lo, c);
+    const int m = max(lo, c);
+    b = min(m, hi);
+    c = max(m, hi);
+}
+
+__device__ __forceinline__ int med3(int a, int b, int c) { return max(min(a, b), min(max(a, b), c)); }
+
+__global__ void __launch_bounds__(256) median_kernel(const uint8_t* __restrict__ raw, uint8_t* __restrict__ out,
+                                                     int W, int H) {
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= W || y >= H) return;
+    const size_t p = (size_t)y * W + x;
+    if (x == 0 || y == 0 || x == W - 1 || y == H - 1) {
+        out[p] = raw[p];
+        return;
+    }
+    int a0 = raw[p - W - 1], b0 = raw[p - W], c0 = raw[p - W + 1];
+    int a1 = raw[p - 1], b1 = raw[p], c1 = raw[p + 1];
+    int a2 = raw[p + W - 1], b2 = raw[p + W], c2 = raw[p + W + 1];
+    sort3(a0, b0, c0);
+    sort3(a1, b1, c1);
+    sort3(a2, b2, c2);
+    const int lo = max(max(a0, a1), a2);
+    const int mid = med3(b0, b1, b2);
+    const int hi = min(min(c0, c1), c2);
+    out[p] = static_cast<uint8_t>(med3(lo, mid, hi));
+}
+
+cudaError_t launch_median(const uint8_t* raw, uint8_t* disp, int W, int H, cudaStream_t stream) {
+    dim3 grid((W + 31) / 32, (H + 7) / 8);
+    median_kernel<<<grid, dim3(32, 8), 0, stream>>>(raw, disp, W, H);
+    return cudaGetLastError();
+}
+
+bool supported_D(int D) { return D >= 32 && D <= 256 && D % 32 == 0; }
+
+}  // namespace sgm

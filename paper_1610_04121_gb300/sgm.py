@@ -1,0 +1,237 @@
+"""Thin ctypes binding of the C ABI in ``include/sgm.h``.
+
+Functions keep the C names and only marshal arguments: every stage of the
+path runs in the CUDA library.  There is no CPU fallback: importing this
+module raises if ``_lib/libsgm_gb300.so`` has not been built.
+
+Array arguments may be numpy arrays (host memory), torch tensors (host or
+CUDA) or raw integer addresses.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, Optional, Sequence
+
+from . import build as _build
+
+LIB_PATH = _build.LIB_PATH
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"the SGM CUDA library is not built ({LIB_PATH} is missing); run "
+        "`python -m paper_1610_04121_gb300.build` (needs nvcc) -- there is no CPU fallback")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+SGM_OK, SGM_EAGAIN, SGM_EINVAL, SGM_ENOMEM = 0, 1, -1, -2
+SGM_ECUDA, SGM_ETIMEDOUT, SGM_ECANCELED, SGM_EDEVICE = -3, -4, -5, -6
+STATUS_NAMES = {0: "SGM_OK", 1: "SGM_EAGAIN", -1: "SGM_EINVAL", -2: "SGM_ENOMEM", -3: "SGM_ECUDA",
+                -4: "SGM_ETIMEDOUT", -5: "SGM_ECANCELED", -6: "SGM_EDEVICE"}
+SGM_FLAG_STAGE_TIMING = 1
+SGM_MAX_D = 256
+SGM_MAX_PENALTY = 224
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+
+
+class sgm_pair(ctypes.Structure):
+    _fields_ = [("left", _vp), ("right", _vp), ("disp_out", _vp), ("W", ctypes.c_int32), ("H", ctypes.c_int32),
+                ("D", ctypes.c_int32), ("P1", ctypes.c_int32), ("P2", ctypes.c_int32),
+                ("n_paths", ctypes.c_int32)]
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_sig("sgm_create", _i, [ctypes.POINTER(_vp), _i, ctypes.c_size_t, ctypes.c_uint])
+_sig("sgm_destroy", _i, [_vp])
+_sig("sgm_last_error", ctypes.c_char_p, [_vp])
+_sig("sgm_set_stream", _i, [_vp, _vp])
+_sig("sgm_compute", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp])
+_sig("sgm_compute_async", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp])
+_sig("sgm_compute_batch", _i, [_vp, _i, ctypes.POINTER(sgm_pair)])
+_sig("sgm_submit", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, ctypes.POINTER(ctypes.c_uint64)])
+_sig("sgm_poll", _i, [_vp, ctypes.c_uint64, ctypes.c_int64])
+_sig("sgm_served_stats", _i, [_vp, ctypes.POINTER(ctypes.c_double), _i])
+_sig("sgm_debug_stages", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp])
+_sig("sgm_kernel_launches", ctypes.c_uint64, [_vp])
+_sig("sgm_stage_times", _i, [_vp, ctypes.POINTER(ctypes.c_float), _i])
+_sig("sgm_stage_name", ctypes.c_char_p, [_i, _i])
+_sig("sgm_version", ctypes.c_char_p, [])
+
+
+class SgmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def addr(x) -> Optional[int]:
+    """Address of a numpy array, torch tensor or integer (None stays None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if hasattr(x, "ctypes"):
+        return int(x.ctypes.data)
+    raise TypeError(f"cannot take the address of {type(x).__name__}")
+
+
+def _check(ctx, rc: int, allow=(SGM_OK,)) -> int:
+    if rc not in allow:
+        raise SgmError(rc, last_error(ctx))
+    return rc
+
+
+def last_error(ctx) -> str:
+    s = _lib.sgm_last_error(ctx)
+    return s.decode() if s else ""
+
+
+def sgm_version() -> str:
+    return _lib.sgm_version().decode()
+
+
+def sgm_create(device: int = 0, mem_cap_bytes: int = 0, flags: int = 0) -> int:
+    out = _vp()
+    _check(None, _lib.sgm_create(ctypes.byref(out), device, mem_cap_bytes, flags))
+    return out.value
+
+
+def sgm_destroy(ctx) -> None:
+    _lib.sgm_destroy(ctx)
+
+
+def sgm_set_stream(ctx, stream) -> None:
+    """`stream`: a torch.cuda.Stream, an integer cudaStream_t, or None."""
+    handle = getattr(stream, "cuda_stream", stream)
+    _check(ctx, _lib.sgm_set_stream(ctx, handle))
+
+
+def sgm_compute(ctx, left, right, W, H, D, P1, P2, n_paths, disp_out) -> None:
+    _check(ctx, _lib.sgm_compute(ctx, addr(left), addr(right), W, H, D, P1, P2, n_paths, addr(disp_out)))
+
+
+def sgm_compute_async(ctx, left, right, W, H, D, P1, P2, n_paths, disp_out) -> None:
+    _check(ctx, _lib.sgm_compute_async(ctx, addr(left), addr(right), W, H, D, P1, P2, n_paths, addr(disp_out)))
+
+
+def sgm_compute_batch(ctx, pairs: Sequence[tuple]) -> None:
+    """pairs: (left, right, disp_out, W, H, D, P1, P2, n_paths) tuples."""
+    arr = (sgm_pair * max(1, len(pairs)))()
+    for i, (l, r, o, W, H, D, P1, P2, npth) in enumerate(pairs):
+        arr[i] = sgm_pair(addr(l), addr(r), addr(o), W, H, D, P1, P2, npth)
+    _check(ctx, _lib.sgm_compute_batch(ctx, len(pairs), arr))
+
+
+def sgm_submit(ctx, left, right, W, H, D, P1, P2, n_paths, disp_out) -> int:
+    t = ctypes.c_uint64()
+    _check(ctx, _lib.sgm_submit(ctx, addr(left), addr(right), W, H, D, P1, P2, n_paths, addr(disp_out),
+                                ctypes.byref(t)))
+    return t.value
+
+
+def sgm_poll(ctx, ticket: int, timeout_us: int = -1) -> int:
+    """Returns SGM_OK, SGM_EAGAIN or SGM_ETIMEDOUT; raises on errors."""
+    return _check(ctx, _lib.sgm_poll(ctx, ticket, timeout_us), allow=(SGM_OK, SGM_EAGAIN, SGM_ETIMEDOUT))
+
+
+def sgm_served_stats(ctx) -> dict:
+    out = (ctypes.c_double * 4)()
+    _check(ctx, _lib.sgm_served_stats(ctx, out, 4))
+    return {"completed": int(out[0]), "p50_us": out[1], "p99_us": out[2], "max_us": out[3]}
+
+
+def sgm_debug_stages(ctx, left, right, W, H, D, P1, P2, n_paths, Fb=None, Fm=None, MC=None, S=None, raw=None,
+                     disp=None) -> None:
+    _check(ctx, _lib.sgm_debug_stages(ctx, addr(left), addr(right), W, H, D, P1, P2, n_paths, addr(Fb), addr(Fm),
+                                      addr(MC), addr(S), addr(raw), addr(disp)))
+
+
+def sgm_stage_times(ctx) -> dict:
+    """Per-kernel device milliseconds of the last enqueued path, by stage name."""
+    buf = (ctypes.c_float * 8)()
+    n = _lib.sgm_stage_times(ctx, buf, 8)
+    if n < 0:
+        raise SgmError(n, last_error(ctx))
+    npaths = 8 if n == 7 else 4
+    return {_lib.sgm_stage_name(npaths, i).decode(): float(buf[i]) for i in range(n)}
+
+
+def sgm_kernel_launches(ctx) -> int:
+    return int(_lib.sgm_kernel_launches(ctx))
+
+
+class Context:
+    """Owns one sgm_ctx; a convenience over the functions above."""
+
+    def __init__(self, device: int = 0, mem_cap_bytes: int = 0, flags: int = 0):
+        self.handle = sgm_create(device, mem_cap_bytes, flags)
+
+    def close(self):
+        if self.handle:
+            sgm_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def compute(self, left, right, D, P1, P2, n_paths, out=None):
+        """Disparity of one pair; numpy in -> numpy out, torch in -> torch out."""
+        H, W = left.shape
+        if out is None:
+            out = _empty_like_u8(left)
+        sgm_compute(self.handle, left, right, W, H, D, P1, P2, n_paths, out)
+        return out
+
+    def debug(self, left, right, D, P1, P2, n_paths):
+        import numpy as np
+
+        H, W = left.shape
+        r = {"Fb": np.zeros((H, W), np.uint32), "Fm": np.zeros((H, W), np.uint32),
+             "MC": np.zeros((H, W, D), np.uint8), "S": np.zeros((H, W, D), np.uint16),
+             "raw": np.zeros((H, W), np.uint8), "disp": np.zeros((H, W), np.uint8)}
+        sgm_debug_stages(self.handle, np.ascontiguousarray(left), np.ascontiguousarray(right), W, H, D, P1, P2,
+                         n_paths, r["Fb"], r["Fm"], r["MC"], r["S"], r["raw"], r["disp"])
+        return r
+
+    @property
+    def launches(self) -> int:
+        return sgm_kernel_launches(self.handle)
+
+
+def _empty_like_u8(x):
+    if hasattr(x, "data_ptr") and hasattr(x, "device"):
+        import torch
+
+        return torch.empty(tuple(x.shape), dtype=torch.uint8, device=x.device)
+    import numpy as np
+
+    return np.empty(x.shape, dtype=np.uint8)
+
+
+def header_functions(header_path: Optional[str] = None) -> Iterable[str]:
+    """Names of the functions declared in include/sgm.h."""
+    import re
+
+    header_path = header_path or os.path.join(_build.INCLUDE, "sgm.h")
+    text = open(header_path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sgm_[a-z_0-9]+)\s*\(", text)))

@@ -1,0 +1,118 @@
+"""Entry points of the C ABI on the GPU: pointer kinds, async, batch, served."""
+import numpy as np
+import pytest
+
+import oracle
+import stereo_synth as synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sgm():
+    from paper_1610_04121_gb300 import sgm as m
+
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(sgm):
+    c = sgm.Context(0)
+    yield c
+    c.close()
+
+
+def _pair(W=96, H=64, D=64, seed=1):
+    return synth.make_pair(synth.PairSpec(W, H, D, 4, 2, min(48, D - 1)), seed)
+
+
+def test_host_device_and_async_agree(sgm, ctx):
+    import torch
+
+    p = _pair()
+    ref = oracle.sgm(p.left, p.right, 64, 7, 84, 4)
+    host = ctx.compute(p.left, p.right, 64, 7, 84, 4)
+    assert (host == ref).all()
+    L = torch.from_numpy(p.left).cuda()
+    R = torch.from_numpy(p.right).cuda()
+    out = torch.empty_like(L)
+    sgm.sgm_compute(ctx.handle, L, R, 96, 64, 64, 7, 84, 4, out)
+    assert (out.cpu().numpy() == ref).all()
+    out2 = torch.zeros_like(L)
+    sgm.sgm_set_stream(ctx.handle, torch.cuda.current_stream())
+    sgm.sgm_compute_async(ctx.handle, L, R, 96, 64, 64, 7, 84, 4, out2)
+    torch.cuda.current_stream().synchronize()
+    sgm.sgm_set_stream(ctx.handle, None)
+    assert (out2.cpu().numpy() == ref).all()
+    # pinned host memory is host memory too
+    Lp, Rp = torch.from_numpy(p.left).pin_memory(), torch.from_numpy(p.right).pin_memory()
+    op = torch.empty((64, 96), dtype=torch.uint8).pin_memory()
+    sgm.sgm_compute(ctx.handle, Lp, Rp, 96, 64, 64, 7, 84, 4, op)
+    assert (op.numpy() == ref).all()
+
+
+def test_async_rejects_host_pointers(sgm, ctx):
+    p = _pair()
+    out = np.zeros_like(p.left)
+    with pytest.raises(sgm.SgmError) as e:
+        sgm.sgm_compute_async(ctx.handle, p.left, p.right, 96, 64, 64, 7, 84, 4, out)
+    assert e.value.code == sgm.SGM_EINVAL
+
+
+@pytest.mark.parametrize("bad", [dict(D=48), dict(D=288), dict(D=0), dict(P1=-1), dict(P2=225), dict(n_paths=3),
+                                 dict(W=0), dict(H=-2)])
+def test_invalid_arguments(sgm, ctx, bad):
+    p = _pair()
+    args = dict(W=96, H=64, D=64, P1=7, P2=84, n_paths=4)
+    args.update(bad)
+    out = np.zeros_like(p.left)
+    with pytest.raises(sgm.SgmError) as e:
+        sgm.sgm_compute(ctx.handle, p.left, p.right, args["W"], args["H"], args["D"], args["P1"], args["P2"],
+                        args["n_paths"], out)
+    assert e.value.code == sgm.SGM_EINVAL
+    assert sgm.last_error(ctx.handle)
+
+
+def test_batch_matches_single_pairs(sgm, ctx):
+    specs = [(96, 64, 64, 4), (50, 33, 32, 8), (130, 70, 128, 2), (64, 64, 256, 8), (40, 20, 96, 4)]
+    pairs, outs, refs = [], [], []
+    for i, (W, H, D, npth) in enumerate(specs):
+        p = _pair(W, H, D, seed=10 + i)
+        o = np.zeros((H, W), np.uint8)
+        pairs.append((p.left, p.right, o, W, H, D, 7, 84, npth))
+        outs.append(o)
+        refs.append(oracle.sgm(p.left, p.right, D, 7, 84, npth))
+    sgm.sgm_compute_batch(ctx.handle, pairs)
+    for o, r in zip(outs, refs):
+        assert (o == r).all()
+
+
+def test_served_results_match_and_tickets_retire(sgm):
+    c = sgm.Context(0)
+    try:
+        items = []
+        for i in range(12):
+            W, H, D = [(96, 64, 64), (64, 40, 128), (120, 50, 32)][i % 3]
+            p = _pair(W, H, D, seed=100 + i)
+            o = np.zeros((H, W), np.uint8)
+            t = sgm.sgm_submit(c.handle, p.left, p.right, W, H, D, 10, 120, 8, o)
+            items.append((t, o, oracle.sgm(p.left, p.right, D, 10, 120, 8)))
+        for t, o, r in items:
+            assert sgm.sgm_poll(c.handle, t, -1) == sgm.SGM_OK
+            assert (o == r).all()
+        with pytest.raises(sgm.SgmError):
+            sgm.sgm_poll(c.handle, items[0][0], 0)  # retired
+        st = sgm.sgm_served_stats(c.handle)
+        assert st["completed"] == 12 and st["p99_us"] >= st["p50_us"] > 0
+    finally:
+        c.close()
+
+
+def test_launch_counter_counts_kernels(ctx):
+    p = _pair()
+    before = ctx.launches
+    ctx.compute(p.left, p.right, 64, 7, 84, 4)
+    assert ctx.launches - before == 5
+    before = ctx.launches
+    ctx.compute(p.left, p.right, 64, 7, 84, 8)
+    assert ctx.launches - before == 7
