@@ -206,7 +206,8 @@ static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, 
     // with stage timing, event k is recorded before kernel k and after the last
     auto mark = [&]() -> cudaError_t {
         if (!timed) return cudaSuccess;
-        return cudaEventRecord(ctx->stage_ev[stage++], s);
+        // External: inside a stream capture this becomes an event-record node of the graph
+        return cudaEventRecordWithFlags(ctx->stage_ev[stage++], s, cudaEventRecordExternal);
     };
     if ((e = mark()) != cudaSuccess) return e;
     if ((e = launch_census(left, right, Fb, Fm, p.W, p.H, s)) != cudaSuccess) return e;
