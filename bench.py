@@ -196,7 +196,9 @@ def main():
     R = torch.from_numpy(pair.right).to(dev)
     out = torch.empty((H, W), dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    # one explicit stream carries the path, the L2 flush and the timing events
+    stream = torch.cuda.Stream(dev)
     ctx = sgm.Context(local, flags=sgm.SGM_FLAG_STAGE_TIMING)
     sgm.sgm_set_stream(ctx.handle, stream)
 
@@ -216,7 +218,8 @@ def main():
     launches0 = ctx.launches
     with ClockSampler(local) as clk:
         for k in range(args.steps):
-            flush.fill_(k & 0xFF)  # evict the previous step's data from L2
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)  # evict the previous step's data from L2
             ev0[k].record(stream)
             step()
             ev1[k].record(stream)

@@ -32,8 +32,9 @@ struct Layout {
     size_t Fb, Fm, MC, Lx, S, raw, in_left, in_right, out, total;
 };
 
-Layout layout_for(int W, int H, int D) {
+Layout layout_for(int W, int H, int D_real) {
     const size_t wh = static_cast<size_t>(W) * H;
+    const size_t D = static_cast<size_t>(padded_D(D_real));
     Layout l{};
     size_t o = 0;
     l.Fb = o;
@@ -377,6 +378,10 @@ int sgm_create(sgm_ctx** out, int device, size_t mem_cap_bytes, unsigned flags) 
         (e = cudaStreamCreateWithFlags(&ctx->serve_stream, cudaStreamNonBlocking)) != cudaSuccess) {
         sgm_destroy(ctx);
         return fail(nullptr, SGM_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    }
+    if ((e = init_kernel_attributes()) != cudaSuccess) {
+        sgm_destroy(ctx);
+        return fail(nullptr, SGM_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
     }
     ctx->stream = ctx->own_stream;
     ctx->stage_timing = (flags & SGM_FLAG_STAGE_TIMING) != 0;

@@ -3,15 +3,18 @@
 // Data layouts in HBM (all row-major, y outermost):
 //   image      uint8  [H][W]
 //   feature    uint32 [H][W]              CSCT of Eq. 1, 31 bits
-//   cost       uint8  [H][W][D]           "paired" order: for word i in [0, D/2)
-//                                         bytes 2i, 2i+1 hold MC(i), MC(i + D/2)
-//   path cost  uint8  [H][W][D]           L_r in the same paired order (L_r <= 255)
-//   sum        uint32 [H][W][D/2]         packed u16x2 word i = (S(i), S(i + D/2))
+//   cost       uint8  [H][W][DP]          "paired" order: for word i in [0, DP/2)
+//                                         bytes 2i, 2i+1 hold MC(i), MC(i + DP/2)
+//   path cost  uint8  [H][W][DP]          L_r in the same paired order (L_r <= 255)
+//   sum        uint32 [H][W][DP/2]        packed u16x2 word i = (S(i), S(i + DP/2))
 //   disparity  uint8  [H][W]
 //
+// DP is D rounded up to a multiple of 64 (a warp of 32 lanes x K words); the
+// padded disparities D <= d < DP carry the cost 255, which never wins a
+// minimum against a real one (every real L_r and S stays <= 255 per path).
 // The paired order makes the disparity neighbours d-1 / d+1 of both halves of
 // word i live in words i-1 / i+1, so the Eq. 3 step needs no byte shuffling
-// inside a word; only the two seams (d = 0 and d = D/2) need a permute.
+// inside a word; only the two seams (d = 0 and d = DP/2) need a permute.
 #pragma once
 
 #include <cstdint>
@@ -33,16 +36,6 @@ __device__ __forceinline__ uint32_t redux_min(uint32_t v, uint32_t mask) {
     uint32_t d;
     asm volatile("redux.sync.min.u32 %0, %1, %2;" : "=r"(d) : "r"(v), "r"(mask));
     return d;
-}
-
-// Lanes [g*G, g*G + G) of the warp that form one chain group.
-template <int G>
-__device__ __forceinline__ uint32_t group_mask(int lane_in_warp) {
-    if constexpr (G == 32) {
-        return 0xffffffffu;
-    } else {
-        return ((1u << G) - 1u) << ((lane_in_warp / G) * G);
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -161,91 +154,108 @@ __device__ __forceinline__ void st_words(uint32_t* p, const uint32_t (&w)[K]) {
 }
 
 // ---------------------------------------------------------------------------
-// One aggregation chain (Eq. 3, Section 3.2) held by a group of G lanes.
+// Cross-lane primitives.  Shuffles are volatile so that their order against
+// the reduction is kept: the next step's neighbour exchange is issued before
+// the current step's minimum reduction, which lets the two latencies overlap.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t shfl_idx(uint32_t v, int src) {
+    uint32_t d;
+    asm volatile("shfl.sync.idx.b32 %0, %1, %2, 0x1f, 0xffffffff;" : "=r"(d) : "r"(v), "r"(src));
+    return d;
+}
+
+// ---------------------------------------------------------------------------
+// One aggregation chain (Eq. 3, Section 3.2) held by one warp.
 //
-// Lane l of the group holds words i = l*K + j, j < K, of the path cost of the
-// previous pixel; word i packs L(i) (low half) and L(i + D/2) (high half).
+// Lane l holds words i = l*K + j, j < K, of the path cost of the previous
+// pixel; word i packs L(i) (low half) and L(i + DP/2) (high half), DP = 64*K.
 // Each step computes, for every d,
 //   L(p, d) = MC(p, d) + min(L(q, d), L(q, d-1) + P1, L(q, d+1) + P1, m(q) + P2) - m(q)
 // with q the previous pixel and m(q) = min_k L(q, k).  Starting a path with
 // L(q, .) = 0 and m(q) = 0 yields L(p, .) = MC(p, .), the reading used for the
-// first pixel of every path.
+// first pixel of every path.  `up` / `dn` hold the neighbour words across the
+// lane boundary, already exchanged at the end of the previous step.
 // ---------------------------------------------------------------------------
-template <int G, int K>
+template <int K>
 struct Chain {
     uint32_t w[K];
-    uint32_t mpx2;  // m(q) in both halves
+    uint32_t up, dn;  // word l*K-1 from lane l-1, word l*K+K from lane l+1 (wrapping)
+    uint32_t mpx2;    // m(q) in both halves
+    uint32_t sel_up, sel_dn;
+    int src_up, src_dn;
+
+    __device__ __forceinline__ void init(int lane) {
+        src_up = (lane + 31) & 31;
+        src_dn = (lane + 1) & 31;
+        // lane 0: d-1 of d=0 is absent, d-1 of d=DP/2 is the low half of word DP/2-1
+        sel_up = (lane == 0) ? 0x1054u : 0x3210u;
+        // lane 31: d+1 of d=DP-1 is absent, d+1 of d=DP/2-1 is the high half of word 0
+        sel_dn = (lane == 31) ? 0x5432u : 0x3210u;
+        reset();
+    }
 
     __device__ __forceinline__ void reset() {
 #pragma unroll
         for (int j = 0; j < K; ++j) w[j] = 0u;
+        up = dn = 0u;
         mpx2 = 0u;
     }
 
-    // mc: packed costs of this lane's words at the new pixel.  Returns the new
-    // path costs in L (also kept as the state for the next step).
-    __device__ __forceinline__ void step(const uint32_t (&mc)[K], uint32_t P1x2, uint32_t P2x2, int lane,
-                                         uint32_t gmask, uint32_t (&L)[K]) {
-        // neighbours across lane boundaries; the group wraps so that lane 0 sees
-        // word D/2 - 1 (for d = D/2 - 1) and lane G-1 sees word 0 (for d = D/2)
-        uint32_t up = __shfl_sync(gmask, w[K - 1], (lane + G - 1) % G, G);
-        uint32_t dn = __shfl_sync(gmask, w[0], (lane + 1) % G, G);
-        if (lane == 0) up = (up << 16) | kInf16;            // d-1 of d=0 is absent
-        if (lane == G - 1) dn = (dn >> 16) | (kInf16 << 16);  // d+1 of d=D-1 is absent
+    __device__ __forceinline__ void step(const uint32_t (&mc)[K], uint32_t P1x2, uint32_t P2x2, uint32_t (&L)[K]) {
+        const uint32_t inf2 = kInf16 * 0x10001u;
+        const uint32_t u = __byte_perm(up, inf2, sel_up);
+        const uint32_t d = __byte_perm(dn, inf2, sel_dn);
         const uint32_t mp2 = mpx2 + P2x2;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            const uint32_t dm1 = (j == 0) ? up : w[j - 1];
-            const uint32_t dp1 = (j == K - 1) ? dn : w[j + 1];
-            const uint32_t a = vmin2(dm1, dp1) + P1x2;
-            const uint32_t b = vmin2(w[j], mp2);
-            // every candidate is >= m(q) lane-wise, so this never borrows
-            L[j] = vmin2(a, b) + mc[j] - mpx2;
+            const uint32_t dm1 = (j == 0) ? u : w[j - 1];
+            const uint32_t dp1 = (j == K - 1) ? d : w[j + 1];
+            // every candidate is >= m(q) lane-wise, so the packed subtraction never borrows
+            L[j] = vmin2(vmin2(dm1, dp1) + P1x2, vmin2(w[j], mp2)) + mc[j] - mpx2;
         }
         uint32_t r = L[0];
 #pragma unroll
         for (int j = 1; j < K; ++j) r = vmin2(r, L[j]);
         r = vmin2(r, __byte_perm(r, 0u, 0x1032u));  // both halves = lane minimum
-        mpx2 = redux_min(r, gmask);
+        up = shfl_idx(L[K - 1], src_up);
+        dn = shfl_idx(L[0], src_dn);
+        mpx2 = redux_min(r, 0xffffffffu);
 #pragma unroll
         for (int j = 0; j < K; ++j) w[j] = L[j];
     }
 };
 
 // Winner-take-all over one lane's words (Eq. 4): key = S << 8 | d, so the
-// u32 minimum is the smallest S and, among equal S, the lowest d.
+// u32 minimum is the smallest S and, among equal S, the lowest d.  Padded
+// disparities d >= D never win.
 template <int K>
-__device__ __forceinline__ uint32_t wta_key(const uint32_t (&s)[K], int lane, int half) {
+__device__ __forceinline__ uint32_t wta_key(const uint32_t (&s)[K], int lane, int half, int D) {
     uint32_t best = 0xffffffffu;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
         const uint32_t i = static_cast<uint32_t>(lane * K + j);
-        const uint32_t dconst = i | ((i + static_cast<uint32_t>(half)) << 8);
+        const uint32_t ih = i + static_cast<uint32_t>(half);
+        const uint32_t dconst = i | (ih << 8);
         const uint32_t klo = __byte_perm(s[j], dconst, 0x6104u);  // [d_lo, S_lo.b0, S_lo.b1, 0]
         const uint32_t khi = __byte_perm(s[j], dconst, 0x6325u);  // [d_hi, S_hi.b0, S_hi.b1, 0]
-        best = min(best, min(klo, khi));
+        best = min(best, (static_cast<int>(i) < D) ? klo : 0xffffffffu);
+        best = min(best, (static_cast<int>(ih) < D) ? khi : 0xffffffffu);
     }
     return best;
 }
 
-// Iterate i = 0 .. n-1 with loads issued PF iterations ahead (register ring).
-template <int PF, class T, class LoadF, class BodyF>
-__device__ __forceinline__ void pipelined(int n, LoadF&& load, BodyF&& body) {
-    T buf[PF];
-#pragma unroll
-    for (int s = 0; s < PF; ++s)
-        if (s < n) buf[s] = load(s);
-    for (int i0 = 0; i0 < n; i0 += PF) {
-#pragma unroll
-        for (int s = 0; s < PF; ++s) {
-            const int i = i0 + s;
-            if (i < n) {
-                T v = buf[s];
-                if (i + PF < n) buf[s] = load(i + PF);
-                body(i, v);
-            }
-        }
-    }
+// ---------------------------------------------------------------------------
+// cp.async staging (16-byte global -> shared copies, completed per thread by
+// wait_group; a __syncwarp then publishes the data to the whole warp).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp16(void* smem_dst, const void* gmem_src) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 }  // namespace sgm

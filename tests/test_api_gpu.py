@@ -116,3 +116,25 @@ def test_launch_counter_counts_kernels(ctx):
     before = ctx.launches
     ctx.compute(p.left, p.right, 64, 7, 84, 8)
     assert ctx.launches - before == 7
+
+
+def test_stage_times_inside_graph_replay(sgm):
+    import torch
+
+    p = _pair(128, 80, 128, seed=9)
+    c = sgm.Context(0, flags=sgm.SGM_FLAG_STAGE_TIMING)
+    try:
+        L = torch.from_numpy(p.left).cuda()
+        R = torch.from_numpy(p.right).cuda()
+        out = torch.empty_like(L)
+        sgm.sgm_set_stream(c.handle, torch.cuda.current_stream())
+        for n_paths, names in [(4, ["census", "cost", "sweep_h", "sweep_v", "median"]),
+                               (8, ["census", "cost", "sweep_h", "sweep_diag+", "sweep_diag-", "sweep_v", "median"])]:
+            for _ in range(2):
+                sgm.sgm_compute_async(c.handle, L, R, 128, 80, 128, 7, 84, n_paths, out)
+                st = sgm.sgm_stage_times(c.handle)
+                assert list(st) == names and all(v > 0 for v in st.values())
+            torch.cuda.synchronize()
+            assert (out.cpu().numpy() == oracle.sgm(p.left, p.right, 128, 7, 84, n_paths)).all()
+    finally:
+        c.close()
