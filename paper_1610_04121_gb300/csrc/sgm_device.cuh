@@ -3,18 +3,15 @@
 // Data layouts in HBM (all row-major, y outermost):
 //   image      uint8  [H][W]
 //   feature    uint32 [H][W]              CSCT of Eq. 1, 31 bits
-//   cost       uint8  [H][W][DP]          "paired" order: for word i in [0, DP/2)
-//                                         bytes 2i, 2i+1 hold MC(i), MC(i + DP/2)
-//   path cost  uint8  [H][W][DP]          L_r in the same paired order (L_r <= 255)
-//   sum        uint32 [H][W][DP/2]        packed u16x2 word i = (S(i), S(i + DP/2))
+//   cost       uint8  [H][W][D]           "paired" order: for word i in [0, D/2)
+//                                         bytes 2i, 2i+1 hold MC(i), MC(i + D/2)
+//   path cost  uint8  [H][W][D]           L_r in the same paired order (L_r <= 255)
+//   sum        uint32 [H][W][D/2]         packed u16x2 word i = (S(i), S(i + D/2))
 //   disparity  uint8  [H][W]
 //
-// DP is D rounded up to a multiple of 64 (a warp of 32 lanes x K words); the
-// padded disparities D <= d < DP carry the cost 255, which never wins a
-// minimum against a real one (every real L_r and S stays <= 255 per path).
 // The paired order makes the disparity neighbours d-1 / d+1 of both halves of
 // word i live in words i-1 / i+1, so the Eq. 3 step needs no byte shuffling
-// inside a word; only the two seams (d = 0 and d = DP/2) need a permute.
+// inside a word; only the two seams (d = 0 and d = D/2) need a permute.
 #pragma once
 
 #include <cstdint>
@@ -32,9 +29,18 @@ __device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b) {
     return d;
 }
 
-__device__ __forceinline__ uint32_t redux_min(uint32_t v, uint32_t mask) {
+__device__ __forceinline__ uint32_t redux_min(uint32_t v) {
     uint32_t d;
-    asm volatile("redux.sync.min.u32 %0, %1, %2;" : "=r"(d) : "r"(v), "r"(mask));
+    asm volatile("redux.sync.min.u32 %0, %1, 0xffffffff;" : "=r"(d) : "r"(v));
+    return d;
+}
+
+// Shuffles are volatile so that their order against the reductions is kept:
+// the next step's neighbour exchange is issued before the current step's
+// minimum reduction, which lets the two latencies overlap.
+__device__ __forceinline__ uint32_t shfl_idx(uint32_t v, int src) {
+    uint32_t d;
+    asm volatile("shfl.sync.idx.b32 %0, %1, %2, 0x1f, 0xffffffff;" : "=r"(d) : "r"(v), "r"(src));
     return d;
 }
 
@@ -54,20 +60,25 @@ __device__ __forceinline__ U8Pairs<K> ld_pairs(const uint8_t* p) {
     } else if constexpr (K == 2) {
         o.r[0] = *reinterpret_cast<const uint32_t*>(p);
     } else if constexpr (K == 4) {
-        uint2 v = *reinterpret_cast<const uint2*>(p);
+        const uint2 v = *reinterpret_cast<const uint2*>(p);
         o.r[0] = v.x;
         o.r[1] = v.y;
     } else if constexpr (K == 8) {
-        uint4 v = *reinterpret_cast<const uint4*>(p);
+        const uint4 v = *reinterpret_cast<const uint4*>(p);
         o.r[0] = v.x;
         o.r[1] = v.y;
         o.r[2] = v.z;
         o.r[3] = v.w;
+    } else if constexpr (K == 6) {
+        const uint32_t* q = reinterpret_cast<const uint32_t*>(p);  // 12 bytes, 4-byte aligned
+        o.r[0] = q[0];
+        o.r[1] = q[1];
+        o.r[2] = q[2];
     } else {
         const uint16_t* h = reinterpret_cast<const uint16_t*>(p);
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            uint32_t v = h[j];
+            const uint32_t v = h[j];
             if (j & 1)
                 o.r[j >> 1] |= v << 16;
             else
@@ -108,6 +119,11 @@ __device__ __forceinline__ void st_pairs(uint8_t* p, const U8Pairs<K>& o) {
         *reinterpret_cast<uint2*>(p) = make_uint2(o.r[0], o.r[1]);
     } else if constexpr (K == 8) {
         *reinterpret_cast<uint4*>(p) = make_uint4(o.r[0], o.r[1], o.r[2], o.r[3]);
+    } else if constexpr (K == 6) {
+        uint32_t* q = reinterpret_cast<uint32_t*>(p);
+        q[0] = o.r[0];
+        q[1] = o.r[1];
+        q[2] = o.r[2];
     } else {
         uint16_t* h = reinterpret_cast<uint16_t*>(p);
 #pragma unroll
@@ -119,18 +135,21 @@ template <int K>
 __device__ __forceinline__ void ld_words(const uint32_t* p, uint32_t (&w)[K]) {
     if constexpr (K == 1) {
         w[0] = p[0];
-    } else if constexpr (K == 2) {
-        uint2 v = *reinterpret_cast<const uint2*>(p);
-        w[0] = v.x;
-        w[1] = v.y;
     } else if constexpr (K % 4 == 0) {
 #pragma unroll
         for (int j = 0; j < K; j += 4) {
-            uint4 v = *reinterpret_cast<const uint4*>(p + j);
+            const uint4 v = *reinterpret_cast<const uint4*>(p + j);
             w[j] = v.x;
             w[j + 1] = v.y;
             w[j + 2] = v.z;
             w[j + 3] = v.w;
+        }
+    } else if constexpr (K % 2 == 0) {
+#pragma unroll
+        for (int j = 0; j < K; j += 2) {
+            const uint2 v = *reinterpret_cast<const uint2*>(p + j);
+            w[j] = v.x;
+            w[j + 1] = v.y;
         }
     } else {
 #pragma unroll
@@ -142,11 +161,12 @@ template <int K>
 __device__ __forceinline__ void st_words(uint32_t* p, const uint32_t (&w)[K]) {
     if constexpr (K == 1) {
         p[0] = w[0];
-    } else if constexpr (K == 2) {
-        *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
     } else if constexpr (K % 4 == 0) {
 #pragma unroll
         for (int j = 0; j < K; j += 4) *reinterpret_cast<uint4*>(p + j) = make_uint4(w[j], w[j + 1], w[j + 2], w[j + 3]);
+    } else if constexpr (K % 2 == 0) {
+#pragma unroll
+        for (int j = 0; j < K; j += 2) *reinterpret_cast<uint2*>(p + j) = make_uint2(w[j], w[j + 1]);
     } else {
 #pragma unroll
         for (int j = 0; j < K; ++j) p[j] = w[j];
@@ -154,22 +174,14 @@ __device__ __forceinline__ void st_words(uint32_t* p, const uint32_t (&w)[K]) {
 }
 
 // ---------------------------------------------------------------------------
-// Cross-lane primitives.  Shuffles are volatile so that their order against
-// the reduction is kept: the next step's neighbour exchange is issued before
-// the current step's minimum reduction, which lets the two latencies overlap.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t shfl_idx(uint32_t v, int src) {
-    uint32_t d;
-    asm volatile("shfl.sync.idx.b32 %0, %1, %2, 0x1f, 0xffffffff;" : "=r"(d) : "r"(v), "r"(src));
-    return d;
-}
-
-// ---------------------------------------------------------------------------
-// One aggregation chain (Eq. 3, Section 3.2) held by one warp.
+// Two aggregation chains (Eq. 3, Section 3.2) per warp: lanes 0-15 carry
+// chain A, lanes 16-31 chain B (the two opposite directions of one row or one
+// column).  Every cross-lane operation is a full-warp instruction; each half
+// shuffles within itself and the two step minima are two masked reductions.
 //
-// Lane l holds words i = l*K + j, j < K, of the path cost of the previous
-// pixel; word i packs L(i) (low half) and L(i + DP/2) (high half), DP = 64*K.
-// Each step computes, for every d,
+// Lane l of a half holds words i = (l mod 16)*K + j, j < K, of the path cost
+// of the previous pixel; word i packs L(i) (low half) and L(i + D/2) (high
+// half), D = 32*K.  Each step computes, for every d,
 //   L(p, d) = MC(p, d) + min(L(q, d), L(q, d-1) + P1, L(q, d+1) + P1, m(q) + P2) - m(q)
 // with q the previous pixel and m(q) = min_k L(q, k).  Starting a path with
 // L(q, .) = 0 and m(q) = 0 yields L(p, .) = MC(p, .), the reading used for the
@@ -177,20 +189,25 @@ __device__ __forceinline__ uint32_t shfl_idx(uint32_t v, int src) {
 // lane boundary, already exchanged at the end of the previous step.
 // ---------------------------------------------------------------------------
 template <int K>
-struct Chain {
+struct Chain2 {
     uint32_t w[K];
-    uint32_t up, dn;  // word l*K-1 from lane l-1, word l*K+K from lane l+1 (wrapping)
-    uint32_t mpx2;    // m(q) in both halves
-    uint32_t sel_up, sel_dn;
+    uint32_t up, dn;  // word hl*K-1 from lane hl-1, word hl*K+K from lane hl+1 (wrapping in the half)
+    uint32_t mpx2;    // m(q) in both u16 halves
+    uint32_t sel_up, sel_dn, mask_a, mask_b;
     int src_up, src_dn;
+    bool in_b;
 
     __device__ __forceinline__ void init(int lane) {
-        src_up = (lane + 31) & 31;
-        src_dn = (lane + 1) & 31;
-        // lane 0: d-1 of d=0 is absent, d-1 of d=DP/2 is the low half of word DP/2-1
-        sel_up = (lane == 0) ? 0x1054u : 0x3210u;
-        // lane 31: d+1 of d=DP-1 is absent, d+1 of d=DP/2-1 is the high half of word 0
-        sel_dn = (lane == 31) ? 0x5432u : 0x3210u;
+        const int hl = lane & 15, base = lane & 16;
+        src_up = base | ((hl + 15) & 15);
+        src_dn = base | ((hl + 1) & 15);
+        // first lane of a half: d-1 of d=0 is absent, d-1 of d=D/2 is the low half of word D/2-1
+        sel_up = (hl == 0) ? 0x1054u : 0x3210u;
+        // last lane of a half: d+1 of d=D-1 is absent, d+1 of d=D/2-1 is the high half of word 0
+        sel_dn = (hl == 15) ? 0x5432u : 0x3210u;
+        in_b = lane >= 16;
+        mask_a = in_b ? 0xffffffffu : 0u;
+        mask_b = ~mask_a;
         reset();
     }
 
@@ -199,6 +216,13 @@ struct Chain {
         for (int j = 0; j < K; ++j) w[j] = 0u;
         up = dn = 0u;
         mpx2 = 0u;
+    }
+
+    // the minimum of v over this lane's half of the warp
+    __device__ __forceinline__ uint32_t half_min(uint32_t v) const {
+        const uint32_t a = redux_min(v | mask_a);
+        const uint32_t b = redux_min(v | mask_b);
+        return in_b ? b : a;
     }
 
     __device__ __forceinline__ void step(const uint32_t (&mc)[K], uint32_t P1x2, uint32_t P2x2, uint32_t (&L)[K]) {
@@ -216,30 +240,35 @@ struct Chain {
         uint32_t r = L[0];
 #pragma unroll
         for (int j = 1; j < K; ++j) r = vmin2(r, L[j]);
-        r = vmin2(r, __byte_perm(r, 0u, 0x1032u));  // both halves = lane minimum
+        r = vmin2(r, __byte_perm(r, 0u, 0x1032u));  // both u16 halves = lane minimum
         up = shfl_idx(L[K - 1], src_up);
         dn = shfl_idx(L[0], src_dn);
-        mpx2 = redux_min(r, 0xffffffffu);
+        mpx2 = half_min(r);
 #pragma unroll
         for (int j = 0; j < K; ++j) w[j] = L[j];
     }
 };
 
 // Winner-take-all over one lane's words (Eq. 4): key = S << 8 | d, so the
-// u32 minimum is the smallest S and, among equal S, the lowest d.  Padded
-// disparities d >= D never win.
+// u32 minimum is the smallest S and, among equal S, the lowest d.  dconst[j]
+// holds, for word i = hl*K + j, the bytes [i, i + D/2, 0, 0].
 template <int K>
-__device__ __forceinline__ uint32_t wta_key(const uint32_t (&s)[K], int lane, int half, int D) {
+__device__ __forceinline__ void wta_consts(int hl, int D, uint32_t (&dconst)[K]) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const uint32_t i = static_cast<uint32_t>(hl * K + j);
+        dconst[j] = i | ((i + static_cast<uint32_t>(D / 2)) << 8);
+    }
+}
+
+template <int K>
+__device__ __forceinline__ uint32_t wta_key(const uint32_t (&s)[K], const uint32_t (&dconst)[K]) {
     uint32_t best = 0xffffffffu;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-        const uint32_t i = static_cast<uint32_t>(lane * K + j);
-        const uint32_t ih = i + static_cast<uint32_t>(half);
-        const uint32_t dconst = i | (ih << 8);
-        const uint32_t klo = __byte_perm(s[j], dconst, 0x6104u);  // [d_lo, S_lo.b0, S_lo.b1, 0]
-        const uint32_t khi = __byte_perm(s[j], dconst, 0x6325u);  // [d_hi, S_hi.b0, S_hi.b1, 0]
-        best = min(best, (static_cast<int>(i) < D) ? klo : 0xffffffffu);
-        best = min(best, (static_cast<int>(ih) < D) ? khi : 0xffffffffu);
+        const uint32_t klo = __byte_perm(s[j], dconst[j], 0x6104u);  // [d_lo, S_lo.b0, S_lo.b1, 0]
+        const uint32_t khi = __byte_perm(s[j], dconst[j], 0x6325u);  // [d_hi, S_hi.b0, S_hi.b1, 0]
+        best = min(best, min(klo, khi));
     }
     return best;
 }

@@ -1,39 +1,42 @@
 // Path aggregation (Eq. 3), the sum S and the winner-take-all disparity
 // (Eq. 4) of the SGM path in arXiv 1610.04121, for sm_103a.
 //
-// Parallel scheme (Section 3.2, with the paper's CTA-to-warp conversion): one
-// warp carries one path, disparities packed two per 32-bit register; the
-// neighbours d-1 / d+1 cross lanes with shuffles and the step minimum m(q) is
-// one redux.sync.  Opposite directions of an axis run at the same time and
-// meet in the middle: each sweeps its first half of the path storing L_r (u8)
-// in a scratch cube, and in its second half adds the other direction's stored
-// L_r to its own.
+// Parallel scheme (Section 3.2, with the paper's CTA-to-warp conversion taken
+// one step further): one warp carries the two opposite paths of one row or one
+// column, 16 lanes each, disparities packed two per 32-bit register.  The two
+// paths meet in the middle: each sweeps its first half of the line storing
+// L_r (u8) in a scratch cube, and in its second half adds the other path's
+// stored L_r to its own.  The exchange between the two halves of the line is
+// warp-local, so no block barrier is involved.
 //
-// Each warp streams its inputs through a private shared-memory ring filled by
-// cp.async a few chunks ahead, keeps its step loop on shared memory only, and
-// writes each chunk's outputs back with 16-byte stores.
+// Each half-warp streams its inputs through a private shared-memory ring
+// filled by cp.async a few chunks ahead, keeps its step loop on shared memory
+// only, and writes each chunk's outputs back with 16-byte stores.
 //
-//   sweep_h : left-to-right and right-to-left, one row per warp pair;
+//   sweep_h : left-to-right with right-to-left, one row per warp;
 //             writes S = L_LR + L_RL (packed u16x2).
-//   sweep_v : top-to-bottom and bottom-to-top along columns (rx = 0) or along
-//             the wrapped diagonals of Section 3.2 (rx = +1 / -1); either adds
+//   sweep_v : top-to-bottom with bottom-to-top along columns (RX = 0) or along
+//             the wrapped diagonals of Section 3.2 (RX = +1 / -1); either adds
 //             its pair sum into S or, for the last axis, finishes with Eq. 4.
 #include "sgm_device.cuh"
 #include "sgm_internal.h"
 
 namespace sgm {
 
-// Per-warp shared-memory staging for K words per lane (DP = 64 K disparities).
+constexpr int kWarpsPerBlock = 4;
+
+// Shared-memory staging of one half-warp (one path) with K words per lane.
 template <int K>
 struct Stage {
-    static constexpr int DP = 64 * K;
-    static constexpr int CH = (16 / K) >= 4 ? (16 / K) : 4;  // pixels per chunk
-    static constexpr int NSLOT = 3;                          // chunks in flight + 1
-    static constexpr int MC_RING = NSLOT * CH * DP;
-    static constexpr int LO_RING = NSLOT * CH * DP;
-    static constexpr int S_RING = NSLOT * CH * 2 * DP;
-    static constexpr int OUT = CH * 2 * DP;
+    static constexpr int D = 32 * K;
+    static constexpr int CH = (K <= 2) ? 16 : (K <= 4 ? 8 : 4);  // pixels per chunk
+    static constexpr int NSLOT = 3;                              // chunks in flight + 1
+    static constexpr int MC_RING = NSLOT * CH * D;
+    static constexpr int LO_RING = NSLOT * CH * D;
+    static constexpr int S_RING = NSLOT * CH * 2 * D;
+    static constexpr int OUT = CH * 2 * D;
     static constexpr int BYTES = MC_RING + LO_RING + S_RING + OUT;
+    static constexpr int BLOCK_BYTES = 2 * kWarpsPerBlock * BYTES;
 };
 
 enum WalkMode {
@@ -50,61 +53,98 @@ struct RowGeo {
     size_t rowbase;
     int x0, dx;
     static constexpr bool kResets = false;
-    __device__ __forceinline__ size_t pix(int i) const { return rowbase + static_cast<size_t>(x0 + dx * i); }
+    __device__ __forceinline__ void origin(int i0, int& xc, int& yc) const {
+        xc = x0 + dx * i0;
+        yc = 0;
+    }
+    __device__ __forceinline__ size_t pix(int xc, int /*yc*/, int k) const {
+        return rowbase + static_cast<size_t>(xc + dx * k);
+    }
 };
 
-// Pixels of a column / wrapped-diagonal walk: y = y0 + dy * i, x = (c + rx*y) mod W.
+// Pixels of a column (RX = 0) or wrapped-diagonal (RX = +1/-1) walk:
+// y = y0 + dy * i, x = (c + RX * y) mod W.
+template <int RX>
 struct ColGeo {
-    int W, H, c, rx, y0, dy;
-    static constexpr bool kResets = true;
+    int W, H, c, y0, dy;
+    static constexpr bool kResets = RX != 0;
     __device__ __forceinline__ int x_at(int y) const {
-        if (rx == 0) return c;
-        int v = (c + rx * y) % W;
-        return v < 0 ? v + W : v;
+        if constexpr (RX == 0) {
+            return c;
+        } else {
+            int v = (c + RX * y) % W;
+            return v < 0 ? v + W : v;
+        }
     }
-    __device__ __forceinline__ size_t pix(int i) const {
-        const int y = y0 + dy * i;
-        return static_cast<size_t>(y) * W + x_at(y);
+    __device__ __forceinline__ void origin(int i0, int& xc, int& yc) const {
+        yc = y0 + dy * i0;
+        xc = x_at(yc);
+    }
+    __device__ __forceinline__ size_t pix(int xc, int yc, int k) const {
+        int x = xc;
+        if constexpr (RX != 0) {
+            x = xc + RX * dy * k;
+            if (x >= W) x -= W;
+            if (x < 0) x += W;
+            if (x >= W || x < 0) {  // only when W is smaller than a chunk
+                x %= W;
+                if (x < 0) x += W;
+            }
+        }
+        return static_cast<size_t>(yc + dy * k) * W + x;
+    }
+    // x of the next pixel of the walk
+    __device__ __forceinline__ int step_x(int x) const {
+        x += RX * dy;
+        return x >= W ? x - W : (x < 0 ? x + W : x);
     }
     // the previous pixel of the path at (x, y) lies outside the image
     __device__ __forceinline__ bool starts(int y, int x) const {
-        if (dy > 0) return y == 0 || (rx == 1 && x == 0) || (rx == -1 && x == W - 1);
-        return y == H - 1 || (rx == 1 && x == W - 1) || (rx == -1 && x == 0);
+        if (dy > 0) return y == 0 || (RX == 1 && x == 0) || (RX == -1 && x == W - 1);
+        return y == H - 1 || (RX == 1 && x == W - 1) || (RX == -1 && x == 0);
     }
 };
 
+// One phase of both half-warp paths.  g / n_own: this lane's half; n_min /
+// n_max: the shorter and the longer of the two halves' step counts.
 template <int K, int MODE, class Geo>
-__device__ __forceinline__ void walk(Chain<K>& ch, const Geo& g, int n, const SweepArgs& a, uint8_t* ws, int lane) {
+__device__ __forceinline__ void walk(Chain2<K>& ch, const Geo& g, int n_own, int n_min, int n_max, const SweepArgs& a,
+                                     uint8_t* ws, int hl) {
     using St = Stage<K>;
-    constexpr int DP = St::DP, CH = St::CH, NS = St::NSLOT;
+    constexpr int D = St::D, CH = St::CH, NS = St::NSLOT;
     constexpr bool IN_LO = MODE == kSumH || MODE == kAcc || MODE == kWta2;
     constexpr bool IN_S = MODE == kAcc || MODE == kWta2 || MODE == kSingleWta;
     constexpr bool OUT_LX = MODE == kStoreL;
     constexpr bool OUT_S = MODE == kSumH || MODE == kAcc || MODE == kSingleH;
     constexpr bool WTA = MODE == kWta2 || MODE == kSingleWta;
-    constexpr int PM = DP / 16;      // 16-byte pieces per pixel of u8 pairs
-    constexpr int PS = 2 * DP / 16;  // 16-byte pieces per pixel of packed sums
+    constexpr int PM = D / 16;      // 16-byte pieces per pixel of u8 pairs
+    constexpr int PS = 2 * D / 16;  // 16-byte pieces per pixel of packed sums
     uint8_t* mc_ring = ws;
     uint8_t* lo_ring = mc_ring + St::MC_RING;
     uint8_t* s_ring = lo_ring + St::LO_RING;
     uint8_t* out = s_ring + St::S_RING;
     const uint8_t* Sb = reinterpret_cast<const uint8_t*>(a.S);
-    const int nch = (n + CH - 1) / CH;
+    const int nch = (n_max + CH - 1) / CH;
+
+    uint32_t dconst[K];
+    if constexpr (WTA) wta_consts<K>(hl, D, dconst);
 
     auto issue = [&](int c) {
         if (c < nch) {
-            const int i0 = c * CH, np = min(CH, n - i0), slot = c % NS;
-            for (int q = lane; q < np * PM; q += 32) {
+            const int i0 = c * CH, np = max(0, min(CH, n_own - i0)), slot = c % NS;
+            int xc = 0, yc = 0;
+            if (np > 0) g.origin(i0, xc, yc);
+            for (int q = hl; q < np * PM; q += 16) {
                 const int pi = q / PM, off = (q % PM) * 16;
-                const size_t p = g.pix(i0 + pi);
-                cp16(mc_ring + (slot * CH + pi) * DP + off, a.MC + p * DP + off);
-                if (IN_LO) cp16(lo_ring + (slot * CH + pi) * DP + off, a.Lx + p * DP + off);
+                const size_t p = g.pix(xc, yc, pi);
+                cp16(mc_ring + (slot * CH + pi) * D + off, a.MC + p * D + off);
+                if constexpr (IN_LO) cp16(lo_ring + (slot * CH + pi) * D + off, a.Lx + p * D + off);
             }
-            if (IN_S) {
-                for (int q = lane; q < np * PS; q += 32) {
+            if constexpr (IN_S) {
+                for (int q = hl; q < np * PS; q += 16) {
                     const int pi = q / PS, off = (q % PS) * 16;
-                    const size_t p = g.pix(i0 + pi);
-                    cp16(s_ring + (slot * CH + pi) * 2 * DP + off, Sb + p * 2 * DP + off);
+                    const size_t p = g.pix(xc, yc, pi);
+                    cp16(s_ring + (slot * CH + pi) * 2 * D + off, Sb + p * 2 * D + off);
                 }
             }
         }
@@ -112,74 +152,92 @@ __device__ __forceinline__ void walk(Chain<K>& ch, const Geo& g, int n, const Sw
     };
 
     int y_body = 0, x_body = 0;
-    if constexpr (Geo::kResets) {
-        y_body = g.y0;
-        x_body = g.x_at(g.y0);
-    }
+    if constexpr (Geo::kResets) g.origin(0, x_body, y_body);
+
+    // one step at chunk position pi; lane pi of each half keeps that step's disparity key
+    auto body = [&](int pi, int slot, int xc, int yc, bool active, uint32_t& dkeep) {
+        if constexpr (Geo::kResets) {
+            if (g.starts(y_body, x_body)) ch.reset();
+            y_body += g.dy;
+            x_body = g.step_x(x_body);
+        }
+        uint32_t mc[K], L[K];
+        unpack_pairs<K>(ld_pairs<K>(mc_ring + (slot * CH + pi) * D + hl * 2 * K), mc);
+        ch.step(mc, a.P1x2, a.P2x2, L);
+        if constexpr (OUT_LX) {
+            st_pairs<K>(out + pi * D + hl * 2 * K, pack_pairs<K>(L));
+        } else {
+            uint32_t s[K];
+#pragma unroll
+            for (int j = 0; j < K; ++j) s[j] = L[j];
+            if constexpr (IN_LO) {
+                uint32_t lo[K];
+                unpack_pairs<K>(ld_pairs<K>(lo_ring + (slot * CH + pi) * D + hl * 2 * K), lo);
+#pragma unroll
+                for (int j = 0; j < K; ++j) s[j] += lo[j];
+            }
+            if constexpr (IN_S) {
+                uint32_t t[K];
+                ld_words<K>(reinterpret_cast<const uint32_t*>(s_ring + (slot * CH + pi) * 2 * D) + hl * K, t);
+#pragma unroll
+                for (int j = 0; j < K; ++j) s[j] += t[j];
+            }
+            if constexpr (OUT_S) st_words<K>(reinterpret_cast<uint32_t*>(out + pi * 2 * D) + hl * K, s);
+            if constexpr (WTA) {
+                const uint32_t key = ch.half_min(wta_key<K>(s, dconst));
+                dkeep = (hl == pi) ? key : dkeep;
+                if (a.Sdbg && active) {  // debug: natural-order S
+                    const size_t p = g.pix(xc, yc, pi);
+#pragma unroll
+                    for (int j = 0; j < K; ++j) {
+                        const int i = hl * K + j;
+                        a.Sdbg[p * D + i] = static_cast<uint16_t>(s[j] & 0xffffu);
+                        a.Sdbg[p * D + i + D / 2] = static_cast<uint16_t>(s[j] >> 16);
+                    }
+                }
+            }
+        }
+    };
+
     for (int c = 0; c < NS - 1; ++c) issue(c);
     for (int c = 0; c < nch; ++c) {
         issue(c + NS - 1);
         cp_wait<NS - 1>();
         __syncwarp();
-        const int i0 = c * CH, np = min(CH, n - i0), slot = c % NS;
+        const int i0 = c * CH, np = max(0, min(CH, n_own - i0)), slot = c % NS;
+        int xc = 0, yc = 0;
+        if (np > 0) g.origin(i0, xc, yc);
+        uint32_t dkeep = 0;
+        if (n_min - i0 >= CH) {
 #pragma unroll
-        for (int pi = 0; pi < CH; ++pi) {
-            if (pi < np) {
-                if constexpr (Geo::kResets) {
-                    if (g.starts(y_body, x_body)) ch.reset();
-                }
-                uint32_t mc[K], L[K];
-                unpack_pairs<K>(ld_pairs<K>(mc_ring + (slot * CH + pi) * DP + lane * 2 * K), mc);
-                ch.step(mc, a.P1x2, a.P2x2, L);
-                if constexpr (OUT_LX) {
-                    st_pairs<K>(out + pi * DP + lane * 2 * K, pack_pairs<K>(L));
-                } else {
-                    uint32_t s[K];
+            for (int pi = 0; pi < CH; ++pi) body(pi, slot, xc, yc, true, dkeep);
+        } else {
+            // last chunk: a half with fewer steps keeps its state through the extra steps
 #pragma unroll
-                    for (int j = 0; j < K; ++j) s[j] = L[j];
-                    if constexpr (IN_LO) {
-                        uint32_t lo[K];
-                        unpack_pairs<K>(ld_pairs<K>(lo_ring + (slot * CH + pi) * DP + lane * 2 * K), lo);
-#pragma unroll
-                        for (int j = 0; j < K; ++j) s[j] += lo[j];
+            for (int pi = 0; pi < CH; ++pi) {
+                if (i0 + pi < n_max) {
+                    const Chain2<K> saved = ch;
+                    const int yb = y_body, xb = x_body;
+                    body(pi, slot, xc, yc, pi < np, dkeep);
+                    if (pi >= np) {
+                        ch = saved;
+                        y_body = yb;
+                        x_body = xb;
                     }
-                    if constexpr (IN_S) {
-                        uint32_t t[K];
-                        ld_words<K>(reinterpret_cast<const uint32_t*>(s_ring + (slot * CH + pi) * 2 * DP) + lane * K, t);
-#pragma unroll
-                        for (int j = 0; j < K; ++j) s[j] += t[j];
-                    }
-                    if constexpr (OUT_S) st_words<K>(reinterpret_cast<uint32_t*>(out + pi * 2 * DP) + lane * K, s);
-                    if constexpr (WTA) {
-                        uint32_t key = wta_key<K>(s, lane, DP / 2, a.D);
-                        key = redux_min(key, 0xffffffffu);
-                        const size_t p = g.pix(i0 + pi);
-                        if (lane == 0) a.raw[p] = static_cast<uint8_t>(key & 0xffu);
-                        if (a.Sdbg) {
-#pragma unroll
-                            for (int j = 0; j < K; ++j) {
-                                const int i = lane * K + j;
-                                if (i < a.D) a.Sdbg[p * a.D + i] = static_cast<uint16_t>(s[j] & 0xffffu);
-                                if (i + DP / 2 < a.D) a.Sdbg[p * a.D + i + DP / 2] = static_cast<uint16_t>(s[j] >> 16);
-                            }
-                        }
-                    }
-                }
-                if constexpr (Geo::kResets) {
-                    y_body += g.dy;
-                    x_body += g.rx * g.dy;
-                    x_body = x_body >= g.W ? x_body - g.W : (x_body < 0 ? x_body + g.W : x_body);
                 }
             }
         }
         __syncwarp();
+        if constexpr (WTA) {
+            if (hl < np) a.raw[g.pix(xc, yc, hl)] = static_cast<uint8_t>(dkeep & 0xffu);
+        }
         if constexpr (OUT_LX || OUT_S) {
             constexpr int P = OUT_LX ? PM : PS;
-            constexpr int BPP = OUT_LX ? DP : 2 * DP;  // bytes per pixel
+            constexpr int BPP = OUT_LX ? D : 2 * D;  // bytes per pixel
             uint8_t* dst = OUT_LX ? a.Lx : reinterpret_cast<uint8_t*>(a.S);
-            for (int q = lane; q < np * P; q += 32) {
+            for (int q = hl; q < np * P; q += 16) {
                 const int pi = q / P, off = (q % P) * 16;
-                const size_t p = g.pix(i0 + pi);
+                const size_t p = g.pix(xc, yc, pi);
                 *reinterpret_cast<uint4*>(dst + p * BPP + off) = *reinterpret_cast<const uint4*>(out + pi * BPP + off);
             }
             __syncwarp();
@@ -189,120 +247,145 @@ __device__ __forceinline__ void walk(Chain<K>& ch, const Geo& g, int n, const Sw
 }
 
 // ---------------------------------------------------------------------------
-// Horizontal axis.  Block = 2 rows x 2 warps; warp 2r walks row r left to
-// right, warp 2r+1 right to left.  Phase 1: LR covers x < W/2 and RL covers
-// x >= W/2, both storing L in Lx.  Phase 2: each covers the other half and
-// writes S = own L + stored L.  Without `pair` (2-path mode) LR covers the
-// whole row and writes S = L_LR.
+// Horizontal axis: one row per warp, lanes 0-15 walk left to right, lanes
+// 16-31 right to left.  Phase 1: LR covers x < W/2, RL covers x >= W/2, both
+// storing L in Lx.  Phase 2: each covers the other half and writes
+// S = own L + stored L.  Without `pair` (2-path mode) LR covers the whole row
+// and writes S = L_LR.
 // ---------------------------------------------------------------------------
 template <int K>
-__global__ void __launch_bounds__(128) sweep_h_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_h_kernel(SweepArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int y = blockIdx.x * 2 + (warp >> 1);
-    const bool rev = (warp & 1) != 0;
-    const bool active = (y < a.H) && (!rev || a.pair);
-    uint8_t* ws = smem + warp * Stage<K>::BYTES;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, hl = lane & 15;
+    const bool in_b = lane >= 16;
+    const int y = blockIdx.x * kWarpsPerBlock + warp;
+    if (y >= a.H) return;  // whole warp: every exchange below is warp-local
+    uint8_t* ws = smem + (2 * warp + (in_b ? 1 : 0)) * Stage<K>::BYTES;
     const int W = a.W;
-    const int Wm = a.pair ? W / 2 : W;
-    const size_t rowbase = static_cast<size_t>(y < a.H ? y : 0) * W;
-    Chain<K> ch;
+    const size_t rowbase = static_cast<size_t>(y) * W;
+    Chain2<K> ch;
     ch.init(lane);
-    if (active) {
-        const RowGeo g{rowbase, rev ? W - 1 : 0, rev ? -1 : 1};
-        const int n1 = rev ? (W - Wm) : Wm;
-        if (a.pair)
-            walk<K, kStoreL>(ch, g, n1, a, ws, lane);
-        else
-            walk<K, kSingleH>(ch, g, n1, a, ws, lane);
+    if (!a.pair) {
+        const RowGeo g{rowbase, 0, 1};
+        walk<K, kSingleH>(ch, g, in_b ? 0 : W, 0, W, a, ws, hl);
+        return;
     }
-    if (!a.pair) return;  // uniform over the launch
-    __syncthreads();
-    if (active) {
-        const RowGeo g{rowbase, rev ? Wm - 1 : Wm, rev ? -1 : 1};
-        const int n2 = rev ? Wm : (W - Wm);
-        walk<K, kSumH>(ch, g, n2, a, ws, lane);
+    const int Wm = W / 2;
+    {
+        const RowGeo g = in_b ? RowGeo{rowbase, W - 1, -1} : RowGeo{rowbase, 0, 1};
+        const int nA = Wm, nB = W - Wm;
+        walk<K, kStoreL>(ch, g, in_b ? nB : nA, min(nA, nB), max(nA, nB), a, ws, hl);
+    }
+    __threadfence_block();  // this half's L stores before the other half reads them
+    __syncwarp();
+    {
+        const RowGeo g = in_b ? RowGeo{rowbase, Wm - 1, -1} : RowGeo{rowbase, Wm, 1};
+        const int nA = W - Wm, nB = Wm;
+        walk<K, kSumH>(ch, g, in_b ? nB : nA, min(nA, nB), max(nA, nB), a, ws, hl);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Vertical-type axis.  Block = 2 chains x 2 warps; warp 2c walks chain c
-// downward (rows 0 .. H-1), warp 2c+1 upward.  Chain c visits pixel
-// x(y) = (c + rx*y) mod W in row y: a column for rx = 0, and for rx = +1/-1 a
-// diagonal that wraps to the other border, restarting its path there
-// (Section 3.2).  Phase 1: down covers y < H/2, up covers y >= H/2, storing L.
-// Phase 2: each covers the other half and combines its L with the stored L
-// and S: S += both (wta = 0) or raw = argmin_d (S + both) (wta = 1).
-// Without `pair` the downward warp covers all rows (2-path mode, wta = 1).
+// Vertical-type axis: one chain per warp, lanes 0-15 walk down (rows 0 ..
+// H-1), lanes 16-31 up.  Chain c visits pixel x(y) = (c + RX*y) mod W in row y:
+// a column for RX = 0, and for RX = +1/-1 a diagonal that wraps to the other
+// border, restarting its path there (Section 3.2).  Phase 1: down covers
+// y < H/2, up covers y >= H/2, storing L.  Phase 2: each covers the other half
+// and combines its L with the stored L and S: S += both (wta = 0) or
+// raw = argmin_d (S + both) (wta = 1).  Without `pair` the downward half covers
+// all rows (2-path mode, wta = 1).
 // ---------------------------------------------------------------------------
-template <int K>
-__global__ void __launch_bounds__(128) sweep_v_kernel(SweepArgs a) {
+template <int K, int RX>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_v_kernel(SweepArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = blockIdx.x * 2 + (warp >> 1);
-    const bool upward = (warp & 1) != 0;
-    const bool active = (c < a.W) && (!upward || a.pair);
-    uint8_t* ws = smem + warp * Stage<K>::BYTES;
-    const int H = a.H;
-    const int Hm = a.pair ? H / 2 : H;
-    Chain<K> ch;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, hl = lane & 15;
+    const bool in_b = lane >= 16;
+    const int c = blockIdx.x * kWarpsPerBlock + warp;
+    if (c >= a.W) return;  // whole warp
+    uint8_t* ws = smem + (2 * warp + (in_b ? 1 : 0)) * Stage<K>::BYTES;
+    const int W = a.W, H = a.H;
+    Chain2<K> ch;
     ch.init(lane);
-    if (active) {
-        const ColGeo g{a.W, H, c, a.rx, upward ? H - 1 : 0, upward ? -1 : 1};
-        const int n1 = upward ? (H - Hm) : Hm;
-        if (a.pair)
-            walk<K, kStoreL>(ch, g, n1, a, ws, lane);
-        else
-            walk<K, kSingleWta>(ch, g, n1, a, ws, lane);
+    if (!a.pair) {
+        const ColGeo<RX> g{W, H, c, 0, 1};
+        walk<K, kSingleWta>(ch, g, in_b ? 0 : H, 0, H, a, ws, hl);
+        return;
     }
-    if (!a.pair) return;  // uniform over the launch
-    __syncthreads();
-    if (active) {
-        const ColGeo g{a.W, H, c, a.rx, upward ? Hm - 1 : Hm, upward ? -1 : 1};
-        const int n2 = upward ? Hm : (H - Hm);
+    const int Hm = H / 2;
+    {
+        const ColGeo<RX> g = in_b ? ColGeo<RX>{W, H, c, H - 1, -1} : ColGeo<RX>{W, H, c, 0, 1};
+        const int nA = Hm, nB = H - Hm;
+        walk<K, kStoreL>(ch, g, in_b ? nB : nA, min(nA, nB), max(nA, nB), a, ws, hl);
+    }
+    __threadfence_block();
+    __syncwarp();
+    {
+        const ColGeo<RX> g = in_b ? ColGeo<RX>{W, H, c, Hm - 1, -1} : ColGeo<RX>{W, H, c, Hm, 1};
+        const int nA = H - Hm, nB = Hm;
         if (a.wta)
-            walk<K, kWta2>(ch, g, n2, a, ws, lane);
+            walk<K, kWta2>(ch, g, in_b ? nB : nA, min(nA, nB), max(nA, nB), a, ws, hl);
         else
-            walk<K, kAcc>(ch, g, n2, a, ws, lane);
+            walk<K, kAcc>(ch, g, in_b ? nB : nA, min(nA, nB), max(nA, nB), a, ws, hl);
     }
 }
 
 template <int K>
 static cudaError_t set_attrs_t() {
-    constexpr int smem = 4 * Stage<K>::BYTES;
+    constexpr int smem = Stage<K>::BLOCK_BYTES;
     cudaError_t e = cudaFuncSetAttribute(sweep_h_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sweep_v_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        e = cudaFuncSetAttribute(sweep_v_kernel<K, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep_v_kernel<K, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep_v_kernel<K, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
 }
 
 cudaError_t init_kernel_attributes() {
-    cudaError_t e;
-    if ((e = set_attrs_t<1>()) != cudaSuccess) return e;
-    if ((e = set_attrs_t<2>()) != cudaSuccess) return e;
-    if ((e = set_attrs_t<3>()) != cudaSuccess) return e;
-    return set_attrs_t<4>();
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = set_attrs_t<1>();
+    if (e == cudaSuccess) e = set_attrs_t<2>();
+    if (e == cudaSuccess) e = set_attrs_t<3>();
+    if (e == cudaSuccess) e = set_attrs_t<4>();
+    if (e == cudaSuccess) e = set_attrs_t<5>();
+    if (e == cudaSuccess) e = set_attrs_t<6>();
+    if (e == cudaSuccess) e = set_attrs_t<7>();
+    if (e == cudaSuccess) e = set_attrs_t<8>();
+    return e;
 }
 
 template <int K>
 static cudaError_t launch_h_t(const SweepArgs& a, cudaStream_t stream) {
-    sweep_h_kernel<K><<<(a.H + 1) / 2, 128, 4 * Stage<K>::BYTES, stream>>>(a);
+    sweep_h_kernel<K><<<(a.H + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, Stage<K>::BLOCK_BYTES,
+                        stream>>>(a);
     return cudaGetLastError();
 }
 
 template <int K>
 static cudaError_t launch_v_t(const SweepArgs& a, cudaStream_t stream) {
-    sweep_v_kernel<K><<<(a.W + 1) / 2, 128, 4 * Stage<K>::BYTES, stream>>>(a);
+    const dim3 grid((a.W + kWarpsPerBlock - 1) / kWarpsPerBlock), block(32 * kWarpsPerBlock);
+    const int smem = Stage<K>::BLOCK_BYTES;
+    if (a.rx == 0)
+        sweep_v_kernel<K, 0><<<grid, block, smem, stream>>>(a);
+    else if (a.rx > 0)
+        sweep_v_kernel<K, 1><<<grid, block, smem, stream>>>(a);
+    else
+        sweep_v_kernel<K, -1><<<grid, block, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
-// K words per lane: DP = 64 K disparities (D rounded up to a multiple of 64).
+// K = D / 32 words per lane (16 lanes per path).
 #define SGM_DISPATCH_K(FN, a, s)               \
-    switch (padded_D((a).D) / 64) {            \
+    switch ((a).D / 32) {                      \
         case 1: return FN<1>(a, s);            \
         case 2: return FN<2>(a, s);            \
         case 3: return FN<3>(a, s);            \
         case 4: return FN<4>(a, s);            \
+        case 5: return FN<5>(a, s);            \
+        case 6: return FN<6>(a, s);            \
+        case 7: return FN<7>(a, s);            \
+        case 8: return FN<8>(a, s);            \
         default: return cudaErrorInvalidValue; \
     }
 
