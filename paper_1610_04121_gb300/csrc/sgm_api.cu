@@ -32,9 +32,9 @@ struct Layout {
     size_t Fb, Fm, MC, Lx, S, raw, in_left, in_right, out, total;
 };
 
-Layout layout_for(int W, int H, int D_real) {
+Layout layout_for(int W, int H, int D_int) {
     const size_t wh = static_cast<size_t>(W) * H;
-    const size_t D = static_cast<size_t>(padded_D(D_real));
+    const size_t D = static_cast<size_t>(D_int);
     Layout l{};
     size_t o = 0;
     l.Fb = o;

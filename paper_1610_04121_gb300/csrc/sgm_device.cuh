@@ -3,19 +3,15 @@
 // Data layouts in HBM (all row-major, y outermost):
 //   image      uint8  [H][W]
 //   feature    uint32 [H][W]              CSCT of Eq. 1, 31 bits
-//   cost       uint8  [H][W][DP]          "paired" order: for word i in [0, DP/2)
-//                                         bytes 2i, 2i+1 hold MC(i), MC(i + DP/2)
-//   path cost  uint8  [H][W][DP]          L_r in the same paired order (L_r <= 255)
-//   sum        uint32 [H][W][DP/2]        packed u16x2 word i = (S(i), S(i + DP/2))
+//   cost       uint8  [H][W][D]           "paired" order: for word i in [0, D/2)
+//                                         bytes 2i, 2i+1 hold MC(i), MC(i + D/2)
+//   path cost  uint8  [H][W][D]           L_r in the same paired order (L_r <= 255)
+//   sum        uint32 [H][W][D/2]         packed u16x2 word i = (S(i), S(i + D/2))
 //   disparity  uint8  [H][W]
 //
-// DP is D rounded up to a multiple of 64 (a warp of 32 lanes x K words); the
-// padded disparities D <= d < DP carry the cost 255.  A real L_r never exceeds
-// 31 + P2 <= 255, so a padded neighbour never lowers a real path cost, the
-// step minimum stays a real one, and the winner-take-all skips padded d.
 // The paired order makes the disparity neighbours d-1 / d+1 of both halves of
 // word i live in words i-1 / i+1, so the Eq. 3 step needs no byte shuffling
-// inside a word; only the two seams (d = 0 and d = DP/2) need a permute.
+// inside a word; only the two seams (d = 0 and d = D/2) need a permute.
 #pragma once
 
 #include <cstdint>
@@ -178,39 +174,42 @@ __device__ __forceinline__ void st_words(uint32_t* p, const uint32_t (&w)[K]) {
 }
 
 // ---------------------------------------------------------------------------
-// Per-lane constants of a 32-lane chain layout.  Lane l holds words
-// i = l*K + j, j < K; word i packs L(i) (low half) and L(i + DP/2) (high
-// half), DP = 64*K.  The seams: d-1 of d=0 and d+1 of d=DP-1 are absent; d-1
-// of d=DP/2 is the low half of word DP/2-1 (lane 31), d+1 of d=DP/2-1 is the
-// high half of word 0 (lane 0).
-// ---------------------------------------------------------------------------
-struct LaneConsts {
-    uint32_t sel_up, sel_dn;
-    int src_up, src_dn;
-    __device__ __forceinline__ void init(int lane) {
-        src_up = (lane + 31) & 31;
-        src_dn = (lane + 1) & 31;
-        sel_up = (lane == 0) ? 0x1054u : 0x3210u;   // lane 0: (INF, low half of word DP/2-1)
-        sel_dn = (lane == 31) ? 0x5432u : 0x3210u;  // lane 31: (high half of word 0, INF)
-    }
-};
-
-// ---------------------------------------------------------------------------
-// One aggregation path (Eq. 3, Section 3.2) over a full warp.  Each step
-// computes, for every d,
+// Two aggregation chains (Eq. 3, Section 3.2) per warp: lanes 0-15 carry
+// chain A, lanes 16-31 chain B (the two opposite directions of one row or one
+// column).  Every cross-lane operation is a full-warp instruction; each half
+// shuffles within itself and the two step minima are two masked reductions.
+//
+// Lane l of a half holds words i = (l mod 16)*K + j, j < K, of the path cost
+// of the previous pixel; word i packs L(i) (low half) and L(i + D/2) (high
+// half), D = 32*K.  Each step computes, for every d,
 //   L(p, d) = MC(p, d) + min(L(q, d), L(q, d-1) + P1, L(q, d+1) + P1, m(q) + P2) - m(q)
 // with q the previous pixel and m(q) = min_k L(q, k).  Starting a path with
 // L(q, .) = 0 and m(q) = 0 yields L(p, .) = MC(p, .), the reading used for the
 // first pixel of every path.  `up` / `dn` hold the neighbour words across the
 // lane boundary, already exchanged at the end of the previous step.
-// A warp carries two independent paths, so the compiler can interleave the two
-// dependency chains.
 // ---------------------------------------------------------------------------
 template <int K>
-struct Chain {
+struct Chain2 {
     uint32_t w[K];
-    uint32_t up, dn;  // word l*K-1 from lane l-1, word l*K+K from lane l+1 (wrapping)
+    uint32_t up, dn;  // word hl*K-1 from lane hl-1, word hl*K+K from lane hl+1 (wrapping in the half)
     uint32_t mpx2;    // m(q) in both u16 halves
+    uint32_t sel_up, sel_dn, mask_a, mask_b;
+    int src_up, src_dn;
+    bool in_b;
+
+    __device__ __forceinline__ void init(int lane) {
+        const int hl = lane & 15, base = lane & 16;
+        src_up = base | ((hl + 15) & 15);
+        src_dn = base | ((hl + 1) & 15);
+        // first lane of a half: d-1 of d=0 is absent, d-1 of d=D/2 is the low half of word D/2-1
+        sel_up = (hl == 0) ? 0x1054u : 0x3210u;
+        // last lane of a half: d+1 of d=D-1 is absent, d+1 of d=D/2-1 is the high half of word 0
+        sel_dn = (hl == 15) ? 0x5432u : 0x3210u;
+        in_b = lane >= 16;
+        mask_a = in_b ? 0xffffffffu : 0u;
+        mask_b = ~mask_a;
+        reset();
+    }
 
     __device__ __forceinline__ void reset() {
 #pragma unroll
@@ -219,11 +218,17 @@ struct Chain {
         mpx2 = 0u;
     }
 
-    __device__ __forceinline__ void step(const LaneConsts& lc, const uint32_t (&mc)[K], uint32_t P1x2, uint32_t P2x2,
-                                         uint32_t (&L)[K]) {
+    // the minimum of v over this lane's half of the warp
+    __device__ __forceinline__ uint32_t half_min(uint32_t v) const {
+        const uint32_t a = redux_min(v | mask_a);
+        const uint32_t b = redux_min(v | mask_b);
+        return in_b ? b : a;
+    }
+
+    __device__ __forceinline__ void step(const uint32_t (&mc)[K], uint32_t P1x2, uint32_t P2x2, uint32_t (&L)[K]) {
         const uint32_t inf2 = kInf16 * 0x10001u;
-        const uint32_t u = __byte_perm(up, inf2, lc.sel_up);
-        const uint32_t d = __byte_perm(dn, inf2, lc.sel_dn);
+        const uint32_t u = __byte_perm(up, inf2, sel_up);
+        const uint32_t d = __byte_perm(dn, inf2, sel_dn);
         const uint32_t mp2 = mpx2 + P2x2;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
@@ -236,9 +241,9 @@ struct Chain {
 #pragma unroll
         for (int j = 1; j < K; ++j) r = vmin2(r, L[j]);
         r = vmin2(r, __byte_perm(r, 0u, 0x1032u));  // both u16 halves = lane minimum
-        up = shfl_idx(L[K - 1], lc.src_up);
-        dn = shfl_idx(L[0], lc.src_dn);
-        mpx2 = redux_min(r);
+        up = shfl_idx(L[K - 1], src_up);
+        dn = shfl_idx(L[0], src_dn);
+        mpx2 = half_min(r);
 #pragma unroll
         for (int j = 0; j < K; ++j) w[j] = L[j];
     }
@@ -246,17 +251,13 @@ struct Chain {
 
 // Winner-take-all over one lane's words (Eq. 4): key = S << 8 | d, so the
 // u32 minimum is the smallest S and, among equal S, the lowest d.  dconst[j]
-// holds, for word i = lane*K + j, the bytes [i, i + DP/2, pad_lo, pad_hi]:
-// pad is 0 for a real disparity and 0xFF for a padded one (d >= D), which
-// makes the padded key larger than every real key (S < 2^16).
+// holds, for word i = hl*K + j, the bytes [i, i + D/2, 0, 0].
 template <int K>
-__device__ __forceinline__ void wta_consts(int lane, int D, uint32_t (&dconst)[K]) {
+__device__ __forceinline__ void wta_consts(int hl, int D, uint32_t (&dconst)[K]) {
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-        const uint32_t i = static_cast<uint32_t>(lane * K + j);
-        const uint32_t ih = i + static_cast<uint32_t>(32 * K);
-        dconst[j] = i | (ih << 8) | ((static_cast<int>(i) < D) ? 0u : 0xFF0000u) |
-                    ((static_cast<int>(ih) < D) ? 0u : 0xFF000000u);
+        const uint32_t i = static_cast<uint32_t>(hl * K + j);
+        dconst[j] = i | ((i + static_cast<uint32_t>(D / 2)) << 8);
     }
 }
 
@@ -265,8 +266,8 @@ __device__ __forceinline__ uint32_t wta_key(const uint32_t (&s)[K], const uint32
     uint32_t best = 0xffffffffu;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-        const uint32_t klo = __byte_perm(s[j], dconst[j], 0x6104u);  // [d_lo, S_lo.b0, S_lo.b1, pad_lo]
-        const uint32_t khi = __byte_perm(s[j], dconst[j], 0x7325u);  // [d_hi, S_hi.b0, S_hi.b1, pad_hi]
+        const uint32_t klo = __byte_perm(s[j], dconst[j], 0x6104u);  // [d_lo, S_lo.b0, S_lo.b1, 0]
+        const uint32_t khi = __byte_perm(s[j], dconst[j], 0x6325u);  // [d_hi, S_hi.b0, S_hi.b1, 0]
         best = min(best, min(klo, khi));
     }
     return best;

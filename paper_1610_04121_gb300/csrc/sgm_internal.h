@@ -8,9 +8,9 @@ namespace sgm {
 
 // Arguments of the aggregation sweeps (Eq. 3) over one pair.
 struct SweepArgs {
-    const uint8_t* MC;  // paired costs [H][W][DP], DP = padded_D(D)
-    uint8_t* Lx;        // scratch: one direction's path costs, paired [H][W][DP]
-    uint32_t* S;        // packed sums [H][W][DP/2]
+    const uint8_t* MC;  // paired costs [H][W][D]
+    uint8_t* Lx;        // scratch: one direction's path costs, paired [H][W][D]
+    uint32_t* S;        // packed sums [H][W][D/2]
     uint8_t* raw;       // winner-take-all disparity [H][W] (final vertical sweep)
     uint16_t* Sdbg;     // optional natural-order S [H][W][D] (debug)
     int W, H, D;
@@ -32,10 +32,6 @@ cudaError_t launch_median(const uint8_t* raw, uint8_t* disp, int W, int H, cudaS
 cudaError_t launch_unpair_cost(const uint8_t* MC, uint8_t* out, int W, int H, int D, cudaStream_t stream);
 
 bool supported_D(int D);
-
-// D rounded up to a multiple of 64: the disparity count the kernels carry
-// (one warp of 32 lanes x K packed words); the padding never wins a minimum.
-__host__ __device__ inline int padded_D(int D) { return (D + 63) / 64 * 64; }
 
 // One-time kernel attributes (shared-memory carve-outs); call before any
 // launch or stream capture on the current device.

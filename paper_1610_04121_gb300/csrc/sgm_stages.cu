@@ -62,7 +62,6 @@ cudaError_t launch_census(const uint8_t* left, const uint8_t* right, uint32_t* F
 // match feature 0 left of the image.  A CTA covers 32 pixels of one row; the
 // match features x0-D+1 .. x0+31 are staged in shared memory (the 1D tiling
 // of Section 3.1) and every thread writes one 32-bit word = two paired words.
-// Padded disparities D <= d < DP get the cost 255.
 // ---------------------------------------------------------------------------
 constexpr int kMcSeg = 32;
 
@@ -71,7 +70,6 @@ __global__ void __launch_bounds__(256) cost_kernel(const uint32_t* __restrict__ 
     extern __shared__ uint32_t smem[];
     uint32_t* fm = smem;                      // D - 1 + kMcSeg match features
     uint32_t* fb = smem + (D - 1 + kMcSeg);   // kMcSeg base features
-    const int DP = padded_D(D);
     const int y = blockIdx.y, x0 = blockIdx.x * kMcSeg;
     const uint32_t* fmrow = Fm + (size_t)y * W;
     for (int i = threadIdx.x; i < D - 1 + kMcSeg; i += blockDim.x) {
@@ -80,18 +78,17 @@ __global__ void __launch_bounds__(256) cost_kernel(const uint32_t* __restrict__ 
     }
     for (int i = threadIdx.x; i < kMcSeg; i += blockDim.x) fb[i] = (x0 + i < W) ? Fb[(size_t)y * W + x0 + i] : 0u;
     __syncthreads();
-    const int Q = DP / 4, half = DP / 2;
+    const int Q = D / 4, half = D / 2;
     const int npx = min(kMcSeg, W - x0);
-    uint32_t* out = reinterpret_cast<uint32_t*>(MC + ((size_t)y * W + x0) * DP);
+    uint32_t* out = reinterpret_cast<uint32_t*>(MC + ((size_t)y * W + x0) * D);
     for (int t = threadIdx.x; t < npx * Q; t += blockDim.x) {
         const int px = t / Q, i0 = 2 * (t % Q);
         const uint32_t b = fb[px];
         const int base = px + D - 1;  // fm[base - d] = F_match(x - d)
-        const int d0 = i0, d1 = i0 + half, d2 = i0 + 1, d3 = i0 + 1 + half;
-        const uint32_t c0 = d0 < D ? __popc(b ^ fm[base - d0]) : 255u;
-        const uint32_t c1 = d1 < D ? __popc(b ^ fm[base - d1]) : 255u;
-        const uint32_t c2 = d2 < D ? __popc(b ^ fm[base - d2]) : 255u;
-        const uint32_t c3 = d3 < D ? __popc(b ^ fm[base - d3]) : 255u;
+        const uint32_t c0 = __popc(b ^ fm[base - i0]);
+        const uint32_t c1 = __popc(b ^ fm[base - i0 - half]);
+        const uint32_t c2 = __popc(b ^ fm[base - i0 - 1]);
+        const uint32_t c3 = __popc(b ^ fm[base - i0 - 1 - half]);
         out[t] = c0 | (c1 << 8) | (c2 << 16) | (c3 << 24);
     }
 }
@@ -104,15 +101,15 @@ cudaError_t launch_cost(const uint32_t* Fb, const uint32_t* Fm, uint8_t* MC, int
     return cudaGetLastError();
 }
 
-// Paired, padded order -> natural order [H][W][D] (debug only).
+// Paired order -> natural order [H][W][D] (debug only).
 __global__ void unpair_kernel(const uint8_t* __restrict__ MC, uint8_t* __restrict__ out, size_t npix, int D) {
     const size_t n = npix * D;
-    const int DP = padded_D(D), half = DP / 2;
+    const int half = D / 2;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
         const size_t p = t / D;
         const int d = static_cast<int>(t % D);
         const int src = (d < half) ? 2 * d : 2 * (d - half) + 1;
-        out[t] = MC[p * DP + src];
+        out[t] = MC[p * D + src];
     }
 }
 
