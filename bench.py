@@ -244,11 +244,17 @@ def main():
     clocks = clk.summary()
     mean_stage = {k: statistics.mean(v) for k, v in stage_ms.items()}
     dom = max(mean_stage, key=mean_stage.get)
-    paths_in = {"sweep_h": 2 if w.n_paths >= 4 else 1, "sweep_v": 2 if w.n_paths >= 4 else 1,
-                "sweep_diag+": 2, "sweep_diag-": 2}
+    # path-equivalents of Eq. 3 work in each timed stage: the horizontal stage
+    # also runs the first halves of the vertical-type pairs beside it
+    n_vert = 3 if w.n_paths == 8 else (1 if w.n_paths == 4 else 1)
+    path_eq = {"sweep_h": (2 + n_vert) if w.n_paths >= 4 else 1,
+               "sweep_v": 1, "sweep_diag+": 1, "sweep_diag-": 1}
+    if w.n_paths == 2:
+        path_eq["sweep_v"] = 1
     roofline = None
-    if dom in paths_in:
-        ops = de * (OPS_PER_DE_PATH * paths_in[dom] + (3 if dom == "sweep_v" else 1))
+    if dom in path_eq:
+        extra = 3 if dom == "sweep_v" else 1  # sums (+ winner-take-all)
+        ops = de * (OPS_PER_DE_PATH * path_eq[dom] + extra)
         sm_mhz = float(peaks.get("sm_max_mhz", SM_MAX_MHZ_GB300))
         peak_tops = SM_COUNT_GB300 * 128 * 2 * sm_mhz * 1e6 / 1e12
         achieved = ops / (mean_stage[dom] / 1e3) / 1e12

@@ -29,10 +29,13 @@ inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 // Offsets of one pair's buffers inside a work arena.
 struct Layout {
-    size_t Fb, Fm, MC, Lx, S, raw, in_left, in_right, out, total;
+    size_t Fb, Fm, MC, Lx, S, raw, state, in_left, in_right, out, total;
 };
 
-Layout layout_for(int W, int H, int D_int) {
+// Scratch cubes of first-half path costs: one per pair of opposite paths.
+int lx_cubes(int n_paths) { return n_paths == 8 ? 4 : (n_paths == 4 ? 2 : 1); }
+
+Layout layout_for(int W, int H, int D_int, int n_paths) {
     const size_t wh = static_cast<size_t>(W) * H;
     const size_t D = static_cast<size_t>(D_int);
     Layout l{};
@@ -43,12 +46,14 @@ Layout layout_for(int W, int H, int D_int) {
     o = align_up(o + 4 * wh);
     l.MC = o;
     o = align_up(o + wh * D);
-    l.Lx = o;
-    o = align_up(o + wh * D);
+    l.Lx = o;  // one path-cost cube per pair: horizontal + vertical-type ones
+    o = align_up(o + lx_cubes(n_paths) * align_up(wh * D));
     l.S = o;
     o = align_up(o + 2 * wh * D);
     l.raw = o;
     o = align_up(o + wh);
+    l.state = o;  // path states of the three vertical-type pairs between their phases
+    o = align_up(o + (lx_cubes(n_paths) - 1) * 4 * sweep_state_words(W, static_cast<int>(D)));
     l.in_left = o;
     o = align_up(o + wh);
     l.in_right = o;
@@ -91,6 +96,13 @@ struct GraphKey {
     }
 };
 
+// Streams and events one enqueuing thread uses: the main stream is the
+// caller's; the side stream runs the vertical first halves concurrently.
+struct StreamSet {
+    cudaStream_t side;
+    cudaEvent_t fork, join;
+};
+
 struct Request {
     uint64_t ticket;
     Problem p;
@@ -106,6 +118,8 @@ struct sgm_ctx {
     cudaStream_t own_stream = nullptr;
     cudaStream_t stream = nullptr;
     cudaStream_t capture_stream = nullptr;
+    StreamSet main_set{};   // side stream + fork/join events of the caller's thread
+    StreamSet serve_set{};  // the same for the served-request worker
     size_t mem_cap = 0;
     uint8_t* arena = nullptr;
     size_t arena_bytes = 0;
@@ -134,6 +148,20 @@ struct sgm_ctx {
 };
 
 static thread_local std::string g_noctx_err;
+
+static cudaError_t create_stream_set(StreamSet* ss) {
+    cudaError_t e = cudaStreamCreateWithFlags(&ss->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss->join, cudaEventDisableTiming);
+    return e;
+}
+
+static void destroy_stream_set(StreamSet* ss) {
+    if (ss->side) cudaStreamDestroy(ss->side);
+    if (ss->fork) cudaEventDestroy(ss->fork);
+    if (ss->join) cudaEventDestroy(ss->join);
+    *ss = StreamSet{};
+}
 
 static int fail(sgm_ctx* ctx, int code, const char* fmt, ...) {
     char buf[512];
@@ -192,13 +220,23 @@ static bool is_device_ptr(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-static int launches_per_path(const Problem& p) { return p.n_paths == 8 ? 7 : 5; }
+static int launches_per_path(const Problem& p) { return p.n_paths == 8 ? 10 : (p.n_paths == 4 ? 6 : 5); }
+
+// Timed stages: census, cost, sweep_h (with the vertical first halves beside
+// it), [sweep_diag+, sweep_diag-,] sweep_v, median.
+static int stages_per_path(const Problem& p) { return p.n_paths == 8 ? 7 : 5; }
+
+// Bytes of one [H][W][D] u8 scratch cube of path costs.
+static size_t lx_cube_bytes(const Problem& p) {
+    return align_up(static_cast<size_t>(p.W) * p.H * static_cast<size_t>(p.D));
+}
 
 // Enqueue the whole path (Section 2, stages 2-4) for one pair whose inputs
 // and output are device pointers.  Returns a cudaError_t.
 static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const uint8_t* left,
-                                const uint8_t* right, uint8_t* disp, uint16_t* Sdbg, cudaStream_t s, bool timed) {
-    const Layout l = layout_for(p.W, p.H, p.D);
+                                const uint8_t* right, uint8_t* disp, uint16_t* Sdbg, cudaStream_t s, bool timed,
+                                const StreamSet& ss) {
+    const Layout l = layout_for(p.W, p.H, p.D, p.n_paths);
     uint32_t* Fb = reinterpret_cast<uint32_t*>(arena + l.Fb);
     uint32_t* Fm = reinterpret_cast<uint32_t*>(arena + l.Fm);
     uint8_t* MC = arena + l.MC;
@@ -229,20 +267,50 @@ static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, 
     a.pair = p.n_paths >= 4;
     a.rx = 0;
     a.wta = 0;
-    if ((e = launch_sweep_h(a, s)) != cudaSuccess) return e;
-    if ((e = mark()) != cudaSuccess) return e;
-    if (p.n_paths == 8) {
-        a.rx = 1;
+    a.phase = 0;
+    uint32_t* states = reinterpret_cast<uint32_t*>(arena + l.state);
+    const size_t sw = sweep_state_words(p.W, p.D);
+    // vertical-type pairs: (rx, wta) in the order their second halves run
+    const int nv = p.n_paths == 8 ? 3 : 1;
+    const int vrx[3] = {1, -1, 0};
+    const int* rxs = p.n_paths == 8 ? vrx : vrx + 2;
+    if (!a.pair) {
+        // 2-path mode: left-to-right, then top-to-bottom with the winner-take-all
+        if ((e = launch_sweep_h(a, s)) != cudaSuccess) return e;
+        if ((e = mark()) != cudaSuccess) return e;
+        a.wta = 1;
         if ((e = launch_sweep_v(a, s)) != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
-        a.rx = -1;
-        if ((e = launch_sweep_v(a, s)) != cudaSuccess) return e;
+    } else {
+        // the first halves of the vertical-type pairs need only the costs: they
+        // run on the side stream while the horizontal pair runs
+        if ((e = cudaEventRecord(ss.fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(ss.side, ss.fork, 0)) != cudaSuccess) return e;
+        for (int v = 0; v < nv; ++v) {
+            SweepArgs b = a;
+            b.rx = rxs[v];
+            b.phase = 1;
+            b.state = states + v * sw;
+            // each vertical-type pair keeps its own first-half L cube: the scratch
+            // is split [H][W][DP] per pair after the horizontal one
+            b.Lx = arena + l.Lx + static_cast<size_t>(v + 1) * lx_cube_bytes(p);
+            if ((e = launch_sweep_v(b, ss.side)) != cudaSuccess) return e;
+        }
+        if ((e = cudaEventRecord(ss.join, ss.side)) != cudaSuccess) return e;
+        if ((e = launch_sweep_h(a, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s, ss.join, 0)) != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
+        for (int v = 0; v < nv; ++v) {
+            SweepArgs b = a;
+            b.rx = rxs[v];
+            b.phase = 2;
+            b.wta = (rxs[v] == 0) ? 1 : 0;
+            b.state = states + v * sw;
+            b.Lx = arena + l.Lx + static_cast<size_t>(v + 1) * lx_cube_bytes(p);
+            if ((e = launch_sweep_v(b, s)) != cudaSuccess) return e;
+            if ((e = mark()) != cudaSuccess) return e;
+        }
     }
-    a.rx = 0;
-    a.wta = 1;
-    if ((e = launch_sweep_v(a, s)) != cudaSuccess) return e;
-    if ((e = mark()) != cudaSuccess) return e;
     if ((e = launch_median(a.raw, disp, p.W, p.H, s)) != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;
     ctx->launches += launches_per_path(p);
@@ -262,7 +330,8 @@ static int enqueue_graph(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const u
         cudaGraph_t g = nullptr;
         CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
         const uint64_t before = ctx->launches.load();
-        cudaError_t e = enqueue_path(ctx, p, arena, left, right, disp, nullptr, ctx->capture_stream, ctx->stage_timing);
+        cudaError_t e = enqueue_path(ctx, p, arena, left, right, disp, nullptr, ctx->capture_stream, ctx->stage_timing,
+                                     ctx->main_set);
         ctx->launches = before;  // captured, not launched
         cudaError_t e2 = cudaStreamEndCapture(ctx->capture_stream, &g);
         if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -278,14 +347,14 @@ static int enqueue_graph(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const u
     }
     CUDA_TRY(ctx, cudaGraphLaunch(it->second, s));
     ctx->launches += launches_per_path(p);
-    ctx->last_stages = ctx->stage_timing ? launches_per_path(p) : 0;
+    ctx->last_stages = ctx->stage_timing ? stages_per_path(p) : 0;
     return SGM_OK;
 }
 
 // Copy-in / path / copy-out for one pair into `arena` (already large enough).
 static int enqueue_pair(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const uint8_t* left, const uint8_t* right,
-                        uint8_t* disp, cudaStream_t s, bool use_graph) {
-    const Layout l = layout_for(p.W, p.H, p.D);
+                        uint8_t* disp, cudaStream_t s, bool use_graph, const StreamSet& ss) {
+    const Layout l = layout_for(p.W, p.H, p.D, p.n_paths);
     const size_t wh = static_cast<size_t>(p.W) * p.H;
     const uint8_t* dl = left;
     const uint8_t* dr = right;
@@ -304,7 +373,7 @@ static int enqueue_pair(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const ui
         int rc = enqueue_graph(ctx, p, arena, dl, dr, dout, s);
         if (rc != SGM_OK) return rc;
     } else {
-        CUDA_TRY(ctx, enqueue_path(ctx, p, arena, dl, dr, dout, nullptr, s, false));
+        CUDA_TRY(ctx, enqueue_path(ctx, p, arena, dl, dr, dout, nullptr, s, false, ss));
     }
     if (out_host) CUDA_TRY(ctx, cudaMemcpyAsync(disp, dout, wh, cudaMemcpyDeviceToHost, s));
     return SGM_OK;
@@ -337,10 +406,11 @@ static void serve_loop(sgm_ctx* ctx) {
         if (ctx->stop) {
             rc = SGM_ECANCELED;
         } else {
-            const Layout l = layout_for(r.p.W, r.p.H, r.p.D);
+            const Layout l = layout_for(r.p.W, r.p.H, r.p.D, r.p.n_paths);
             rc = ensure_arena(ctx, &ctx->serve_arena, &ctx->serve_arena_bytes, l.total, false);
             if (rc == SGM_OK)
-                rc = enqueue_pair(ctx, r.p, ctx->serve_arena, r.left, r.right, r.out, ctx->serve_stream, false);
+                rc = enqueue_pair(ctx, r.p, ctx->serve_arena, r.left, r.right, r.out, ctx->serve_stream, false,
+                                  ctx->serve_set);
             if (rc == SGM_OK) {
                 cudaError_t e = cudaStreamSynchronize(ctx->serve_stream);
                 if (e != cudaSuccess) rc = fail(ctx, SGM_ECUDA, "served request: %s", cudaGetErrorString(e));
@@ -375,7 +445,8 @@ int sgm_create(sgm_ctx** out, int device, size_t mem_cap_bytes, unsigned flags) 
     ctx->mem_cap = mem_cap_bytes;
     if ((e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&ctx->serve_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        (e = cudaStreamCreateWithFlags(&ctx->serve_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = create_stream_set(&ctx->main_set)) != cudaSuccess || (e = create_stream_set(&ctx->serve_set)) != cudaSuccess) {
         sgm_destroy(ctx);
         return fail(nullptr, SGM_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
     }
@@ -413,6 +484,8 @@ int sgm_destroy(sgm_ctx* ctx) {
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     if (ctx->serve_stream) cudaStreamDestroy(ctx->serve_stream);
+    destroy_stream_set(&ctx->main_set);
+    destroy_stream_set(&ctx->serve_set);
     for (auto& ev : ctx->stage_ev)
         if (ev) cudaEventDestroy(ev);
     delete ctx;
@@ -433,9 +506,9 @@ int sgm_compute(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, 
     int rc = check_args(ctx, p, left, right, disp_out);
     if (rc != SGM_OK) return rc;
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-    rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, layout_for(W, H, D).total, true);
+    rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, layout_for(W, H, D, n_paths).total, true);
     if (rc != SGM_OK) return rc;
-    rc = enqueue_pair(ctx, p, ctx->arena, left, right, disp_out, ctx->stream, true);
+    rc = enqueue_pair(ctx, p, ctx->arena, left, right, disp_out, ctx->stream, true, ctx->main_set);
     if (rc != SGM_OK) return rc;
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     return SGM_OK;
@@ -449,7 +522,7 @@ int sgm_compute_async(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, i
     if (!is_device_ptr(left) || !is_device_ptr(right) || !is_device_ptr(disp_out))
         return fail(ctx, SGM_EINVAL, "sgm_compute_async takes device pointers only");
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-    rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, layout_for(W, H, D).total, true);
+    rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, layout_for(W, H, D, n_paths).total, true);
     if (rc != SGM_OK) return rc;
     return enqueue_graph(ctx, p, ctx->arena, left, right, disp_out, ctx->stream);
 }
@@ -463,7 +536,7 @@ int sgm_compute_batch(sgm_ctx* ctx, int n, const sgm_pair* pairs) {
         const Problem p{q.W, q.H, q.D, q.P1, q.P2, q.n_paths};
         int rc = check_args(ctx, p, q.left, q.right, q.disp_out);
         if (rc != SGM_OK) return fail(ctx, rc, "pair %d: %s", i, ctx->err.c_str());
-        need = std::max(need, layout_for(q.W, q.H, q.D).total);
+        need = std::max(need, layout_for(q.W, q.H, q.D, q.n_paths).total);
     }
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     int rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, need, true);
@@ -471,7 +544,7 @@ int sgm_compute_batch(sgm_ctx* ctx, int n, const sgm_pair* pairs) {
     for (int i = 0; i < n; ++i) {
         const sgm_pair& q = pairs[i];
         const Problem p{q.W, q.H, q.D, q.P1, q.P2, q.n_paths};
-        rc = enqueue_pair(ctx, p, ctx->arena, q.left, q.right, q.disp_out, ctx->stream, false);
+        rc = enqueue_pair(ctx, p, ctx->arena, q.left, q.right, q.disp_out, ctx->stream, false, ctx->main_set);
         if (rc != SGM_OK) return rc;
     }
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
@@ -484,7 +557,7 @@ int sgm_submit(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, i
     int rc = check_args(ctx, p, left, right, disp_out);
     if (rc != SGM_OK) return rc;
     if (!ticket) return fail(ctx, SGM_EINVAL, "null ticket pointer");
-    if (ctx->mem_cap && layout_for(W, H, D).total + ctx->arena_bytes > ctx->mem_cap)
+    if (ctx->mem_cap && layout_for(W, H, D, n_paths).total + ctx->arena_bytes > ctx->mem_cap)
         return fail(ctx, SGM_ENOMEM, "pair %dx%d D=%d needs more than the context's memory cap", W, H, D);
     std::lock_guard<std::mutex> lk(ctx->mu);
     if (!ctx->worker_started) {
@@ -539,7 +612,7 @@ int sgm_debug_stages(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, in
     int rc = check_args(ctx, p, left, right, left);
     if (rc != SGM_OK) return rc;
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-    const Layout l = layout_for(W, H, D);
+    const Layout l = layout_for(W, H, D, n_paths);
     const size_t wh = static_cast<size_t>(W) * H;
     const size_t extra = align_up(wh * D * 2) + align_up(wh * D);
     rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, l.total + extra, true);
@@ -550,7 +623,8 @@ int sgm_debug_stages(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, in
     cudaStream_t s = ctx->stream;
     CUDA_TRY(ctx, cudaMemcpyAsync(a + l.in_left, left, wh, cudaMemcpyHostToDevice, s));
     CUDA_TRY(ctx, cudaMemcpyAsync(a + l.in_right, right, wh, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(ctx, enqueue_path(ctx, p, a, a + l.in_left, a + l.in_right, a + l.out, S ? Sdev : nullptr, s, false));
+    CUDA_TRY(ctx, enqueue_path(ctx, p, a, a + l.in_left, a + l.in_right, a + l.out, S ? Sdev : nullptr, s, false,
+                               ctx->main_set));
     if (Fb) CUDA_TRY(ctx, cudaMemcpyAsync(Fb, a + l.Fb, 4 * wh, cudaMemcpyDeviceToHost, s));
     if (Fm) CUDA_TRY(ctx, cudaMemcpyAsync(Fm, a + l.Fm, 4 * wh, cudaMemcpyDeviceToHost, s));
     if (MC) {

@@ -18,6 +18,9 @@ struct SweepArgs {
     int rx;               // vertical-type sweeps: 0 (vertical), +1 / -1 (diagonals)
     int pair;             // 1: both opposite directions, 0: the forward one only
     int wta;              // vertical-type sweeps: 1 = finish with Eq. 4, 0 = add into S
+    int phase;            // vertical-type pairs: 0 = both phases, 1 = first half of each path
+                          // (saves the path state), 2 = second half (restores it)
+    uint32_t* state;      // path states between phases 1 and 2: [W][32 lanes][K + 3] words
 };
 
 // Each launcher enqueues one kernel on `stream` and returns the launch error.
@@ -27,6 +30,8 @@ cudaError_t launch_cost(const uint32_t* Fb, const uint32_t* Fm, uint8_t* MC, int
                         cudaStream_t stream);
 cudaError_t launch_sweep_h(const SweepArgs& a, cudaStream_t stream);
 cudaError_t launch_sweep_v(const SweepArgs& a, cudaStream_t stream);
+// Words of path state saved per vertical-type line between its two phases.
+inline size_t sweep_state_words(int W, int D) { return static_cast<size_t>(W) * 32 * (D / 32 + 3); }
 cudaError_t launch_median(const uint8_t* raw, uint8_t* disp, int W, int H, cudaStream_t stream);
 // Debug: paired costs -> natural order [H][W][D].
 cudaError_t launch_unpair_cost(const uint8_t* MC, uint8_t* out, int W, int H, int D, cudaStream_t stream);

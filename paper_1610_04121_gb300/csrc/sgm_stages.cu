@@ -59,46 +59,62 @@ cudaError_t launch_census(const uint8_t* left, const uint8_t* right, uint32_t* F
 
 // ---------------------------------------------------------------------------
 // Eq. 2: MC(x, y, d) = bitcount(F_base(x, y) XOR F_match(x - d, y)), with the
-// match feature 0 left of the image.  A CTA covers 32 pixels of one row; the
-// match features x0-D+1 .. x0+31 are staged in shared memory (the 1D tiling
-// of Section 3.1) and every thread writes one 32-bit word = two paired words.
+// match feature 0 left of the image.  A CTA covers kMcSeg pixels of one row;
+// the match features x0-D+1 .. x0+kMcSeg-1 are staged in shared memory (the 1D
+// tiling of Section 3.1) and every thread writes 32-bit words of two paired
+// words each (D known at compile time, so the item split is shifts and
+// multiplies).  The kernel is bound by the bit-count pipe (16 lanes/clk/SM).
 // ---------------------------------------------------------------------------
-constexpr int kMcSeg = 32;
+constexpr int kMcSeg = 64;
 
+template <int D>
 __global__ void __launch_bounds__(256) cost_kernel(const uint32_t* __restrict__ Fb, const uint32_t* __restrict__ Fm,
-                                                   uint8_t* __restrict__ MC, int W, int H, int D) {
-    extern __shared__ uint32_t smem[];
-    uint32_t* fm = smem;                      // D - 1 + kMcSeg match features
-    uint32_t* fb = smem + (D - 1 + kMcSeg);   // kMcSeg base features
+                                                   uint8_t* __restrict__ MC, int W) {
+    __shared__ uint32_t fm[D - 1 + kMcSeg];  // match features x0-D+1 .. x0+kMcSeg-1
+    __shared__ uint32_t fb[kMcSeg];
+    constexpr int Q = D / 4, half = D / 2;
     const int y = blockIdx.y, x0 = blockIdx.x * kMcSeg;
     const uint32_t* fmrow = Fm + (size_t)y * W;
-    for (int i = threadIdx.x; i < D - 1 + kMcSeg; i += blockDim.x) {
+    for (int i = threadIdx.x; i < D - 1 + kMcSeg; i += 256) {
         const int gx = x0 - (D - 1) + i;
         fm[i] = (gx >= 0 && gx < W) ? fmrow[gx] : 0u;
     }
-    for (int i = threadIdx.x; i < kMcSeg; i += blockDim.x) fb[i] = (x0 + i < W) ? Fb[(size_t)y * W + x0 + i] : 0u;
+    for (int i = threadIdx.x; i < kMcSeg; i += 256) fb[i] = (x0 + i < W) ? Fb[(size_t)y * W + x0 + i] : 0u;
     __syncthreads();
-    const int Q = D / 4, half = D / 2;
     const int npx = min(kMcSeg, W - x0);
     uint32_t* out = reinterpret_cast<uint32_t*>(MC + ((size_t)y * W + x0) * D);
-    for (int t = threadIdx.x; t < npx * Q; t += blockDim.x) {
+    for (int t = threadIdx.x; t < npx * Q; t += 256) {
         const int px = t / Q, i0 = 2 * (t % Q);
         const uint32_t b = fb[px];
-        const int base = px + D - 1;  // fm[base - d] = F_match(x - d)
-        const uint32_t c0 = __popc(b ^ fm[base - i0]);
-        const uint32_t c1 = __popc(b ^ fm[base - i0 - half]);
-        const uint32_t c2 = __popc(b ^ fm[base - i0 - 1]);
-        const uint32_t c3 = __popc(b ^ fm[base - i0 - 1 - half]);
-        out[t] = c0 | (c1 << 8) | (c2 << 16) | (c3 << 24);
+        const uint32_t* f = fm + px + D - 1 - i0;  // f[-d'] = F_match(x - i0 - d')
+        const uint32_t c0 = __popc(b ^ f[0]);
+        const uint32_t c1 = __popc(b ^ f[-half]);
+        const uint32_t c2 = __popc(b ^ f[-1]);
+        const uint32_t c3 = __popc(b ^ f[-1 - half]);
+        out[t] = __byte_perm(c0 | (c2 << 16), c1 | (c3 << 16), 0x6240u);  // [c0, c1, c2, c3]
     }
+}
+
+template <int D>
+static cudaError_t launch_cost_t(const uint32_t* Fb, const uint32_t* Fm, uint8_t* MC, int W, int H, cudaStream_t s) {
+    const dim3 grid((W + kMcSeg - 1) / kMcSeg, H);
+    cost_kernel<D><<<grid, 256, 0, s>>>(Fb, Fm, MC, W);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_cost(const uint32_t* Fb, const uint32_t* Fm, uint8_t* MC, int W, int H, int D,
                         cudaStream_t stream) {
-    dim3 grid((W + kMcSeg - 1) / kMcSeg, H);
-    const size_t smem = (size_t)(D - 1 + 2 * kMcSeg) * sizeof(uint32_t);
-    cost_kernel<<<grid, 256, smem, stream>>>(Fb, Fm, MC, W, H, D);
-    return cudaGetLastError();
+    switch (D) {
+        case 32: return launch_cost_t<32>(Fb, Fm, MC, W, H, stream);
+        case 64: return launch_cost_t<64>(Fb, Fm, MC, W, H, stream);
+        case 96: return launch_cost_t<96>(Fb, Fm, MC, W, H, stream);
+        case 128: return launch_cost_t<128>(Fb, Fm, MC, W, H, stream);
+        case 160: return launch_cost_t<160>(Fb, Fm, MC, W, H, stream);
+        case 192: return launch_cost_t<192>(Fb, Fm, MC, W, H, stream);
+        case 224: return launch_cost_t<224>(Fb, Fm, MC, W, H, stream);
+        case 256: return launch_cost_t<256>(Fb, Fm, MC, W, H, stream);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 // Paired order -> natural order [H][W][D] (debug only).
@@ -134,29 +150,45 @@ __device__ __forceinline__ void sort3(int& a, int& b, int& c) {
 
 __device__ __forceinline__ int med3(int a, int b, int c) { return max(min(a, b), min(max(a, b), c)); }
 
+// A CTA covers a 128 x 8 tile (4 pixels per thread along x) staged with its
+// one-pixel halo in shared memory.
 __global__ void __launch_bounds__(256) median_kernel(const uint8_t* __restrict__ raw, uint8_t* __restrict__ out,
                                                      int W, int H) {
-    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
-    if (x >= W || y >= H) return;
-    const size_t p = (size_t)y * W + x;
-    if (x == 0 || y == 0 || x == W - 1 || y == H - 1) {
-        out[p] = raw[p];
-        return;
+    __shared__ uint8_t t[10][136];
+    const int x0 = blockIdx.x * 128, y0 = blockIdx.y * 8;
+    for (int i = threadIdx.y * 32 + threadIdx.x; i < 10 * 130; i += 256) {
+        const int ty = i / 130, tx = i % 130;
+        const int gx = min(max(x0 - 1 + tx, 0), W - 1), gy = min(max(y0 - 1 + ty, 0), H - 1);
+        t[ty][tx] = raw[(size_t)gy * W + gx];
     }
-    int a0 = raw[p - W - 1], b0 = raw[p - W], c0 = raw[p - W + 1];
-    int a1 = raw[p - 1], b1 = raw[p], c1 = raw[p + 1];
-    int a2 = raw[p + W - 1], b2 = raw[p + W], c2 = raw[p + W + 1];
-    sort3(a0, b0, c0);
-    sort3(a1, b1, c1);
-    sort3(a2, b2, c2);
-    const int lo = max(max(a0, a1), a2);
-    const int mid = med3(b0, b1, b2);
-    const int hi = min(min(c0, c1), c2);
-    out[p] = static_cast<uint8_t>(med3(lo, mid, hi));
+    __syncthreads();
+    const int y = y0 + threadIdx.y;
+    if (y >= H) return;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int lx = threadIdx.x + 32 * k, x = x0 + lx;
+        if (x >= W) continue;
+        const int cx = lx + 1, cy = threadIdx.y + 1;
+        const size_t p = (size_t)y * W + x;
+        if (x == 0 || y == 0 || x == W - 1 || y == H - 1) {
+            out[p] = t[cy][cx];
+            continue;
+        }
+        int a0 = t[cy - 1][cx - 1], b0 = t[cy - 1][cx], c0 = t[cy - 1][cx + 1];
+        int a1 = t[cy][cx - 1], b1 = t[cy][cx], c1 = t[cy][cx + 1];
+        int a2 = t[cy + 1][cx - 1], b2 = t[cy + 1][cx], c2 = t[cy + 1][cx + 1];
+        sort3(a0, b0, c0);
+        sort3(a1, b1, c1);
+        sort3(a2, b2, c2);
+        const int lo = max(max(a0, a1), a2);
+        const int mid = med3(b0, b1, b2);
+        const int hi = min(min(c0, c1), c2);
+        out[p] = static_cast<uint8_t>(med3(lo, mid, hi));
+    }
 }
 
 cudaError_t launch_median(const uint8_t* raw, uint8_t* disp, int W, int H, cudaStream_t stream) {
-    dim3 grid((W + 31) / 32, (H + 7) / 8);
+    dim3 grid((W + 127) / 128, (H + 7) / 8);
     median_kernel<<<grid, dim3(32, 8), 0, stream>>>(raw, disp, W, H);
     return cudaGetLastError();
 }

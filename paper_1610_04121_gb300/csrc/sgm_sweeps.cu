@@ -312,10 +312,27 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_v_kernel(SweepArgs 
         return;
     }
     const int Hm = H / 2;
-    {
+    // saved path state of this lane: K words, the two neighbour words and m
+    uint32_t* st = a.state + (static_cast<size_t>(c) * 32 + lane) * (K + 3);
+    if (a.phase != 2) {
         const ColGeo<RX> g = in_b ? ColGeo<RX>{W, H, c, H - 1, -1} : ColGeo<RX>{W, H, c, 0, 1};
         const int nA = Hm, nB = H - Hm;
         walk<K, kStoreL>(ch, g, in_b ? nB : nA, min(nA, nB), max(nA, nB), a, ws, hl);
+    }
+    if (a.phase == 1) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) st[j] = ch.w[j];
+        st[K] = ch.up;
+        st[K + 1] = ch.dn;
+        st[K + 2] = ch.mpx2;
+        return;
+    }
+    if (a.phase == 2) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) ch.w[j] = st[j];
+        ch.up = st[K];
+        ch.dn = st[K + 1];
+        ch.mpx2 = st[K + 2];
     }
     __threadfence_block();
     __syncwarp();

@@ -112,10 +112,13 @@ def test_launch_counter_counts_kernels(ctx):
     p = _pair()
     before = ctx.launches
     ctx.compute(p.left, p.right, 64, 7, 84, 4)
-    assert ctx.launches - before == 5
+    assert ctx.launches - before == 6  # census, cost, vertical first halves, horizontal, vertical rest, median
     before = ctx.launches
     ctx.compute(p.left, p.right, 64, 7, 84, 8)
-    assert ctx.launches - before == 7
+    assert ctx.launches - before == 10  # three vertical-type pairs in two phases each
+    before = ctx.launches
+    ctx.compute(p.left, p.right, 64, 7, 84, 2)
+    assert ctx.launches - before == 5
 
 
 def test_stage_times_inside_graph_replay(sgm):
