@@ -212,6 +212,34 @@ SGM_API uint64_t sgm_kernel_launches(const sgm_ctx *ctx);
 /* Library version string. */
 SGM_API const char *sgm_version(void);
 
+/*
+ * Allocation-free form of sgm_compute_async, for callers that cannot allocate
+ * device memory: code running where cudaMalloc is forbidden or unavailable
+ * (an embedding runtime that owns all device memory, a plugin that may only
+ * use what its host hands it, or a real-time loop that must never allocate).
+ * The paper has no counterpart: it is an interface addition of this library.
+ *
+ * `left`, `right` and `disp_out` are device pointers on the current device;
+ * the call enqueues the whole path on `cuda_stream` (NULL = the legacy default
+ * stream) and returns without waiting.  It needs no context and calls no
+ * cudaMalloc, cudaFree or other allocating routine: every intermediate lives
+ * in one static device array of 48 MiB that each GPU which loads the library
+ * keeps until the process exits.  Sizes whose intermediates do not fit are
+ * rejected with SGM_EINVAL (320x240 with D = 64 and 8 paths fits; 640x480
+ * with D = 128 does not).
+ *
+ * The first call on a device looks up the array's device address and sets
+ * kernel attributes; make that first call before any stream capture.  Every
+ * call shares the one array and leaves the last call's contents in it (no
+ * part of it needs to start at zero: each byte is written before it is read),
+ * so calls that overlap on the GPU -- on different streams, or from different
+ * threads -- race: serialise them.  Results are bit-identical to sgm_compute.
+ * Errors (sgm_last_error(NULL) gives the text): SGM_EINVAL (null or host
+ * pointer, bad sizes, D, penalties or paths, scratch too small), SGM_ECUDA.
+ */
+SGM_API int sgm_compute_static(const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
+                               int n_paths, uint8_t *disp_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -661,3 +661,103 @@ uint64_t sgm_kernel_launches(const sgm_ctx* ctx) { return ctx ? ctx->launches.lo
 const char* sgm_version(void) { return "sgm-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point (sgm_compute_static).
+//
+// Every intermediate of the path lives in one file-scope device array of
+// kStaticScratchBytes, which each GPU that loads this library keeps until the
+// process exits.  Host code may not use `g_static_scratch` as an address (it
+// is a host-side stand-in); the device address is looked up once per device
+// with cudaGetSymbolAddress while that device is current.
+// ---------------------------------------------------------------------------
+constexpr size_t kStaticScratchBytes = size_t(48) << 20;  // 48 MiB
+__device__ __align__(256) uint8_t g_static_scratch[kStaticScratchBytes];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+uint8_t* g_static_ptr[kMaxDevices] = {};
+
+// Device address of the static scratch on the current device (set-up on the
+// first call per device).
+cudaError_t static_scratch_for_current_device(uint8_t** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        e = init_kernel_attributes();
+        if (e != cudaSuccess) return e;
+        g_static_ptr[dev] = static_cast<uint8_t*>(ptr);
+    }
+    *out = g_static_ptr[dev];
+    return cudaSuccess;
+}
+
+// The path of Section 2, stages 2-4, with every phase on one stream.
+cudaError_t enqueue_path_static(const Problem& p, uint8_t* arena, const uint8_t* left, const uint8_t* right,
+                                uint8_t* disp, cudaStream_t s) {
+    const Layout l = layout_for(p.W, p.H, p.D, p.n_paths);
+    uint32_t* Fb = reinterpret_cast<uint32_t*>(arena + l.Fb);
+    uint32_t* Fm = reinterpret_cast<uint32_t*>(arena + l.Fm);
+    cudaError_t e;
+    if ((e = launch_census(left, right, Fb, Fm, p.W, p.H, s)) != cudaSuccess) return e;
+    if ((e = launch_cost(Fb, Fm, arena + l.MC, p.W, p.H, p.D, s)) != cudaSuccess) return e;
+    SweepArgs a{};
+    a.MC = arena + l.MC;
+    a.Lx = arena + l.Lx;
+    a.S = reinterpret_cast<uint32_t*>(arena + l.S);
+    a.raw = arena + l.raw;
+    a.W = p.W;
+    a.H = p.H;
+    a.D = p.D;
+    a.P1x2 = static_cast<uint32_t>(p.P1) * 0x10001u;
+    a.P2x2 = static_cast<uint32_t>(p.P2) * 0x10001u;
+    a.pair = p.n_paths >= 4;
+    if ((e = launch_sweep_h(a, s)) != cudaSuccess) return e;
+    if (!a.pair) {
+        a.wta = 1;
+        if ((e = launch_sweep_v(a, s)) != cudaSuccess) return e;
+    } else {
+        const int vrx[3] = {1, -1, 0};
+        const int* rxs = p.n_paths == 8 ? vrx : vrx + 2;
+        const int nv = p.n_paths == 8 ? 3 : 1;
+        for (int v = 0; v < nv; ++v) {  // both phases of each vertical-type pair in one launch
+            SweepArgs b = a;
+            b.rx = rxs[v];
+            b.wta = (rxs[v] == 0) ? 1 : 0;
+            b.phase = 0;
+            if ((e = launch_sweep_v(b, s)) != cudaSuccess) return e;
+        }
+    }
+    return launch_median(a.raw, disp, p.W, p.H, s);
+}
+
+}  // namespace
+
+extern "C" int sgm_compute_static(const uint8_t* left, const uint8_t* right, int W, int H, int D, int P1, int P2,
+                                  int n_paths, uint8_t* disp_out, void* cuda_stream) {
+    const Problem p{W, H, D, P1, P2, n_paths};
+    if (!left || !right || !disp_out) return fail(nullptr, SGM_EINVAL, "null image or output pointer");
+    std::string why;
+    if (!valid_problem(p, &why)) return fail(nullptr, SGM_EINVAL, "%s", why.c_str());
+    if (!is_device_ptr(left) || !is_device_ptr(right) || !is_device_ptr(disp_out))
+        return fail(nullptr, SGM_EINVAL, "sgm_compute_static takes device pointers only");
+    const size_t need = layout_for(W, H, D, n_paths).total;
+    if (need > kStaticScratchBytes)
+        return fail(nullptr, SGM_EINVAL,
+                    "%dx%d D=%d with %d paths needs %zu bytes of scratch; the static scratch holds %zu bytes", W, H, D,
+                    n_paths, need, kStaticScratchBytes);
+    uint8_t* scratch = nullptr;
+    cudaError_t e = static_scratch_for_current_device(&scratch);
+    if (e != cudaSuccess) return fail(nullptr, SGM_ECUDA, "static scratch set-up: %s", cudaGetErrorString(e));
+    e = enqueue_path_static(p, scratch, left, right, disp_out, static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return fail(nullptr, SGM_ECUDA, "sgm_compute_static: %s", cudaGetErrorString(e));
+    return SGM_OK;
+}

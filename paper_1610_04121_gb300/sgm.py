@@ -64,6 +64,7 @@ _sig("sgm_kernel_launches", ctypes.c_uint64, [_vp])
 _sig("sgm_stage_times", _i, [_vp, ctypes.POINTER(ctypes.c_float), _i])
 _sig("sgm_stage_name", ctypes.c_char_p, [_i, _i])
 _sig("sgm_version", ctypes.c_char_p, [])
+_sig("sgm_compute_static", _i, [_vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _vp])
 
 
 class SgmError(RuntimeError):
@@ -164,6 +165,12 @@ def sgm_stage_times(ctx) -> dict:
         raise SgmError(n, last_error(ctx))
     npaths = 8 if n == 7 else 4
     return {_lib.sgm_stage_name(npaths, i).decode(): float(buf[i]) for i in range(n)}
+
+
+def sgm_compute_static(left, right, W, H, D, P1, P2, n_paths, disp_out, stream=None) -> None:
+    """Allocation-free path on device buffers; enqueued on `stream` (not waited for)."""
+    handle = getattr(stream, "cuda_stream", stream)
+    _check(None, _lib.sgm_compute_static(addr(left), addr(right), W, H, D, P1, P2, n_paths, addr(disp_out), handle))
 
 
 def sgm_kernel_launches(ctx) -> int:
