@@ -40,6 +40,9 @@ SM_MAX_MHZ_GB300 = 2070.0
 # minimum.  Packed u16x2 arithmetic does two of them per lane instruction.
 OPS_PER_DE_PATH = 8
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) per launch of a kernel, from the ncu capture summarised
+# under profiles/ (None once the kernel has changed since the capture)
+MEASURED_TRAFFIC = {}
 
 
 def parse():
@@ -166,6 +169,22 @@ def run_reference(args, w, ws, rank):
     return 0
 
 
+def max_over_ranks(x: float, pg, device=None) -> float:
+    """The maximum of x over all ranks (x itself without a process group)."""
+    if pg is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mdes(world_size: int, steps: int, de_per_step: int, max_ms: float) -> float:
+    """Whole-job MDE/s: every rank ran `steps` pairs; time = slowest rank."""
+    return world_size * steps * de_per_step / (max_ms / 1e3) / 1e6
+
+
 def workload_config(w):
     return {"workload": w.name, "W": w.spec.W, "H": w.spec.H, "D": w.spec.D, "P1": w.P1, "P2": w.P2,
             "n_paths": w.n_paths, "pairs_per_step": 1}
@@ -230,38 +249,31 @@ def main():
             pg.barrier()
     launches = ctx.launches - launches0
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    total_ms = sum(step_ms)
-    if pg:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), pg, dev)
     ms_per_step = total_ms / args.steps
     de = W * H * D
-    value = ws * args.steps * de / (total_ms / 1e3) / 1e6
+    value = job_mdes(ws, args.steps, de, total_ms)
 
     # dominant kernel and its roofline (integer ALU: packed u16x2 lanes)
     peaks, peak_kind = load_peaks()
     clocks = clk.summary()
     mean_stage = {k: statistics.mean(v) for k, v in stage_ms.items()}
-    dom = max(mean_stage, key=mean_stage.get)
-    # path-equivalents of Eq. 3 work in each timed stage: the horizontal stage
-    # also runs the first halves of the vertical-type pairs beside it
-    n_vert = 3 if w.n_paths == 8 else (1 if w.n_paths == 4 else 1)
-    path_eq = {"sweep_h": (2 + n_vert) if w.n_paths >= 4 else 1,
-               "sweep_v": 1, "sweep_diag+": 1, "sweep_diag-": 1}
+    # the dominant kernel: each sweep stage is one kernel launch (the vertical
+    # first halves run on a second stream beside sweep_h, outside its events)
+    kernel_stages = {"sweep_h": 2, "sweep_v": 1, "sweep_diag+": 1, "sweep_diag-": 1}
     if w.n_paths == 2:
-        path_eq["sweep_v"] = 1
-    roofline = None
-    if dom in path_eq:
-        extra = 3 if dom == "sweep_v" else 1  # sums (+ winner-take-all)
-        ops = de * (OPS_PER_DE_PATH * path_eq[dom] + extra)
-        sm_mhz = float(peaks.get("sm_max_mhz", SM_MAX_MHZ_GB300))
-        peak_tops = SM_COUNT_GB300 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        achieved = ops / (mean_stage[dom] / 1e3) / 1e12
-        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-                    "frac": achieved / peak_tops, "traffic": None,
-                    "peak_source": f"152 SMs x 128 lanes x 2 (u16x2) x {sm_mhz:.0f} MHz (recipe unit counts, "
-                                   f"max clock)", "ops_per_launch": ops}
+        kernel_stages = {"sweep_h": 1, "sweep_v": 1}
+    dom = max((k for k in mean_stage if k in kernel_stages), key=mean_stage.get)
+    extra = 3 if dom == "sweep_v" else 1  # adds of the sums (+ winner-take-all)
+    ops = de * (OPS_PER_DE_PATH * kernel_stages[dom] + extra)
+    sm_mhz = float(peaks.get("sm_max_mhz", SM_MAX_MHZ_GB300))
+    peak_tops = SM_COUNT_GB300 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = ops / (mean_stage[dom] / 1e3) / 1e12
+    traffic = MEASURED_TRAFFIC.get((w.name, dom))
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                "frac": achieved / peak_tops, "traffic": traffic,
+                "peak_source": f"152 SMs x 128 lanes x 2 (u16x2) x {sm_mhz:.0f} MHz (recipe unit counts, max clock)",
+                "ops_per_launch": ops}
     frame_bytes = 2 * W * H + W * H + 4 * de
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     frame_gbs = frame_bytes / (ms_per_step / 1e3) / 1e9
@@ -282,12 +294,8 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             sgm.sgm_compute(ctx2.handle, Lh, Rh, W, H, D, w.P1, w.P2, w.n_paths, Oh)
-        dt = time.perf_counter() - t0
-        if pg:
-            t = torch.tensor([dt], device=dev, dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": ws * args.e2e_steps * de / dt / 1e6, "unit": "MDE/s", "h2d_bytes_per_step": 2 * W * H,
+        dt = max_over_ranks(time.perf_counter() - t0, pg, dev)
+        e2e = {"value": job_mdes(ws, args.e2e_steps, de, dt * 1e3), "unit": "MDE/s", "h2d_bytes_per_step": 2 * W * H,
                "d2h_bytes_per_step": W * H, "ms_per_step": dt / args.e2e_steps * 1e3, "api": "sgm_compute"}
         ctx2.close()
 

@@ -127,7 +127,7 @@ struct sgm_ctx {
     std::string err;
     std::atomic<uint64_t> launches{0};
     bool stage_timing = false;
-    cudaEvent_t stage_ev[8] = {};
+    cudaEvent_t stage_ev[10] = {};
     int last_stages = 0;
 
     // served requests
@@ -222,9 +222,10 @@ static bool is_device_ptr(const void* p) {
 
 static int launches_per_path(const Problem& p) { return p.n_paths == 8 ? 10 : (p.n_paths == 4 ? 6 : 5); }
 
-// Timed stages: census, cost, sweep_h (with the vertical first halves beside
-// it), [sweep_diag+, sweep_diag-,] sweep_v, median.
-static int stages_per_path(const Problem& p) { return p.n_paths == 8 ? 7 : 5; }
+// Timed stages: census, cost, sweep_h (the vertical first halves run beside
+// it), v_first_tail (waiting for them after the horizontal pair ends),
+// [sweep_diag+, sweep_diag-,] sweep_v, median; 2-path mode has no tail stage.
+static int stages_per_path(const Problem& p) { return p.n_paths == 8 ? 8 : (p.n_paths == 4 ? 6 : 5); }
 
 // Bytes of one [H][W][D] u8 scratch cube of path costs.
 static size_t lx_cube_bytes(const Problem& p) {
@@ -298,8 +299,9 @@ static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, 
         }
         if ((e = cudaEventRecord(ss.join, ss.side)) != cudaSuccess) return e;
         if ((e = launch_sweep_h(a, s)) != cudaSuccess) return e;
+        if ((e = mark()) != cudaSuccess) return e;  // the horizontal pair alone
         if ((e = cudaStreamWaitEvent(s, ss.join, 0)) != cudaSuccess) return e;
-        if ((e = mark()) != cudaSuccess) return e;
+        if ((e = mark()) != cudaSuccess) return e;  // any remainder of the first halves
         for (int v = 0; v < nv; ++v) {
             SweepArgs b = a;
             b.rx = rxs[v];
@@ -649,10 +651,13 @@ int sgm_stage_times(sgm_ctx* ctx, float* ms_out, int n) {
 }
 
 const char* sgm_stage_name(int n_paths, int i) {
-    static const char* four[] = {"census", "cost", "sweep_h", "sweep_v", "median"};
-    static const char* eight[] = {"census", "cost", "sweep_h", "sweep_diag+", "sweep_diag-", "sweep_v", "median"};
-    if (n_paths == 8) return (i >= 0 && i < 7) ? eight[i] : nullptr;
-    if (n_paths == 2 || n_paths == 4) return (i >= 0 && i < 5) ? four[i] : nullptr;
+    static const char* two[] = {"census", "cost", "sweep_h", "sweep_v", "median"};
+    static const char* four[] = {"census", "cost", "sweep_h", "v_first_tail", "sweep_v", "median"};
+    static const char* eight[] = {"census",       "cost",        "sweep_h", "v_first_tail",
+                                  "sweep_diag+", "sweep_diag-", "sweep_v", "median"};
+    if (n_paths == 8) return (i >= 0 && i < 8) ? eight[i] : nullptr;
+    if (n_paths == 4) return (i >= 0 && i < 6) ? four[i] : nullptr;
+    if (n_paths == 2) return (i >= 0 && i < 5) ? two[i] : nullptr;
     return nullptr;
 }
 

@@ -159,11 +159,11 @@ def sgm_debug_stages(ctx, left, right, W, H, D, P1, P2, n_paths, Fb=None, Fm=Non
 
 def sgm_stage_times(ctx) -> dict:
     """Per-kernel device milliseconds of the last enqueued path, by stage name."""
-    buf = (ctypes.c_float * 8)()
-    n = _lib.sgm_stage_times(ctx, buf, 8)
+    buf = (ctypes.c_float * 10)()
+    n = _lib.sgm_stage_times(ctx, buf, 10)
     if n < 0:
         raise SgmError(n, last_error(ctx))
-    npaths = 8 if n == 7 else 4
+    npaths = {8: 8, 6: 4, 5: 2}[n]
     return {_lib.sgm_stage_name(npaths, i).decode(): float(buf[i]) for i in range(n)}
 
 
