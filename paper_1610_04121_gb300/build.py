@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB_NAME = "libsgm_gb300.so"
 LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
-SOURCES = ["sgm_stages.cu", "sgm_sweeps.cu", "sgm_api.cu"]
+SOURCES = ["sgm_stages.cu", "sgm_sweeps.cu", "sgm_api.cu"] + [f"sgm_sweeps_k{k}.cu" for k in range(1, 9)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -66,7 +66,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    workers = max(1, min(len(SOURCES), os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
         results = list(ex.map(compile_one, SOURCES))
     if verbose or ptxas_info:
         for _, err in results:

@@ -1,395 +1,20 @@
-// Path aggregation (Eq. 3), the sum S and the winner-take-all disparity
-// (Eq. 4) of the SGM path in arXiv 1610.04121, for sm_103a.
-//
-// Parallel scheme (Section 3.2, with the paper's CTA-to-warp conversion taken
-// one step further): one warp carries the two opposite paths of one row or one
-// column, 16 lanes each, disparities packed two per 32-bit register.  The two
-// paths meet in the middle: each sweeps its first half of the line storing
-// L_r (u8) in a scratch cube, and in its second half adds the other path's
-// stored L_r to its own.  The exchange between the two halves of the line is
-// warp-local, so no block barrier is involved.
-//
-// Each half-warp streams its inputs through a private shared-memory ring
-// filled by cp.async a few chunks ahead, keeps its step loop on shared memory
-// only, and writes each chunk's outputs back with 16-byte stores.
-//
-//   sweep_h : left-to-right with right-to-left, one row per warp;
-//             writes S = L_LR + L_RL (packed u16x2).
-//   sweep_v : top-to-bottom with bottom-to-top along columns (RX = 0) or along
-//             the wrapped diagonals of Section 3.2 (RX = +1 / -1); either adds
-//             its pair sum into S or, for the last axis, finishes with Eq. 4.
-#include "sgm_device.cuh"
-#include "sgm_internal.h"
+// Dispatch of the aggregation sweeps (Eq. 3, Eq. 4) by disparity count; the
+// kernels themselves are in sgm_sweeps.cuh, instantiated per K in
+// sgm_sweeps_k<K>.cu so that the translation units compile in parallel.
+#include "sgm_sweeps.cuh"
 
 namespace sgm {
 
-constexpr int kWarpsPerBlock = 4;
-
-// Shared-memory staging of one half-warp (one path) with K words per lane.
-template <int K>
-struct Stage {
-    static constexpr int D = 32 * K;
-    static constexpr int CH = (K <= 2) ? 16 : (K <= 4 ? 8 : 4);  // pixels per chunk
-    static constexpr int NSLOT = 3;                              // chunks in flight + 1
-    static constexpr int MC_RING = NSLOT * CH * D;
-    static constexpr int LO_RING = NSLOT * CH * D;
-    static constexpr int S_RING = NSLOT * CH * 2 * D;
-    static constexpr int OUT = CH * 2 * D;
-    static constexpr int BYTES = MC_RING + LO_RING + S_RING + OUT;
-    static constexpr int BLOCK_BYTES = 2 * kWarpsPerBlock * BYTES;
-};
-
-enum WalkMode {
-    kStoreL = 0,    // phase 1 of a pair: store L_r
-    kSumH = 1,      // phase 2 of the horizontal pair: S = L + stored L
-    kAcc = 2,       // phase 2 of a diagonal pair: S += L + stored L
-    kWta2 = 3,      // phase 2 of the vertical pair: raw = argmin_d (S + L + stored L)
-    kSingleH = 4,   // 2-path mode, left-to-right: S = L
-    kSingleWta = 5  // 2-path mode, top-to-bottom: raw = argmin_d (S + L)
-};
-
-// Pixels of a row walk: x = x0 + dx * i.
-struct RowGeo {
-    size_t rowbase;
-    int x0, dx;
-    static constexpr bool kResets = false;
-    __device__ __forceinline__ void origin(int i0, int& xc, int& yc) const {
-        xc = x0 + dx * i0;
-        yc = 0;
-    }
-    __device__ __forceinline__ size_t pix(int xc, int /*yc*/, int k) const {
-        return rowbase + static_cast<size_t>(xc + dx * k);
-    }
-};
-
-// Pixels of a column (RX = 0) or wrapped-diagonal (RX = +1/-1) walk:
-// y = y0 + dy * i, x = (c + RX * y) mod W.
-template <int RX>
-struct ColGeo {
-    int W, H, c, y0, dy;
-    static constexpr bool kResets = RX != 0;
-    __device__ __forceinline__ int x_at(int y) const {
-        if constexpr (RX == 0) {
-            return c;
-        } else {
-            int v = (c + RX * y) % W;
-            return v < 0 ? v + W : v;
-        }
-    }
-    __device__ __forceinline__ void origin(int i0, int& xc, int& yc) const {
-        yc = y0 + dy * i0;
-        xc = x_at(yc);
-    }
-    __device__ __forceinline__ size_t pix(int xc, int yc, int k) const {
-        int x = xc;
-        if constexpr (RX != 0) {
-            x = xc + RX * dy * k;
-            if (x >= W) x -= W;
-            if (x < 0) x += W;
-            if (x >= W || x < 0) {  // only when W is smaller than a chunk
-                x %= W;
-                if (x < 0) x += W;
-            }
-        }
-        return static_cast<size_t>(yc + dy * k) * W + x;
-    }
-    // x of the next pixel of the walk
-    __device__ __forceinline__ int step_x(int x) const {
-        x += RX * dy;
-        return x >= W ? x - W : (x < 0 ? x + W : x);
-    }
-    // the previous pixel of the path at (x, y) lies outside the image
-    __device__ __forceinline__ bool starts(int y, int x) const {
-        if (dy > 0) return y == 0 || (RX == 1 && x == 0) || (RX == -1 && x == W - 1);
-        return y == H - 1 || (RX == 1 && x == W - 1) || (RX == -1 && x == 0);
-    }
-};
-
-// One phase of both half-warp paths.  g / n_own: this lane's half; n_min /
-// n_max: the shorter and the longer of the two halves' step counts.
-template <int K, int MODE, class Geo>
-__device__ __forceinline__ void walk(Chain2<K>& ch, const Geo& g, int n_own, int n_min, int n_max, const SweepArgs& a,
-                                     uint8_t* ws, int hl) {
-    using St = Stage<K>;
-    constexpr int D = St::D, CH = St::CH, NS = St::NSLOT;
-    constexpr bool IN_LO = MODE == kSumH || MODE == kAcc || MODE == kWta2;
-    constexpr bool IN_S = MODE == kAcc || MODE == kWta2 || MODE == kSingleWta;
-    constexpr bool OUT_LX = MODE == kStoreL;
-    constexpr bool OUT_S = MODE == kSumH || MODE == kAcc || MODE == kSingleH;
-    constexpr bool WTA = MODE == kWta2 || MODE == kSingleWta;
-    constexpr int PM = D / 16;      // 16-byte pieces per pixel of u8 pairs
-    constexpr int PS = 2 * D / 16;  // 16-byte pieces per pixel of packed sums
-    uint8_t* mc_ring = ws;
-    uint8_t* lo_ring = mc_ring + St::MC_RING;
-    uint8_t* s_ring = lo_ring + St::LO_RING;
-    uint8_t* out = s_ring + St::S_RING;
-    const uint8_t* Sb = reinterpret_cast<const uint8_t*>(a.S);
-    const int nch = (n_max + CH - 1) / CH;
-
-    uint32_t dconst[K];
-    if constexpr (WTA) wta_consts<K>(hl, D, dconst);
-
-    auto issue = [&](int c) {
-        if (c < nch) {
-            const int i0 = c * CH, np = max(0, min(CH, n_own - i0)), slot = c % NS;
-            int xc = 0, yc = 0;
-            if (np > 0) g.origin(i0, xc, yc);
-            for (int q = hl; q < np * PM; q += 16) {
-                const int pi = q / PM, off = (q % PM) * 16;
-                const size_t p = g.pix(xc, yc, pi);
-                cp16(mc_ring + (slot * CH + pi) * D + off, a.MC + p * D + off);
-                if constexpr (IN_LO) cp16(lo_ring + (slot * CH + pi) * D + off, a.Lx + p * D + off);
-            }
-            if constexpr (IN_S) {
-                for (int q = hl; q < np * PS; q += 16) {
-                    const int pi = q / PS, off = (q % PS) * 16;
-                    const size_t p = g.pix(xc, yc, pi);
-                    cp16(s_ring + (slot * CH + pi) * 2 * D + off, Sb + p * 2 * D + off);
-                }
-            }
-        }
-        cp_commit();
-    };
-
-    int y_body = 0, x_body = 0;
-    if constexpr (Geo::kResets) g.origin(0, x_body, y_body);
-
-    // one step at chunk position pi; lane pi of each half keeps that step's disparity key
-    auto body = [&](int pi, int slot, int xc, int yc, bool active, uint32_t& dkeep) {
-        if constexpr (Geo::kResets) {
-            if (g.starts(y_body, x_body)) ch.reset();
-            y_body += g.dy;
-            x_body = g.step_x(x_body);
-        }
-        uint32_t mc[K], L[K];
-        unpack_pairs<K>(ld_pairs<K>(mc_ring + (slot * CH + pi) * D + hl * 2 * K), mc);
-        ch.step(mc, a.P1x2, a.P2x2, L);
-        if constexpr (OUT_LX) {
-            st_pairs<K>(out + pi * D + hl * 2 * K, pack_pairs<K>(L));
-        } else {
-            uint32_t s[K];
-#pragma unroll
-            for (int j = 0; j < K; ++j) s[j] = L[j];
-            if constexpr (IN_LO) {
-                uint32_t lo[K];
-                unpack_pairs<K>(ld_pairs<K>(lo_ring + (slot * CH + pi) * D + hl * 2 * K), lo);
-#pragma unroll
-                for (int j = 0; j < K; ++j) s[j] += lo[j];
-            }
-            if constexpr (IN_S) {
-                uint32_t t[K];
-                ld_words<K>(reinterpret_cast<const uint32_t*>(s_ring + (slot * CH + pi) * 2 * D) + hl * K, t);
-#pragma unroll
-                for (int j = 0; j < K; ++j) s[j] += t[j];
-            }
-            if constexpr (OUT_S) st_words<K>(reinterpret_cast<uint32_t*>(out + pi * 2 * D) + hl * K, s);
-            if constexpr (WTA) {
-                const uint32_t key = ch.half_min(wta_key<K>(s, dconst));
-                dkeep = (hl == pi) ? key : dkeep;
-                if (a.Sdbg && active) {  // debug: natural-order S
-                    const size_t p = g.pix(xc, yc, pi);
-#pragma unroll
-                    for (int j = 0; j < K; ++j) {
-                        const int i = hl * K + j;
-                        a.Sdbg[p * D + i] = static_cast<uint16_t>(s[j] & 0xffffu);
-                        a.Sdbg[p * D + i + D / 2] = static_cast<uint16_t>(s[j] >> 16);
-                    }
-                }
-            }
-        }
-    };
-
-    for (int c = 0; c < NS - 1; ++c) issue(c);
-    for (int c = 0; c < nch; ++c) {
-        issue(c + NS - 1);
-        cp_wait<NS - 1>();
-        __syncwarp();
-        const int i0 = c * CH, np = max(0, min(CH, n_own - i0)), slot = c % NS;
-        int xc = 0, yc = 0;
-        if (np > 0) g.origin(i0, xc, yc);
-        uint32_t dkeep = 0;
-        if (n_min - i0 >= CH) {
-#pragma unroll
-            for (int pi = 0; pi < CH; ++pi) body(pi, slot, xc, yc, true, dkeep);
-        } else {
-            // last chunk: a half with fewer steps keeps its state through the extra steps
-#pragma unroll
-            for (int pi = 0; pi < CH; ++pi) {
-                if (i0 + pi < n_max) {
-                    const Chain2<K> saved = ch;
-                    const int yb = y_body, xb = x_body;
-                    body(pi, slot, xc, yc, pi < np, dkeep);
-                    if (pi >= np) {
-                        ch = saved;
-                        y_body = yb;
-                        x_body = xb;
-                    }
-                }
-            }
-        }
-        __syncwarp();
-        if constexpr (WTA) {
-            if (hl < np) a.raw[g.pix(xc, yc, hl)] = static_cast<uint8_t>(dkeep & 0xffu);
-        }
-        if constexpr (OUT_LX || OUT_S) {
-            constexpr int P = OUT_LX ? PM : PS;
-            constexpr int BPP = OUT_LX ? D : 2 * D;  // bytes per pixel
-            uint8_t* dst = OUT_LX ? a.Lx : reinterpret_cast<uint8_t*>(a.S);
-            for (int q = hl; q < np * P; q += 16) {
-                const int pi = q / P, off = (q % P) * 16;
-                const size_t p = g.pix(xc, yc, pi);
-                *reinterpret_cast<uint4*>(dst + p * BPP + off) = *reinterpret_cast<const uint4*>(out + pi * BPP + off);
-            }
-            __syncwarp();
-        }
-    }
-    cp_wait<0>();
-}
-
-// ---------------------------------------------------------------------------
-// Horizontal axis: one row per warp, lanes 0-15 walk left to right, lanes
-// 16-31 right to left.  Phase 1: LR covers x < W/2, RL covers x >= W/2, both
-// storing L in Lx.  Phase 2: each covers the other half and writes
-// S = own L + stored L.  Without `pair` (2-path mode) LR covers the whole row
-// and writes S = L_LR.
-// ---------------------------------------------------------------------------
-template <int K>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_h_kernel(SweepArgs a) {
-    extern __shared__ __align__(16) uint8_t smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, hl = lane & 15;
-    const bool in_b = lane >= 16;
-    const int y = blockIdx.x * kWarpsPerBlock + warp;
-    if (y >= a.H) return;  // whole warp: every exchange below is warp-local
-    uint8_t* ws = smem + (2 * warp + (in_b ? 1 : 0)) * Stage<K>::BYTES;
-    const int W = a.W;
-    const size_t rowbase = static_cast<size_t>(y) * W;
-    Chain2<K> ch;
-    ch.init(lane);
-    if (!a.pair) {
-        const RowGeo g{rowbase, 0, 1};
-        walk<K, kSingleH>(ch, g, in_b ? 0 : W, 0, W, a, ws, hl);
-        return;
-    }
-    const int Wm = W / 2;
-    {
-        const RowGeo g = in_b ? RowGeo{rowbase, W - 1, -1} : RowGeo{rowbase, 0, 1};
-        const int nA = Wm, nB = W - Wm;
-        walk<K, kStoreL>(ch, g, in_b ? nB : nA, min(nA, nB), max(nA, nB), a, ws, hl);
-    }
-    __threadfence_block();  // this half's L stores before the other half reads them
-    __syncwarp();
-    {
-        const RowGeo g = in_b ? RowGeo{rowbase, Wm - 1, -1} : RowGeo{rowbase, Wm, 1};
-        const int nA = W - Wm, nB = Wm;
-        walk<K, kSumH>(ch, g, in_b ? nB : nA, min(nA, nB), max(nA, nB), a, ws, hl);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Vertical-type axis: one chain per warp, lanes 0-15 walk down (rows 0 ..
-// H-1), lanes 16-31 up.  Chain c visits pixel x(y) = (c + RX*y) mod W in row y:
-// a column for RX = 0, and for RX = +1/-1 a diagonal that wraps to the other
-// border, restarting its path there (Section 3.2).  Phase 1: down covers
-// y < H/2, up covers y >= H/2, storing L.  Phase 2: each covers the other half
-// and combines its L with the stored L and S: S += both (wta = 0) or
-// raw = argmin_d (S + both) (wta = 1).  Without `pair` the downward half covers
-// all rows (2-path mode, wta = 1).
-// ---------------------------------------------------------------------------
-template <int K, int RX>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_v_kernel(SweepArgs a) {
-    extern __shared__ __align__(16) uint8_t smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, hl = lane & 15;
-    const bool in_b = lane >= 16;
-    const int c = blockIdx.x * kWarpsPerBlock + warp;
-    if (c >= a.W) return;  // whole warp
-    uint8_t* ws = smem + (2 * warp + (in_b ? 1 : 0)) * Stage<K>::BYTES;
-    const int W = a.W, H = a.H;
-    Chain2<K> ch;
-    ch.init(lane);
-    if (!a.pair) {
-        const ColGeo<RX> g{W, H, c, 0, 1};
-        walk<K, kSingleWta>(ch, g, in_b ? 0 : H, 0, H, a, ws, hl);
-        return;
-    }
-    const int Hm = H / 2;
-    // saved path state of this lane: K words, the two neighbour words and m
-    uint32_t* st = a.state + (static_cast<size_t>(c) * 32 + lane) * (K + 3);
-    if (a.phase != 2) {
-        const ColGeo<RX> g = in_b ? ColGeo<RX>{W, H, c, H - 1, -1} : ColGeo<RX>{W, H, c, 0, 1};
-        const int nA = Hm, nB = H - Hm;
-        walk<K, kStoreL>(ch, g, in_b ? nB : nA, min(nA, nB), max(nA, nB), a, ws, hl);
-    }
-    if (a.phase == 1) {
-#pragma unroll
-        for (int j = 0; j < K; ++j) st[j] = ch.w[j];
-        st[K] = ch.up;
-        st[K + 1] = ch.dn;
-        st[K + 2] = ch.mpx2;
-        return;
-    }
-    if (a.phase == 2) {
-#pragma unroll
-        for (int j = 0; j < K; ++j) ch.w[j] = st[j];
-        ch.up = st[K];
-        ch.dn = st[K + 1];
-        ch.mpx2 = st[K + 2];
-    }
-    __threadfence_block();
-    __syncwarp();
-    {
-        const ColGeo<RX> g = in_b ? ColGeo<RX>{W, H, c, Hm - 1, -1} : ColGeo<RX>{W, H, c, Hm, 1};
-        const int nA = H - Hm, nB = Hm;
-        if (a.wta)
-            walk<K, kWta2>(ch, g, in_b ? nB : nA, min(nA, nB), max(nA, nB), a, ws, hl);
-        else
-            walk<K, kAcc>(ch, g, in_b ? nB : nA, min(nA, nB), max(nA, nB), a, ws, hl);
-    }
-}
-
-template <int K>
-static cudaError_t set_attrs_t() {
-    constexpr int smem = Stage<K>::BLOCK_BYTES;
-    cudaError_t e = cudaFuncSetAttribute(sweep_h_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sweep_v_kernel<K, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sweep_v_kernel<K, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sweep_v_kernel<K, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    return e;
-}
-
 cudaError_t init_kernel_attributes() {
-    cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = set_attrs_t<1>();
-    if (e == cudaSuccess) e = set_attrs_t<2>();
-    if (e == cudaSuccess) e = set_attrs_t<3>();
-    if (e == cudaSuccess) e = set_attrs_t<4>();
-    if (e == cudaSuccess) e = set_attrs_t<5>();
-    if (e == cudaSuccess) e = set_attrs_t<6>();
-    if (e == cudaSuccess) e = set_attrs_t<7>();
-    if (e == cudaSuccess) e = set_attrs_t<8>();
+    cudaError_t e = sweep_set_attrs<1>();
+    if (e == cudaSuccess) e = sweep_set_attrs<2>();
+    if (e == cudaSuccess) e = sweep_set_attrs<3>();
+    if (e == cudaSuccess) e = sweep_set_attrs<4>();
+    if (e == cudaSuccess) e = sweep_set_attrs<5>();
+    if (e == cudaSuccess) e = sweep_set_attrs<6>();
+    if (e == cudaSuccess) e = sweep_set_attrs<7>();
+    if (e == cudaSuccess) e = sweep_set_attrs<8>();
     return e;
-}
-
-template <int K>
-static cudaError_t launch_h_t(const SweepArgs& a, cudaStream_t stream) {
-    sweep_h_kernel<K><<<(a.H + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, Stage<K>::BLOCK_BYTES,
-                        stream>>>(a);
-    return cudaGetLastError();
-}
-
-template <int K>
-static cudaError_t launch_v_t(const SweepArgs& a, cudaStream_t stream) {
-    const dim3 grid((a.W + kWarpsPerBlock - 1) / kWarpsPerBlock), block(32 * kWarpsPerBlock);
-    const int smem = Stage<K>::BLOCK_BYTES;
-    if (a.rx == 0)
-        sweep_v_kernel<K, 0><<<grid, block, smem, stream>>>(a);
-    else if (a.rx > 0)
-        sweep_v_kernel<K, 1><<<grid, block, smem, stream>>>(a);
-    else
-        sweep_v_kernel<K, -1><<<grid, block, smem, stream>>>(a);
-    return cudaGetLastError();
 }
 
 // K = D / 32 words per lane (16 lanes per path).
@@ -406,8 +31,8 @@ static cudaError_t launch_v_t(const SweepArgs& a, cudaStream_t stream) {
         default: return cudaErrorInvalidValue; \
     }
 
-cudaError_t launch_sweep_h(const SweepArgs& a, cudaStream_t stream) { SGM_DISPATCH_K(launch_h_t, a, stream) }
+cudaError_t launch_sweep_h(const SweepArgs& a, cudaStream_t stream) { SGM_DISPATCH_K(sweep_launch_h, a, stream) }
 
-cudaError_t launch_sweep_v(const SweepArgs& a, cudaStream_t stream) { SGM_DISPATCH_K(launch_v_t, a, stream) }
+cudaError_t launch_sweep_v(const SweepArgs& a, cudaStream_t stream) { SGM_DISPATCH_K(sweep_launch_v, a, stream) }
 
 }  // namespace sgm
