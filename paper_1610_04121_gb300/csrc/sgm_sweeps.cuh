@@ -410,25 +410,26 @@ struct SweepK {
     }
 };
 
-// defined in sgm_sweeps_k<K>.cu
+// defined in sgm_sweeps_k<K>.cu; internal to the library (not part of the C ABI)
+#define SGM_INTERNAL __attribute__((visibility("hidden")))
 template <int K>
-cudaError_t sweep_set_attrs();
+SGM_INTERNAL cudaError_t sweep_set_attrs();
 template <int K>
-cudaError_t sweep_launch_h(const SweepArgs& a, cudaStream_t s);
+SGM_INTERNAL cudaError_t sweep_launch_h(const SweepArgs& a, cudaStream_t s);
 template <int K>
-cudaError_t sweep_launch_v(const SweepArgs& a, cudaStream_t s);
+SGM_INTERNAL cudaError_t sweep_launch_v(const SweepArgs& a, cudaStream_t s);
 
 #define SGM_INSTANTIATE_SWEEPS(K)                                                                           \
     template <>                                                                                             \
-    cudaError_t sweep_set_attrs<K>() {                                                                      \
+    SGM_INTERNAL cudaError_t sweep_set_attrs<K>() {                                                         \
         return SweepK<K>::set_attrs();                                                                      \
     }                                                                                                       \
     template <>                                                                                             \
-    cudaError_t sweep_launch_h<K>(const SweepArgs& a, cudaStream_t s) {                                     \
+    SGM_INTERNAL cudaError_t sweep_launch_h<K>(const SweepArgs& a, cudaStream_t s) {                        \
         return SweepK<K>::launch_h(a, s);                                                                   \
     }                                                                                                       \
     template <>                                                                                             \
-    cudaError_t sweep_launch_v<K>(const SweepArgs& a, cudaStream_t s) {                                     \
+    SGM_INTERNAL cudaError_t sweep_launch_v<K>(const SweepArgs& a, cudaStream_t s) {                        \
         return SweepK<K>::launch_v(a, s);                                                                   \
     }
 
