@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(synth.WORKLOADS) + ["batch64"])
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -190,10 +190,117 @@ def workload_config(w):
             "n_paths": w.n_paths, "pairs_per_step": 1}
 
 
+def run_batch_bench(args, ws, rank, local):
+    """64 uneven pairs per step through sgm_compute_batch, against the same
+    pairs as plain per-pair launches (sgm_compute_async, one after another)."""
+    import torch
+    from paper_1610_04121_gb300 import sgm
+
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+        pg = dist
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    recipe = synth.batch_recipe(64)
+    pairs = [synth.make_pair(w.spec, synth.BASE_SEED + 3000 + i + 7919 * rank) for i, w in enumerate(recipe)]
+    tuples, host_tuples = [], []
+    for w, p in zip(recipe, pairs):
+        W, H, D = w.spec.W, w.spec.H, w.spec.D
+        L, R = torch.from_numpy(p.left).to(dev), torch.from_numpy(p.right).to(dev)
+        O = torch.empty((H, W), dtype=torch.uint8, device=dev)
+        tuples.append((L, R, O, W, H, D, w.P1, w.P2, w.n_paths))
+        host_tuples.append((torch.from_numpy(p.left).pin_memory(), torch.from_numpy(p.right).pin_memory(),
+                            torch.empty((H, W), dtype=torch.uint8).pin_memory(), W, H, D, w.P1, w.P2, w.n_paths))
+    de = sum(t[3] * t[4] * t[5] for t in tuples)
+    stream = torch.cuda.Stream(dev)
+    ctx = sgm.Context(local)
+    sgm.sgm_set_stream(ctx.handle, stream)
+    for _ in range(max(args.warmup, 3)):
+        sgm.sgm_compute_batch(ctx.handle, tuples)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = ctx.launches
+    with ClockSampler(local) as clk:
+        for a, b in ev:
+            a.record(stream)
+            sgm.sgm_compute_batch(ctx.handle, tuples)  # inputs (~58 GB of buffers) far exceed L2
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        if pg:
+            pg.barrier()
+    launches = ctx.launches - launches0
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), pg, dev)
+    value = job_mdes(ws, args.steps, de, total_ms)
+    # the same pairs as plain per-pair launches
+    for t in tuples:  # warm-up: captures one graph per pair
+        sgm.sgm_compute_async(ctx.handle, t[0], t[1], t[3], t[4], t[5], t[6], t[7], t[8], t[2])
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for t in tuples:
+        sgm.sgm_compute_async(ctx.handle, t[0], t[1], t[3], t[4], t[5], t[6], t[7], t[8], t[2])
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_ms = max_over_ranks(a.elapsed_time(b), pg, dev)
+    plain = job_mdes(ws, 1, de, plain_ms)
+    # end to end with pinned host buffers
+    t0 = time.perf_counter()
+    sgm.sgm_compute_batch(ctx.handle, host_tuples)
+    dt = max_over_ranks(time.perf_counter() - t0, pg, dev)
+    h2d = sum(2 * t[3] * t[4] for t in host_tuples)
+    d2h = sum(t[3] * t[4] for t in host_tuples)
+    peaks, peak_kind = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    alg_bytes = sum(3 * t[3] * t[4] + 4 * t[3] * t[4] * t[5] for t in tuples)
+    gbs = alg_bytes / (total_ms / args.steps / 1e3) / 1e9
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        small = [(w, p) for w, p in zip(recipe, pairs) if w.spec.W == 320][:2]
+        t0, n_de = time.perf_counter(), 0
+        for w, p in small:
+            oracle.sgm(p.left, p.right, w.spec.D, w.P1, w.P2, w.n_paths)
+            n_de += w.spec.W * w.spec.H * w.spec.D
+        cpu = {"value": n_de / (time.perf_counter() - t0) / 1e6, "unit": "MDE/s", "cores": 1, "kind": "oracle",
+               "sample": f"the {len(small)} 320x240 pairs of the batch, single thread"}
+    if rank == 0:
+        line = {
+            "metric": "MDE/s", "value": value, "unit": "MDE/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u16", "data": "synthetic (seeded stereo_synth batch, resident in HBM)",
+            "config": {"workload": "batch64", "pairs_per_step": len(tuples), "de_per_step": de,
+                       "sizes": "320x240/640x480/1242x375/1920x1080, D 64/128/256, 4 or 8 paths",
+                       "parallelism": f"replicas x{ws}", "l2": "inputs and buffers (~58 GB) exceed L2",
+                       "plain_per_pair_mdes": plain, "batched_over_plain": value / plain},
+            "roofline": {"bound": "hbm", "kernel": "whole batch", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                         "frac": gbs / hbm, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": job_mdes(ws, 1, de, dt * 1e3), "unit": "MDE/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "api": "sgm_compute_batch"},
+            "gpu_launches": launches, "clocks": clk.summary(),
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
-    w = synth.WORKLOADS[args.workload]
     ws, rank, local = dist_env()
+    if args.workload == "batch64":
+        if args.impl == "reference":
+            return run_reference(args, synth.WORKLOADS[DEFAULT_WORKLOAD], ws, rank)
+        return run_batch_bench(args, ws, rank, local)
+    w = synth.WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w, ws, rank)
 

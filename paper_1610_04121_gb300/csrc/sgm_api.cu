@@ -390,6 +390,141 @@ static int check_args(sgm_ctx* ctx, const Problem& p, const void* left, const vo
 }
 
 // ---------------------------------------------------------------------------
+// Batched execution: pairs grouped by (D, n_paths); every stage is one launch
+// per group over a job table covering the group's pairs (up to kMaxBatch per
+// launch).  Pairs are packed into waves whose buffers fit the memory budget;
+// each pair has its own region of the arena.
+// ---------------------------------------------------------------------------
+struct BatchItem {
+    Problem p;
+    const uint8_t *left, *right;
+    uint8_t* out;
+    size_t offset;  // of the pair's region in the arena
+};
+
+static int launches_per_group(int n_paths) { return 4 + (n_paths == 8 ? 3 : 1); }
+
+// Enqueue the batched path for items[b, e) (one wave, same stream).
+static int enqueue_wave(sgm_ctx* ctx, std::vector<BatchItem>& items, size_t b, size_t e, uint8_t* arena,
+                        cudaStream_t s) {
+    // copy-in of host inputs
+    for (size_t i = b; i < e; ++i) {
+        BatchItem& it = items[i];
+        const Layout l = layout_for(it.p.W, it.p.H, it.p.D, it.p.n_paths);
+        const size_t wh = static_cast<size_t>(it.p.W) * it.p.H;
+        uint8_t* base = arena + it.offset;
+        if (!is_device_ptr(it.left)) {
+            CUDA_TRY(ctx, cudaMemcpyAsync(base + l.in_left, it.left, wh, cudaMemcpyHostToDevice, s));
+            it.left = base + l.in_left;
+        }
+        if (!is_device_ptr(it.right)) {
+            CUDA_TRY(ctx, cudaMemcpyAsync(base + l.in_right, it.right, wh, cudaMemcpyHostToDevice, s));
+            it.right = base + l.in_right;
+        }
+    }
+    // groups of equal (D, n_paths) are contiguous (items are sorted)
+    for (size_t g0 = b; g0 < e;) {
+        size_t g1 = g0;
+        while (g1 < e && g1 - g0 < static_cast<size_t>(kMaxBatch) && items[g1].p.D == items[g0].p.D &&
+               items[g1].p.n_paths == items[g0].p.n_paths)
+            ++g1;
+        const int n = static_cast<int>(g1 - g0), D = items[g0].p.D, n_paths = items[g0].p.n_paths;
+        JobTable<CensusJob> ct{};
+        JobTable<CostJob> mt{};
+        JobTable<SweepArgs> st{};
+        JobTable<MedianJob> dt{};
+        ct.n = mt.n = st.n = dt.n = n;
+        for (int k = 0; k < n; ++k) {
+            const BatchItem& it = items[g0 + k];
+            const Layout l = layout_for(it.p.W, it.p.H, it.p.D, it.p.n_paths);
+            uint8_t* base = arena + it.offset;
+            uint32_t* Fb = reinterpret_cast<uint32_t*>(base + l.Fb);
+            uint32_t* Fm = reinterpret_cast<uint32_t*>(base + l.Fm);
+            ct.job[k] = CensusJob{it.left, it.right, Fb, Fm, it.p.W, it.p.H};
+            mt.job[k] = CostJob{Fb, Fm, base + l.MC, it.p.W, it.p.H};
+            SweepArgs a{};
+            a.MC = base + l.MC;
+            a.Lx = base + l.Lx;
+            a.S = reinterpret_cast<uint32_t*>(base + l.S);
+            a.raw = base + l.raw;
+            a.W = it.p.W;
+            a.H = it.p.H;
+            a.D = it.p.D;
+            a.P1x2 = static_cast<uint32_t>(it.p.P1) * 0x10001u;
+            a.P2x2 = static_cast<uint32_t>(it.p.P2) * 0x10001u;
+            a.pair = it.p.n_paths >= 4;
+            st.job[k] = a;
+            uint8_t* dst = is_device_ptr(it.out) ? it.out : base + l.out;
+            dt.job[k] = MedianJob{base + l.raw, dst, it.p.W, it.p.H};
+        }
+        CUDA_TRY(ctx, launch_census_batch(ct, s));
+        CUDA_TRY(ctx, launch_cost_batch(mt, D, s));
+        CUDA_TRY(ctx, launch_sweep_h_batch(st, s));
+        const int vrx[3] = {1, -1, 0};
+        const int nv = n_paths == 8 ? 3 : 1;
+        for (int v = 0; v < nv; ++v) {
+            for (int k = 0; k < n; ++k) {
+                st.job[k].rx = (n_paths == 8) ? vrx[v] : 0;
+                st.job[k].wta = (st.job[k].rx == 0) ? 1 : 0;
+                st.job[k].phase = 0;
+            }
+            CUDA_TRY(ctx, launch_sweep_v_batch(st, s));
+        }
+        CUDA_TRY(ctx, launch_median_batch(dt, s));
+        ctx->launches += launches_per_group(n_paths);
+        g0 = g1;
+    }
+    // copy-out of host outputs
+    for (size_t i = b; i < e; ++i) {
+        const BatchItem& it = items[i];
+        if (!is_device_ptr(it.out)) {
+            const Layout l = layout_for(it.p.W, it.p.H, it.p.D, it.p.n_paths);
+            CUDA_TRY(ctx, cudaMemcpyAsync(it.out, arena + it.offset + l.out,
+                                          static_cast<size_t>(it.p.W) * it.p.H, cudaMemcpyDeviceToHost, s));
+        }
+    }
+    return SGM_OK;
+}
+
+// Run a batch through one arena: sort by (D, n_paths), pack waves that fit the
+// budget (the context's memory cap, else the device's free memory plus what the
+// arena already holds), grow the arena once per wave.
+static int run_batch(sgm_ctx* ctx, std::vector<BatchItem>& items, uint8_t** arena, size_t* arena_bytes,
+                     bool clear_graphs, cudaStream_t s, const StreamSet& /*ss*/) {
+    std::stable_sort(items.begin(), items.end(), [](const BatchItem& x, const BatchItem& y) {
+        return std::tie(x.p.D, x.p.n_paths) < std::tie(y.p.D, y.p.n_paths);
+    });
+    size_t free_b = 0, total_b = 0;
+    CUDA_TRY(ctx, cudaMemGetInfo(&free_b, &total_b));
+    size_t budget = (free_b + *arena_bytes) / 10 * 9;
+    if (ctx->mem_cap) {
+        const size_t other = (arena == &ctx->arena) ? ctx->serve_arena_bytes : ctx->arena_bytes;
+        budget = std::min(budget, ctx->mem_cap > other ? ctx->mem_cap - other : 0);
+    }
+    size_t b = 0;
+    while (b < items.size()) {
+        size_t e = b, total = 0;
+        while (e < items.size()) {
+            const size_t sz = layout_for(items[e].p.W, items[e].p.H, items[e].p.D, items[e].p.n_paths).total;
+            if (e > b && total + sz > budget) break;
+            items[e].offset = total;
+            total += sz;
+            ++e;
+        }
+        if (total > budget)
+            return fail(ctx, SGM_ENOMEM, "a %dx%d D=%d pair needs %zu bytes, over the memory budget of %zu", items[b].p.W,
+                        items[b].p.H, items[b].p.D, total, budget);
+        if (b > 0) CUDA_TRY(ctx, cudaStreamSynchronize(s));  // the previous wave still uses the arena
+        int rc = ensure_arena(ctx, arena, arena_bytes, total, clear_graphs);
+        if (rc != SGM_OK) return rc;
+        rc = enqueue_wave(ctx, items, b, e, *arena, s);
+        if (rc != SGM_OK) return rc;
+        b = e;
+    }
+    return SGM_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Served requests: a worker thread runs queued pairs in submission order on
 // its own stream and arena and records each ticket's status.
 // ---------------------------------------------------------------------------
@@ -532,23 +667,18 @@ int sgm_compute_async(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, i
 int sgm_compute_batch(sgm_ctx* ctx, int n, const sgm_pair* pairs) {
     if (!ctx) return fail(nullptr, SGM_EINVAL, "null context");
     if (n < 0 || (n > 0 && !pairs)) return fail(ctx, SGM_EINVAL, "bad batch (n=%d, pairs=%p)", n, (const void*)pairs);
-    size_t need = 0;
+    std::vector<BatchItem> items;
+    items.reserve(n);
     for (int i = 0; i < n; ++i) {
         const sgm_pair& q = pairs[i];
         const Problem p{q.W, q.H, q.D, q.P1, q.P2, q.n_paths};
         int rc = check_args(ctx, p, q.left, q.right, q.disp_out);
         if (rc != SGM_OK) return fail(ctx, rc, "pair %d: %s", i, ctx->err.c_str());
-        need = std::max(need, layout_for(q.W, q.H, q.D, q.n_paths).total);
+        items.push_back(BatchItem{p, q.left, q.right, q.disp_out, 0});
     }
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-    int rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, need, true);
+    int rc = run_batch(ctx, items, &ctx->arena, &ctx->arena_bytes, true, ctx->stream, ctx->main_set);
     if (rc != SGM_OK) return rc;
-    for (int i = 0; i < n; ++i) {
-        const sgm_pair& q = pairs[i];
-        const Problem p{q.W, q.H, q.D, q.P1, q.P2, q.n_paths};
-        rc = enqueue_pair(ctx, p, ctx->arena, q.left, q.right, q.disp_out, ctx->stream, false, ctx->main_set);
-        if (rc != SGM_OK) return rc;
-    }
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     return SGM_OK;
 }

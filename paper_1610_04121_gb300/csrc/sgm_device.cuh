@@ -273,6 +273,20 @@ __device__ __forceinline__ uint32_t wta_key(const uint32_t (&s)[K], const uint32
     return best;
 }
 
+// Index of the job that owns block b in a job table (start[] ascending).
+template <class Table>
+__device__ __forceinline__ int find_job(const Table& t, int b) {
+    int lo = 0, hi = t.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t.start[mid] <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
 // ---------------------------------------------------------------------------
 // cp.async staging (16-byte global -> shared copies, completed per thread by
 // wait_group; a __syncwarp then publishes the data to the whole warp).

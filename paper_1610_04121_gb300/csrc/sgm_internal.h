@@ -23,6 +23,36 @@ struct SweepArgs {
     uint32_t* state;      // path states between phases 1 and 2: [W][32 lanes][K + 3] words
 };
 
+// ---------------------------------------------------------------------------
+// Batched execution: one launch per stage covers many pairs.  A job table is
+// passed by value as the kernel parameter (up to kMaxBatch jobs); block b
+// belongs to the job p with start[p] <= b < start[p + 1].
+// ---------------------------------------------------------------------------
+constexpr int kMaxBatch = 64;
+
+struct CensusJob {
+    const uint8_t *left, *right;
+    uint32_t *Fb, *Fm;
+    int W, H;
+};
+struct CostJob {
+    const uint32_t *Fb, *Fm;
+    uint8_t* MC;
+    int W, H;
+};
+struct MedianJob {
+    const uint8_t* raw;
+    uint8_t* out;
+    int W, H;
+};
+
+template <class Job>
+struct JobTable {
+    int n;
+    int start[kMaxBatch + 1];
+    Job job[kMaxBatch];
+};
+
 // Each launcher enqueues one kernel on `stream` and returns the launch error.
 cudaError_t launch_census(const uint8_t* left, const uint8_t* right, uint32_t* Fb, uint32_t* Fm, int W, int H,
                           cudaStream_t stream);
@@ -33,6 +63,13 @@ cudaError_t launch_sweep_v(const SweepArgs& a, cudaStream_t stream);
 // Words of path state saved per vertical-type line between its two phases.
 inline size_t sweep_state_words(int W, int D) { return static_cast<size_t>(W) * 32 * (D / 32 + 3); }
 cudaError_t launch_median(const uint8_t* raw, uint8_t* disp, int W, int H, cudaStream_t stream);
+// Batched forms; every job of a cost or sweep table has the same D (and, for
+// sweeps, the same pair / rx / phase / wta settings).  `start` is filled in.
+cudaError_t launch_census_batch(JobTable<CensusJob>& t, cudaStream_t stream);
+cudaError_t launch_cost_batch(JobTable<CostJob>& t, int D, cudaStream_t stream);
+cudaError_t launch_median_batch(JobTable<MedianJob>& t, cudaStream_t stream);
+cudaError_t launch_sweep_h_batch(JobTable<SweepArgs>& t, cudaStream_t stream);
+cudaError_t launch_sweep_v_batch(JobTable<SweepArgs>& t, cudaStream_t stream);
 // Debug: paired costs -> natural order [H][W][D].
 cudaError_t launch_unpair_cost(const uint8_t* MC, uint8_t* out, int W, int H, int D, cudaStream_t stream);
 

@@ -15,13 +15,13 @@ namespace sgm {
 // ---------------------------------------------------------------------------
 constexpr int kCtW = 32, kCtH = 16;
 
-__global__ void __launch_bounds__(256) census_kernel(const uint8_t* __restrict__ left,
-                                                     const uint8_t* __restrict__ right, uint32_t* __restrict__ Fb,
-                                                     uint32_t* __restrict__ Fm, int W, int H) {
+__device__ __forceinline__ void census_body(const uint8_t* __restrict__ left, const uint8_t* __restrict__ right,
+                                            uint32_t* __restrict__ Fb, uint32_t* __restrict__ Fm, int W, int H,
+                                            int bx, int by, int bz) {
     __shared__ uint8_t tile[kCtH + 6][kCtW + 8];
-    const uint8_t* img = blockIdx.z ? right : left;
-    uint32_t* F = blockIdx.z ? Fm : Fb;
-    const int x0 = blockIdx.x * kCtW, y0 = blockIdx.y * kCtH;
+    const uint8_t* img = bz ? right : left;
+    uint32_t* F = bz ? Fm : Fb;
+    const int x0 = bx * kCtW, y0 = by * kCtH;
     const int t = threadIdx.y * 32 + threadIdx.x;
     for (int i = t; i < (kCtH + 6) * (kCtW + 8); i += 256) {
         const int ty = i / (kCtW + 8), tx = i % (kCtW + 8);
@@ -50,6 +50,28 @@ __global__ void __launch_bounds__(256) census_kernel(const uint8_t* __restrict__
     }
 }
 
+__global__ void __launch_bounds__(256) census_kernel(const uint8_t* __restrict__ left,
+                                                     const uint8_t* __restrict__ right, uint32_t* __restrict__ Fb,
+                                                     uint32_t* __restrict__ Fm, int W, int H) {
+    census_body(left, right, Fb, Fm, W, H, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+__global__ void __launch_bounds__(256) census_batch_kernel(const __grid_constant__ JobTable<CensusJob> t) {
+    const int p = find_job(t, blockIdx.x);
+    const CensusJob& j = t.job[p];
+    const int b = blockIdx.x - t.start[p];
+    const int tx = (j.W + kCtW - 1) / kCtW, ty = (j.H + kCtH - 1) / kCtH;
+    census_body(j.left, j.right, j.Fb, j.Fm, j.W, j.H, b % tx, (b / tx) % ty, b / (tx * ty));
+}
+
+cudaError_t launch_census_batch(JobTable<CensusJob>& t, cudaStream_t stream) {
+    t.start[0] = 0;
+    for (int i = 0; i < t.n; ++i)
+        t.start[i + 1] = t.start[i] + 2 * ((t.job[i].W + kCtW - 1) / kCtW) * ((t.job[i].H + kCtH - 1) / kCtH);
+    census_batch_kernel<<<t.start[t.n], dim3(32, 8), 0, stream>>>(t);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_census(const uint8_t* left, const uint8_t* right, uint32_t* Fb, uint32_t* Fm, int W, int H,
                           cudaStream_t stream) {
     dim3 grid((W + kCtW - 1) / kCtW, (H + kCtH - 1) / kCtH, 2);
@@ -68,12 +90,12 @@ cudaError_t launch_census(const uint8_t* left, const uint8_t* right, uint32_t* F
 constexpr int kMcSeg = 64;
 
 template <int D>
-__global__ void __launch_bounds__(256) cost_kernel(const uint32_t* __restrict__ Fb, const uint32_t* __restrict__ Fm,
-                                                   uint8_t* __restrict__ MC, int W) {
+__device__ __forceinline__ void cost_body(const uint32_t* __restrict__ Fb, const uint32_t* __restrict__ Fm,
+                                          uint8_t* __restrict__ MC, int W, int seg, int y) {
     __shared__ uint32_t fm[D - 1 + kMcSeg];  // match features x0-D+1 .. x0+kMcSeg-1
     __shared__ uint32_t fb[kMcSeg];
     constexpr int Q = D / 4, half = D / 2;
-    const int y = blockIdx.y, x0 = blockIdx.x * kMcSeg;
+    const int x0 = seg * kMcSeg;
     const uint32_t* fmrow = Fm + (size_t)y * W;
     for (int i = threadIdx.x; i < D - 1 + kMcSeg; i += 256) {
         const int gx = x0 - (D - 1) + i;
@@ -92,6 +114,43 @@ __global__ void __launch_bounds__(256) cost_kernel(const uint32_t* __restrict__ 
         const uint32_t c2 = __popc(b ^ f[-1]);
         const uint32_t c3 = __popc(b ^ f[-1 - half]);
         out[t] = __byte_perm(c0 | (c2 << 16), c1 | (c3 << 16), 0x6240u);  // [c0, c1, c2, c3]
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) cost_kernel(const uint32_t* __restrict__ Fb, const uint32_t* __restrict__ Fm,
+                                                   uint8_t* __restrict__ MC, int W) {
+    cost_body<D>(Fb, Fm, MC, W, blockIdx.x, blockIdx.y);
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) cost_batch_kernel(const __grid_constant__ JobTable<CostJob> t) {
+    const int p = find_job(t, blockIdx.x);
+    const CostJob& j = t.job[p];
+    const int b = blockIdx.x - t.start[p];
+    const int segs = (j.W + kMcSeg - 1) / kMcSeg;
+    cost_body<D>(j.Fb, j.Fm, j.MC, j.W, b % segs, b / segs);
+}
+
+template <int D>
+static cudaError_t launch_cost_batch_t(JobTable<CostJob>& t, cudaStream_t s) {
+    t.start[0] = 0;
+    for (int i = 0; i < t.n; ++i) t.start[i + 1] = t.start[i] + ((t.job[i].W + kMcSeg - 1) / kMcSeg) * t.job[i].H;
+    cost_batch_kernel<D><<<t.start[t.n], 256, 0, s>>>(t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cost_batch(JobTable<CostJob>& t, int D, cudaStream_t stream) {
+    switch (D) {
+        case 32: return launch_cost_batch_t<32>(t, stream);
+        case 64: return launch_cost_batch_t<64>(t, stream);
+        case 96: return launch_cost_batch_t<96>(t, stream);
+        case 128: return launch_cost_batch_t<128>(t, stream);
+        case 160: return launch_cost_batch_t<160>(t, stream);
+        case 192: return launch_cost_batch_t<192>(t, stream);
+        case 224: return launch_cost_batch_t<224>(t, stream);
+        case 256: return launch_cost_batch_t<256>(t, stream);
+        default: return cudaErrorInvalidValue;
     }
 }
 
@@ -152,10 +211,10 @@ __device__ __forceinline__ int med3(int a, int b, int c) { return max(min(a, b),
 
 // A CTA covers a 128 x 8 tile (4 pixels per thread along x) staged with its
 // one-pixel halo in shared memory.
-__global__ void __launch_bounds__(256) median_kernel(const uint8_t* __restrict__ raw, uint8_t* __restrict__ out,
-                                                     int W, int H) {
+__device__ __forceinline__ void median_body(const uint8_t* __restrict__ raw, uint8_t* __restrict__ out, int W, int H,
+                                            int bx, int by) {
     __shared__ uint8_t t[10][136];
-    const int x0 = blockIdx.x * 128, y0 = blockIdx.y * 8;
+    const int x0 = bx * 128, y0 = by * 8;
     for (int i = threadIdx.y * 32 + threadIdx.x; i < 10 * 130; i += 256) {
         const int ty = i / 130, tx = i % 130;
         const int gx = min(max(x0 - 1 + tx, 0), W - 1), gy = min(max(y0 - 1 + ty, 0), H - 1);
@@ -185,6 +244,26 @@ __global__ void __launch_bounds__(256) median_kernel(const uint8_t* __restrict__
         const int hi = min(min(c0, c1), c2);
         out[p] = static_cast<uint8_t>(med3(lo, mid, hi));
     }
+}
+
+__global__ void __launch_bounds__(256) median_kernel(const uint8_t* __restrict__ raw, uint8_t* __restrict__ out,
+                                                     int W, int H) {
+    median_body(raw, out, W, H, blockIdx.x, blockIdx.y);
+}
+
+__global__ void __launch_bounds__(256) median_batch_kernel(const __grid_constant__ JobTable<MedianJob> t) {
+    const int p = find_job(t, blockIdx.x);
+    const MedianJob& j = t.job[p];
+    const int b = blockIdx.x - t.start[p];
+    const int tx = (j.W + 127) / 128;
+    median_body(j.raw, j.out, j.W, j.H, b % tx, b / tx);
+}
+
+cudaError_t launch_median_batch(JobTable<MedianJob>& t, cudaStream_t stream) {
+    t.start[0] = 0;
+    for (int i = 0; i < t.n; ++i) t.start[i + 1] = t.start[i] + ((t.job[i].W + 127) / 128) * ((t.job[i].H + 7) / 8);
+    median_batch_kernel<<<t.start[t.n], dim3(32, 8), 0, stream>>>(t);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_median(const uint8_t* raw, uint8_t* disp, int W, int H, cudaStream_t stream) {

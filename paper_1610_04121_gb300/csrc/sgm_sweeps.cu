@@ -35,4 +35,27 @@ cudaError_t launch_sweep_h(const SweepArgs& a, cudaStream_t stream) { SGM_DISPAT
 
 cudaError_t launch_sweep_v(const SweepArgs& a, cudaStream_t stream) { SGM_DISPATCH_K(sweep_launch_v, a, stream) }
 
+#define SGM_DISPATCH_K_TABLE(FN, t, s)         \
+    switch ((t).job[0].D / 32) {               \
+        case 1: return FN<1>(t, s);            \
+        case 2: return FN<2>(t, s);            \
+        case 3: return FN<3>(t, s);            \
+        case 4: return FN<4>(t, s);            \
+        case 5: return FN<5>(t, s);            \
+        case 6: return FN<6>(t, s);            \
+        case 7: return FN<7>(t, s);            \
+        case 8: return FN<8>(t, s);            \
+        default: return cudaErrorInvalidValue; \
+    }
+
+cudaError_t launch_sweep_h_batch(JobTable<SweepArgs>& t, cudaStream_t stream) {
+    if (t.n < 1) return cudaSuccess;
+    SGM_DISPATCH_K_TABLE(sweep_launch_h_batch, t, stream)
+}
+
+cudaError_t launch_sweep_v_batch(JobTable<SweepArgs>& t, cudaStream_t stream) {
+    if (t.n < 1) return cudaSuccess;
+    SGM_DISPATCH_K_TABLE(sweep_launch_v_batch, t, stream)
+}
+
 }  // namespace sgm

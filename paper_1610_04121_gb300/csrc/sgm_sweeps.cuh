@@ -256,11 +256,11 @@ __device__ __forceinline__ void walk(Chain2<K>& ch, const Geo& g, int n_own, int
 // and writes S = L_LR.
 // ---------------------------------------------------------------------------
 template <int K, bool PAIR>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_h_kernel(SweepArgs a) {
+__device__ __forceinline__ void sweep_h_body(const SweepArgs& a, int bx) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, hl = lane & 15;
     const bool in_b = lane >= 16;
-    const int y = blockIdx.x * kWarpsPerBlock + warp;
+    const int y = bx * kWarpsPerBlock + warp;
     if (y >= a.H) return;  // whole warp: every exchange below is warp-local
     uint8_t* ws = smem + (2 * warp + (in_b ? 1 : 0)) * Stage<K>::BYTES;
     const int W = a.W;
@@ -287,6 +287,17 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_h_kernel(SweepArgs 
     }
 }
 
+template <int K, bool PAIR>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_h_kernel(SweepArgs a) {
+    sweep_h_body<K, PAIR>(a, blockIdx.x);
+}
+
+template <int K, bool PAIR>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_h_batch_kernel(const __grid_constant__ JobTable<SweepArgs> t) {
+    const int p = find_job(t, blockIdx.x);
+    sweep_h_body<K, PAIR>(t.job[p], blockIdx.x - t.start[p]);
+}
+
 // ---------------------------------------------------------------------------
 // Vertical-type axis: one chain per warp, lanes 0-15 walk down (rows 0 ..
 // H-1), lanes 16-31 up.  Chain c visits pixel x(y) = (c + RX*y) mod W in row y:
@@ -301,11 +312,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_h_kernel(SweepArgs 
 // 2 = second halves (restoring it).  WTA: the pair finishes with Eq. 4
 // instead of adding into S.  PAIR = false is the 2-path top-to-bottom sweep.
 template <int K, int RX, int PH, bool WTA, bool PAIR>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_v_kernel(SweepArgs a) {
+__device__ __forceinline__ void sweep_v_body(const SweepArgs& a, int bx) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, hl = lane & 15;
     const bool in_b = lane >= 16;
-    const int c = blockIdx.x * kWarpsPerBlock + warp;
+    const int c = bx * kWarpsPerBlock + warp;
     if (c >= a.W) return;  // whole warp
     uint8_t* ws = smem + (2 * warp + (in_b ? 1 : 0)) * Stage<K>::BYTES;
     const int W = a.W, H = a.H;
@@ -348,6 +359,18 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_v_kernel(SweepArgs 
     }
 }
 
+template <int K, int RX, int PH, bool WTA, bool PAIR>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_v_kernel(SweepArgs a) {
+    sweep_v_body<K, RX, PH, WTA, PAIR>(a, blockIdx.x);
+}
+
+// Batched form: both phases in one launch (PH = 0).
+template <int K, int RX, bool WTA, bool PAIR>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_v_batch_kernel(const __grid_constant__ JobTable<SweepArgs> t) {
+    const int p = find_job(t, blockIdx.x);
+    sweep_v_body<K, RX, 0, WTA, PAIR>(t.job[p], blockIdx.x - t.start[p]);
+}
+
 // ---------------------------------------------------------------------------
 // Per-K entry points, instantiated one K per translation unit.
 // ---------------------------------------------------------------------------
@@ -369,6 +392,12 @@ struct SweepK {
     static cudaError_t set_attrs() {
         cudaError_t e = attr(sweep_h_kernel<K, true>);
         if (e == cudaSuccess) e = attr(sweep_h_kernel<K, false>);
+        if (e == cudaSuccess) e = attr(sweep_h_batch_kernel<K, true>);
+        if (e == cudaSuccess) e = attr(sweep_h_batch_kernel<K, false>);
+        if (e == cudaSuccess) e = attr(sweep_v_batch_kernel<K, 0, true, true>);
+        if (e == cudaSuccess) e = attr(sweep_v_batch_kernel<K, 0, true, false>);
+        if (e == cudaSuccess) e = attr(sweep_v_batch_kernel<K, 1, false, true>);
+        if (e == cudaSuccess) e = attr(sweep_v_batch_kernel<K, -1, false, true>);
         if (e == cudaSuccess) e = attr(sweep_v_kernel<K, 0, 0, true, false>);
         if (e == cudaSuccess) e = attrs_rx<0, true>();
         if (e == cudaSuccess) e = attrs_rx<1, false>();
@@ -396,6 +425,34 @@ struct SweepK {
             sweep_v_kernel<K, RX, 0, WTA, true><<<grid, block, smem, s>>>(a);
     }
 
+    static cudaError_t launch_h_batch(JobTable<SweepArgs>& t, cudaStream_t s) {
+        t.start[0] = 0;
+        for (int i = 0; i < t.n; ++i) t.start[i + 1] = t.start[i] + (t.job[i].H + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        const dim3 block(32 * kWarpsPerBlock);
+        if (t.job[0].pair)
+            sweep_h_batch_kernel<K, true><<<t.start[t.n], block, Stage<K>::BLOCK_BYTES, s>>>(t);
+        else
+            sweep_h_batch_kernel<K, false><<<t.start[t.n], block, Stage<K>::BLOCK_BYTES, s>>>(t);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t launch_v_batch(JobTable<SweepArgs>& t, cudaStream_t s) {
+        t.start[0] = 0;
+        for (int i = 0; i < t.n; ++i) t.start[i + 1] = t.start[i] + (t.job[i].W + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        const dim3 grid(t.start[t.n]), block(32 * kWarpsPerBlock);
+        const int smem = Stage<K>::BLOCK_BYTES;
+        const SweepArgs& a = t.job[0];
+        if (!a.pair)
+            sweep_v_batch_kernel<K, 0, true, false><<<grid, block, smem, s>>>(t);
+        else if (a.rx == 0)
+            sweep_v_batch_kernel<K, 0, true, true><<<grid, block, smem, s>>>(t);
+        else if (a.rx > 0)
+            sweep_v_batch_kernel<K, 1, false, true><<<grid, block, smem, s>>>(t);
+        else
+            sweep_v_batch_kernel<K, -1, false, true><<<grid, block, smem, s>>>(t);
+        return cudaGetLastError();
+    }
+
     static cudaError_t launch_v(const SweepArgs& a, cudaStream_t s) {
         const dim3 grid((a.W + kWarpsPerBlock - 1) / kWarpsPerBlock), block(32 * kWarpsPerBlock);
         if (!a.pair)
@@ -418,6 +475,10 @@ template <int K>
 SGM_INTERNAL cudaError_t sweep_launch_h(const SweepArgs& a, cudaStream_t s);
 template <int K>
 SGM_INTERNAL cudaError_t sweep_launch_v(const SweepArgs& a, cudaStream_t s);
+template <int K>
+SGM_INTERNAL cudaError_t sweep_launch_h_batch(JobTable<SweepArgs>& t, cudaStream_t s);
+template <int K>
+SGM_INTERNAL cudaError_t sweep_launch_v_batch(JobTable<SweepArgs>& t, cudaStream_t s);
 
 #define SGM_INSTANTIATE_SWEEPS(K)                                                                           \
     template <>                                                                                             \
@@ -431,6 +492,14 @@ SGM_INTERNAL cudaError_t sweep_launch_v(const SweepArgs& a, cudaStream_t s);
     template <>                                                                                             \
     SGM_INTERNAL cudaError_t sweep_launch_v<K>(const SweepArgs& a, cudaStream_t s) {                        \
         return SweepK<K>::launch_v(a, s);                                                                   \
+    }                                                                                                       \
+    template <>                                                                                             \
+    SGM_INTERNAL cudaError_t sweep_launch_h_batch<K>(JobTable<SweepArgs> & t, cudaStream_t s) {             \
+        return SweepK<K>::launch_h_batch(t, s);                                                             \
+    }                                                                                                       \
+    template <>                                                                                             \
+    SGM_INTERNAL cudaError_t sweep_launch_v_batch<K>(JobTable<SweepArgs> & t, cudaStream_t s) {             \
+        return SweepK<K>::launch_v_batch(t, s);                                                             \
     }
 
 }  // namespace sgm

@@ -144,3 +144,65 @@ def test_stage_times_inside_graph_replay(sgm):
             assert (out.cpu().numpy() == oracle.sgm(p.left, p.right, 128, 7, 84, n_paths)).all()
     finally:
         c.close()
+
+
+def _mixed_batch(n, seed0):
+    import stereo_synth as synth
+
+    shapes = [(96, 64), (130, 70), (64, 64), (200, 41), (33, 90)]
+    out = []
+    for i in range(n):
+        W, H = shapes[i % len(shapes)]
+        D = [32, 64, 96, 128, 256][(i * 7) % 5]
+        npth = [2, 4, 8][(i * 5) % 3]
+        P1, P2 = [(7, 84), (10, 120), (3, 20)][i % 3]
+        p = synth.make_pair(synth.PairSpec(W, H, D, 4, 2, min(48, D - 1)), seed0 + i)
+        out.append((p, W, H, D, P1, P2, npth))
+    return out
+
+
+def test_batch_of_many_mixed_pairs_equals_oracle(sgm, ctx):
+    items = _mixed_batch(24, 500)
+    pairs, outs = [], []
+    for p, W, H, D, P1, P2, npth in items:
+        o = np.zeros((H, W), np.uint8)
+        pairs.append((p.left, p.right, o, W, H, D, P1, P2, npth))
+        outs.append(o)
+    sgm.sgm_compute_batch(ctx.handle, pairs)
+    for (p, W, H, D, P1, P2, npth), o in zip(items, outs):
+        assert (o == oracle.sgm(p.left, p.right, D, P1, P2, npth)).all(), (W, H, D, npth)
+
+
+def test_batch_with_device_pointers_and_waves(sgm):
+    import torch
+
+    items = _mixed_batch(10, 900)
+    refs = [oracle.sgm(p.left, p.right, D, P1, P2, npth) for p, W, H, D, P1, P2, npth in items]
+    # the pairs need 0.8-7.3 MiB each, 33 MiB together: a 12 MiB cap forces
+    # several waves through one arena
+    c = sgm.Context(0, mem_cap_bytes=12 << 20)
+    try:
+        pairs, outs = [], []
+        for p, W, H, D, P1, P2, npth in items:
+            L = torch.from_numpy(p.left).cuda()
+            R = torch.from_numpy(p.right).cuda()
+            o = torch.zeros((H, W), dtype=torch.uint8, device="cuda")
+            pairs.append((L, R, o, W, H, D, P1, P2, npth))
+            outs.append(o)
+        sgm.sgm_compute_batch(c.handle, pairs)
+        for o, r in zip(outs, refs):
+            assert (o.cpu().numpy() == r).all()
+    finally:
+        c.close()
+
+
+def test_batch_rejects_a_pair_over_the_cap(sgm):
+    c = sgm.Context(0, mem_cap_bytes=1 << 20)
+    try:
+        p = _pair(320, 240, 128, seed=3)
+        o = np.zeros((240, 320), np.uint8)
+        with pytest.raises(sgm.SgmError) as e:
+            sgm.sgm_compute_batch(c.handle, [(p.left, p.right, o, 320, 240, 128, 7, 84, 4)])
+        assert e.value.code == sgm.SGM_ENOMEM
+    finally:
+        c.close()
