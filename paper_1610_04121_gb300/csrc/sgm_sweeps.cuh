@@ -27,20 +27,6 @@ namespace sgm {
 
 constexpr int kWarpsPerBlock = 4;
 
-// Shared-memory staging of one half-warp (one path) with K words per lane.
-template <int K>
-struct Stage {
-    static constexpr int D = 32 * K;
-    static constexpr int CH = (K <= 2) ? 16 : (K <= 4 ? 8 : 4);  // pixels per chunk
-    static constexpr int NSLOT = 3;                              // chunks in flight + 1
-    static constexpr int MC_RING = NSLOT * CH * D;
-    static constexpr int LO_RING = NSLOT * CH * D;
-    static constexpr int S_RING = NSLOT * CH * 2 * D;
-    static constexpr int OUT = CH * 2 * D;
-    static constexpr int BYTES = MC_RING + LO_RING + S_RING + OUT;
-    static constexpr int BLOCK_BYTES = 2 * kWarpsPerBlock * BYTES;
-};
-
 enum WalkMode {
     kStoreL = 0,    // phase 1 of a pair: store L_r
     kSumH = 1,      // phase 2 of the horizontal pair: S = L + stored L
@@ -48,6 +34,43 @@ enum WalkMode {
     kWta2 = 3,      // phase 2 of the vertical pair: raw = argmin_d (S + L + stored L)
     kSingleH = 4,   // 2-path mode, left-to-right: S = L
     kSingleWta = 5  // 2-path mode, top-to-bottom: raw = argmin_d (S + L)
+};
+
+// Shared-memory staging of one half-warp (one path) with K words per lane
+// during a walk in MODE: a ring of NSLOT chunks per input stream it reads
+// (costs; stored L of the other path; sums) and one chunk of outputs.
+template <int K, int MODE>
+struct Stage {
+    static constexpr bool IN_LO = MODE == kSumH || MODE == kAcc || MODE == kWta2;
+    static constexpr bool IN_S = MODE == kAcc || MODE == kWta2 || MODE == kSingleWta;
+    static constexpr bool OUT_LX = MODE == kStoreL;
+    static constexpr bool OUT_S = MODE == kSumH || MODE == kAcc || MODE == kSingleH;
+    static constexpr bool WTA = MODE == kWta2 || MODE == kSingleWta;
+    static constexpr int D = 32 * K;
+    static constexpr int CH = (K <= 2) ? 16 : (K <= 4 ? 8 : 4);  // pixels per chunk
+    static constexpr int NSLOT = 3;                              // chunks in flight + 1
+    static constexpr int MC_RING = NSLOT * CH * D;
+    static constexpr int LO_RING = IN_LO ? NSLOT * CH * D : 0;
+    static constexpr int S_RING = IN_S ? NSLOT * CH * 2 * D : 0;
+    static constexpr int OUT = OUT_LX ? CH * D : (OUT_S ? CH * 2 * D : 0);
+    static constexpr int BYTES = MC_RING + LO_RING + S_RING + OUT;
+};
+
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
+
+// Bytes per half-warp and per block of each kernel (the largest of its walks).
+template <int K, bool PAIR>
+struct HStage {
+    static constexpr int HALF = PAIR ? cmax(Stage<K, kStoreL>::BYTES, Stage<K, kSumH>::BYTES) : Stage<K, kSingleH>::BYTES;
+    static constexpr int BLOCK = 2 * kWarpsPerBlock * HALF;
+};
+template <int K, int PH, bool WTA, bool PAIR>
+struct VStage {
+    static constexpr int SECOND = WTA ? Stage<K, kWta2>::BYTES : Stage<K, kAcc>::BYTES;
+    static constexpr int HALF = !PAIR ? Stage<K, kSingleWta>::BYTES
+                                      : (PH == 1 ? Stage<K, kStoreL>::BYTES
+                                                 : (PH == 2 ? SECOND : cmax(Stage<K, kStoreL>::BYTES, SECOND)));
+    static constexpr int BLOCK = 2 * kWarpsPerBlock * HALF;
 };
 
 // Pixels of a row walk: x = x0 + dx * i.
@@ -112,13 +135,9 @@ struct ColGeo {
 template <int K, int MODE, class Geo>
 __device__ __forceinline__ void walk(Chain2<K>& ch, const Geo& g, int n_own, int n_min, int n_max, const SweepArgs& a,
                                      uint8_t* ws, int hl) {
-    using St = Stage<K>;
+    using St = Stage<K, MODE>;
     constexpr int D = St::D, CH = St::CH, NS = St::NSLOT;
-    constexpr bool IN_LO = MODE == kSumH || MODE == kAcc || MODE == kWta2;
-    constexpr bool IN_S = MODE == kAcc || MODE == kWta2 || MODE == kSingleWta;
-    constexpr bool OUT_LX = MODE == kStoreL;
-    constexpr bool OUT_S = MODE == kSumH || MODE == kAcc || MODE == kSingleH;
-    constexpr bool WTA = MODE == kWta2 || MODE == kSingleWta;
+    constexpr bool IN_LO = St::IN_LO, IN_S = St::IN_S, OUT_LX = St::OUT_LX, OUT_S = St::OUT_S, WTA = St::WTA;
     constexpr int PM = D / 16;      // 16-byte pieces per pixel of u8 pairs
     constexpr int PS = 2 * D / 16;  // 16-byte pieces per pixel of packed sums
     uint8_t* mc_ring = ws;
@@ -262,7 +281,7 @@ __device__ __forceinline__ void sweep_h_body(const SweepArgs& a, int bx) {
     const bool in_b = lane >= 16;
     const int y = bx * kWarpsPerBlock + warp;
     if (y >= a.H) return;  // whole warp: every exchange below is warp-local
-    uint8_t* ws = smem + (2 * warp + (in_b ? 1 : 0)) * Stage<K>::BYTES;
+    uint8_t* ws = smem + (2 * warp + (in_b ? 1 : 0)) * HStage<K, PAIR>::HALF;
     const int W = a.W;
     const size_t rowbase = static_cast<size_t>(y) * W;
     Chain2<K> ch;
@@ -318,7 +337,7 @@ __device__ __forceinline__ void sweep_v_body(const SweepArgs& a, int bx) {
     const bool in_b = lane >= 16;
     const int c = bx * kWarpsPerBlock + warp;
     if (c >= a.W) return;  // whole warp
-    uint8_t* ws = smem + (2 * warp + (in_b ? 1 : 0)) * Stage<K>::BYTES;
+    uint8_t* ws = smem + (2 * warp + (in_b ? 1 : 0)) * VStage<K, PH, WTA, PAIR>::HALF;
     const int W = a.W, H = a.H;
     using G = ColGeo<RX>;
     Chain2<K> ch;
@@ -377,28 +396,26 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_v_batch_kernel(cons
 template <int K>
 struct SweepK {
     template <class Kern>
-    static cudaError_t attr(Kern kern) {
-        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage<K>::BLOCK_BYTES);
+    static cudaError_t attr(Kern kern, int bytes) {
+        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     }
 
     template <int RX, bool WTA>
     static cudaError_t attrs_rx() {
-        cudaError_t e = attr(sweep_v_kernel<K, RX, 0, WTA, true>);
-        if (e == cudaSuccess) e = attr(sweep_v_kernel<K, RX, 1, false, true>);
-        if (e == cudaSuccess) e = attr(sweep_v_kernel<K, RX, 2, WTA, true>);
+        cudaError_t e = attr(sweep_v_kernel<K, RX, 0, WTA, true>, VStage<K, 0, WTA, true>::BLOCK);
+        if (e == cudaSuccess) e = attr(sweep_v_kernel<K, RX, 1, false, true>, VStage<K, 1, false, true>::BLOCK);
+        if (e == cudaSuccess) e = attr(sweep_v_kernel<K, RX, 2, WTA, true>, VStage<K, 2, WTA, true>::BLOCK);
+        if (e == cudaSuccess) e = attr(sweep_v_batch_kernel<K, RX, WTA, true>, VStage<K, 0, WTA, true>::BLOCK);
         return e;
     }
 
     static cudaError_t set_attrs() {
-        cudaError_t e = attr(sweep_h_kernel<K, true>);
-        if (e == cudaSuccess) e = attr(sweep_h_kernel<K, false>);
-        if (e == cudaSuccess) e = attr(sweep_h_batch_kernel<K, true>);
-        if (e == cudaSuccess) e = attr(sweep_h_batch_kernel<K, false>);
-        if (e == cudaSuccess) e = attr(sweep_v_batch_kernel<K, 0, true, true>);
-        if (e == cudaSuccess) e = attr(sweep_v_batch_kernel<K, 0, true, false>);
-        if (e == cudaSuccess) e = attr(sweep_v_batch_kernel<K, 1, false, true>);
-        if (e == cudaSuccess) e = attr(sweep_v_batch_kernel<K, -1, false, true>);
-        if (e == cudaSuccess) e = attr(sweep_v_kernel<K, 0, 0, true, false>);
+        cudaError_t e = attr(sweep_h_kernel<K, true>, HStage<K, true>::BLOCK);
+        if (e == cudaSuccess) e = attr(sweep_h_kernel<K, false>, HStage<K, false>::BLOCK);
+        if (e == cudaSuccess) e = attr(sweep_h_batch_kernel<K, true>, HStage<K, true>::BLOCK);
+        if (e == cudaSuccess) e = attr(sweep_h_batch_kernel<K, false>, HStage<K, false>::BLOCK);
+        if (e == cudaSuccess) e = attr(sweep_v_kernel<K, 0, 0, true, false>, VStage<K, 0, true, false>::BLOCK);
+        if (e == cudaSuccess) e = attr(sweep_v_batch_kernel<K, 0, true, false>, VStage<K, 0, true, false>::BLOCK);
         if (e == cudaSuccess) e = attrs_rx<0, true>();
         if (e == cudaSuccess) e = attrs_rx<1, false>();
         if (e == cudaSuccess) e = attrs_rx<-1, false>();
@@ -408,21 +425,20 @@ struct SweepK {
     static cudaError_t launch_h(const SweepArgs& a, cudaStream_t s) {
         const dim3 grid((a.H + kWarpsPerBlock - 1) / kWarpsPerBlock), block(32 * kWarpsPerBlock);
         if (a.pair)
-            sweep_h_kernel<K, true><<<grid, block, Stage<K>::BLOCK_BYTES, s>>>(a);
+            sweep_h_kernel<K, true><<<grid, block, HStage<K, true>::BLOCK, s>>>(a);
         else
-            sweep_h_kernel<K, false><<<grid, block, Stage<K>::BLOCK_BYTES, s>>>(a);
+            sweep_h_kernel<K, false><<<grid, block, HStage<K, false>::BLOCK, s>>>(a);
         return cudaGetLastError();
     }
 
     template <int RX, bool WTA>
     static void launch_v_rx(const SweepArgs& a, dim3 grid, dim3 block, cudaStream_t s) {
-        const int smem = Stage<K>::BLOCK_BYTES;
         if (a.phase == 1)
-            sweep_v_kernel<K, RX, 1, false, true><<<grid, block, smem, s>>>(a);
+            sweep_v_kernel<K, RX, 1, false, true><<<grid, block, VStage<K, 1, false, true>::BLOCK, s>>>(a);
         else if (a.phase == 2)
-            sweep_v_kernel<K, RX, 2, WTA, true><<<grid, block, smem, s>>>(a);
+            sweep_v_kernel<K, RX, 2, WTA, true><<<grid, block, VStage<K, 2, WTA, true>::BLOCK, s>>>(a);
         else
-            sweep_v_kernel<K, RX, 0, WTA, true><<<grid, block, smem, s>>>(a);
+            sweep_v_kernel<K, RX, 0, WTA, true><<<grid, block, VStage<K, 0, WTA, true>::BLOCK, s>>>(a);
     }
 
     static cudaError_t launch_h_batch(JobTable<SweepArgs>& t, cudaStream_t s) {
@@ -430,9 +446,9 @@ struct SweepK {
         for (int i = 0; i < t.n; ++i) t.start[i + 1] = t.start[i] + (t.job[i].H + kWarpsPerBlock - 1) / kWarpsPerBlock;
         const dim3 block(32 * kWarpsPerBlock);
         if (t.job[0].pair)
-            sweep_h_batch_kernel<K, true><<<t.start[t.n], block, Stage<K>::BLOCK_BYTES, s>>>(t);
+            sweep_h_batch_kernel<K, true><<<t.start[t.n], block, HStage<K, true>::BLOCK, s>>>(t);
         else
-            sweep_h_batch_kernel<K, false><<<t.start[t.n], block, Stage<K>::BLOCK_BYTES, s>>>(t);
+            sweep_h_batch_kernel<K, false><<<t.start[t.n], block, HStage<K, false>::BLOCK, s>>>(t);
         return cudaGetLastError();
     }
 
@@ -440,23 +456,22 @@ struct SweepK {
         t.start[0] = 0;
         for (int i = 0; i < t.n; ++i) t.start[i + 1] = t.start[i] + (t.job[i].W + kWarpsPerBlock - 1) / kWarpsPerBlock;
         const dim3 grid(t.start[t.n]), block(32 * kWarpsPerBlock);
-        const int smem = Stage<K>::BLOCK_BYTES;
         const SweepArgs& a = t.job[0];
         if (!a.pair)
-            sweep_v_batch_kernel<K, 0, true, false><<<grid, block, smem, s>>>(t);
+            sweep_v_batch_kernel<K, 0, true, false><<<grid, block, VStage<K, 0, true, false>::BLOCK, s>>>(t);
         else if (a.rx == 0)
-            sweep_v_batch_kernel<K, 0, true, true><<<grid, block, smem, s>>>(t);
+            sweep_v_batch_kernel<K, 0, true, true><<<grid, block, VStage<K, 0, true, true>::BLOCK, s>>>(t);
         else if (a.rx > 0)
-            sweep_v_batch_kernel<K, 1, false, true><<<grid, block, smem, s>>>(t);
+            sweep_v_batch_kernel<K, 1, false, true><<<grid, block, VStage<K, 0, false, true>::BLOCK, s>>>(t);
         else
-            sweep_v_batch_kernel<K, -1, false, true><<<grid, block, smem, s>>>(t);
+            sweep_v_batch_kernel<K, -1, false, true><<<grid, block, VStage<K, 0, false, true>::BLOCK, s>>>(t);
         return cudaGetLastError();
     }
 
     static cudaError_t launch_v(const SweepArgs& a, cudaStream_t s) {
         const dim3 grid((a.W + kWarpsPerBlock - 1) / kWarpsPerBlock), block(32 * kWarpsPerBlock);
         if (!a.pair)
-            sweep_v_kernel<K, 0, 0, true, false><<<grid, block, Stage<K>::BLOCK_BYTES, s>>>(a);
+            sweep_v_kernel<K, 0, 0, true, false><<<grid, block, VStage<K, 0, true, false>::BLOCK, s>>>(a);
         else if (a.rx == 0)
             launch_v_rx<0, true>(a, grid, block, s);
         else if (a.rx > 0)
