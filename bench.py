@@ -41,6 +41,8 @@ SM_MAX_MHZ_GB300 = 2070.0
 # minimum.  Packed u16x2 arithmetic does two of them per lane instruction.
 OPS_PER_DE_PATH = 8
 L2_FLUSH_BYTES = 256 << 20
+SERVED_RATE_HZ = 2000.0
+SERVED_OUT_RING = 4  # output buffers per pool pair (a pair can be in flight more than once)
 # DRAM bytes (read + write) per launch of a kernel, from the ncu capture summarised
 # under profiles/, with the fingerprint of the kernel sources it was taken on;
 # reported as null once those sources have changed since the capture.
@@ -72,7 +74,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(synth.WORKLOADS) + ["batch64"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    choices=sorted(synth.WORKLOADS) + ["batch64", "served"])
+    ap.add_argument("--duration", type=float, default=10.0, help="served: seconds of Poisson arrivals")
+    ap.add_argument("--rate", type=float, default=SERVED_RATE_HZ, help="served: arrivals per second")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -314,12 +319,115 @@ def run_batch_bench(args, ws, rank, local):
     return 0
 
 
+def run_served_bench(args, ws, rank, local):
+    """Poisson arrivals of mixed pairs (sizes up to 1920x1080, D up to 256, 4
+    or 8 paths) through sgm_submit / sgm_poll with pinned host buffers; the
+    context batches whatever is queued and keeps two batches in flight."""
+    import threading
+
+    import torch
+    from paper_1610_04121_gb300 import sgm
+
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+        pg = dist
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    recipe = synth.batch_recipe(64, config=4)
+    pool = []
+    for i, w in enumerate(recipe):
+        p = synth.make_pair(w.spec, synth.BASE_SEED + 4000 + i + 7919 * rank)
+        W, H, D = w.spec.W, w.spec.H, w.spec.D
+        pool.append((torch.from_numpy(p.left).pin_memory(), torch.from_numpy(p.right).pin_memory(),
+                     torch.empty((SERVED_OUT_RING, H, W), dtype=torch.uint8).pin_memory(), W, H, D, w.P1, w.P2,
+                     w.n_paths))
+    arrivals = synth.poisson_arrivals(args.rate, args.duration, synth.BASE_SEED + 4 + 7919 * rank)
+    ctx = sgm.Context(local)
+
+    def submit(k, ring):
+        L, R, O, W, H, D, P1, P2, npth = pool[k]
+        return sgm.sgm_submit(ctx.handle, L, R, W, H, D, P1, P2, npth, O[ring])
+
+    # warm-up: every pool pair once (grows the slot arenas and the kernels' caches)
+    for _ in range(max(1, args.warmup // 3)):
+        for t in [submit(k, 0) for k in range(len(pool))]:
+            sgm.sgm_poll(ctx.handle, t, -1)
+    sgm.sgm_served_reset_stats(ctx.handle)
+    launches0 = ctx.launches
+    tickets = [None] * len(arrivals)
+    submitted = threading.Semaphore(0)
+
+    def producer(t0):
+        for i, ta in enumerate(arrivals):
+            delay = t0 + ta - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets[i] = submit(i % len(pool), (i // len(pool)) % SERVED_OUT_RING)
+            submitted.release()
+
+    if pg:
+        pg.barrier()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        th = threading.Thread(target=producer, args=(t0,))
+        th.start()
+        for i in range(len(arrivals)):
+            submitted.acquire()
+            sgm.sgm_poll(ctx.handle, tickets[i], -1)
+        wall = time.perf_counter() - t0
+        th.join()
+    wall = max_over_ranks(wall, pg, dev)
+    st = sgm.sgm_served_stats(ctx.handle)
+    launches = ctx.launches - launches0
+    n = len(arrivals)
+    de = sum(pool[i % len(pool)][3] * pool[i % len(pool)][4] * pool[i % len(pool)][5] for i in range(n))
+    value = job_mdes(ws, 1, de, wall * 1e3)
+    # the same pool as plain one-pair calls, one after another (the first pass
+    # sizes the arena and captures one graph per pair)
+    for timed in (False, True):
+        t1 = time.perf_counter()
+        for L, R, O, W, H, D, P1, P2, npth in pool:
+            sgm.sgm_compute(ctx.handle, L, R, W, H, D, P1, P2, npth, O[0])
+        plain_s = time.perf_counter() - t1
+    pool_de = sum(t[3] * t[4] * t[5] for t in pool)
+    plain = job_mdes(ws, 1, pool_de, max_over_ranks(plain_s, pg, dev) * 1e3)
+    h2d = sum(2 * pool[i % len(pool)][3] * pool[i % len(pool)][4] for i in range(n)) / max(n, 1)
+    if rank == 0:
+        line = {
+            "metric": "MDE/s", "value": value, "unit": "MDE/s", "n_gpus": ws, "steps": n, "warmup": args.warmup,
+            "ms_per_step": wall * 1e3 / max(n, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u16", "data": "synthetic (seeded stereo_synth pairs, pinned host buffers)",
+            "config": {"workload": "served", "arrival_rate_hz": args.rate, "duration_s": args.duration,
+                       "requests": n, "pool": "64 pairs: 320x240/640x480/1242x375/1920x1080, D 64/128/256, 4 or 8 paths",
+                       "offered_mdes": de / args.duration / 1e6, "step": "one request",
+                       "parallelism": f"replicas x{ws}", "l2": "inputs and buffers far exceed L2",
+                       "plain_per_pair_mdes": plain, "served_over_plain": value / plain if plain else None},
+            "latency_us": {"p50": st["p50_us"], "p99": st["p99_us"], "max": st["max_us"]},
+            "batching": {"batches": st["batches"], "mean_pairs_per_batch": st["mean_batch"],
+                         "max_in_flight": st["max_in_flight"]},
+            "cpu_baseline": None,
+            "e2e": {"value": value, "unit": "MDE/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d / 2,
+                    "api": "sgm_submit / sgm_poll (host buffers, copies inside)"},
+            "gpu_launches": launches, "clocks": clk.summary(),
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
-    if args.workload == "batch64":
+    if args.workload in ("batch64", "served"):
         if args.impl == "reference":
             return run_reference(args, synth.WORKLOADS[DEFAULT_WORKLOAD], ws, rank)
+        if args.workload == "served":
+            return run_served_bench(args, ws, rank, local)
         return run_batch_bench(args, ws, rank, local)
     w = synth.WORKLOADS[args.workload]
     if args.impl == "reference":

@@ -147,9 +147,13 @@ SGM_API int sgm_compute_batch(sgm_ctx *ctx, int n, const sgm_pair *pairs);
 
 /*
  * Served form: queue one pair and return a ticket at once.  A scheduler
- * thread owned by the context admits queued requests while device memory
- * (within mem_cap_bytes) allows, batches whatever is admitted into one
- * launch sequence, and keeps up to two batches in flight on the GPU.
+ * thread owned by the context admits queued requests in arrival order while
+ * device memory (within mem_cap_bytes) allows, batches whatever is admitted
+ * into one launch sequence (the batched path of sgm_compute_batch, each
+ * batch on its own stream with its own arena from a device-resident pool),
+ * and keeps up to two batches in flight on the GPU: requests that arrive
+ * while a batch runs are admitted into the next one as soon as a slot is
+ * free.  Each result is bit-identical to sgm_compute of that pair alone.
  * The caller keeps left/right/disp_out alive and unmodified until sgm_poll
  * returns something other than SGM_EAGAIN for the ticket.
  * Errors: SGM_EINVAL (bad pair or null ticket), SGM_ENOMEM (the pair alone
@@ -168,12 +172,23 @@ SGM_API int sgm_submit(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, 
 SGM_API int sgm_poll(sgm_ctx *ctx, uint64_t ticket, int64_t timeout_us);
 
 /*
- * Served-request latency statistics since the context was created:
+ * Served-request statistics since the context was created:
  * out[0] = completed requests, out[1] = p50 latency (us), out[2] = p99
- * latency (us), out[3] = max latency (us); latency = poll-visible completion
- * time minus submit time.  `n_out` must be >= 4.
+ * latency (us), out[3] = max latency (us); latency = completion of the
+ * request's batch on the GPU (its last copy) minus submit time.  `n_out`
+ * must be >= 4.  With n_out >= 8 also: out[4] = batches launched, out[5] =
+ * mean pairs per batch, out[6] = most batches in flight at once, out[7] =
+ * disparity evaluations (W*H*D) of the completed requests.
  */
 SGM_API int sgm_served_stats(sgm_ctx *ctx, double *out, int n_out);
+
+/*
+ * Start a new statistics window for sgm_served_stats (for example after a
+ * warm-up): clears the latencies, batch counts and DE total; requests in
+ * flight are counted in the new window when they complete.
+ * Errors: SGM_EINVAL (null context).
+ */
+SGM_API int sgm_served_reset_stats(sgm_ctx *ctx);
 
 /*
  * Debug form of sgm_compute for localising a mismatch stage by stage.  All

@@ -35,7 +35,10 @@ struct Layout {
 // Scratch cubes of first-half path costs: one per pair of opposite paths.
 int lx_cubes(int n_paths) { return n_paths == 8 ? 4 : (n_paths == 4 ? 2 : 1); }
 
-Layout layout_for(int W, int H, int D_int, int n_paths) {
+// Batched execution runs every sweep in one launch (no phases), so a batched
+// pair needs one path-cost cube and no phase state.
+Layout layout_for(int W, int H, int D_int, int n_paths, bool batched = false) {
+    const int cubes = batched ? 1 : lx_cubes(n_paths);
     const size_t wh = static_cast<size_t>(W) * H;
     const size_t D = static_cast<size_t>(D_int);
     Layout l{};
@@ -47,13 +50,13 @@ Layout layout_for(int W, int H, int D_int, int n_paths) {
     l.MC = o;
     o = align_up(o + wh * D);
     l.Lx = o;  // one path-cost cube per pair: horizontal + vertical-type ones
-    o = align_up(o + lx_cubes(n_paths) * align_up(wh * D));
+    o = align_up(o + cubes * align_up(wh * D));
     l.S = o;
     o = align_up(o + 2 * wh * D);
     l.raw = o;
     o = align_up(o + wh);
     l.state = o;  // path states of the three vertical-type pairs between their phases
-    o = align_up(o + (lx_cubes(n_paths) - 1) * 4 * sweep_state_words(W, static_cast<int>(D)));
+    o = align_up(o + (cubes - 1) * 4 * sweep_state_words(W, static_cast<int>(D)));
     l.in_left = o;
     o = align_up(o + wh);
     l.in_right = o;
@@ -111,6 +114,27 @@ struct Request {
     std::chrono::steady_clock::time_point t_submit;
 };
 
+// Served execution: up to kServeSlots batches in flight, each on its own
+// stream with its own arena from a device-resident pool.
+constexpr int kServeSlots = 2;
+constexpr int kServeMaxPairs = kMaxBatch;
+
+struct ServeSlot {
+    sgm_ctx* ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    uint8_t* arena = nullptr;
+    size_t arena_bytes = 0;
+    std::vector<Request> reqs;  // the batch in flight
+    // pinned host staging for pageable inputs and outputs, so that no copy
+    // blocks the scheduler; outputs are copied to the caller at retirement
+    uint8_t* pinned = nullptr;
+    size_t pinned_bytes = 0;
+    std::vector<std::tuple<uint8_t*, const uint8_t*, size_t>> out_copies;
+    bool busy = false;          // reserved by the scheduler or running
+    bool finished = false;      // set by the stream callback after the batch's last copy
+    std::chrono::steady_clock::time_point t_done;
+};
+
 }  // namespace
 
 struct sgm_ctx {
@@ -119,7 +143,6 @@ struct sgm_ctx {
     cudaStream_t stream = nullptr;
     cudaStream_t capture_stream = nullptr;
     StreamSet main_set{};   // side stream + fork/join events of the caller's thread
-    StreamSet serve_set{};  // the same for the served-request worker
     size_t mem_cap = 0;
     uint8_t* arena = nullptr;
     size_t arena_bytes = 0;
@@ -142,9 +165,12 @@ struct sgm_ctx {
     bool stop = false;
     bool worker_started = false;
     std::thread worker;
-    cudaStream_t serve_stream = nullptr;
-    uint8_t* serve_arena = nullptr;
-    size_t serve_arena_bytes = 0;
+    ServeSlot slots[kServeSlots];
+    std::atomic<size_t> serve_bytes{0};  // sum of the slots' arenas
+    cudaMemPool_t serve_pool = nullptr;
+    uint64_t batches = 0, batched_pairs = 0;
+    int in_flight = 0, max_in_flight = 0;
+    double served_de = 0.0;
 };
 
 static thread_local std::string g_noctx_err;
@@ -186,7 +212,7 @@ static int fail(sgm_ctx* ctx, int code, const char* fmt, ...) {
 
 static int ensure_arena(sgm_ctx* ctx, uint8_t** arena, size_t* bytes, size_t need, bool clear_graphs) {
     if (*bytes >= need) return SGM_OK;
-    const size_t used_elsewhere = (arena == &ctx->arena) ? ctx->serve_arena_bytes : ctx->arena_bytes;
+    const size_t used_elsewhere = ctx->serve_bytes.load();
     if (ctx->mem_cap && need + used_elsewhere > ctx->mem_cap)
         return fail(ctx, SGM_ENOMEM, "work arena of %zu bytes exceeds the context's memory cap of %zu bytes", need,
                     ctx->mem_cap);
@@ -211,13 +237,18 @@ static int ensure_arena(sgm_ctx* ctx, uint8_t** arena, size_t* bytes, size_t nee
     return SGM_OK;
 }
 
-static bool is_device_ptr(const void* p) {
+static cudaMemoryType pointer_kind(const void* p) {
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return cudaMemoryTypeUnregistered;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    return at.type;
+}
+
+static bool is_device_ptr(const void* p) {
+    const cudaMemoryType t = pointer_kind(p);
+    return t == cudaMemoryTypeDevice || t == cudaMemoryTypeManaged;
 }
 
 static int launches_per_path(const Problem& p) { return p.n_paths == 8 ? 10 : (p.n_paths == 4 ? 6 : 5); }
@@ -410,7 +441,7 @@ static int enqueue_wave(sgm_ctx* ctx, std::vector<BatchItem>& items, size_t b, s
     // copy-in of host inputs
     for (size_t i = b; i < e; ++i) {
         BatchItem& it = items[i];
-        const Layout l = layout_for(it.p.W, it.p.H, it.p.D, it.p.n_paths);
+        const Layout l = layout_for(it.p.W, it.p.H, it.p.D, it.p.n_paths, true);
         const size_t wh = static_cast<size_t>(it.p.W) * it.p.H;
         uint8_t* base = arena + it.offset;
         if (!is_device_ptr(it.left)) {
@@ -436,7 +467,7 @@ static int enqueue_wave(sgm_ctx* ctx, std::vector<BatchItem>& items, size_t b, s
         ct.n = mt.n = st.n = dt.n = n;
         for (int k = 0; k < n; ++k) {
             const BatchItem& it = items[g0 + k];
-            const Layout l = layout_for(it.p.W, it.p.H, it.p.D, it.p.n_paths);
+            const Layout l = layout_for(it.p.W, it.p.H, it.p.D, it.p.n_paths, true);
             uint8_t* base = arena + it.offset;
             uint32_t* Fb = reinterpret_cast<uint32_t*>(base + l.Fb);
             uint32_t* Fm = reinterpret_cast<uint32_t*>(base + l.Fm);
@@ -478,7 +509,7 @@ static int enqueue_wave(sgm_ctx* ctx, std::vector<BatchItem>& items, size_t b, s
     for (size_t i = b; i < e; ++i) {
         const BatchItem& it = items[i];
         if (!is_device_ptr(it.out)) {
-            const Layout l = layout_for(it.p.W, it.p.H, it.p.D, it.p.n_paths);
+            const Layout l = layout_for(it.p.W, it.p.H, it.p.D, it.p.n_paths, true);
             CUDA_TRY(ctx, cudaMemcpyAsync(it.out, arena + it.offset + l.out,
                                           static_cast<size_t>(it.p.W) * it.p.H, cudaMemcpyDeviceToHost, s));
         }
@@ -498,14 +529,14 @@ static int run_batch(sgm_ctx* ctx, std::vector<BatchItem>& items, uint8_t** aren
     CUDA_TRY(ctx, cudaMemGetInfo(&free_b, &total_b));
     size_t budget = (free_b + *arena_bytes) / 10 * 9;
     if (ctx->mem_cap) {
-        const size_t other = (arena == &ctx->arena) ? ctx->serve_arena_bytes : ctx->arena_bytes;
+        const size_t other = ctx->serve_bytes.load();
         budget = std::min(budget, ctx->mem_cap > other ? ctx->mem_cap - other : 0);
     }
     size_t b = 0;
     while (b < items.size()) {
         size_t e = b, total = 0;
         while (e < items.size()) {
-            const size_t sz = layout_for(items[e].p.W, items[e].p.H, items[e].p.D, items[e].p.n_paths).total;
+            const size_t sz = layout_for(items[e].p.W, items[e].p.H, items[e].p.D, items[e].p.n_paths, true).total;
             if (e > b && total + sz > budget) break;
             items[e].offset = total;
             total += sz;
@@ -525,43 +556,253 @@ static int run_batch(sgm_ctx* ctx, std::vector<BatchItem>& items, uint8_t** aren
 }
 
 // ---------------------------------------------------------------------------
-// Served requests: a worker thread runs queued pairs in submission order on
-// its own stream and arena and records each ticket's status.
+// Served requests (continuous batching).  A scheduler thread owned by the
+// context takes whatever is queued, in arrival order, as one batch for a free
+// slot while the batch's buffers fit that slot's memory budget, and launches
+// it through the batched path on the slot's stream; with kServeSlots slots,
+// later arrivals are admitted and run while earlier batches are still on the
+// GPU.  A stream callback marks a slot finished; the scheduler then retires
+// its tickets and reuses the slot.
 // ---------------------------------------------------------------------------
+static void CUDART_CB slot_finished(void* data) {
+    ServeSlot* sl = static_cast<ServeSlot*>(data);
+    sgm_ctx* ctx = sl->ctx;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        sl->finished = true;
+        sl->t_done = std::chrono::steady_clock::now();
+    }
+    ctx->cv_work.notify_all();
+}
+
+// Bytes a slot may hold for its next batch: the device's free memory plus the
+// slot's own arena, at most a 1/kServeSlots share of the device, and within the
+// context's memory cap after the other arenas.
+static int slot_budget(sgm_ctx* ctx, const ServeSlot& sl, size_t* budget) {
+    size_t free_b = 0, total_b = 0;
+    CUDA_TRY(ctx, cudaMemGetInfo(&free_b, &total_b));
+    size_t b = std::min((free_b + sl.arena_bytes) / 10 * 9, total_b / 10 * 9 / kServeSlots);
+    if (ctx->mem_cap) {
+        const size_t other = ctx->arena_bytes + (ctx->serve_bytes.load() - sl.arena_bytes);
+        b = std::min(b, ctx->mem_cap > other ? ctx->mem_cap - other : 0);
+    }
+    *budget = b;
+    return SGM_OK;
+}
+
+static int slot_release(sgm_ctx* ctx, ServeSlot& sl) {
+    if (!sl.arena) return SGM_OK;
+    CUDA_TRY(ctx, cudaFreeAsync(sl.arena, sl.stream));
+    ctx->serve_bytes -= sl.arena_bytes;
+    sl.arena = nullptr;
+    sl.arena_bytes = 0;
+    return SGM_OK;
+}
+
+// Grow a slot's arena (stream-ordered, from the context's device pool),
+// rounded up to a 64 MiB grain where the budget allows.
+static int slot_reserve(sgm_ctx* ctx, ServeSlot& sl, size_t need, size_t budget) {
+    if (sl.arena_bytes >= need) return SGM_OK;
+    const size_t grain = size_t(64) << 20;
+    need = std::max(need, std::min((need + grain - 1) / grain * grain, budget));
+    int rc = slot_release(ctx, sl);
+    if (rc != SGM_OK) return rc;
+    void* p = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&p, need, ctx->serve_pool, sl.stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, SGM_ENOMEM, "served batch arena of %zu bytes: %s", need, cudaGetErrorString(e));
+    }
+    sl.arena = static_cast<uint8_t*>(p);
+    sl.arena_bytes = need;
+    ctx->serve_bytes += need;
+    return SGM_OK;
+}
+
+// Enqueue one admitted batch on a slot; the callback fires after its copies.
+static int slot_launch(sgm_ctx* ctx, ServeSlot& sl, size_t budget) {
+    std::vector<BatchItem> items;
+    items.reserve(sl.reqs.size());
+    for (const Request& r : sl.reqs) items.push_back(BatchItem{r.p, r.left, r.right, r.out, 0});
+    // pageable host buffers go through the slot's pinned staging
+    auto pageable = [](const void* q) { return pointer_kind(q) == cudaMemoryTypeUnregistered; };
+    size_t host = 0;
+    for (const BatchItem& it : items) {
+        const size_t wh = align_up(static_cast<size_t>(it.p.W) * it.p.H);
+        host += (pageable(it.left) + pageable(it.right) + pageable(it.out)) * wh;
+    }
+    if (host > sl.pinned_bytes) {
+        const size_t want = std::max(host, sl.pinned_bytes / 2 * 3);
+        if (sl.pinned) CUDA_TRY(ctx, cudaFreeHost(sl.pinned));
+        sl.pinned = nullptr;
+        sl.pinned_bytes = 0;
+        void* q = nullptr;
+        CUDA_TRY(ctx, cudaMallocHost(&q, want));
+        sl.pinned = static_cast<uint8_t*>(q);
+        sl.pinned_bytes = want;
+    }
+    sl.out_copies.clear();
+    size_t off = 0;
+    for (BatchItem& it : items) {
+        const size_t wh = static_cast<size_t>(it.p.W) * it.p.H;
+        if (pageable(it.left)) {
+            std::memcpy(sl.pinned + off, it.left, wh);
+            it.left = sl.pinned + off;
+            off += align_up(wh);
+        }
+        if (pageable(it.right)) {
+            std::memcpy(sl.pinned + off, it.right, wh);
+            it.right = sl.pinned + off;
+            off += align_up(wh);
+        }
+        if (pageable(it.out)) {
+            sl.out_copies.emplace_back(it.out, sl.pinned + off, wh);
+            it.out = sl.pinned + off;
+            off += align_up(wh);
+        }
+    }
+    std::stable_sort(items.begin(), items.end(), [](const BatchItem& x, const BatchItem& y) {
+        return std::tie(x.p.D, x.p.n_paths) < std::tie(y.p.D, y.p.n_paths);
+    });
+    size_t total = 0;
+    for (BatchItem& it : items) {
+        it.offset = total;
+        total += layout_for(it.p.W, it.p.H, it.p.D, it.p.n_paths, true).total;
+    }
+    int rc = slot_reserve(ctx, sl, total, budget);
+    if (rc == SGM_OK) rc = enqueue_wave(ctx, items, 0, items.size(), sl.arena, sl.stream);
+    if (rc == SGM_OK) CUDA_TRY(ctx, cudaLaunchHostFunc(sl.stream, slot_finished, &sl));
+    return rc;
+}
+
+static void retire(sgm_ctx* ctx, const std::vector<Request>& reqs, int rc,
+                   std::chrono::steady_clock::time_point t_done) {
+    for (const Request& r : reqs) {
+        ctx->done[r.ticket] = rc;
+        if (rc == SGM_OK) {
+            ctx->latencies_us.push_back(std::chrono::duration<double, std::micro>(t_done - r.t_submit).count());
+            ctx->served_de += static_cast<double>(r.p.W) * r.p.H * r.p.D;
+        }
+        --ctx->pending;
+    }
+}
+
 static void serve_loop(sgm_ctx* ctx) {
     cudaSetDevice(ctx->device);
+    std::unique_lock<std::mutex> lk(ctx->mu);
+    auto free_slot = [&]() -> ServeSlot* {  // the idle slot with the largest arena
+        ServeSlot* best = nullptr;
+        for (auto& sl : ctx->slots)
+            if (!sl.busy && (!best || sl.arena_bytes > best->arena_bytes)) best = &sl;
+        return best;
+    };
+    auto done_slot = [&]() -> ServeSlot* {
+        for (auto& sl : ctx->slots)
+            if (sl.busy && sl.finished) return &sl;
+        return nullptr;
+    };
     for (;;) {
-        Request r;
-        {
-            std::unique_lock<std::mutex> lk(ctx->mu);
-            ctx->cv_work.wait(lk, [&] { return ctx->stop || !ctx->queue.empty(); });
-            if (ctx->queue.empty()) return;  // stop requested and nothing queued
-            r = ctx->queue.front();
+        ctx->cv_work.wait(lk, [&] {
+            return done_slot() || (ctx->stop && (!ctx->queue.empty() || ctx->in_flight == 0)) ||
+                   (!ctx->stop && !ctx->queue.empty() && free_slot());
+        });
+        if (ServeSlot* sl = done_slot()) {
+            lk.unlock();
+            cudaError_t e = cudaStreamSynchronize(sl->stream);  // the callback has run: returns at once
+            int rc = SGM_OK;
+            if (e != cudaSuccess) rc = fail(ctx, SGM_ECUDA, "served batch: %s", cudaGetErrorString(e));
+            if (rc == SGM_OK)
+                for (auto& c : sl->out_copies) std::memcpy(std::get<0>(c), std::get<1>(c), std::get<2>(c));
+            lk.lock();
+            retire(ctx, sl->reqs, rc, sl->t_done);
+            sl->reqs.clear();
+            sl->busy = sl->finished = false;
+            --ctx->in_flight;
+            ctx->cv_done.notify_all();
+            continue;
+        }
+        if (ctx->stop) {
+            if (!ctx->queue.empty()) {
+                const auto now = std::chrono::steady_clock::now();
+                std::vector<Request> cancelled(ctx->queue.begin(), ctx->queue.end());
+                ctx->queue.clear();
+                retire(ctx, cancelled, SGM_ECANCELED, now);
+                ctx->cv_done.notify_all();
+            }
+            if (ctx->in_flight == 0) return;
+            continue;
+        }
+        // admission: reserve a slot, size its budget outside the lock, then take
+        // queued requests in arrival order while they fit
+        ServeSlot* sl = free_slot();
+        sl->busy = true;
+        lk.unlock();
+        size_t budget = 0;
+        int rc = slot_budget(ctx, *sl, &budget);
+        lk.lock();
+        size_t used = 0;
+        while (rc == SGM_OK && !ctx->queue.empty() && sl->reqs.size() < static_cast<size_t>(kServeMaxPairs)) {
+            const Request& r = ctx->queue.front();
+            const size_t sz = layout_for(r.p.W, r.p.H, r.p.D, r.p.n_paths, true).total;
+            if (used + sz > budget) break;
+            used += sz;
+            sl->reqs.push_back(r);
             ctx->queue.pop_front();
         }
-        int rc;
-        if (ctx->stop) {
-            rc = SGM_ECANCELED;
-        } else {
-            const Layout l = layout_for(r.p.W, r.p.H, r.p.D, r.p.n_paths);
-            rc = ensure_arena(ctx, &ctx->serve_arena, &ctx->serve_arena_bytes, l.total, false);
-            if (rc == SGM_OK)
-                rc = enqueue_pair(ctx, r.p, ctx->serve_arena, r.left, r.right, r.out, ctx->serve_stream, false,
-                                  ctx->serve_set);
-            if (rc == SGM_OK) {
-                cudaError_t e = cudaStreamSynchronize(ctx->serve_stream);
-                if (e != cudaSuccess) rc = fail(ctx, SGM_ECUDA, "served request: %s", cudaGetErrorString(e));
+        if (rc == SGM_OK && sl->reqs.empty()) {
+            if (ctx->in_flight > 0) {
+                sl->busy = false;  // wait for a batch in flight to free memory
+                ctx->cv_work.wait(lk, [&] { return done_slot() != nullptr || ctx->stop; });
+                continue;
             }
+            // nothing runs: give the memory of the other idle arenas back and retry
+            bool released = false;
+            for (auto& o : ctx->slots) {
+                if (&o != sl && o.arena) {
+                    lk.unlock();
+                    slot_release(ctx, o);
+                    cudaStreamSynchronize(o.stream);
+                    lk.lock();
+                    released = true;
+                }
+            }
+            if (released) {
+                sl->busy = false;
+                continue;
+            }
+            // nothing runs and the oldest request alone exceeds the budget
+            std::vector<Request> one{ctx->queue.front()};
+            ctx->queue.pop_front();
+            rc = fail(ctx, SGM_ENOMEM, "served %dx%d D=%d pair exceeds the memory budget of %zu bytes", one[0].p.W,
+                      one[0].p.H, one[0].p.D, budget);
+            retire(ctx, one, rc, std::chrono::steady_clock::now());
+            sl->busy = false;
+            ctx->cv_done.notify_all();
+            continue;
         }
-        const double us =
-            std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - r.t_submit).count();
-        {
-            std::lock_guard<std::mutex> lk(ctx->mu);
-            ctx->done[r.ticket] = rc;
-            if (rc == SGM_OK) ctx->latencies_us.push_back(us);
-            --ctx->pending;
+        if (rc != SGM_OK) {  // the budget query failed: fail what is queued
+            std::vector<Request> failed(ctx->queue.begin(), ctx->queue.end());
+            ctx->queue.clear();
+            retire(ctx, failed, rc, std::chrono::steady_clock::now());
+            sl->busy = false;
+            ctx->cv_done.notify_all();
+            continue;
         }
-        ctx->cv_done.notify_all();
+        ++ctx->in_flight;
+        ctx->max_in_flight = std::max(ctx->max_in_flight, ctx->in_flight);
+        ++ctx->batches;
+        ctx->batched_pairs += sl->reqs.size();
+        lk.unlock();
+        rc = slot_launch(ctx, *sl, budget);
+        lk.lock();
+        if (rc != SGM_OK) {
+            cudaStreamSynchronize(sl->stream);
+            retire(ctx, sl->reqs, rc, std::chrono::steady_clock::now());
+            sl->reqs.clear();
+            sl->busy = sl->finished = false;
+            --ctx->in_flight;
+            ctx->cv_done.notify_all();
+        }
     }
 }
 
@@ -582,10 +823,29 @@ int sgm_create(sgm_ctx** out, int device, size_t mem_cap_bytes, unsigned flags) 
     ctx->mem_cap = mem_cap_bytes;
     if ((e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&ctx->serve_stream, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = create_stream_set(&ctx->main_set)) != cudaSuccess || (e = create_stream_set(&ctx->serve_set)) != cudaSuccess) {
+        (e = create_stream_set(&ctx->main_set)) != cudaSuccess) {
         sgm_destroy(ctx);
         return fail(nullptr, SGM_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    }
+    for (auto& sl : ctx->slots) {
+        sl.ctx = ctx;
+        if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) != cudaSuccess) {
+            sgm_destroy(ctx);
+            return fail(nullptr, SGM_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        }
+    }
+    {
+        // the served arenas come from a pool that keeps freed memory resident
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        uint64_t keep = UINT64_MAX;
+        if ((e = cudaMemPoolCreate(&ctx->serve_pool, &props)) != cudaSuccess ||
+            (e = cudaMemPoolSetAttribute(ctx->serve_pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+            sgm_destroy(ctx);
+            return fail(nullptr, SGM_ECUDA, "device memory pool: %s", cudaGetErrorString(e));
+        }
     }
     if ((e = init_kernel_attributes()) != cudaSuccess) {
         sgm_destroy(ctx);
@@ -617,12 +877,18 @@ int sgm_destroy(sgm_ctx* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
     if (ctx->arena) cudaFree(ctx->arena);
-    if (ctx->serve_arena) cudaFree(ctx->serve_arena);
+    for (auto& sl : ctx->slots) {
+        if (sl.arena) cudaFreeAsync(sl.arena, sl.stream);
+        if (sl.pinned) cudaFreeHost(sl.pinned);
+        if (sl.stream) {
+            cudaStreamSynchronize(sl.stream);
+            cudaStreamDestroy(sl.stream);
+        }
+    }
+    if (ctx->serve_pool) cudaMemPoolDestroy(ctx->serve_pool);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
-    if (ctx->serve_stream) cudaStreamDestroy(ctx->serve_stream);
     destroy_stream_set(&ctx->main_set);
-    destroy_stream_set(&ctx->serve_set);
     for (auto& ev : ctx->stage_ev)
         if (ev) cudaEventDestroy(ev);
     delete ctx;
@@ -689,7 +955,7 @@ int sgm_submit(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, i
     int rc = check_args(ctx, p, left, right, disp_out);
     if (rc != SGM_OK) return rc;
     if (!ticket) return fail(ctx, SGM_EINVAL, "null ticket pointer");
-    if (ctx->mem_cap && layout_for(W, H, D, n_paths).total + ctx->arena_bytes > ctx->mem_cap)
+    if (ctx->mem_cap && layout_for(W, H, D, n_paths, true).total + ctx->arena_bytes > ctx->mem_cap)
         return fail(ctx, SGM_ENOMEM, "pair %dx%d D=%d needs more than the context's memory cap", W, H, D);
     std::lock_guard<std::mutex> lk(ctx->mu);
     if (!ctx->worker_started) {
@@ -735,6 +1001,22 @@ int sgm_served_stats(sgm_ctx* ctx, double* out, int n_out) {
     out[1] = q(0.50);
     out[2] = q(0.99);
     out[3] = v.empty() ? 0.0 : v.back();
+    if (n_out >= 8) {
+        out[4] = static_cast<double>(ctx->batches);
+        out[5] = ctx->batches ? static_cast<double>(ctx->batched_pairs) / ctx->batches : 0.0;
+        out[6] = static_cast<double>(ctx->max_in_flight);
+        out[7] = ctx->served_de;
+    }
+    return SGM_OK;
+}
+
+int sgm_served_reset_stats(sgm_ctx* ctx) {
+    if (!ctx) return fail(nullptr, SGM_EINVAL, "null context");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->latencies_us.clear();
+    ctx->batches = ctx->batched_pairs = 0;
+    ctx->max_in_flight = ctx->in_flight;
+    ctx->served_de = 0.0;
     return SGM_OK;
 }
 

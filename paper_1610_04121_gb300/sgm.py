@@ -59,6 +59,7 @@ _sig("sgm_compute_batch", _i, [_vp, _i, ctypes.POINTER(sgm_pair)])
 _sig("sgm_submit", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, ctypes.POINTER(ctypes.c_uint64)])
 _sig("sgm_poll", _i, [_vp, ctypes.c_uint64, ctypes.c_int64])
 _sig("sgm_served_stats", _i, [_vp, ctypes.POINTER(ctypes.c_double), _i])
+_sig("sgm_served_reset_stats", _i, [_vp])
 _sig("sgm_debug_stages", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp])
 _sig("sgm_kernel_launches", ctypes.c_uint64, [_vp])
 _sig("sgm_stage_times", _i, [_vp, ctypes.POINTER(ctypes.c_float), _i])
@@ -146,9 +147,14 @@ def sgm_poll(ctx, ticket: int, timeout_us: int = -1) -> int:
 
 
 def sgm_served_stats(ctx) -> dict:
-    out = (ctypes.c_double * 4)()
-    _check(ctx, _lib.sgm_served_stats(ctx, out, 4))
-    return {"completed": int(out[0]), "p50_us": out[1], "p99_us": out[2], "max_us": out[3]}
+    out = (ctypes.c_double * 8)()
+    _check(ctx, _lib.sgm_served_stats(ctx, out, 8))
+    return {"completed": int(out[0]), "p50_us": out[1], "p99_us": out[2], "max_us": out[3], "batches": int(out[4]),
+            "mean_batch": out[5], "max_in_flight": int(out[6]), "de": out[7]}
+
+
+def sgm_served_reset_stats(ctx) -> None:
+    _check(ctx, _lib.sgm_served_reset_stats(ctx))
 
 
 def sgm_debug_stages(ctx, left, right, W, H, D, P1, P2, n_paths, Fb=None, Fm=None, MC=None, S=None, raw=None,
