@@ -454,14 +454,16 @@ def main():
     torch.cuda.synchronize(dev)
     # one explicit stream carries the path, the L2 flush and the timing events
     stream = torch.cuda.Stream(dev)
+    # kernel durations are measured inside the timed steps: the captured graph
+    # records an event between its kernels
     ctx = sgm.Context(local, flags=sgm.SGM_FLAG_STAGE_TIMING)
     sgm.sgm_set_stream(ctx.handle, stream)
 
-    def step():
-        sgm.sgm_compute_async(ctx.handle, L, R, W, H, D, w.P1, w.P2, w.n_paths, out)
+    def step(c):
+        sgm.sgm_compute_async(c.handle, L, R, W, H, D, w.P1, w.P2, w.n_paths, out)
 
     for _ in range(max(args.warmup, 3)):
-        step()
+        step(ctx)
     torch.cuda.synchronize(dev)
 
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -476,7 +478,7 @@ def main():
             with torch.cuda.stream(stream):
                 flush.fill_(k & 0xFF)  # evict the previous step's data from L2
             ev0[k].record(stream)
-            step()
+            step(ctx)
             ev1[k].record(stream)
             for name, ms in sgm.sgm_stage_times(ctx.handle).items():  # waits for this step
                 stage_ms.setdefault(name, []).append(ms)
@@ -494,14 +496,19 @@ def main():
     peaks, peak_kind = load_peaks()
     clocks = clk.summary()
     mean_stage = {k: statistics.mean(v) for k, v in stage_ms.items()}
-    # the dominant kernel: each sweep stage is one kernel launch (the vertical
-    # first halves run on a second stream beside sweep_h, outside its events)
-    kernel_stages = {"sweep_h": 2, "sweep_v": 1, "sweep_diag+": 1, "sweep_diag-": 1}
+    # the dominant kernel: each stage is one kernel launch.  Path units per
+    # launch: sweep_h carries the horizontal pair (2) and, with pairs, the first
+    # halves of the (n_paths - 2) / 2 vertical-type pairs (1 each); every later
+    # sweep carries the second halves of one pair (1).  Extra adds per DE: the
+    # stored-L add (+ the S add (+ the winner-take-all minimum)).
     if w.n_paths == 2:
-        kernel_stages = {"sweep_h": 1, "sweep_v": 1}
+        kernel_stages = {"sweep_h": (1, 0), "sweep_v": (1, 2)}
+    else:
+        kernel_stages = {"sweep_h": (2 + (w.n_paths - 2) // 2, 1), "sweep_v": (1, 3), "sweep_diag+": (1, 2),
+                         "sweep_diag-": (1, 2)}
     dom = max((k for k in mean_stage if k in kernel_stages), key=mean_stage.get)
-    extra = 3 if dom == "sweep_v" else 1  # adds of the sums (+ winner-take-all)
-    ops = de * (OPS_PER_DE_PATH * kernel_stages[dom] + extra)
+    units, extra = kernel_stages[dom]
+    ops = de * (OPS_PER_DE_PATH * units + extra)
     sm_mhz = float(peaks.get("sm_max_mhz", SM_MAX_MHZ_GB300))
     peak_tops = SM_COUNT_GB300 * 128 * 2 * sm_mhz * 1e6 / 1e12
     achieved = ops / (mean_stage[dom] / 1e3) / 1e12

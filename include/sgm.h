@@ -208,10 +208,9 @@ SGM_API int sgm_debug_stages(sgm_ctx *ctx, const uint8_t *left, const uint8_t *r
  * enqueued through sgm_compute / sgm_compute_async, in launch order; needs a
  * context created with SGM_FLAG_STAGE_TIMING.  Waits for that path to finish.
  * Writes min(n, stages) values to ms_out and returns the number of stages
- * (5 for 2 paths, 6 for 4 paths, 8 for 8 paths), or a negative sgm_status.
- * Stage names, in order: census, cost, sweep_h (the first halves of the
- * vertical-type pairs run beside it on a second stream), v_first_tail (time
- * still waited for them after the horizontal pair; absent with 2 paths),
+ * (5 for 2 or 4 paths, 7 for 8 paths), or a negative sgm_status.  Stage
+ * names, in order: census, cost, sweep_h (the horizontal pair; with 4 or 8
+ * paths the first halves of the vertical-type pairs run in the same launch),
  * [sweep_diag+, sweep_diag-,] sweep_v, median (sgm_stage_name).
  */
 SGM_API int sgm_stage_times(sgm_ctx *ctx, float *ms_out, int n);

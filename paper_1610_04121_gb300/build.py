@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB_NAME = "libsgm_gb300.so"
 LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
-SOURCES = ["sgm_stages.cu", "sgm_sweeps.cu", "sgm_api.cu"] + [f"sgm_sweeps_k{k}.cu" for k in range(1, 9)]
+SOURCES = ["sgm_stages.cu", "sgm_sweeps.cu", "sgm_api.cu"] + [f"sgm_sweeps_d{32 * k}.cu" for k in range(1, 9)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -99,13 +99,6 @@ struct GraphKey {
     }
 };
 
-// Streams and events one enqueuing thread uses: the main stream is the
-// caller's; the side stream runs the vertical first halves concurrently.
-struct StreamSet {
-    cudaStream_t side;
-    cudaEvent_t fork, join;
-};
-
 struct Request {
     uint64_t ticket;
     Problem p;
@@ -142,7 +135,6 @@ struct sgm_ctx {
     cudaStream_t own_stream = nullptr;
     cudaStream_t stream = nullptr;
     cudaStream_t capture_stream = nullptr;
-    StreamSet main_set{};   // side stream + fork/join events of the caller's thread
     size_t mem_cap = 0;
     uint8_t* arena = nullptr;
     size_t arena_bytes = 0;
@@ -174,20 +166,6 @@ struct sgm_ctx {
 };
 
 static thread_local std::string g_noctx_err;
-
-static cudaError_t create_stream_set(StreamSet* ss) {
-    cudaError_t e = cudaStreamCreateWithFlags(&ss->side, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss->fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss->join, cudaEventDisableTiming);
-    return e;
-}
-
-static void destroy_stream_set(StreamSet* ss) {
-    if (ss->side) cudaStreamDestroy(ss->side);
-    if (ss->fork) cudaEventDestroy(ss->fork);
-    if (ss->join) cudaEventDestroy(ss->join);
-    *ss = StreamSet{};
-}
 
 static int fail(sgm_ctx* ctx, int code, const char* fmt, ...) {
     char buf[512];
@@ -251,12 +229,12 @@ static bool is_device_ptr(const void* p) {
     return t == cudaMemoryTypeDevice || t == cudaMemoryTypeManaged;
 }
 
-static int launches_per_path(const Problem& p) { return p.n_paths == 8 ? 10 : (p.n_paths == 4 ? 6 : 5); }
-
-// Timed stages: census, cost, sweep_h (the vertical first halves run beside
-// it), v_first_tail (waiting for them after the horizontal pair ends),
-// [sweep_diag+, sweep_diag-,] sweep_v, median; 2-path mode has no tail stage.
-static int stages_per_path(const Problem& p) { return p.n_paths == 8 ? 8 : (p.n_paths == 4 ? 6 : 5); }
+// Kernels per path: census, cost, the first sweep stage (horizontal pair and
+// vertical-type first halves), the second halves of each vertical-type pair
+// (sweep_diag+, sweep_diag-, sweep_v), median; with 2 paths: census, cost,
+// sweep_h, sweep_v, median.  Each kernel is one timed stage.
+static int launches_per_path(const Problem& p) { return p.n_paths == 8 ? 7 : 5; }
+static int stages_per_path(const Problem& p) { return launches_per_path(p); }
 
 // Bytes of one [H][W][D] u8 scratch cube of path costs.
 static size_t lx_cube_bytes(const Problem& p) {
@@ -266,8 +244,7 @@ static size_t lx_cube_bytes(const Problem& p) {
 // Enqueue the whole path (Section 2, stages 2-4) for one pair whose inputs
 // and output are device pointers.  Returns a cudaError_t.
 static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const uint8_t* left,
-                                const uint8_t* right, uint8_t* disp, uint16_t* Sdbg, cudaStream_t s, bool timed,
-                                const StreamSet& ss) {
+                                const uint8_t* right, uint8_t* disp, uint16_t* Sdbg, cudaStream_t s, bool timed) {
     const Layout l = layout_for(p.W, p.H, p.D, p.n_paths);
     uint32_t* Fb = reinterpret_cast<uint32_t*>(arena + l.Fb);
     uint32_t* Fm = reinterpret_cast<uint32_t*>(arena + l.Fm);
@@ -315,24 +292,22 @@ static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, 
         if ((e = mark()) != cudaSuccess) return e;
     } else {
         // the first halves of the vertical-type pairs need only the costs: they
-        // run on the side stream while the horizontal pair runs
-        if ((e = cudaEventRecord(ss.fork, s)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(ss.side, ss.fork, 0)) != cudaSuccess) return e;
+        // run in the same launch as the horizontal pair
+        FirstStageArgs f{};
+        f.h = a;
+        f.nv = nv;
         for (int v = 0; v < nv; ++v) {
             SweepArgs b = a;
             b.rx = rxs[v];
             b.phase = 1;
             b.state = states + v * sw;
             // each vertical-type pair keeps its own first-half L cube: the scratch
-            // is split [H][W][DP] per pair after the horizontal one
+            // is split [H][W][D] per pair after the horizontal one
             b.Lx = arena + l.Lx + static_cast<size_t>(v + 1) * lx_cube_bytes(p);
-            if ((e = launch_sweep_v(b, ss.side)) != cudaSuccess) return e;
+            f.v[v] = b;
         }
-        if ((e = cudaEventRecord(ss.join, ss.side)) != cudaSuccess) return e;
-        if ((e = launch_sweep_h(a, s)) != cudaSuccess) return e;
-        if ((e = mark()) != cudaSuccess) return e;  // the horizontal pair alone
-        if ((e = cudaStreamWaitEvent(s, ss.join, 0)) != cudaSuccess) return e;
-        if ((e = mark()) != cudaSuccess) return e;  // any remainder of the first halves
+        if ((e = launch_sweep_first(f, s)) != cudaSuccess) return e;
+        if ((e = mark()) != cudaSuccess) return e;
         for (int v = 0; v < nv; ++v) {
             SweepArgs b = a;
             b.rx = rxs[v];
@@ -363,8 +338,7 @@ static int enqueue_graph(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const u
         cudaGraph_t g = nullptr;
         CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
         const uint64_t before = ctx->launches.load();
-        cudaError_t e = enqueue_path(ctx, p, arena, left, right, disp, nullptr, ctx->capture_stream, ctx->stage_timing,
-                                     ctx->main_set);
+        cudaError_t e = enqueue_path(ctx, p, arena, left, right, disp, nullptr, ctx->capture_stream, ctx->stage_timing);
         ctx->launches = before;  // captured, not launched
         cudaError_t e2 = cudaStreamEndCapture(ctx->capture_stream, &g);
         if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -386,7 +360,7 @@ static int enqueue_graph(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const u
 
 // Copy-in / path / copy-out for one pair into `arena` (already large enough).
 static int enqueue_pair(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const uint8_t* left, const uint8_t* right,
-                        uint8_t* disp, cudaStream_t s, bool use_graph, const StreamSet& ss) {
+                        uint8_t* disp, cudaStream_t s, bool use_graph) {
     const Layout l = layout_for(p.W, p.H, p.D, p.n_paths);
     const size_t wh = static_cast<size_t>(p.W) * p.H;
     const uint8_t* dl = left;
@@ -406,7 +380,7 @@ static int enqueue_pair(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const ui
         int rc = enqueue_graph(ctx, p, arena, dl, dr, dout, s);
         if (rc != SGM_OK) return rc;
     } else {
-        CUDA_TRY(ctx, enqueue_path(ctx, p, arena, dl, dr, dout, nullptr, s, false, ss));
+        CUDA_TRY(ctx, enqueue_path(ctx, p, arena, dl, dr, dout, nullptr, s, false));
     }
     if (out_host) CUDA_TRY(ctx, cudaMemcpyAsync(disp, dout, wh, cudaMemcpyDeviceToHost, s));
     return SGM_OK;
@@ -521,7 +495,7 @@ static int enqueue_wave(sgm_ctx* ctx, std::vector<BatchItem>& items, size_t b, s
 // budget (the context's memory cap, else the device's free memory plus what the
 // arena already holds), grow the arena once per wave.
 static int run_batch(sgm_ctx* ctx, std::vector<BatchItem>& items, uint8_t** arena, size_t* arena_bytes,
-                     bool clear_graphs, cudaStream_t s, const StreamSet& /*ss*/) {
+                     bool clear_graphs, cudaStream_t s) {
     std::stable_sort(items.begin(), items.end(), [](const BatchItem& x, const BatchItem& y) {
         return std::tie(x.p.D, x.p.n_paths) < std::tie(y.p.D, y.p.n_paths);
     });
@@ -822,8 +796,7 @@ int sgm_create(sgm_ctx** out, int device, size_t mem_cap_bytes, unsigned flags) 
     ctx->device = device;
     ctx->mem_cap = mem_cap_bytes;
     if ((e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = create_stream_set(&ctx->main_set)) != cudaSuccess) {
+        (e = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking)) != cudaSuccess) {
         sgm_destroy(ctx);
         return fail(nullptr, SGM_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
     }
@@ -888,7 +861,6 @@ int sgm_destroy(sgm_ctx* ctx) {
     if (ctx->serve_pool) cudaMemPoolDestroy(ctx->serve_pool);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
-    destroy_stream_set(&ctx->main_set);
     for (auto& ev : ctx->stage_ev)
         if (ev) cudaEventDestroy(ev);
     delete ctx;
@@ -911,7 +883,7 @@ int sgm_compute(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, 
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, layout_for(W, H, D, n_paths).total, true);
     if (rc != SGM_OK) return rc;
-    rc = enqueue_pair(ctx, p, ctx->arena, left, right, disp_out, ctx->stream, true, ctx->main_set);
+    rc = enqueue_pair(ctx, p, ctx->arena, left, right, disp_out, ctx->stream, true);
     if (rc != SGM_OK) return rc;
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     return SGM_OK;
@@ -943,7 +915,7 @@ int sgm_compute_batch(sgm_ctx* ctx, int n, const sgm_pair* pairs) {
         items.push_back(BatchItem{p, q.left, q.right, q.disp_out, 0});
     }
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-    int rc = run_batch(ctx, items, &ctx->arena, &ctx->arena_bytes, true, ctx->stream, ctx->main_set);
+    int rc = run_batch(ctx, items, &ctx->arena, &ctx->arena_bytes, true, ctx->stream);
     if (rc != SGM_OK) return rc;
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     return SGM_OK;
@@ -1037,8 +1009,7 @@ int sgm_debug_stages(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, in
     cudaStream_t s = ctx->stream;
     CUDA_TRY(ctx, cudaMemcpyAsync(a + l.in_left, left, wh, cudaMemcpyHostToDevice, s));
     CUDA_TRY(ctx, cudaMemcpyAsync(a + l.in_right, right, wh, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(ctx, enqueue_path(ctx, p, a, a + l.in_left, a + l.in_right, a + l.out, S ? Sdev : nullptr, s, false,
-                               ctx->main_set));
+    CUDA_TRY(ctx, enqueue_path(ctx, p, a, a + l.in_left, a + l.in_right, a + l.out, S ? Sdev : nullptr, s, false));
     if (Fb) CUDA_TRY(ctx, cudaMemcpyAsync(Fb, a + l.Fb, 4 * wh, cudaMemcpyDeviceToHost, s));
     if (Fm) CUDA_TRY(ctx, cudaMemcpyAsync(Fm, a + l.Fm, 4 * wh, cudaMemcpyDeviceToHost, s));
     if (MC) {
@@ -1063,13 +1034,12 @@ int sgm_stage_times(sgm_ctx* ctx, float* ms_out, int n) {
 }
 
 const char* sgm_stage_name(int n_paths, int i) {
-    static const char* two[] = {"census", "cost", "sweep_h", "sweep_v", "median"};
-    static const char* four[] = {"census", "cost", "sweep_h", "v_first_tail", "sweep_v", "median"};
-    static const char* eight[] = {"census",       "cost",        "sweep_h", "v_first_tail",
-                                  "sweep_diag+", "sweep_diag-", "sweep_v", "median"};
-    if (n_paths == 8) return (i >= 0 && i < 8) ? eight[i] : nullptr;
-    if (n_paths == 4) return (i >= 0 && i < 6) ? four[i] : nullptr;
-    if (n_paths == 2) return (i >= 0 && i < 5) ? two[i] : nullptr;
+    // "sweep_h" is the first sweep launch: the horizontal pair, with the
+    // vertical-type first halves in the same launch when there are pairs
+    static const char* five[] = {"census", "cost", "sweep_h", "sweep_v", "median"};
+    static const char* eight[] = {"census", "cost", "sweep_h", "sweep_diag+", "sweep_diag-", "sweep_v", "median"};
+    if (n_paths == 8) return (i >= 0 && i < 7) ? eight[i] : nullptr;
+    if (n_paths == 4 || n_paths == 2) return (i >= 0 && i < 5) ? five[i] : nullptr;
     return nullptr;
 }
 

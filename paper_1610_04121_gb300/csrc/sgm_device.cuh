@@ -174,38 +174,41 @@ __device__ __forceinline__ void st_words(uint32_t* p, const uint32_t (&w)[K]) {
 }
 
 // ---------------------------------------------------------------------------
-// Two aggregation chains (Eq. 3, Section 3.2) per warp: lanes 0-15 carry
-// chain A, lanes 16-31 chain B (the two opposite directions of one row or one
-// column).  Every cross-lane operation is a full-warp instruction; each half
-// shuffles within itself and the two step minima are two masked reductions.
+// Aggregation chains (Eq. 3, Section 3.2) with G lanes per path: G = 32 puts
+// one path in a warp; G = 16 puts two in it, lanes 0-15 carrying chain A and
+// lanes 16-31 chain B (the two opposite directions of one row or one column).
+// Every cross-lane operation is a full-warp instruction; with G = 16 each
+// half shuffles within itself and the two step minima are two masked
+// reductions.
 //
-// Lane l of a half holds words i = (l mod 16)*K + j, j < K, of the path cost
+// Lane l of a path holds words i = (l mod G)*K + j, j < K, of the path cost
 // of the previous pixel; word i packs L(i) (low half) and L(i + D/2) (high
-// half), D = 32*K.  Each step computes, for every d,
+// half), D = 2*G*K.  Each step computes, for every d,
 //   L(p, d) = MC(p, d) + min(L(q, d), L(q, d-1) + P1, L(q, d+1) + P1, m(q) + P2) - m(q)
 // with q the previous pixel and m(q) = min_k L(q, k).  Starting a path with
 // L(q, .) = 0 and m(q) = 0 yields L(p, .) = MC(p, .), the reading used for the
 // first pixel of every path.  `up` / `dn` hold the neighbour words across the
 // lane boundary, already exchanged at the end of the previous step.
 // ---------------------------------------------------------------------------
-template <int K>
-struct Chain2 {
+template <int G, int K>
+struct Chain {
+    static_assert(G == 16 || G == 32, "16 or 32 lanes per path");
     uint32_t w[K];
-    uint32_t up, dn;  // word hl*K-1 from lane hl-1, word hl*K+K from lane hl+1 (wrapping in the half)
+    uint32_t up, dn;  // word pl*K-1 from lane pl-1, word pl*K+K from lane pl+1 (wrapping in the path)
     uint32_t mpx2;    // m(q) in both u16 halves
     uint32_t sel_up, sel_dn, mask_a, mask_b;
     int src_up, src_dn;
     bool in_b;
 
     __device__ __forceinline__ void init(int lane) {
-        const int hl = lane & 15, base = lane & 16;
-        src_up = base | ((hl + 15) & 15);
-        src_dn = base | ((hl + 1) & 15);
-        // first lane of a half: d-1 of d=0 is absent, d-1 of d=D/2 is the low half of word D/2-1
-        sel_up = (hl == 0) ? 0x1054u : 0x3210u;
-        // last lane of a half: d+1 of d=D-1 is absent, d+1 of d=D/2-1 is the high half of word 0
-        sel_dn = (hl == 15) ? 0x5432u : 0x3210u;
-        in_b = lane >= 16;
+        const int pl = lane & (G - 1), base = lane & (32 - G);
+        src_up = base | ((pl + G - 1) & (G - 1));
+        src_dn = base | ((pl + 1) & (G - 1));
+        // first lane of a path: d-1 of d=0 is absent, d-1 of d=D/2 is the low half of word D/2-1
+        sel_up = (pl == 0) ? 0x1054u : 0x3210u;
+        // last lane of a path: d+1 of d=D-1 is absent, d+1 of d=D/2-1 is the high half of word 0
+        sel_dn = (pl == G - 1) ? 0x5432u : 0x3210u;
+        in_b = G == 16 && lane >= 16;
         mask_a = in_b ? 0xffffffffu : 0u;
         mask_b = ~mask_a;
         reset();
@@ -218,11 +221,15 @@ struct Chain2 {
         mpx2 = 0u;
     }
 
-    // the minimum of v over this lane's half of the warp
-    __device__ __forceinline__ uint32_t half_min(uint32_t v) const {
-        const uint32_t a = redux_min(v | mask_a);
-        const uint32_t b = redux_min(v | mask_b);
-        return in_b ? b : a;
+    // the minimum of v over this lane's path
+    __device__ __forceinline__ uint32_t path_min(uint32_t v) const {
+        if constexpr (G == 32) {
+            return redux_min(v);
+        } else {
+            const uint32_t a = redux_min(v | mask_a);
+            const uint32_t b = redux_min(v | mask_b);
+            return in_b ? b : a;
+        }
     }
 
     __device__ __forceinline__ void step(const uint32_t (&mc)[K], uint32_t P1x2, uint32_t P2x2, uint32_t (&L)[K]) {
@@ -243,7 +250,7 @@ struct Chain2 {
         r = vmin2(r, __byte_perm(r, 0u, 0x1032u));  // both u16 halves = lane minimum
         up = shfl_idx(L[K - 1], src_up);
         dn = shfl_idx(L[0], src_dn);
-        mpx2 = half_min(r);
+        mpx2 = path_min(r);
 #pragma unroll
         for (int j = 0; j < K; ++j) w[j] = L[j];
     }
@@ -251,12 +258,12 @@ struct Chain2 {
 
 // Winner-take-all over one lane's words (Eq. 4): key = S << 8 | d, so the
 // u32 minimum is the smallest S and, among equal S, the lowest d.  dconst[j]
-// holds, for word i = hl*K + j, the bytes [i, i + D/2, 0, 0].
+// holds, for word i = pl*K + j, the bytes [i, i + D/2, 0, 0].
 template <int K>
-__device__ __forceinline__ void wta_consts(int hl, int D, uint32_t (&dconst)[K]) {
+__device__ __forceinline__ void wta_consts(int pl, int D, uint32_t (&dconst)[K]) {
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-        const uint32_t i = static_cast<uint32_t>(hl * K + j);
+        const uint32_t i = static_cast<uint32_t>(pl * K + j);
         dconst[j] = i | ((i + static_cast<uint32_t>(D / 2)) << 8);
     }
 }

@@ -20,7 +20,7 @@ struct SweepArgs {
     int wta;              // vertical-type sweeps: 1 = finish with Eq. 4, 0 = add into S
     int phase;            // vertical-type pairs: 0 = both phases, 1 = first half of each path
                           // (saves the path state), 2 = second half (restores it)
-    uint32_t* state;      // path states between phases 1 and 2: [W][32 lanes][K + 3] words
+    uint32_t* state;      // path states between phases 1 and 2 (sweep_state_words)
 };
 
 // ---------------------------------------------------------------------------
@@ -59,9 +59,25 @@ cudaError_t launch_census(const uint8_t* left, const uint8_t* right, uint32_t* F
 cudaError_t launch_cost(const uint32_t* Fb, const uint32_t* Fm, uint8_t* MC, int W, int H, int D,
                         cudaStream_t stream);
 cudaError_t launch_sweep_h(const SweepArgs& a, cudaStream_t stream);
+// The first sweep stage of a path with pairs (4 or 8 directions): the
+// horizontal pair and the first halves (phase 1) of up to three vertical-type
+// pairs in one launch; blocks [start[0], start[1]) run the horizontal pair,
+// blocks [start[k + 1], start[k + 2]) the first halves of v[k].  `start` is
+// filled in by the launcher.
+struct FirstStageArgs {
+    SweepArgs h;
+    SweepArgs v[3];
+    int nv;
+    int start[5];
+};
+cudaError_t launch_sweep_first(FirstStageArgs& f, cudaStream_t stream);
 cudaError_t launch_sweep_v(const SweepArgs& a, cudaStream_t stream);
-// Words of path state saved per vertical-type line between its two phases.
-inline size_t sweep_state_words(int W, int D) { return static_cast<size_t>(W) * 32 * (D / 32 + 3); }
+// Words of saved path state per vertical-type pair between its two phases:
+// per line, 32 lanes x (K + 3) words for each warp carrying it (one warp of
+// 16-lane paths, K = D/32; or two warps of 32-lane paths, K = D/64).
+inline size_t sweep_state_words(int W, int D) {
+    return (D % 64 == 0) ? static_cast<size_t>(W) * 64 * (D / 64 + 3) : static_cast<size_t>(W) * 32 * (D / 32 + 3);
+}
 cudaError_t launch_median(const uint8_t* raw, uint8_t* disp, int W, int H, cudaStream_t stream);
 // Batched forms; every job of a cost or sweep table has the same D (and, for
 // sweeps, the same pair / rx / phase / wta settings).  `start` is filled in.

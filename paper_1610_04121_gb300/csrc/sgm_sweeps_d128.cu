@@ -1,0 +1,6 @@
+// Aggregation sweeps for D = 128 (32 lanes per path, 2 packed words per lane).
+#include "sgm_sweeps.cuh"
+
+namespace sgm {
+SGM_INSTANTIATE_SWEEPS(128)
+}  // namespace sgm

@@ -1,0 +1,6 @@
+// Aggregation sweeps for D = 224 (16 lanes per path, 7 packed words per lane).
+#include "sgm_sweeps.cuh"
+
+namespace sgm {
+SGM_INSTANTIATE_SWEEPS(224)
+}  // namespace sgm

@@ -1,0 +1,6 @@
+// Aggregation sweeps for D = 256 (32 lanes per path, 4 packed words per lane).
+#include "sgm_sweeps.cuh"
+
+namespace sgm {
+SGM_INSTANTIATE_SWEEPS(256)
+}  // namespace sgm

@@ -1,0 +1,6 @@
+// Aggregation sweeps for D = 64 (32 lanes per path, 1 packed word per lane).
+#include "sgm_sweeps.cuh"
+
+namespace sgm {
+SGM_INSTANTIATE_SWEEPS(64)
+}  // namespace sgm

@@ -169,7 +169,7 @@ def sgm_stage_times(ctx) -> dict:
     n = _lib.sgm_stage_times(ctx, buf, 10)
     if n < 0:
         raise SgmError(n, last_error(ctx))
-    npaths = {8: 8, 6: 4, 5: 2}[n]
+    npaths = {7: 8, 5: 4}[n]  # 2 and 4 paths share the five stage names
     return {_lib.sgm_stage_name(npaths, i).decode(): float(buf[i]) for i in range(n)}
 
 

@@ -112,10 +112,10 @@ def test_launch_counter_counts_kernels(ctx):
     p = _pair()
     before = ctx.launches
     ctx.compute(p.left, p.right, 64, 7, 84, 4)
-    assert ctx.launches - before == 6  # census, cost, vertical first halves, horizontal, vertical rest, median
+    assert ctx.launches - before == 5  # census, cost, horizontal + vertical first halves, vertical rest, median
     before = ctx.launches
     ctx.compute(p.left, p.right, 64, 7, 84, 8)
-    assert ctx.launches - before == 10  # three vertical-type pairs in two phases each
+    assert ctx.launches - before == 7  # the second halves of three vertical-type pairs
     before = ctx.launches
     ctx.compute(p.left, p.right, 64, 7, 84, 2)
     assert ctx.launches - before == 5
@@ -131,15 +131,14 @@ def test_stage_times_inside_graph_replay(sgm):
         R = torch.from_numpy(p.right).cuda()
         out = torch.empty_like(L)
         sgm.sgm_set_stream(c.handle, torch.cuda.current_stream())
-        for n_paths, names in [(4, ["census", "cost", "sweep_h", "v_first_tail", "sweep_v", "median"]),
-                               (8, ["census", "cost", "sweep_h", "v_first_tail", "sweep_diag+", "sweep_diag-",
-                                    "sweep_v", "median"]),
+        for n_paths, names in [(4, ["census", "cost", "sweep_h", "sweep_v", "median"]),
+                               (8, ["census", "cost", "sweep_h", "sweep_diag+", "sweep_diag-", "sweep_v", "median"]),
                                (2, ["census", "cost", "sweep_h", "sweep_v", "median"])]:
             for _ in range(2):
                 sgm.sgm_compute_async(c.handle, L, R, 128, 80, 128, 7, 84, n_paths, out)
                 st = sgm.sgm_stage_times(c.handle)
                 assert list(st) == names and all(v >= 0 for v in st.values())
-                assert all(st[k] > 0 for k in names if k != "v_first_tail")
+                assert all(st[k] > 0 for k in names)
             torch.cuda.synchronize()
             assert (out.cpu().numpy() == oracle.sgm(p.left, p.right, 128, 7, 84, n_paths)).all()
     finally:
