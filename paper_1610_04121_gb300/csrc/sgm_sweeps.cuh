@@ -48,15 +48,15 @@ enum WalkMode {
 
 // Shared-memory staging of one path during a walk in MODE: a ring of NSLOT
 // chunks of CH pixels per input stream it reads (costs; stored L of the other
-// direction; sums).
-template <int D, int MODE>
+// direction; sums).  Row walks read contiguous pixels and take longer chunks.
+template <int D, int MODE, bool ROW>
 struct Stage {
     static constexpr bool IN_LO = MODE == kSumH || MODE == kAcc || MODE == kWta2;
     static constexpr bool IN_S = MODE == kAcc || MODE == kWta2 || MODE == kSingleWta;
     static constexpr bool OUT_LX = MODE == kStoreL;
     static constexpr bool OUT_S = MODE == kSumH || MODE == kAcc || MODE == kSingleH;
     static constexpr bool WTA = MODE == kWta2 || MODE == kSingleWta;
-    static constexpr int CH = D <= 64 ? 16 : (D <= 128 ? 8 : 4);  // pixels per chunk
+    static constexpr int CH = ROW ? (D <= 128 ? 16 : 8) : (D <= 64 ? 16 : (D <= 128 ? 8 : 4));  // pixels per chunk
     static constexpr int NSLOT = 3;                                // chunks in flight + 1
     static constexpr int MC_RING = NSLOT * CH * D;
     static constexpr int LO_RING = IN_LO ? NSLOT * CH * D : 0;
@@ -69,15 +69,16 @@ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 // Staging bytes per path and per block of each kernel (the largest of its walks).
 template <int D, bool PAIR>
 struct HStage {
-    static constexpr int PATH = PAIR ? cmax(Stage<D, kStoreL>::BYTES, Stage<D, kSumH>::BYTES) : Stage<D, kSingleH>::BYTES;
+    static constexpr int PATH =
+        PAIR ? cmax(Stage<D, kStoreL, true>::BYTES, Stage<D, kSumH, true>::BYTES) : Stage<D, kSingleH, true>::BYTES;
     static constexpr int BLOCK = kWarpsPerBlock * PathShape<D>::PPW * PATH;
 };
 template <int D, int PH, bool WTA, bool PAIR>
 struct VStage {
-    static constexpr int SECOND = WTA ? Stage<D, kWta2>::BYTES : Stage<D, kAcc>::BYTES;
-    static constexpr int PATH = !PAIR ? Stage<D, kSingleWta>::BYTES
-                                      : (PH == 1 ? Stage<D, kStoreL>::BYTES
-                                                 : (PH == 2 ? SECOND : cmax(Stage<D, kStoreL>::BYTES, SECOND)));
+    static constexpr int SECOND = WTA ? Stage<D, kWta2, false>::BYTES : Stage<D, kAcc, false>::BYTES;
+    static constexpr int FIRST = Stage<D, kStoreL, false>::BYTES;
+    static constexpr int PATH =
+        !PAIR ? Stage<D, kSingleWta, false>::BYTES : (PH == 1 ? FIRST : (PH == 2 ? SECOND : cmax(FIRST, SECOND)));
     static constexpr int BLOCK = kWarpsPerBlock * PathShape<D>::PPW * PATH;
 };
 
@@ -133,6 +134,7 @@ struct RowGeo {
     size_t rowbase;
     int x0, dx;
     static constexpr bool kResets = false;
+    static constexpr bool kRow = true;
     __device__ __forceinline__ void origin(int i0, int& xc, int& yc) const {
         xc = x0 + dx * i0;
         yc = 0;
@@ -148,6 +150,7 @@ template <int RX>
 struct ColGeo {
     int W, H, c, y0, dy;
     static constexpr bool kResets = RX != 0;
+    static constexpr bool kRow = false;
     __device__ __forceinline__ int x_at(int y) const {
         if constexpr (RX == 0) {
             return c;
@@ -187,12 +190,13 @@ struct ColGeo {
 
 // One phase of this warp's path(s).  g / n_own: this lane's path; n_min /
 // n_max: the shorter and the longer step count of the warp's paths (equal to
-// n_own when the warp carries one path).
-template <int D, int MODE, class Geo>
+// n_own when the warp carries one path).  DBG: a winner-take-all walk also
+// writes S in natural order to a.Sdbg.
+template <int D, int MODE, class Geo, bool DBG = false>
 __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch, const Geo& g, int n_own,
                                      int n_min, int n_max, const SweepArgs& a, uint8_t* ws, int pl) {
     constexpr int G = PathShape<D>::G, K = PathShape<D>::K;
-    using St = Stage<D, MODE>;
+    using St = Stage<D, MODE, Geo::kRow>;
     constexpr int CH = St::CH, NS = St::NSLOT;
     constexpr bool IN_LO = St::IN_LO, IN_S = St::IN_S, OUT_LX = St::OUT_LX, OUT_S = St::OUT_S, WTA = St::WTA;
     constexpr int PM = D / 16;      // 16-byte pieces per pixel of u8 pairs
@@ -265,7 +269,7 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
             if constexpr (WTA) {
                 const uint32_t key = ch.path_min(wta_key<K>(s, dconst));
                 dkeep = (pl == pi) ? key : dkeep;
-                if (a.Sdbg && active) {  // debug: natural-order S
+                if (DBG && active) {  // debug: natural-order S
                     const size_t p = g.pix(xc, yc, pi);
 #pragma unroll
                     for (int j = 0; j < K; ++j) {
@@ -378,7 +382,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_h_batch_kernel(cons
 // PH: 0 = both phases in one launch, 1 = first halves (saving the path state),
 // 2 = second halves (restoring it).  WTA: the pair finishes with Eq. 4
 // instead of adding into S.  PAIR = false is the 2-path top-to-bottom sweep.
-template <int D, int RX, int PH, bool WTA, bool PAIR>
+template <int D, int RX, int PH, bool WTA, bool PAIR, bool DBG = false>
 __device__ __forceinline__ void sweep_v_body(const SweepArgs& a, int bx) {
     extern __shared__ __align__(16) uint8_t smem[];
     constexpr int G = PathShape<D>::G, K = PathShape<D>::K;
@@ -394,7 +398,7 @@ __device__ __forceinline__ void sweep_v_body(const SweepArgs& a, int bx) {
     ch.init(lane);
     if constexpr (!PAIR) {
         const int n = in_b ? 0 : H;
-        walk<D, kSingleWta>(ch, Geo{W, H, c, 0, 1}, n, G == 16 ? 0 : n, H, a, ws, r.pl);
+        walk<D, kSingleWta, Geo, DBG>(ch, Geo{W, H, c, 0, 1}, n, G == 16 ? 0 : n, H, a, ws, r.pl);
     } else {
         const int Hm = H / 2;
         // saved path state of this lane: K words, the two neighbour words and m
@@ -426,15 +430,15 @@ __device__ __forceinline__ void sweep_v_body(const SweepArgs& a, int bx) {
             if constexpr (PH == 0) pair_barrier<D>();
             const Geo g = in_b ? Geo{W, H, c, Hm - 1, -1} : Geo{W, H, c, Hm, 1};
             const int nA = H - Hm, nB = Hm, n = in_b ? nB : nA;
-            walk<D, WTA ? kWta2 : kAcc>(ch, g, n, G == 16 ? min(nA, nB) : n, G == 16 ? max(nA, nB) : n, a, ws,
-                                        r.pl);
+            walk<D, WTA ? kWta2 : kAcc, Geo, DBG>(ch, g, n, G == 16 ? min(nA, nB) : n, G == 16 ? max(nA, nB) : n, a,
+                                                  ws, r.pl);
         }
     }
 }
 
-template <int D, int RX, int PH, bool WTA, bool PAIR>
+template <int D, int RX, int PH, bool WTA, bool PAIR, bool DBG = false>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_v_kernel(SweepArgs a) {
-    sweep_v_body<D, RX, PH, WTA, PAIR>(a, blockIdx.x);
+    sweep_v_body<D, RX, PH, WTA, PAIR, DBG>(a, blockIdx.x);
 }
 
 // Batched form: both phases in one launch (PH = 0).
@@ -500,6 +504,8 @@ struct SweepD {
         if (e == cudaSuccess) e = attr(sweep_h_batch_kernel<D, true>, HStage<D, true>::BLOCK);
         if (e == cudaSuccess) e = attr(sweep_h_batch_kernel<D, false>, HStage<D, false>::BLOCK);
         if (e == cudaSuccess) e = attr(sweep_v_kernel<D, 0, 0, true, false>, VStage<D, 0, true, false>::BLOCK);
+        if (e == cudaSuccess) e = attr(sweep_v_kernel<D, 0, 0, true, false, true>, VStage<D, 0, true, false>::BLOCK);
+        if (e == cudaSuccess) e = attr(sweep_v_kernel<D, 0, 2, true, true, true>, VStage<D, 2, true, true>::BLOCK);
         if (e == cudaSuccess) e = attr(sweep_v_batch_kernel<D, 0, true, false>, VStage<D, 0, true, false>::BLOCK);
         if (e == cudaSuccess) e = attrs_rx<0, true>();
         if (e == cudaSuccess) e = attrs_rx<1, false>();
@@ -532,7 +538,9 @@ struct SweepD {
 
     template <int RX, bool WTA>
     static void launch_v_rx(const SweepArgs& a, dim3 grid, dim3 block, cudaStream_t s) {
-        if (a.phase == 1)
+        if (WTA && a.Sdbg && a.phase == 2)
+            sweep_v_kernel<D, RX, 2, WTA, true, true><<<grid, block, VStage<D, 2, WTA, true>::BLOCK, s>>>(a);
+        else if (a.phase == 1)
             sweep_v_kernel<D, RX, 1, false, true><<<grid, block, VStage<D, 1, false, true>::BLOCK, s>>>(a);
         else if (a.phase == 2)
             sweep_v_kernel<D, RX, 2, WTA, true><<<grid, block, VStage<D, 2, WTA, true>::BLOCK, s>>>(a);
@@ -569,7 +577,9 @@ struct SweepD {
 
     static cudaError_t launch_v(const SweepArgs& a, cudaStream_t s) {
         const dim3 grid(blocks(a.W, a.pair)), block(32 * kWarpsPerBlock);
-        if (!a.pair)
+        if (!a.pair && a.Sdbg)
+            sweep_v_kernel<D, 0, 0, true, false, true><<<grid, block, VStage<D, 0, true, false>::BLOCK, s>>>(a);
+        else if (!a.pair)
             sweep_v_kernel<D, 0, 0, true, false><<<grid, block, VStage<D, 0, true, false>::BLOCK, s>>>(a);
         else if (a.rx == 0)
             launch_v_rx<0, true>(a, grid, block, s);
