@@ -6,14 +6,19 @@
 namespace sgm {
 
 // ---------------------------------------------------------------------------
-// Eq. 1: 9x7 center-symmetric Census transform.  A CTA computes a 32x16 tile
-// of features from a (32+8)x(16+6) byte tile staged in shared memory (the
-// read-cooperative 2D tiling of Section 3.1); blockIdx.z picks the image.
-// The feature is 0 where the 9x7 window leaves the image.
+// Eq. 1: 9x7 center-symmetric Census transform.  A CTA of kCtW threads covers
+// a kCtW x kCtH tile: the (kCtW+8) x (kCtH+6) bytes around it are staged in
+// shared memory (the read-cooperative 2D tiling of Section 3.1) and each
+// thread walks one column of the tile downwards with the 7 x 9 window in
+// registers, loading one new row of 9 bytes per pixel; blockIdx.z picks the
+// image.  The feature is 0 where the 9x7 window leaves the image.
 // Bit k follows the printed order of Eq. 1: i = 1..4, j = -3..3 give bit
 // (i-1)*7 + j+3; the i = 0 pairs j = 1..3 give bits 28..30; s(u,v) = u >= v.
+// Each bit costs two instructions: for bytes u, v the value v + ~u = v - u - 1
+// is negative exactly when u >= v, and a funnel shift moves its sign bit in
+// below the bits already collected (highest bit first).
 // ---------------------------------------------------------------------------
-constexpr int kCtW = 32, kCtH = 16;
+constexpr int kCtW = 64, kCtH = 16;
 
 __device__ __forceinline__ void census_body(const uint8_t* __restrict__ left, const uint8_t* __restrict__ right,
                                             uint32_t* __restrict__ Fb, uint32_t* __restrict__ Fm, int W, int H,
@@ -22,41 +27,48 @@ __device__ __forceinline__ void census_body(const uint8_t* __restrict__ left, co
     const uint8_t* img = bz ? right : left;
     uint32_t* F = bz ? Fm : Fb;
     const int x0 = bx * kCtW, y0 = by * kCtH;
-    const int t = threadIdx.y * 32 + threadIdx.x;
-    for (int i = t; i < (kCtH + 6) * (kCtW + 8); i += 256) {
+    for (int i = threadIdx.x; i < (kCtH + 6) * (kCtW + 8); i += kCtW) {
         const int ty = i / (kCtW + 8), tx = i % (kCtW + 8);
         const int gx = x0 - 4 + tx, gy = y0 - 3 + ty;
         tile[ty][tx] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? img[(size_t)gy * W + gx] : 0;
     }
     __syncthreads();
+    const int lx = threadIdx.x, x = x0 + lx;
+    if (x >= W) return;
+    const bool x_ok = x >= 4 && x <= W - 5;
+    uint32_t win[7][9];  // win[r % 7][c]: tile row r, tile column lx + c (image x - 4 + c)
 #pragma unroll
-    for (int r = 0; r < kCtH / 8; ++r) {
-        const int lx = threadIdx.x, ly = threadIdx.y + 8 * r;
-        const int x = x0 + lx, y = y0 + ly;
-        if (x >= W || y >= H) continue;
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = 0; c < 9; ++c) win[r][c] = tile[r][lx + c];
+#pragma unroll
+    for (int r = 0; r < kCtH; ++r) {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) win[(r + 6) % 7][c] = tile[r + 6][lx + c];
+        const int y = y0 + r;
+        if (y >= H) break;
+        // window row k (image y - 3 + k) is win[(r + k) % 7]
         uint32_t f = 0;
-        if (x >= 4 && x <= W - 5 && y >= 3 && y <= H - 4) {
-            const int cx = lx + 4, cy = ly + 3;
-            int k = 0;
 #pragma unroll
-            for (int i = 1; i <= 4; ++i)
+        for (int j = 3; j >= 1; --j)  // bits 30..28: i = 0
+            f = __funnelshift_l(win[(r + 3 - j) % 7][4] + ~win[(r + 3 + j) % 7][4], f, 1);
 #pragma unroll
-                for (int j = -3; j <= 3; ++j, ++k)
-                    f |= static_cast<uint32_t>(tile[cy + j][cx + i] >= tile[cy - j][cx - i]) << k;
+        for (int i = 4; i >= 1; --i)
 #pragma unroll
-            for (int j = 1; j <= 3; ++j, ++k) f |= static_cast<uint32_t>(tile[cy + j][cx] >= tile[cy - j][cx]) << k;
-        }
-        F[(size_t)y * W + x] = f;
+            for (int j = 3; j >= -3; --j)  // bits (i-1)*7 + j+3, highest first
+                f = __funnelshift_l(win[(r + 3 - j) % 7][4 - i] + ~win[(r + 3 + j) % 7][4 + i], f, 1);
+        const bool ok = x_ok && y >= 3 && y <= H - 4;
+        F[(size_t)y * W + x] = ok ? f : 0u;
     }
 }
 
-__global__ void __launch_bounds__(256) census_kernel(const uint8_t* __restrict__ left,
-                                                     const uint8_t* __restrict__ right, uint32_t* __restrict__ Fb,
-                                                     uint32_t* __restrict__ Fm, int W, int H) {
+__global__ void __launch_bounds__(kCtW) census_kernel(const uint8_t* __restrict__ left, const uint8_t* __restrict__ right,
+                                                      uint32_t* __restrict__ Fb, uint32_t* __restrict__ Fm, int W,
+                                                      int H) {
     census_body(left, right, Fb, Fm, W, H, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-__global__ void __launch_bounds__(256) census_batch_kernel(const __grid_constant__ JobTable<CensusJob> t) {
+__global__ void __launch_bounds__(kCtW) census_batch_kernel(const __grid_constant__ JobTable<CensusJob> t) {
     const int p = find_job(t, blockIdx.x);
     const CensusJob& j = t.job[p];
     const int b = blockIdx.x - t.start[p];
@@ -68,63 +80,86 @@ cudaError_t launch_census_batch(JobTable<CensusJob>& t, cudaStream_t stream) {
     t.start[0] = 0;
     for (int i = 0; i < t.n; ++i)
         t.start[i + 1] = t.start[i] + 2 * ((t.job[i].W + kCtW - 1) / kCtW) * ((t.job[i].H + kCtH - 1) / kCtH);
-    census_batch_kernel<<<t.start[t.n], dim3(32, 8), 0, stream>>>(t);
+    census_batch_kernel<<<t.start[t.n], kCtW, 0, stream>>>(t);
     return cudaGetLastError();
 }
 
 cudaError_t launch_census(const uint8_t* left, const uint8_t* right, uint32_t* Fb, uint32_t* Fm, int W, int H,
                           cudaStream_t stream) {
     dim3 grid((W + kCtW - 1) / kCtW, (H + kCtH - 1) / kCtH, 2);
-    census_kernel<<<grid, dim3(32, 8), 0, stream>>>(left, right, Fb, Fm, W, H);
+    census_kernel<<<grid, kCtW, 0, stream>>>(left, right, Fb, Fm, W, H);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // Eq. 2: MC(x, y, d) = bitcount(F_base(x, y) XOR F_match(x - d, y)), with the
 // match feature 0 left of the image.  A CTA covers kMcSeg pixels of one row;
-// the match features x0-D+1 .. x0+kMcSeg-1 are staged in shared memory (the 1D
-// tiling of Section 3.1) and every thread writes 32-bit words of two paired
-// words each (D known at compile time, so the item split is shifts and
-// multiplies).  The kernel is bound by the bit-count pipe (16 lanes/clk/SM).
+// the match features x0-D+1 .. x0+kMcSeg-1 and the base features are staged in
+// shared memory (the 1D tiling of Section 3.1).  A thread computes one output
+// word (paired words i0 = 2*wi and i0 + 1, i.e. d = i0, i0 + D/2, i0 + 1,
+// i0 + 1 + D/2) for kMcPix consecutive pixels, so that the match features it
+// loads are shared between neighbouring pixels; consecutive threads take
+// consecutive words, which keeps the stores coalesced.  The kernel is bound by
+// the bit-count pipe.
 // ---------------------------------------------------------------------------
-constexpr int kMcSeg = 64;
+constexpr int kMcSeg = 128, kMcPix = 4, kMcThreads = 128;
 
 template <int D>
 __device__ __forceinline__ void cost_body(const uint32_t* __restrict__ Fb, const uint32_t* __restrict__ Fm,
                                           uint8_t* __restrict__ MC, int W, int seg, int y) {
-    __shared__ uint32_t fm[D - 1 + kMcSeg];  // match features x0-D+1 .. x0+kMcSeg-1
-    __shared__ uint32_t fb[kMcSeg];
-    constexpr int Q = D / 4, half = D / 2;
+    constexpr int Q = D / 4, half = D / 2, NF = kMcSeg + D;  // words per pixel; staged match features (even)
+    __shared__ __align__(16) uint32_t fm[NF];  // fm[k] = F_match(x0 - D + k)
+    __shared__ __align__(16) uint32_t fb[kMcSeg];
     const int x0 = seg * kMcSeg;
     const uint32_t* fmrow = Fm + (size_t)y * W;
-    for (int i = threadIdx.x; i < D - 1 + kMcSeg; i += 256) {
-        const int gx = x0 - (D - 1) + i;
+    for (int i = threadIdx.x; i < NF; i += kMcThreads) {
+        const int gx = x0 - D + i;
         fm[i] = (gx >= 0 && gx < W) ? fmrow[gx] : 0u;
     }
-    for (int i = threadIdx.x; i < kMcSeg; i += 256) fb[i] = (x0 + i < W) ? Fb[(size_t)y * W + x0 + i] : 0u;
+    for (int i = threadIdx.x; i < kMcSeg; i += kMcThreads) fb[i] = (x0 + i < W) ? Fb[(size_t)y * W + x0 + i] : 0u;
     __syncthreads();
     const int npx = min(kMcSeg, W - x0);
+    const int items = ((npx + kMcPix - 1) / kMcPix) * Q;
     uint32_t* out = reinterpret_cast<uint32_t*>(MC + ((size_t)y * W + x0) * D);
-    for (int t = threadIdx.x; t < npx * Q; t += 256) {
-        const int px = t / Q, i0 = 2 * (t % Q);
-        const uint32_t b = fb[px];
-        const uint32_t* f = fm + px + D - 1 - i0;  // f[-d'] = F_match(x - i0 - d')
-        const uint32_t c0 = __popc(b ^ f[0]);
-        const uint32_t c1 = __popc(b ^ f[-half]);
-        const uint32_t c2 = __popc(b ^ f[-1]);
-        const uint32_t c3 = __popc(b ^ f[-1 - half]);
-        out[t] = __byte_perm(c0 | (c2 << 16), c1 | (c3 << 16), 0x6240u);  // [c0, c1, c2, c3]
+    for (int t = threadIdx.x; t < items; t += kMcThreads) {
+        const int g = t / Q, wi = t - g * Q, i0 = 2 * wi, px = g * kMcPix;
+        // F_match(x - d) for x = x0 + px + p lives at fm[px + p + D - d]
+        const int ba = px + D - i0 - 2;  // d = i0 + 1 - p' ... : fm[ba + p + 1] is d = i0 + 1, fm[ba + p + 2] is d = i0
+        const int bb = ba - half;
+        uint32_t ra[kMcPix + 2], rb[kMcPix + 2];
+#pragma unroll
+        for (int k = 0; k < kMcPix + 2; k += 2) {
+            const uint2 va = *reinterpret_cast<const uint2*>(fm + ba + k);
+            const uint2 vb = *reinterpret_cast<const uint2*>(fm + bb + k);
+            ra[k] = va.x;
+            ra[k + 1] = va.y;
+            rb[k] = vb.x;
+            rb[k + 1] = vb.y;
+        }
+        const uint4 vb4 = *reinterpret_cast<const uint4*>(fb + px);
+        const uint32_t b4[4] = {vb4.x, vb4.y, vb4.z, vb4.w};
+#pragma unroll
+        for (int p = 0; p < kMcPix; ++p) {
+            if (px + p >= npx) break;
+            const uint32_t b = b4[p];
+            const uint32_t c0 = __popc(b ^ ra[p + 2]);  // d = i0
+            const uint32_t c1 = __popc(b ^ rb[p + 2]);  // d = i0 + D/2
+            const uint32_t c2 = __popc(b ^ ra[p + 1]);  // d = i0 + 1
+            const uint32_t c3 = __popc(b ^ rb[p + 1]);  // d = i0 + 1 + D/2
+            out[(px + p) * Q + wi] = __byte_perm(c0 | (c2 << 16), c1 | (c3 << 16), 0x6240u);  // [c0, c1, c2, c3]
+        }
     }
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) cost_kernel(const uint32_t* __restrict__ Fb, const uint32_t* __restrict__ Fm,
-                                                   uint8_t* __restrict__ MC, int W) {
+__global__ void __launch_bounds__(kMcThreads) cost_kernel(const uint32_t* __restrict__ Fb,
+                                                          const uint32_t* __restrict__ Fm, uint8_t* __restrict__ MC,
+                                                          int W) {
     cost_body<D>(Fb, Fm, MC, W, blockIdx.x, blockIdx.y);
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) cost_batch_kernel(const __grid_constant__ JobTable<CostJob> t) {
+__global__ void __launch_bounds__(kMcThreads) cost_batch_kernel(const __grid_constant__ JobTable<CostJob> t) {
     const int p = find_job(t, blockIdx.x);
     const CostJob& j = t.job[p];
     const int b = blockIdx.x - t.start[p];
@@ -136,7 +171,7 @@ template <int D>
 static cudaError_t launch_cost_batch_t(JobTable<CostJob>& t, cudaStream_t s) {
     t.start[0] = 0;
     for (int i = 0; i < t.n; ++i) t.start[i + 1] = t.start[i] + ((t.job[i].W + kMcSeg - 1) / kMcSeg) * t.job[i].H;
-    cost_batch_kernel<D><<<t.start[t.n], 256, 0, s>>>(t);
+    cost_batch_kernel<D><<<t.start[t.n], kMcThreads, 0, s>>>(t);
     return cudaGetLastError();
 }
 
@@ -157,7 +192,7 @@ cudaError_t launch_cost_batch(JobTable<CostJob>& t, int D, cudaStream_t stream) 
 template <int D>
 static cudaError_t launch_cost_t(const uint32_t* Fb, const uint32_t* Fm, uint8_t* MC, int W, int H, cudaStream_t s) {
     const dim3 grid((W + kMcSeg - 1) / kMcSeg, H);
-    cost_kernel<D><<<grid, 256, 0, s>>>(Fb, Fm, MC, W);
+    cost_kernel<D><<<grid, kMcThreads, 0, s>>>(Fb, Fm, MC, W);
     return cudaGetLastError();
 }
 
