@@ -274,6 +274,7 @@ static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, 
     a.P1x2 = static_cast<uint32_t>(p.P1) * 0x10001u;
     a.P2x2 = static_cast<uint32_t>(p.P2) * 0x10001u;
     a.pair = p.n_paths >= 4;
+    a.s8 = sum_fits_u8(p.n_paths, p.P2);
     a.rx = 0;
     a.wta = 0;
     a.phase = 0;
@@ -407,6 +408,11 @@ struct BatchItem {
     size_t offset;  // of the pair's region in the arena
 };
 
+// Items launched together share D, the path count and the sum storage.
+static std::tuple<int, int, bool> batch_key(const BatchItem& it) {
+    return std::make_tuple(it.p.D, it.p.n_paths, sum_fits_u8(it.p.n_paths, it.p.P2));
+}
+
 static int launches_per_group(int n_paths) { return 4 + (n_paths == 8 ? 3 : 1); }
 
 // Enqueue the batched path for items[b, e) (one wave, same stream).
@@ -427,11 +433,10 @@ static int enqueue_wave(sgm_ctx* ctx, std::vector<BatchItem>& items, size_t b, s
             it.right = base + l.in_right;
         }
     }
-    // groups of equal (D, n_paths) are contiguous (items are sorted)
+    // groups of equal (D, n_paths, byte sums) are contiguous (items are sorted)
     for (size_t g0 = b; g0 < e;) {
         size_t g1 = g0;
-        while (g1 < e && g1 - g0 < static_cast<size_t>(kMaxBatch) && items[g1].p.D == items[g0].p.D &&
-               items[g1].p.n_paths == items[g0].p.n_paths)
+        while (g1 < e && g1 - g0 < static_cast<size_t>(kMaxBatch) && batch_key(items[g1]) == batch_key(items[g0]))
             ++g1;
         const int n = static_cast<int>(g1 - g0), D = items[g0].p.D, n_paths = items[g0].p.n_paths;
         JobTable<CensusJob> ct{};
@@ -458,6 +463,7 @@ static int enqueue_wave(sgm_ctx* ctx, std::vector<BatchItem>& items, size_t b, s
             a.P1x2 = static_cast<uint32_t>(it.p.P1) * 0x10001u;
             a.P2x2 = static_cast<uint32_t>(it.p.P2) * 0x10001u;
             a.pair = it.p.n_paths >= 4;
+            a.s8 = sum_fits_u8(it.p.n_paths, it.p.P2);
             st.job[k] = a;
             uint8_t* dst = is_device_ptr(it.out) ? it.out : base + l.out;
             dt.job[k] = MedianJob{base + l.raw, dst, it.p.W, it.p.H};
@@ -497,7 +503,7 @@ static int enqueue_wave(sgm_ctx* ctx, std::vector<BatchItem>& items, size_t b, s
 static int run_batch(sgm_ctx* ctx, std::vector<BatchItem>& items, uint8_t** arena, size_t* arena_bytes,
                      bool clear_graphs, cudaStream_t s) {
     std::stable_sort(items.begin(), items.end(), [](const BatchItem& x, const BatchItem& y) {
-        return std::tie(x.p.D, x.p.n_paths) < std::tie(y.p.D, y.p.n_paths);
+        return batch_key(x) < batch_key(y);
     });
     size_t free_b = 0, total_b = 0;
     CUDA_TRY(ctx, cudaMemGetInfo(&free_b, &total_b));
@@ -636,7 +642,7 @@ static int slot_launch(sgm_ctx* ctx, ServeSlot& sl, size_t budget) {
         }
     }
     std::stable_sort(items.begin(), items.end(), [](const BatchItem& x, const BatchItem& y) {
-        return std::tie(x.p.D, x.p.n_paths) < std::tie(y.p.D, y.p.n_paths);
+        return batch_key(x) < batch_key(y);
     });
     size_t total = 0;
     for (BatchItem& it : items) {
@@ -1107,6 +1113,7 @@ cudaError_t enqueue_path_static(const Problem& p, uint8_t* arena, const uint8_t*
     a.P1x2 = static_cast<uint32_t>(p.P1) * 0x10001u;
     a.P2x2 = static_cast<uint32_t>(p.P2) * 0x10001u;
     a.pair = p.n_paths >= 4;
+    a.s8 = sum_fits_u8(p.n_paths, p.P2);
     if ((e = launch_sweep_h(a, s)) != cudaSuccess) return e;
     if (!a.pair) {
         a.wta = 1;

@@ -29,19 +29,15 @@ __device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b) {
     return d;
 }
 
-__device__ __forceinline__ uint32_t redux_min(uint32_t v) {
-    uint32_t d;
-    asm volatile("redux.sync.min.u32 %0, %1, 0xffffffff;" : "=r"(d) : "r"(v));
-    return d;
-}
+__device__ __forceinline__ uint32_t redux_min(uint32_t v) { return __reduce_min_sync(0xffffffffu, v); }
 
-// Shuffles are volatile so that their order against the reductions is kept:
-// the next step's neighbour exchange is issued before the current step's
-// minimum reduction, which lets the two latencies overlap.
-__device__ __forceinline__ uint32_t shfl_idx(uint32_t v, int src) {
-    uint32_t d;
-    asm volatile("shfl.sync.idx.b32 %0, %1, %2, 0x1f, 0xffffffff;" : "=r"(d) : "r"(v), "r"(src));
-    return d;
+__device__ __forceinline__ uint32_t shfl_idx(uint32_t v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
+// Paired bytes held in registers -> packed u16x2 words.
+template <int K>
+__device__ __forceinline__ void unpack_regs(const uint32_t (&b)[(K + 1) / 2], uint32_t (&w)[K]) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) w[j] = __byte_perm(b[j >> 1], 0u, (j & 1) ? 0x4342u : 0x4140u);
 }
 
 // ---------------------------------------------------------------------------
@@ -292,20 +288,6 @@ __device__ __forceinline__ int find_job(const Table& t, int b) {
             hi = mid - 1;
     }
     return lo;
-}
-
-// ---------------------------------------------------------------------------
-// cp.async staging (16-byte global -> shared copies, completed per thread by
-// wait_group; a __syncwarp then publishes the data to the whole warp).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp16(void* smem_dst, const void* gmem_src) {
-    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 }  // namespace sgm

@@ -10,7 +10,7 @@ namespace sgm {
 struct SweepArgs {
     const uint8_t* MC;  // paired costs [H][W][D]
     uint8_t* Lx;        // scratch: one direction's path costs, paired [H][W][D]
-    uint32_t* S;        // packed sums [H][W][D/2]
+    uint32_t* S;        // sums: packed u16x2 words [H][W][D/2], or paired bytes [H][W][D] (s8)
     uint8_t* raw;       // winner-take-all disparity [H][W] (final vertical sweep)
     uint16_t* Sdbg;     // optional natural-order S [H][W][D] (debug)
     int W, H, D;
@@ -21,7 +21,13 @@ struct SweepArgs {
     int phase;            // vertical-type pairs: 0 = both phases, 1 = first half of each path
                           // (saves the path state), 2 = second half (restores it)
     uint32_t* state;      // path states between phases 1 and 2 (sweep_state_words)
+    int s8;               // pairs: S kept as paired bytes [H][W][D] instead of u16x2 words
 };
+
+// Every sum S held between sweeps fits a byte: with 2 paths S = L_LR <= 31 + P2
+// <= 255 always; with 4 paths S = L_LR + L_RL <= 2 * (31 + P2) before the
+// vertical pair's winner-take-all (L_r - MC <= P2 from Eq. 3, MC <= 31).
+inline bool sum_fits_u8(int n_paths, int P2) { return n_paths == 2 || (n_paths == 4 && 2 * (31 + P2) <= 255); }
 
 // ---------------------------------------------------------------------------
 // Batched execution: one launch per stage covers many pairs.  A job table is
@@ -80,7 +86,7 @@ inline size_t sweep_state_words(int W, int D) {
 }
 cudaError_t launch_median(const uint8_t* raw, uint8_t* disp, int W, int H, cudaStream_t stream);
 // Batched forms; every job of a cost or sweep table has the same D (and, for
-// sweeps, the same pair / rx / phase / wta settings).  `start` is filled in.
+// sweeps, the same pair / rx / phase / wta / s8 settings).  `start` is filled in.
 cudaError_t launch_census_batch(JobTable<CensusJob>& t, cudaStream_t stream);
 cudaError_t launch_cost_batch(JobTable<CostJob>& t, int D, cudaStream_t stream);
 cudaError_t launch_median_batch(JobTable<MedianJob>& t, cudaStream_t stream);
@@ -91,8 +97,8 @@ cudaError_t launch_unpair_cost(const uint8_t* MC, uint8_t* out, int W, int H, in
 
 bool supported_D(int D);
 
-// One-time kernel attributes (shared-memory carve-outs); call before any
-// launch or stream capture on the current device.
+// One-time kernel attributes; call before any launch or stream capture on the
+// current device.
 cudaError_t init_kernel_attributes();
 
 }  // namespace sgm

@@ -23,14 +23,33 @@ constexpr int kCtW = 64, kCtH = 16;
 __device__ __forceinline__ void census_body(const uint8_t* __restrict__ left, const uint8_t* __restrict__ right,
                                             uint32_t* __restrict__ Fb, uint32_t* __restrict__ Fm, int W, int H,
                                             int bx, int by, int bz) {
-    __shared__ uint8_t tile[kCtH + 6][kCtW + 8];
+    constexpr int TW = kCtW + 8, TH = kCtH + 6;
+    __shared__ uint8_t tile[TH][TW];
     const uint8_t* img = bz ? right : left;
     uint32_t* F = bz ? Fm : Fb;
     const int x0 = bx * kCtW, y0 = by * kCtH;
-    for (int i = threadIdx.x; i < (kCtH + 6) * (kCtW + 8); i += kCtW) {
-        const int ty = i / (kCtW + 8), tx = i % (kCtW + 8);
-        const int gx = x0 - 4 + tx, gy = y0 - 3 + ty;
-        tile[ty][tx] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? img[(size_t)gy * W + gx] : 0;
+    // Thread t stages tile column t (and t + kCtW for the last 8 columns): all
+    // loads are issued before the first shared-memory store.
+    {
+        uint8_t v[2][TH];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int tx = threadIdx.x + h * kCtW, gx = x0 - 4 + tx;
+            const bool xin = tx < TW && gx >= 0 && gx < W;
+#pragma unroll
+            for (int ty = 0; ty < TH; ++ty) {
+                const int gy = y0 - 3 + ty;
+                v[h][ty] = (xin && gy >= 0 && gy < H) ? __ldg(img + (size_t)gy * W + gx) : uint8_t(0);
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int tx = threadIdx.x + h * kCtW;
+            if (tx < TW) {
+#pragma unroll
+                for (int ty = 0; ty < TH; ++ty) tile[ty][tx] = v[h][ty];
+            }
+        }
     }
     __syncthreads();
     const int lx = threadIdx.x, x = x0 + lx;
@@ -112,11 +131,28 @@ __device__ __forceinline__ void cost_body(const uint32_t* __restrict__ Fb, const
     __shared__ __align__(16) uint32_t fb[kMcSeg];
     const int x0 = seg * kMcSeg;
     const uint32_t* fmrow = Fm + (size_t)y * W;
-    for (int i = threadIdx.x; i < NF; i += kMcThreads) {
-        const int gx = x0 - D + i;
-        fm[i] = (gx >= 0 && gx < W) ? fmrow[gx] : 0u;
+    {
+        // every load is issued before the first shared-memory store
+        constexpr int NI = (NF + kMcThreads - 1) / kMcThreads, NB = kMcSeg / kMcThreads;
+        uint32_t vm[NI], vb[NB];
+#pragma unroll
+        for (int it = 0; it < NI; ++it) {
+            const int i = threadIdx.x + it * kMcThreads, gx = x0 - D + i;
+            vm[it] = (i < NF && gx >= 0 && gx < W) ? __ldg(fmrow + gx) : 0u;
+        }
+#pragma unroll
+        for (int it = 0; it < NB; ++it) {
+            const int i = threadIdx.x + it * kMcThreads;
+            vb[it] = (x0 + i < W) ? __ldg(Fb + (size_t)y * W + x0 + i) : 0u;
+        }
+#pragma unroll
+        for (int it = 0; it < NI; ++it) {
+            const int i = threadIdx.x + it * kMcThreads;
+            if (i < NF) fm[i] = vm[it];
+        }
+#pragma unroll
+        for (int it = 0; it < NB; ++it) fb[threadIdx.x + it * kMcThreads] = vb[it];
     }
-    for (int i = threadIdx.x; i < kMcSeg; i += kMcThreads) fb[i] = (x0 + i < W) ? Fb[(size_t)y * W + x0 + i] : 0u;
     __syncthreads();
     const int npx = min(kMcSeg, W - x0);
     const int items = ((npx + kMcPix - 1) / kMcPix) * Q;
@@ -244,66 +280,71 @@ __device__ __forceinline__ void sort3(int& a, int& b, int& c) {
 
 __device__ __forceinline__ int med3(int a, int b, int c) { return max(min(a, b), min(max(a, b), c)); }
 
-// A CTA covers a 128 x 8 tile (4 pixels per thread along x) staged with its
-// one-pixel halo in shared memory.
+// A CTA of 128 threads covers a 128 x 8 tile: thread t walks column x0 + t
+// down the tile with its three columns of the 3 x 10 neighbourhood loaded
+// (clamped to the image) into registers up front; each row's three values are
+// sorted once and shared by the three windows that contain the row.
+constexpr int kMedW = 128, kMedH = 8;
+
 __device__ __forceinline__ void median_body(const uint8_t* __restrict__ raw, uint8_t* __restrict__ out, int W, int H,
                                             int bx, int by) {
-    __shared__ uint8_t t[10][136];
-    const int x0 = bx * 128, y0 = by * 8;
-    for (int i = threadIdx.y * 32 + threadIdx.x; i < 10 * 130; i += 256) {
-        const int ty = i / 130, tx = i % 130;
-        const int gx = min(max(x0 - 1 + tx, 0), W - 1), gy = min(max(y0 - 1 + ty, 0), H - 1);
-        t[ty][tx] = raw[(size_t)gy * W + gx];
-    }
-    __syncthreads();
-    const int y = y0 + threadIdx.y;
-    if (y >= H) return;
+    const int x = bx * kMedW + threadIdx.x, y0 = by * kMedH;
+    if (x >= W) return;
+    const int xl = max(x - 1, 0), xr = min(x + 1, W - 1);
+    int lo[kMedH + 2], mid[kMedH + 2], hi[kMedH + 2];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int lx = threadIdx.x + 32 * k, x = x0 + lx;
-        if (x >= W) continue;
-        const int cx = lx + 1, cy = threadIdx.y + 1;
-        const size_t p = (size_t)y * W + x;
-        if (x == 0 || y == 0 || x == W - 1 || y == H - 1) {
-            out[p] = t[cy][cx];
-            continue;
+    for (int r = 0; r < kMedH + 2; ++r) {
+        const int gy = min(max(y0 - 1 + r, 0), H - 1);
+        const uint8_t* row = raw + (size_t)gy * W;
+        lo[r] = __ldg(row + xl);
+        mid[r] = __ldg(row + x);
+        hi[r] = __ldg(row + xr);
+    }
+    int c[kMedH];  // raw centre values: the border ring keeps them
+#pragma unroll
+    for (int k = 0; k < kMedH; ++k) c[k] = mid[k + 1];
+#pragma unroll
+    for (int r = 0; r < kMedH + 2; ++r) sort3(lo[r], mid[r], hi[r]);
+    const bool x_inner = x > 0 && x < W - 1;
+#pragma unroll
+    for (int k = 0; k < kMedH; ++k) {
+        const int y = y0 + k;
+        if (y >= H) break;
+        int v = c[k];
+        if (x_inner && y > 0 && y < H - 1) {
+            const int l = max(max(lo[k], lo[k + 1]), lo[k + 2]);
+            const int m = med3(mid[k], mid[k + 1], mid[k + 2]);
+            const int h = min(min(hi[k], hi[k + 1]), hi[k + 2]);
+            v = med3(l, m, h);
         }
-        int a0 = t[cy - 1][cx - 1], b0 = t[cy - 1][cx], c0 = t[cy - 1][cx + 1];
-        int a1 = t[cy][cx - 1], b1 = t[cy][cx], c1 = t[cy][cx + 1];
-        int a2 = t[cy + 1][cx - 1], b2 = t[cy + 1][cx], c2 = t[cy + 1][cx + 1];
-        sort3(a0, b0, c0);
-        sort3(a1, b1, c1);
-        sort3(a2, b2, c2);
-        const int lo = max(max(a0, a1), a2);
-        const int mid = med3(b0, b1, b2);
-        const int hi = min(min(c0, c1), c2);
-        out[p] = static_cast<uint8_t>(med3(lo, mid, hi));
+        out[(size_t)y * W + x] = static_cast<uint8_t>(v);
     }
 }
 
-__global__ void __launch_bounds__(256) median_kernel(const uint8_t* __restrict__ raw, uint8_t* __restrict__ out,
+__global__ void __launch_bounds__(kMedW) median_kernel(const uint8_t* __restrict__ raw, uint8_t* __restrict__ out,
                                                      int W, int H) {
     median_body(raw, out, W, H, blockIdx.x, blockIdx.y);
 }
 
-__global__ void __launch_bounds__(256) median_batch_kernel(const __grid_constant__ JobTable<MedianJob> t) {
+__global__ void __launch_bounds__(kMedW) median_batch_kernel(const __grid_constant__ JobTable<MedianJob> t) {
     const int p = find_job(t, blockIdx.x);
     const MedianJob& j = t.job[p];
     const int b = blockIdx.x - t.start[p];
-    const int tx = (j.W + 127) / 128;
+    const int tx = (j.W + kMedW - 1) / kMedW;
     median_body(j.raw, j.out, j.W, j.H, b % tx, b / tx);
 }
 
 cudaError_t launch_median_batch(JobTable<MedianJob>& t, cudaStream_t stream) {
     t.start[0] = 0;
-    for (int i = 0; i < t.n; ++i) t.start[i + 1] = t.start[i] + ((t.job[i].W + 127) / 128) * ((t.job[i].H + 7) / 8);
-    median_batch_kernel<<<t.start[t.n], dim3(32, 8), 0, stream>>>(t);
+    for (int i = 0; i < t.n; ++i)
+        t.start[i + 1] = t.start[i] + ((t.job[i].W + kMedW - 1) / kMedW) * ((t.job[i].H + kMedH - 1) / kMedH);
+    median_batch_kernel<<<t.start[t.n], kMedW, 0, stream>>>(t);
     return cudaGetLastError();
 }
 
 cudaError_t launch_median(const uint8_t* raw, uint8_t* disp, int W, int H, cudaStream_t stream) {
-    dim3 grid((W + 127) / 128, (H + 7) / 8);
-    median_kernel<<<grid, dim3(32, 8), 0, stream>>>(raw, disp, W, H);
+    dim3 grid((W + kMedW - 1) / kMedW, (H + kMedH - 1) / kMedH);
+    median_kernel<<<grid, kMedW, 0, stream>>>(raw, disp, W, H);
     return cudaGetLastError();
 }
 

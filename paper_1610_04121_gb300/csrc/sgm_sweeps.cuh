@@ -11,15 +11,21 @@
 // second half adds the other direction's stored L_r to its own.  The exchange
 // is warp-local (G = 16) or through a 64-thread named barrier (G = 32).
 //
-// Each path streams its inputs through a private shared-memory ring filled
-// by cp.async a few chunks ahead, keeps its step loop on shared memory and
-// registers, and writes its outputs with coalesced vector stores.
+// Each lane streams its own bytes of every step's inputs (costs, the other
+// direction's stored L_r, sums) straight from global memory into registers,
+// one chunk of PF steps ahead of the recurrence, and writes its outputs with
+// one coalesced store per step; no shared memory is used.
 //
 //   sweep_h : left-to-right with right-to-left, one row per line;
-//             writes S = L_LR + L_RL (packed u16x2).
+//             writes S = L_LR + L_RL.
 //   sweep_v : top-to-bottom with bottom-to-top along columns (RX = 0) or along
 //             the wrapped diagonals of Section 3.2 (RX = +1 / -1); either adds
 //             its pair sum into S or, for the last axis, finishes with Eq. 4.
+//
+// S is kept either as packed u16x2 words [H][W][D/2] or, when every value it
+// holds before the winner-take-all fits a byte (2 or 4 paths with
+// 2 * (31 + P2) <= 255, see sum_fits_u8), as paired bytes [H][W][D] like the
+// costs (template flag S8).
 #pragma once
 
 #include "sgm_device.cuh"
@@ -46,69 +52,161 @@ enum WalkMode {
     kSingleWta = 5  // 2-path mode, top-to-bottom: raw = argmin_d (S + L)
 };
 
-// Shared-memory staging of one path during a walk in MODE: a ring of NSLOT
-// chunks of CH pixels per input stream it reads (costs; stored L of the other
-// direction; sums).  Row walks read contiguous pixels and take longer chunks.
-template <int D, int MODE, bool ROW>
-struct Stage {
+template <int MODE>
+struct ModeIO {
     static constexpr bool IN_LO = MODE == kSumH || MODE == kAcc || MODE == kWta2;
     static constexpr bool IN_S = MODE == kAcc || MODE == kWta2 || MODE == kSingleWta;
     static constexpr bool OUT_LX = MODE == kStoreL;
     static constexpr bool OUT_S = MODE == kSumH || MODE == kAcc || MODE == kSingleH;
     static constexpr bool WTA = MODE == kWta2 || MODE == kSingleWta;
-    static constexpr int CH = ROW ? (D <= 128 ? 16 : 8) : (D <= 64 ? 16 : (D <= 128 ? 8 : 4));  // pixels per chunk
-    static constexpr int NSLOT = 3;                                // chunks in flight + 1
-    static constexpr int MC_RING = NSLOT * CH * D;
-    static constexpr int LO_RING = IN_LO ? NSLOT * CH * D : 0;
-    static constexpr int S_RING = IN_S ? NSLOT * CH * 2 * D : 0;
-    static constexpr int BYTES = MC_RING + LO_RING + S_RING;
 };
 
-constexpr int cmax(int a, int b) { return a > b ? a : b; }
-
-// Staging bytes per path and per block of each kernel (the largest of its walks).
-template <int D, bool PAIR>
-struct HStage {
-    static constexpr int PATH =
-        PAIR ? cmax(Stage<D, kStoreL, true>::BYTES, Stage<D, kSumH, true>::BYTES) : Stage<D, kSingleH, true>::BYTES;
-    static constexpr int BLOCK = kWarpsPerBlock * PathShape<D>::PPW * PATH;
-};
-template <int D, int PH, bool WTA, bool PAIR>
-struct VStage {
-    static constexpr int SECOND = WTA ? Stage<D, kWta2, false>::BYTES : Stage<D, kAcc, false>::BYTES;
-    static constexpr int FIRST = Stage<D, kStoreL, false>::BYTES;
-    static constexpr int PATH =
-        !PAIR ? Stage<D, kSingleWta, false>::BYTES : (PH == 1 ? FIRST : (PH == 2 ? SECOND : cmax(FIRST, SECOND)));
-    static constexpr int BLOCK = kWarpsPerBlock * PathShape<D>::PPW * PATH;
-};
-
-// Lines (rows or columns) per block: with G = 32 a pair takes two warps.
-template <int D, bool PAIR>
-constexpr int lines_per_block() {
-    return (PathShape<D>::G == 32 && PAIR) ? kWarpsPerBlock / 2 : kWarpsPerBlock;
+// Register prefetch: a walk proceeds in chunks of PF steps; at the start of a
+// chunk the loads of the next chunk are issued, so every load has at least one
+// chunk (PF steps of the recurrence) to arrive.  PF is chosen so that the two
+// chunks of inputs held in registers stay near 96 registers.
+__host__ __device__ constexpr int prefetch_steps(int regs_per_step) {
+    return 48 / regs_per_step > 16 ? 16 : (48 / regs_per_step < 4 ? 4 : 48 / regs_per_step);
 }
 
-// Which line and direction this warp (or, for G = 16, this lane's half) walks.
-template <int D, bool PAIR>
-struct LaneRole {
-    int line, dir, pl, slot;  // slot: index of this path's staging area in the block
-    __device__ __forceinline__ LaneRole(int bx) {
-        constexpr int G = PathShape<D>::G;
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        pl = lane & (G - 1);
-        if constexpr (G == 16) {
-            line = bx * kWarpsPerBlock + warp;
-            dir = lane >> 4;
-            slot = 2 * warp + dir;
-        } else if constexpr (PAIR) {
-            line = bx * (kWarpsPerBlock / 2) + (warp >> 1);
-            dir = warp & 1;
-            slot = warp;
-        } else {
-            line = bx * kWarpsPerBlock + warp;
-            dir = 0;
-            slot = warp;
+template <int N>
+struct Regs {
+    uint32_t r[N];
+};
+template <>
+struct Regs<0> {};
+
+// Global loads of one lane's share of a step: K paired-byte values (2K bytes
+// at byte offset 2K * pl of the pixel) or K packed words.  Costs are read
+// through the non-coherent path (written by an earlier kernel); stored L_r
+// and sums may have been written earlier in the same kernel or by the other
+// warp of the pair, so they bypass L1.
+template <int K, bool NC>
+__device__ __forceinline__ void ldg_pairs(const uint8_t* p, uint32_t (&r)[(K + 1) / 2]) {
+    if constexpr (K == 2) {
+        r[0] = NC ? __ldg(reinterpret_cast<const unsigned*>(p)) : __ldcg(reinterpret_cast<const unsigned*>(p));
+    } else if constexpr (K == 4) {
+        const uint2 v = NC ? __ldg(reinterpret_cast<const uint2*>(p)) : __ldcg(reinterpret_cast<const uint2*>(p));
+        r[0] = v.x;
+        r[1] = v.y;
+    } else if constexpr (K == 8) {
+        const uint4 v = NC ? __ldg(reinterpret_cast<const uint4*>(p)) : __ldcg(reinterpret_cast<const uint4*>(p));
+        r[0] = v.x;
+        r[1] = v.y;
+        r[2] = v.z;
+        r[3] = v.w;
+    } else {
+        // odd K (16-lane paths with D = 32, 96, 160, 224): 2-byte aligned
+        const unsigned short* h = reinterpret_cast<const unsigned short*>(p);
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const uint32_t v = NC ? __ldg(h + j) : __ldcg(h + j);
+            if (j & 1)
+                r[j >> 1] |= v << 16;
+            else
+                r[j >> 1] = v;
         }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void ldg_words(const uint32_t* p, uint32_t (&w)[K]) {
+    if constexpr (K % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < K; j += 4) {
+            const uint4 v = __ldcg(reinterpret_cast<const uint4*>(p + j));
+            w[j] = v.x;
+            w[j + 1] = v.y;
+            w[j + 2] = v.z;
+            w[j + 3] = v.w;
+        }
+    } else if constexpr (K % 2 == 0) {
+#pragma unroll
+        for (int j = 0; j < K; j += 2) {
+            const uint2 v = __ldcg(reinterpret_cast<const uint2*>(p + j));
+            w[j] = v.x;
+            w[j + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < K; ++j) w[j] = __ldcg(p + j);
+    }
+}
+
+// One step's inputs for one lane, and their loads at byte offset `off` of the
+// pixel's paired cube entry (the word offset of u16 sums is off / 2).
+template <int K, int MODE, bool S8>
+struct StepIn {
+    using M = ModeIO<MODE>;
+    static constexpr int PW = (K + 1) / 2;
+    static constexpr int REGS = PW + (M::IN_LO ? PW : 0) + (M::IN_S ? (S8 ? PW : K) : 0);
+    Regs<PW> mc;
+    Regs<M::IN_LO ? PW : 0> lo;
+    Regs<M::IN_S ? (S8 ? PW : K) : 0> s;
+
+    __device__ __forceinline__ void load(const SweepArgs& a, size_t off) {
+        ldg_pairs<K, true>(a.MC + off, mc.r);
+        if constexpr (M::IN_LO) ldg_pairs<K, false>(a.Lx + off, lo.r);
+        if constexpr (M::IN_S) {
+            if constexpr (S8)
+                ldg_pairs<K, false>(reinterpret_cast<const uint8_t*>(a.S) + off, s.r);
+            else
+                ldg_words<K>(a.S + off / 2, s.r);
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Walk geometry.  A cursor names the pixel of one step; `advance` moves it to
+// the next pixel of the walk.
+// ---------------------------------------------------------------------------
+// Pixels of a row walk: x = x0 + dx * i in row y.
+struct RowGeo {
+    static constexpr bool kResets = false;
+    int rowbase, x0, dx;
+    struct Cursor {
+        int pix;
+    };
+    __device__ __forceinline__ Cursor start() const { return Cursor{rowbase + x0}; }
+    __device__ __forceinline__ void advance(Cursor& c) const { c.pix += dx; }
+};
+
+// Pixels of a column (RX = 0) or wrapped-diagonal (RX = +1/-1) walk:
+// y = y0 + dy * i, x = (c + RX * y) mod W.
+template <int RX>
+struct ColGeo {
+    static constexpr bool kResets = RX != 0;
+    int W, H, c, y0, dy;
+    struct Cursor {
+        int pix, x, y;
+    };
+    __device__ __forceinline__ int x_at(int y) const {
+        if constexpr (RX == 0) {
+            return c;
+        } else {
+            int v = (c + RX * y) % W;
+            return v < 0 ? v + W : v;
+        }
+    }
+    __device__ __forceinline__ Cursor start() const {
+        const int x = x_at(y0);
+        return Cursor{y0 * W + x, x, y0};
+    }
+    __device__ __forceinline__ void advance(Cursor& k) const {
+        if constexpr (RX == 0) {
+            k.pix += dy * W;
+        } else {
+            int x = k.x + RX * dy;
+            x = x >= W ? x - W : (x < 0 ? x + W : x);
+            k.y += dy;
+            k.x = x;
+            k.pix = k.y * W + x;
+        }
+    }
+    // the previous pixel of the path at the cursor lies outside the image
+    __device__ __forceinline__ bool starts(const Cursor& k) const {
+        if (dy > 0) return k.y == 0 || (RX == 1 && k.x == 0) || (RX == -1 && k.x == W - 1);
+        return k.y == H - 1 || (RX == 1 && k.x == W - 1) || (RX == -1 && k.x == 0);
     }
 };
 
@@ -129,148 +227,111 @@ __device__ __forceinline__ void pair_barrier() {
     }
 }
 
-// Pixels of a row walk: x = x0 + dx * i.
-struct RowGeo {
-    size_t rowbase;
-    int x0, dx;
-    static constexpr bool kResets = false;
-    static constexpr bool kRow = true;
-    __device__ __forceinline__ void origin(int i0, int& xc, int& yc) const {
-        xc = x0 + dx * i0;
-        yc = 0;
-    }
-    __device__ __forceinline__ size_t pix(int xc, int /*yc*/, int k) const {
-        return rowbase + static_cast<size_t>(xc + dx * k);
-    }
-};
+// Lines (rows or columns) per block: with G = 32 a pair takes two warps.
+template <int D, bool PAIR>
+constexpr int lines_per_block() {
+    return PathShape<D>::G == 32 ? (PAIR ? kWarpsPerBlock / 2 : kWarpsPerBlock) : (PAIR ? kWarpsPerBlock : 2 * kWarpsPerBlock);
+}
 
-// Pixels of a column (RX = 0) or wrapped-diagonal (RX = +1/-1) walk:
-// y = y0 + dy * i, x = (c + RX * y) mod W.
-template <int RX>
-struct ColGeo {
-    int W, H, c, y0, dy;
-    static constexpr bool kResets = RX != 0;
-    static constexpr bool kRow = false;
-    __device__ __forceinline__ int x_at(int y) const {
-        if constexpr (RX == 0) {
-            return c;
+// Which line and direction this warp (or, for G = 16, this lane's half) walks.
+template <int D, bool PAIR>
+struct LaneRole {
+    int line, dir, pl;
+    __device__ __forceinline__ LaneRole(int bx) {
+        constexpr int G = PathShape<D>::G;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        pl = lane & (G - 1);
+        if constexpr (G == 16 && PAIR) {
+            line = bx * kWarpsPerBlock + warp;
+            dir = lane >> 4;
+        } else if constexpr (G == 16) {
+            // 2-path mode: the second half-warp carries the next line
+            line = (bx * kWarpsPerBlock + warp) * 2 + (lane >> 4);
+            dir = 0;
+        } else if constexpr (PAIR) {
+            line = bx * (kWarpsPerBlock / 2) + (warp >> 1);
+            dir = warp & 1;
         } else {
-            int v = (c + RX * y) % W;
-            return v < 0 ? v + W : v;
+            line = bx * kWarpsPerBlock + warp;
+            dir = 0;
         }
-    }
-    __device__ __forceinline__ void origin(int i0, int& xc, int& yc) const {
-        yc = y0 + dy * i0;
-        xc = x_at(yc);
-    }
-    __device__ __forceinline__ size_t pix(int xc, int yc, int k) const {
-        int x = xc;
-        if constexpr (RX != 0) {
-            x = xc + RX * dy * k;
-            if (x >= W) x -= W;
-            if (x < 0) x += W;
-            if (x >= W || x < 0) {  // only when W is smaller than a chunk
-                x %= W;
-                if (x < 0) x += W;
-            }
-        }
-        return static_cast<size_t>(yc + dy * k) * W + x;
-    }
-    // x of the next pixel of the walk
-    __device__ __forceinline__ int step_x(int x) const {
-        x += RX * dy;
-        return x >= W ? x - W : (x < 0 ? x + W : x);
-    }
-    // the previous pixel of the path at (x, y) lies outside the image
-    __device__ __forceinline__ bool starts(int y, int x) const {
-        if (dy > 0) return y == 0 || (RX == 1 && x == 0) || (RX == -1 && x == W - 1);
-        return y == H - 1 || (RX == 1 && x == W - 1) || (RX == -1 && x == 0);
     }
 };
 
-// One phase of this warp's path(s).  g / n_own: this lane's path; n_min /
-// n_max: the shorter and the longer step count of the warp's paths (equal to
-// n_own when the warp carries one path).  DBG: a winner-take-all walk also
-// writes S in natural order to a.Sdbg.
-template <int D, int MODE, class Geo, bool DBG = false>
+// One phase of this warp's path(s).  g / n_own: this lane's path and its step
+// count; n_other: the step count of the warp's other path (G = 16), else
+// n_own.  DBG: a winner-take-all walk also writes S in natural order to
+// a.Sdbg.
+template <int D, int MODE, bool S8, class Geo, bool DBG = false>
 __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch, const Geo& g, int n_own,
-                                     int n_min, int n_max, const SweepArgs& a, uint8_t* ws, int pl) {
+                                     int n_other, const SweepArgs& a, int pl) {
     constexpr int G = PathShape<D>::G, K = PathShape<D>::K;
-    using St = Stage<D, MODE, Geo::kRow>;
-    constexpr int CH = St::CH, NS = St::NSLOT;
-    constexpr bool IN_LO = St::IN_LO, IN_S = St::IN_S, OUT_LX = St::OUT_LX, OUT_S = St::OUT_S, WTA = St::WTA;
-    constexpr int PM = D / 16;      // 16-byte pieces per pixel of u8 pairs
-    constexpr int PS = 2 * D / 16;  // 16-byte pieces per pixel of packed sums
-    uint8_t* mc_ring = ws;
-    uint8_t* lo_ring = mc_ring + St::MC_RING;
-    uint8_t* s_ring = lo_ring + St::LO_RING;
-    const uint8_t* Sb = reinterpret_cast<const uint8_t*>(a.S);
-    const int nch = (n_max + CH - 1) / CH;
-
-    uint32_t dconst[K];
-    if constexpr (WTA) wta_consts<K>(pl, D, dconst);
-
-    auto issue = [&](int c) {
-        if (c < nch) {
-            const int i0 = c * CH, np = max(0, min(CH, n_own - i0)), slot = c % NS;
-            int xc = 0, yc = 0;
-            if (np > 0) g.origin(i0, xc, yc);
-            for (int q = pl; q < np * PM; q += G) {
-                const int pi = q / PM, off = (q % PM) * 16;
-                const size_t p = g.pix(xc, yc, pi);
-                cp16(mc_ring + (slot * CH + pi) * D + off, a.MC + p * D + off);
-                if constexpr (IN_LO) cp16(lo_ring + (slot * CH + pi) * D + off, a.Lx + p * D + off);
-            }
-            if constexpr (IN_S) {
-                for (int q = pl; q < np * PS; q += G) {
-                    const int pi = q / PS, off = (q % PS) * 16;
-                    const size_t p = g.pix(xc, yc, pi);
-                    cp16(s_ring + (slot * CH + pi) * 2 * D + off, Sb + p * 2 * D + off);
-                }
-            }
-        }
-        cp_commit();
+    using M = ModeIO<MODE>;
+    using In = StepIn<K, MODE, S8>;
+    constexpr int PF = prefetch_steps(In::REGS);
+    const int n_min = min(n_own, n_other), n_max = max(n_own, n_other);
+    const size_t lane_off = static_cast<size_t>(pl) * 2 * K;
+    // Every load is issued unconditionally: past the end of this lane's path it
+    // re-reads the path's first pixel (a predicated load would keep the old
+    // register value alive and make the step wait for the load).
+    In nxt[PF];
+    typename Geo::Cursor ld = g.start(), cur = ld;
+    const int pix0 = n_own > 0 ? ld.pix : 0;  // an empty path (W or H of 1) may start outside the image
+    auto prefetch = [&](In& b, int i) {
+        const int pix = i < n_own ? ld.pix : pix0;
+        b.load(a, static_cast<size_t>(pix) * D + lane_off);
+        g.advance(ld);
     };
+#pragma unroll
+    for (int k = 0; k < PF; ++k) prefetch(nxt[k], k);
+    uint32_t dconst[K];
+    if constexpr (M::WTA) wta_consts<K>(pl, D, dconst);
 
-    int y_body = 0, x_body = 0;
-    if constexpr (Geo::kResets) g.origin(0, x_body, y_body);
-
-    // one step at chunk position pi; lane pi of each path keeps that step's disparity key
-    auto body = [&](int pi, int slot, int xc, int yc, bool active, uint32_t& dkeep) {
+    // one step of the recurrence at `cur` and its outputs
+    auto body = [&](const In& in, bool active) {
         if constexpr (Geo::kResets) {
-            if (g.starts(y_body, x_body)) ch.reset();
-            y_body += g.dy;
-            x_body = g.step_x(x_body);
+            if (g.starts(cur)) ch.reset();
         }
         uint32_t mc[K], L[K];
-        unpack_pairs<K>(ld_pairs<K>(mc_ring + (slot * CH + pi) * D + pl * 2 * K), mc);
+        unpack_regs<K>(in.mc.r, mc);
         ch.step(mc, a.P1x2, a.P2x2, L);
-        if constexpr (OUT_LX) {
-            if (active) st_pairs<K>(a.Lx + g.pix(xc, yc, pi) * D + pl * 2 * K, pack_pairs<K>(L));
+        const size_t off = static_cast<size_t>(cur.pix) * D + lane_off;
+        if constexpr (M::OUT_LX) {
+            if (active) st_pairs<K>(a.Lx + off, pack_pairs<K>(L));
         } else {
             uint32_t s[K];
 #pragma unroll
             for (int j = 0; j < K; ++j) s[j] = L[j];
-            if constexpr (IN_LO) {
+            if constexpr (M::IN_LO) {
                 uint32_t lo[K];
-                unpack_pairs<K>(ld_pairs<K>(lo_ring + (slot * CH + pi) * D + pl * 2 * K), lo);
+                unpack_regs<K>(in.lo.r, lo);
 #pragma unroll
                 for (int j = 0; j < K; ++j) s[j] += lo[j];
             }
-            if constexpr (IN_S) {
-                uint32_t t[K];
-                ld_words<K>(reinterpret_cast<const uint32_t*>(s_ring + (slot * CH + pi) * 2 * D) + pl * K, t);
+            if constexpr (M::IN_S) {
+                if constexpr (S8) {
+                    uint32_t t[K];
+                    unpack_regs<K>(in.s.r, t);
 #pragma unroll
-                for (int j = 0; j < K; ++j) s[j] += t[j];
+                    for (int j = 0; j < K; ++j) s[j] += t[j];
+                } else {
+#pragma unroll
+                    for (int j = 0; j < K; ++j) s[j] += in.s.r[j];
+                }
             }
-            if constexpr (OUT_S) {
-                if (active) st_words<K>(a.S + g.pix(xc, yc, pi) * (D / 2) + pl * K, s);
+            if constexpr (M::OUT_S) {
+                if (active) {
+                    if constexpr (S8)
+                        st_pairs<K>(reinterpret_cast<uint8_t*>(a.S) + off, pack_pairs<K>(s));
+                    else
+                        st_words<K>(a.S + off / 2, s);
+                }
             }
-            if constexpr (WTA) {
+            if constexpr (M::WTA) {
                 const uint32_t key = ch.path_min(wta_key<K>(s, dconst));
-                dkeep = (pl == pi) ? key : dkeep;
+                if (active && pl == 0) a.raw[cur.pix] = static_cast<uint8_t>(key & 0xffu);
                 if (DBG && active) {  // debug: natural-order S
-                    const size_t p = g.pix(xc, yc, pi);
+                    const size_t p = static_cast<size_t>(cur.pix);
 #pragma unroll
                     for (int j = 0; j < K; ++j) {
                         const int i = pl * K + j;
@@ -282,40 +343,34 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
         }
     };
 
-    for (int c = 0; c < NS - 1; ++c) issue(c);
-    for (int c = 0; c < nch; ++c) {
-        issue(c + NS - 1);
-        cp_wait<NS - 1>();
-        __syncwarp();
-        const int i0 = c * CH, np = max(0, min(CH, n_own - i0)), slot = c % NS;
-        int xc = 0, yc = 0;
-        if (np > 0) g.origin(i0, xc, yc);
-        uint32_t dkeep = 0;
-        if (n_min - i0 >= CH) {
+    for (int i0 = 0; i0 < n_max; i0 += PF) {
+        In in[PF];
 #pragma unroll
-            for (int pi = 0; pi < CH; ++pi) body(pi, slot, xc, yc, true, dkeep);
+        for (int k = 0; k < PF; ++k) in[k] = nxt[k];
+#pragma unroll
+        for (int k = 0; k < PF; ++k) prefetch(nxt[k], i0 + PF + k);
+        if (n_min - i0 >= PF) {
+#pragma unroll
+            for (int k = 0; k < PF; ++k) {
+                body(in[k], true);
+                g.advance(cur);
+            }
         } else {
-            // last chunk: a path with fewer steps keeps its state through the extra steps
+            // last steps: a path with fewer steps keeps its state through the extra ones
 #pragma unroll
-            for (int pi = 0; pi < CH; ++pi) {
-                if (i0 + pi < n_max) {
+            for (int k = 0; k < PF; ++k) {
+                const int i = i0 + k;
+                if (i < n_max) {  // warp-uniform
+                    // every lane runs the step (it holds warp-synchronous
+                    // exchanges); a finished path then takes its state back
                     const Chain<G, K> saved = ch;
-                    const int yb = y_body, xb = x_body;
-                    body(pi, slot, xc, yc, pi < np, dkeep);
-                    if (pi >= np) {
-                        ch = saved;
-                        y_body = yb;
-                        x_body = xb;
-                    }
+                    body(in[k], i < n_own);
+                    if (i >= n_own) ch = saved;
+                    g.advance(cur);
                 }
             }
         }
-        if constexpr (WTA) {
-            if (pl < np) a.raw[g.pix(xc, yc, pl)] = static_cast<uint8_t>(dkeep & 0xffu);
-        }
-        __syncwarp();  // every lane is done with this slot before it is refilled
     }
-    cp_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
@@ -325,48 +380,49 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
 // S = own L + stored L.  Without `pair` (2-path mode) A covers the whole row
 // and writes S = L_LR.
 // ---------------------------------------------------------------------------
-template <int D, bool PAIR>
+template <int D, bool PAIR, bool S8>
 __device__ __forceinline__ void sweep_h_body(const SweepArgs& a, int bx) {
-    extern __shared__ __align__(16) uint8_t smem[];
     constexpr int G = PathShape<D>::G, K = PathShape<D>::K;
     const LaneRole<D, PAIR> r(bx);
     const int y = r.line;
-    if (y >= a.H) return;  // whole warp (and its pair): every exchange below is local to them
+    // whole warp (and its pair): every exchange below is local to them; in
+    // 2-path mode with 16-lane paths the warp's lines are y & ~1 and y | 1
+    if ((G == 16 && !PAIR ? (y & ~1) : y) >= a.H) return;
     const bool in_b = r.dir != 0;
-    uint8_t* ws = smem + r.slot * HStage<D, PAIR>::PATH;
-    const int W = a.W;
-    const size_t rowbase = static_cast<size_t>(y) * W;
+    const int W = a.W, rowbase = y * W;
     Chain<G, K> ch;
     ch.init(threadIdx.x & 31);
     if constexpr (!PAIR) {
-        const RowGeo g{rowbase, 0, 1};
-        const int n = in_b ? 0 : W;
-        walk<D, kSingleH>(ch, g, n, G == 16 ? 0 : n, W, a, ws, r.pl);
+        // a half-warp past the last row walks nothing (it still joins the exchanges)
+        const bool valid = y < a.H;
+        const RowGeo g{valid ? rowbase : 0, 0, 1};
+        const int n = valid ? W : 0;
+        walk<D, kSingleH, S8>(ch, g, n, G == 16 ? ((y ^ 1) < a.H ? W : 0) : n, a, r.pl);
     } else {
         const int Wm = W / 2;
         {
             const RowGeo g = in_b ? RowGeo{rowbase, W - 1, -1} : RowGeo{rowbase, 0, 1};
-            const int nA = Wm, nB = W - Wm, n = in_b ? nB : nA;
-            walk<D, kStoreL>(ch, g, n, G == 16 ? min(nA, nB) : n, G == 16 ? max(nA, nB) : n, a, ws, r.pl);
+            const int nA = Wm, nB = W - Wm;
+            walk<D, kStoreL, S8>(ch, g, in_b ? nB : nA, G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
         }
         pair_barrier<D>();
         {
             const RowGeo g = in_b ? RowGeo{rowbase, Wm - 1, -1} : RowGeo{rowbase, Wm, 1};
-            const int nA = W - Wm, nB = Wm, n = in_b ? nB : nA;
-            walk<D, kSumH>(ch, g, n, G == 16 ? min(nA, nB) : n, G == 16 ? max(nA, nB) : n, a, ws, r.pl);
+            const int nA = W - Wm, nB = Wm;
+            walk<D, kSumH, S8>(ch, g, in_b ? nB : nA, G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
         }
     }
 }
 
-template <int D, bool PAIR>
+template <int D, bool PAIR, bool S8>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_h_kernel(SweepArgs a) {
-    sweep_h_body<D, PAIR>(a, blockIdx.x);
+    sweep_h_body<D, PAIR, S8>(a, blockIdx.x);
 }
 
-template <int D, bool PAIR>
+template <int D, bool PAIR, bool S8>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_h_batch_kernel(const __grid_constant__ JobTable<SweepArgs> t) {
     const int p = find_job(t, blockIdx.x);
-    sweep_h_body<D, PAIR>(t.job[p], blockIdx.x - t.start[p]);
+    sweep_h_body<D, PAIR, S8>(t.job[p], blockIdx.x - t.start[p]);
 }
 
 // ---------------------------------------------------------------------------
@@ -382,23 +438,23 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_h_batch_kernel(cons
 // PH: 0 = both phases in one launch, 1 = first halves (saving the path state),
 // 2 = second halves (restoring it).  WTA: the pair finishes with Eq. 4
 // instead of adding into S.  PAIR = false is the 2-path top-to-bottom sweep.
-template <int D, int RX, int PH, bool WTA, bool PAIR, bool DBG = false>
+template <int D, int RX, int PH, bool WTA, bool PAIR, bool S8, bool DBG = false>
 __device__ __forceinline__ void sweep_v_body(const SweepArgs& a, int bx) {
-    extern __shared__ __align__(16) uint8_t smem[];
     constexpr int G = PathShape<D>::G, K = PathShape<D>::K;
     const LaneRole<D, PAIR> r(bx);
     const int c = r.line;
-    if (c >= a.W) return;  // whole warp (and its pair)
+    if ((G == 16 && !PAIR ? (c & ~1) : c) >= a.W) return;  // whole warp (and its pair)
     const bool in_b = r.dir != 0;
-    uint8_t* ws = smem + r.slot * VStage<D, PH, WTA, PAIR>::PATH;
     const int W = a.W, H = a.H;
     using Geo = ColGeo<RX>;
     Chain<G, K> ch;
     const int lane = threadIdx.x & 31;
     ch.init(lane);
     if constexpr (!PAIR) {
-        const int n = in_b ? 0 : H;
-        walk<D, kSingleWta, Geo, DBG>(ch, Geo{W, H, c, 0, 1}, n, G == 16 ? 0 : n, H, a, ws, r.pl);
+        const bool valid = c < W;
+        const int n = valid ? H : 0;
+        walk<D, kSingleWta, S8, Geo, DBG>(ch, Geo{W, H, valid ? c : 0, 0, 1}, n,
+                                          G == 16 ? ((c ^ 1) < W ? H : 0) : n, a, r.pl);
     } else {
         const int Hm = H / 2;
         // saved path state of this lane: K words, the two neighbour words and m
@@ -408,8 +464,8 @@ __device__ __forceinline__ void sweep_v_body(const SweepArgs& a, int bx) {
                                (K + 3);
         if constexpr (PH != 2) {
             const Geo g = in_b ? Geo{W, H, c, H - 1, -1} : Geo{W, H, c, 0, 1};
-            const int nA = Hm, nB = H - Hm, n = in_b ? nB : nA;
-            walk<D, kStoreL>(ch, g, n, G == 16 ? min(nA, nB) : n, G == 16 ? max(nA, nB) : n, a, ws, r.pl);
+            const int nA = Hm, nB = H - Hm;
+            walk<D, kStoreL, S8>(ch, g, in_b ? nB : nA, G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
         }
         if constexpr (PH == 1) {
 #pragma unroll
@@ -421,41 +477,41 @@ __device__ __forceinline__ void sweep_v_body(const SweepArgs& a, int bx) {
         }
         if constexpr (PH == 2) {
 #pragma unroll
-            for (int j = 0; j < K; ++j) ch.w[j] = st[j];
-            ch.up = st[K];
-            ch.dn = st[K + 1];
-            ch.mpx2 = st[K + 2];
+            for (int j = 0; j < K; ++j) ch.w[j] = __ldcg(st + j);
+            ch.up = __ldcg(st + K);
+            ch.dn = __ldcg(st + K + 1);
+            ch.mpx2 = __ldcg(st + K + 2);
         }
         if constexpr (PH != 1) {
             if constexpr (PH == 0) pair_barrier<D>();
             const Geo g = in_b ? Geo{W, H, c, Hm - 1, -1} : Geo{W, H, c, Hm, 1};
-            const int nA = H - Hm, nB = Hm, n = in_b ? nB : nA;
-            walk<D, WTA ? kWta2 : kAcc, Geo, DBG>(ch, g, n, G == 16 ? min(nA, nB) : n, G == 16 ? max(nA, nB) : n, a,
-                                                  ws, r.pl);
+            const int nA = H - Hm, nB = Hm;
+            walk<D, WTA ? kWta2 : kAcc, S8, Geo, DBG>(ch, g, in_b ? nB : nA,
+                                                      G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
         }
     }
 }
 
-template <int D, int RX, int PH, bool WTA, bool PAIR, bool DBG = false>
+template <int D, int RX, int PH, bool WTA, bool PAIR, bool S8, bool DBG = false>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_v_kernel(SweepArgs a) {
-    sweep_v_body<D, RX, PH, WTA, PAIR, DBG>(a, blockIdx.x);
+    sweep_v_body<D, RX, PH, WTA, PAIR, S8, DBG>(a, blockIdx.x);
 }
 
 // Batched form: both phases in one launch (PH = 0).
-template <int D, int RX, bool WTA, bool PAIR>
+template <int D, int RX, bool WTA, bool PAIR, bool S8>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_v_batch_kernel(const __grid_constant__ JobTable<SweepArgs> t) {
     const int p = find_job(t, blockIdx.x);
-    sweep_v_body<D, RX, 0, WTA, PAIR>(t.job[p], blockIdx.x - t.start[p]);
+    sweep_v_body<D, RX, 0, WTA, PAIR, S8>(t.job[p], blockIdx.x - t.start[p]);
 }
 
 // The horizontal pair and the vertical-type first halves in one grid: one
 // block distribution over the SMs for all of them (two kernels sharing the
 // SMs through concurrent streams ran far slower than either alone).
-template <int D>
+template <int D, bool S8>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_first_kernel(const __grid_constant__ FirstStageArgs f) {
     const int b = blockIdx.x;
     if (b < f.start[1]) {
-        sweep_h_body<D, true>(f.h, b);
+        sweep_h_body<D, true, S8>(f.h, b);
         return;
     }
     for (int k = 0; k < f.nv; ++k) {
@@ -463,67 +519,39 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_first_kernel(const 
             const SweepArgs& v = f.v[k];
             const int bx = b - f.start[k + 1];
             if (v.rx == 0)
-                sweep_v_body<D, 0, 1, false, true>(v, bx);
+                sweep_v_body<D, 0, 1, false, true, S8>(v, bx);
             else if (v.rx > 0)
-                sweep_v_body<D, 1, 1, false, true>(v, bx);
+                sweep_v_body<D, 1, 1, false, true, S8>(v, bx);
             else
-                sweep_v_body<D, -1, 1, false, true>(v, bx);
+                sweep_v_body<D, -1, 1, false, true, S8>(v, bx);
             return;
         }
     }
 }
 
-template <int D>
-struct FirstStage {
-    static constexpr int BLOCK = cmax(HStage<D, true>::BLOCK, VStage<D, 1, false, true>::BLOCK);
-};
-
 // ---------------------------------------------------------------------------
-// Per-D entry points, instantiated one D per translation unit.
+// Per-D entry points, instantiated one D per translation unit.  The sums are
+// bytes (S8) in 2-path mode always and in 4-path mode when SweepArgs::s8 is
+// set; 8-path sums are u16 words.
 // ---------------------------------------------------------------------------
 template <int D>
 struct SweepD {
-    template <class Kern>
-    static cudaError_t attr(Kern kern, int bytes) {
-        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    }
-
-    template <int RX, bool WTA>
-    static cudaError_t attrs_rx() {
-        cudaError_t e = attr(sweep_v_kernel<D, RX, 0, WTA, true>, VStage<D, 0, WTA, true>::BLOCK);
-        if (e == cudaSuccess) e = attr(sweep_v_kernel<D, RX, 1, false, true>, VStage<D, 1, false, true>::BLOCK);
-        if (e == cudaSuccess) e = attr(sweep_v_kernel<D, RX, 2, WTA, true>, VStage<D, 2, WTA, true>::BLOCK);
-        if (e == cudaSuccess) e = attr(sweep_v_batch_kernel<D, RX, WTA, true>, VStage<D, 0, WTA, true>::BLOCK);
-        return e;
-    }
-
-    static cudaError_t set_attrs() {
-        cudaError_t e = attr(sweep_first_kernel<D>, FirstStage<D>::BLOCK);
-        if (e == cudaSuccess) e = attr(sweep_h_kernel<D, true>, HStage<D, true>::BLOCK);
-        if (e == cudaSuccess) e = attr(sweep_h_kernel<D, false>, HStage<D, false>::BLOCK);
-        if (e == cudaSuccess) e = attr(sweep_h_batch_kernel<D, true>, HStage<D, true>::BLOCK);
-        if (e == cudaSuccess) e = attr(sweep_h_batch_kernel<D, false>, HStage<D, false>::BLOCK);
-        if (e == cudaSuccess) e = attr(sweep_v_kernel<D, 0, 0, true, false>, VStage<D, 0, true, false>::BLOCK);
-        if (e == cudaSuccess) e = attr(sweep_v_kernel<D, 0, 0, true, false, true>, VStage<D, 0, true, false>::BLOCK);
-        if (e == cudaSuccess) e = attr(sweep_v_kernel<D, 0, 2, true, true, true>, VStage<D, 2, true, true>::BLOCK);
-        if (e == cudaSuccess) e = attr(sweep_v_batch_kernel<D, 0, true, false>, VStage<D, 0, true, false>::BLOCK);
-        if (e == cudaSuccess) e = attrs_rx<0, true>();
-        if (e == cudaSuccess) e = attrs_rx<1, false>();
-        if (e == cudaSuccess) e = attrs_rx<-1, false>();
-        return e;
-    }
-
     static int blocks(int lines, bool pair) {
         const int per = pair ? lines_per_block<D, true>() : lines_per_block<D, false>();
         return (lines + per - 1) / per;
     }
 
+    // No kernel needs an attribute (no dynamic shared memory).
+    static cudaError_t set_attrs() { return cudaSuccess; }
+
     static cudaError_t launch_h(const SweepArgs& a, cudaStream_t s) {
         const dim3 grid(blocks(a.H, a.pair)), block(32 * kWarpsPerBlock);
-        if (a.pair)
-            sweep_h_kernel<D, true><<<grid, block, HStage<D, true>::BLOCK, s>>>(a);
+        if (!a.pair)
+            sweep_h_kernel<D, false, true><<<grid, block, 0, s>>>(a);
+        else if (a.s8)
+            sweep_h_kernel<D, true, true><<<grid, block, 0, s>>>(a);
         else
-            sweep_h_kernel<D, false><<<grid, block, HStage<D, false>::BLOCK, s>>>(a);
+            sweep_h_kernel<D, true, false><<<grid, block, 0, s>>>(a);
         return cudaGetLastError();
     }
 
@@ -532,30 +560,24 @@ struct SweepD {
         f.start[1] = blocks(f.h.H, true);
         for (int k = 0; k < f.nv; ++k) f.start[k + 2] = f.start[k + 1] + blocks(f.v[k].W, true);
         const dim3 block(32 * kWarpsPerBlock);
-        sweep_first_kernel<D><<<f.start[f.nv + 1], block, FirstStage<D>::BLOCK, s>>>(f);
-        return cudaGetLastError();
-    }
-
-    template <int RX, bool WTA>
-    static void launch_v_rx(const SweepArgs& a, dim3 grid, dim3 block, cudaStream_t s) {
-        if (WTA && a.Sdbg && a.phase == 2)
-            sweep_v_kernel<D, RX, 2, WTA, true, true><<<grid, block, VStage<D, 2, WTA, true>::BLOCK, s>>>(a);
-        else if (a.phase == 1)
-            sweep_v_kernel<D, RX, 1, false, true><<<grid, block, VStage<D, 1, false, true>::BLOCK, s>>>(a);
-        else if (a.phase == 2)
-            sweep_v_kernel<D, RX, 2, WTA, true><<<grid, block, VStage<D, 2, WTA, true>::BLOCK, s>>>(a);
+        if (f.h.s8)
+            sweep_first_kernel<D, true><<<f.start[f.nv + 1], block, 0, s>>>(f);
         else
-            sweep_v_kernel<D, RX, 0, WTA, true><<<grid, block, VStage<D, 0, WTA, true>::BLOCK, s>>>(a);
+            sweep_first_kernel<D, false><<<f.start[f.nv + 1], block, 0, s>>>(f);
+        return cudaGetLastError();
     }
 
     static cudaError_t launch_h_batch(JobTable<SweepArgs>& t, cudaStream_t s) {
         t.start[0] = 0;
         for (int i = 0; i < t.n; ++i) t.start[i + 1] = t.start[i] + blocks(t.job[i].H, t.job[i].pair);
-        const dim3 block(32 * kWarpsPerBlock);
-        if (t.job[0].pair)
-            sweep_h_batch_kernel<D, true><<<t.start[t.n], block, HStage<D, true>::BLOCK, s>>>(t);
+        const dim3 grid(t.start[t.n]), block(32 * kWarpsPerBlock);
+        const SweepArgs& a = t.job[0];
+        if (!a.pair)
+            sweep_h_batch_kernel<D, false, true><<<grid, block, 0, s>>>(t);
+        else if (a.s8)
+            sweep_h_batch_kernel<D, true, true><<<grid, block, 0, s>>>(t);
         else
-            sweep_h_batch_kernel<D, false><<<t.start[t.n], block, HStage<D, false>::BLOCK, s>>>(t);
+            sweep_h_batch_kernel<D, true, false><<<grid, block, 0, s>>>(t);
         return cudaGetLastError();
     }
 
@@ -565,28 +587,45 @@ struct SweepD {
         const dim3 grid(t.start[t.n]), block(32 * kWarpsPerBlock);
         const SweepArgs& a = t.job[0];
         if (!a.pair)
-            sweep_v_batch_kernel<D, 0, true, false><<<grid, block, VStage<D, 0, true, false>::BLOCK, s>>>(t);
+            sweep_v_batch_kernel<D, 0, true, false, true><<<grid, block, 0, s>>>(t);
+        else if (a.rx == 0 && a.s8)
+            sweep_v_batch_kernel<D, 0, true, true, true><<<grid, block, 0, s>>>(t);
         else if (a.rx == 0)
-            sweep_v_batch_kernel<D, 0, true, true><<<grid, block, VStage<D, 0, true, true>::BLOCK, s>>>(t);
+            sweep_v_batch_kernel<D, 0, true, true, false><<<grid, block, 0, s>>>(t);
         else if (a.rx > 0)
-            sweep_v_batch_kernel<D, 1, false, true><<<grid, block, VStage<D, 0, false, true>::BLOCK, s>>>(t);
+            sweep_v_batch_kernel<D, 1, false, true, false><<<grid, block, 0, s>>>(t);
         else
-            sweep_v_batch_kernel<D, -1, false, true><<<grid, block, VStage<D, 0, false, true>::BLOCK, s>>>(t);
+            sweep_v_batch_kernel<D, -1, false, true, false><<<grid, block, 0, s>>>(t);
         return cudaGetLastError();
+    }
+
+    // Vertical-type sweeps of a pair in phase 1 or 2 (or both, phase 0).
+    template <int RX, bool WTA, bool S8>
+    static void launch_v_rx(const SweepArgs& a, dim3 grid, dim3 block, cudaStream_t s) {
+        if (WTA && a.Sdbg && a.phase == 2)
+            sweep_v_kernel<D, RX, 2, WTA, true, S8, true><<<grid, block, 0, s>>>(a);
+        else if (a.phase == 1)
+            sweep_v_kernel<D, RX, 1, false, true, S8><<<grid, block, 0, s>>>(a);
+        else if (a.phase == 2)
+            sweep_v_kernel<D, RX, 2, WTA, true, S8><<<grid, block, 0, s>>>(a);
+        else
+            sweep_v_kernel<D, RX, 0, WTA, true, S8><<<grid, block, 0, s>>>(a);
     }
 
     static cudaError_t launch_v(const SweepArgs& a, cudaStream_t s) {
         const dim3 grid(blocks(a.W, a.pair)), block(32 * kWarpsPerBlock);
         if (!a.pair && a.Sdbg)
-            sweep_v_kernel<D, 0, 0, true, false, true><<<grid, block, VStage<D, 0, true, false>::BLOCK, s>>>(a);
+            sweep_v_kernel<D, 0, 0, true, false, true, true><<<grid, block, 0, s>>>(a);
         else if (!a.pair)
-            sweep_v_kernel<D, 0, 0, true, false><<<grid, block, VStage<D, 0, true, false>::BLOCK, s>>>(a);
+            sweep_v_kernel<D, 0, 0, true, false, true><<<grid, block, 0, s>>>(a);
+        else if (a.rx == 0 && a.s8)
+            launch_v_rx<0, true, true>(a, grid, block, s);
         else if (a.rx == 0)
-            launch_v_rx<0, true>(a, grid, block, s);
+            launch_v_rx<0, true, false>(a, grid, block, s);
         else if (a.rx > 0)
-            launch_v_rx<1, false>(a, grid, block, s);
+            launch_v_rx<1, false, false>(a, grid, block, s);
         else
-            launch_v_rx<-1, false>(a, grid, block, s);
+            launch_v_rx<-1, false, false>(a, grid, block, s);
         return cudaGetLastError();
     }
 };
@@ -606,30 +645,30 @@ SGM_INTERNAL cudaError_t sweep_launch_h_batch(JobTable<SweepArgs>& t, cudaStream
 template <int D>
 SGM_INTERNAL cudaError_t sweep_launch_v_batch(JobTable<SweepArgs>& t, cudaStream_t s);
 
-#define SGM_INSTANTIATE_SWEEPS(D)                                                                           \
-    template <>                                                                                             \
-    SGM_INTERNAL cudaError_t sweep_set_attrs<D>() {                                                         \
-        return SweepD<D>::set_attrs();                                                                      \
-    }                                                                                                       \
-    template <>                                                                                             \
-    SGM_INTERNAL cudaError_t sweep_launch_h<D>(const SweepArgs& a, cudaStream_t s) {                        \
-        return SweepD<D>::launch_h(a, s);                                                                   \
-    }                                                                                                       \
-    template <>                                                                                             \
-    SGM_INTERNAL cudaError_t sweep_launch_v<D>(const SweepArgs& a, cudaStream_t s) {                        \
-        return SweepD<D>::launch_v(a, s);                                                                   \
-    }                                                                                                       \
-    template <>                                                                                             \
-    SGM_INTERNAL cudaError_t sweep_launch_first<D>(FirstStageArgs & f, cudaStream_t s) {                    \
-        return SweepD<D>::launch_first(f, s);                                                               \
-    }                                                                                                       \
-    template <>                                                                                             \
-    SGM_INTERNAL cudaError_t sweep_launch_h_batch<D>(JobTable<SweepArgs> & t, cudaStream_t s) {             \
-        return SweepD<D>::launch_h_batch(t, s);                                                             \
-    }                                                                                                       \
-    template <>                                                                                             \
-    SGM_INTERNAL cudaError_t sweep_launch_v_batch<D>(JobTable<SweepArgs> & t, cudaStream_t s) {             \
-        return SweepD<D>::launch_v_batch(t, s);                                                             \
+#define SGM_INSTANTIATE_SWEEPS(D)                                                               \
+    template <>                                                                                 \
+    SGM_INTERNAL cudaError_t sweep_set_attrs<D>() {                                             \
+        return SweepD<D>::set_attrs();                                                          \
+    }                                                                                           \
+    template <>                                                                                 \
+    SGM_INTERNAL cudaError_t sweep_launch_h<D>(const SweepArgs& a, cudaStream_t s) {            \
+        return SweepD<D>::launch_h(a, s);                                                       \
+    }                                                                                           \
+    template <>                                                                                 \
+    SGM_INTERNAL cudaError_t sweep_launch_v<D>(const SweepArgs& a, cudaStream_t s) {            \
+        return SweepD<D>::launch_v(a, s);                                                       \
+    }                                                                                           \
+    template <>                                                                                 \
+    SGM_INTERNAL cudaError_t sweep_launch_first<D>(FirstStageArgs & f, cudaStream_t s) {        \
+        return SweepD<D>::launch_first(f, s);                                                   \
+    }                                                                                           \
+    template <>                                                                                 \
+    SGM_INTERNAL cudaError_t sweep_launch_h_batch<D>(JobTable<SweepArgs> & t, cudaStream_t s) { \
+        return SweepD<D>::launch_h_batch(t, s);                                                 \
+    }                                                                                           \
+    template <>                                                                                 \
+    SGM_INTERNAL cudaError_t sweep_launch_v_batch<D>(JobTable<SweepArgs> & t, cudaStream_t s) { \
+        return SweepD<D>::launch_v_batch(t, s);                                                 \
     }
 
 }  // namespace sgm
