@@ -506,25 +506,30 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_v_batch_kernel(cons
 
 // The horizontal pair and the vertical-type first halves in one grid: one
 // block distribution over the SMs for all of them (two kernels sharing the
-// SMs through concurrent streams ran far slower than either alone).
-template <int D, bool S8>
+// SMs through concurrent streams ran far slower than either alone).  NV = 1
+// (4 paths: the vertical pair only) keeps the diagonal code out of the kernel.
+template <int D, bool S8, int NV>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_first_kernel(const __grid_constant__ FirstStageArgs f) {
     const int b = blockIdx.x;
     if (b < f.start[1]) {
         sweep_h_body<D, true, S8>(f.h, b);
         return;
     }
-    for (int k = 0; k < f.nv; ++k) {
-        if (b < f.start[k + 2]) {
-            const SweepArgs& v = f.v[k];
-            const int bx = b - f.start[k + 1];
-            if (v.rx == 0)
-                sweep_v_body<D, 0, 1, false, true, S8>(v, bx);
-            else if (v.rx > 0)
-                sweep_v_body<D, 1, 1, false, true, S8>(v, bx);
-            else
-                sweep_v_body<D, -1, 1, false, true, S8>(v, bx);
-            return;
+    if constexpr (NV == 1) {
+        sweep_v_body<D, 0, 1, false, true, S8>(f.v[0], b - f.start[1]);
+    } else {
+        for (int k = 0; k < NV; ++k) {
+            if (b < f.start[k + 2]) {
+                const SweepArgs& v = f.v[k];
+                const int bx = b - f.start[k + 1];
+                if (v.rx == 0)
+                    sweep_v_body<D, 0, 1, false, true, S8>(v, bx);
+                else if (v.rx > 0)
+                    sweep_v_body<D, 1, 1, false, true, S8>(v, bx);
+                else
+                    sweep_v_body<D, -1, 1, false, true, S8>(v, bx);
+                return;
+            }
         }
     }
 }
@@ -560,10 +565,13 @@ struct SweepD {
         f.start[1] = blocks(f.h.H, true);
         for (int k = 0; k < f.nv; ++k) f.start[k + 2] = f.start[k + 1] + blocks(f.v[k].W, true);
         const dim3 block(32 * kWarpsPerBlock);
-        if (f.h.s8)
-            sweep_first_kernel<D, true><<<f.start[f.nv + 1], block, 0, s>>>(f);
+        const int grid = f.start[f.nv + 1];
+        if (f.nv == 1 && f.h.s8)
+            sweep_first_kernel<D, true, 1><<<grid, block, 0, s>>>(f);
+        else if (f.nv == 1)
+            sweep_first_kernel<D, false, 1><<<grid, block, 0, s>>>(f);
         else
-            sweep_first_kernel<D, false><<<f.start[f.nv + 1], block, 0, s>>>(f);
+            sweep_first_kernel<D, false, 3><<<grid, block, 0, s>>>(f);
         return cudaGetLastError();
     }
 
