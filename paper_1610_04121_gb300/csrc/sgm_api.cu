@@ -29,34 +29,35 @@ inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 // Offsets of one pair's buffers inside a work arena.
 struct Layout {
-    size_t Fb, Fm, MC, Lx, S, raw, state, in_left, in_right, out, total;
+    size_t Fb, Fm, rec, raw, state, in_left, in_right, out, total;
+    int RB;    // bytes per pixel record (sgm_internal.h): MC, S (room for u16 words), stored L_r fields
+    int n_lx;  // stored-L_r fields per record
 };
 
-// Scratch cubes of first-half path costs: one per pair of opposite paths.
-int lx_cubes(int n_paths) { return n_paths == 8 ? 4 : (n_paths == 4 ? 2 : 1); }
+// Stored-L_r fields: one per pair of opposite paths whose first halves run
+// concurrently (the horizontal pair and every vertical-type pair); none in
+// 2-path mode.  Batched execution runs each pair's phases in one launch, one
+// pair after the other, so a batched pair needs a single field and no phase
+// state.
+int lx_fields(int n_paths, bool batched) { return n_paths == 2 ? 0 : (batched ? 1 : (n_paths == 8 ? 4 : 2)); }
 
-// Batched execution runs every sweep in one launch (no phases), so a batched
-// pair needs one path-cost cube and no phase state.
 Layout layout_for(int W, int H, int D_int, int n_paths, bool batched = false) {
-    const int cubes = batched ? 1 : lx_cubes(n_paths);
     const size_t wh = static_cast<size_t>(W) * H;
     const size_t D = static_cast<size_t>(D_int);
     Layout l{};
+    l.n_lx = lx_fields(n_paths, batched);
+    l.RB = record_bytes(D_int, false, l.n_lx);
     size_t o = 0;
     l.Fb = o;
     o = align_up(o + 4 * wh);
     l.Fm = o;
     o = align_up(o + 4 * wh);
-    l.MC = o;
-    o = align_up(o + wh * D);
-    l.Lx = o;  // one path-cost cube per pair: horizontal + vertical-type ones
-    o = align_up(o + cubes * align_up(wh * D));
-    l.S = o;
-    o = align_up(o + 2 * wh * D);
+    l.rec = o;
+    o = align_up(o + wh * static_cast<size_t>(l.RB));
     l.raw = o;
     o = align_up(o + wh);
-    l.state = o;  // path states of the three vertical-type pairs between their phases
-    o = align_up(o + (cubes - 1) * 4 * sweep_state_words(W, static_cast<int>(D)));
+    l.state = o;  // path states of the vertical-type pairs between their phases
+    o = align_up(o + (n_paths == 8 ? 3 : 1) * 4 * sweep_state_words(W, static_cast<int>(D)));
     l.in_left = o;
     o = align_up(o + wh);
     l.in_right = o;
@@ -81,8 +82,9 @@ bool valid_problem(const Problem& p, std::string* why) {
         snprintf(buf, sizeof buf, "P1 and P2 must lie in [0, %d] (got %d, %d)", SGM_MAX_PENALTY, p.P1, p.P2);
     } else if (p.n_paths != 2 && p.n_paths != 4 && p.n_paths != 8) {
         snprintf(buf, sizeof buf, "n_paths must be 2, 4 or 8 (got %d)", p.n_paths);
-    } else if (static_cast<double>(p.W) * p.H * p.D > 8.0e9) {
-        snprintf(buf, sizeof buf, "W*H*D too large (%d x %d x %d)", p.W, p.H, p.D);
+    } else if (static_cast<double>(p.W) * p.H * record_bytes(p.D, false, lx_fields(p.n_paths, false)) >= 4294967296.0) {
+        snprintf(buf, sizeof buf, "W*H*D too large (%d x %d x %d): the per-pixel records must stay below 4 GiB", p.W,
+                 p.H, p.D);
     } else {
         return true;
     }
@@ -237,10 +239,6 @@ static int launches_per_path(const Problem& p) { return p.n_paths == 8 ? 7 : 5; 
 static int stages_per_path(const Problem& p) { return launches_per_path(p); }
 
 // Bytes of one [H][W][D] u8 scratch cube of path costs.
-static size_t lx_cube_bytes(const Problem& p) {
-    return align_up(static_cast<size_t>(p.W) * p.H * static_cast<size_t>(p.D));
-}
-
 // Enqueue the whole path (Section 2, stages 2-4) for one pair whose inputs
 // and output are device pointers.  Returns a cudaError_t.
 static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const uint8_t* left,
@@ -248,7 +246,6 @@ static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, 
     const Layout l = layout_for(p.W, p.H, p.D, p.n_paths);
     uint32_t* Fb = reinterpret_cast<uint32_t*>(arena + l.Fb);
     uint32_t* Fm = reinterpret_cast<uint32_t*>(arena + l.Fm);
-    uint8_t* MC = arena + l.MC;
     cudaError_t e;
     int stage = 0;
     // with stage timing, event k is recorded before kernel k and after the last
@@ -260,12 +257,12 @@ static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, 
     if ((e = mark()) != cudaSuccess) return e;
     if ((e = launch_census(left, right, Fb, Fm, p.W, p.H, s)) != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;
-    if ((e = launch_cost(Fb, Fm, MC, p.W, p.H, p.D, s)) != cudaSuccess) return e;
+    if ((e = launch_cost(Fb, Fm, arena + l.rec, l.RB, p.W, p.H, p.D, s)) != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;
     SweepArgs a{};
-    a.MC = MC;
-    a.Lx = arena + l.Lx;
-    a.S = reinterpret_cast<uint32_t*>(arena + l.S);
+    a.rec = arena + l.rec;
+    a.RB = l.RB;
+    a.lx_off = 3 * p.D;  // stored-L_r field k at 3D + kD: the horizontal pair takes field 0
     a.raw = arena + l.raw;
     a.Sdbg = Sdbg;
     a.W = p.W;
@@ -302,9 +299,8 @@ static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, 
             b.rx = rxs[v];
             b.phase = 1;
             b.state = states + v * sw;
-            // each vertical-type pair keeps its own first-half L cube: the scratch
-            // is split [H][W][D] per pair after the horizontal one
-            b.Lx = arena + l.Lx + static_cast<size_t>(v + 1) * lx_cube_bytes(p);
+            // each vertical-type pair keeps its own stored-L_r field
+            b.lx_off = (4 + v) * p.D;
             f.v[v] = b;
         }
         if ((e = launch_sweep_first(f, s)) != cudaSuccess) return e;
@@ -315,7 +311,7 @@ static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, 
             b.phase = 2;
             b.wta = (rxs[v] == 0) ? 1 : 0;
             b.state = states + v * sw;
-            b.Lx = arena + l.Lx + static_cast<size_t>(v + 1) * lx_cube_bytes(p);
+            b.lx_off = (4 + v) * p.D;
             if ((e = launch_sweep_v(b, s)) != cudaSuccess) return e;
             if ((e = mark()) != cudaSuccess) return e;
         }
@@ -451,11 +447,11 @@ static int enqueue_wave(sgm_ctx* ctx, std::vector<BatchItem>& items, size_t b, s
             uint32_t* Fb = reinterpret_cast<uint32_t*>(base + l.Fb);
             uint32_t* Fm = reinterpret_cast<uint32_t*>(base + l.Fm);
             ct.job[k] = CensusJob{it.left, it.right, Fb, Fm, it.p.W, it.p.H};
-            mt.job[k] = CostJob{Fb, Fm, base + l.MC, it.p.W, it.p.H};
+            mt.job[k] = CostJob{Fb, Fm, base + l.rec, l.RB, it.p.W, it.p.H};
             SweepArgs a{};
-            a.MC = base + l.MC;
-            a.Lx = base + l.Lx;
-            a.S = reinterpret_cast<uint32_t*>(base + l.S);
+            a.rec = base + l.rec;
+            a.RB = l.RB;
+            a.lx_off = 3 * it.p.D;  // one stored-L_r field, reused pair after pair
             a.raw = base + l.raw;
             a.W = it.p.W;
             a.H = it.p.H;
@@ -1019,7 +1015,7 @@ int sgm_debug_stages(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, in
     if (Fb) CUDA_TRY(ctx, cudaMemcpyAsync(Fb, a + l.Fb, 4 * wh, cudaMemcpyDeviceToHost, s));
     if (Fm) CUDA_TRY(ctx, cudaMemcpyAsync(Fm, a + l.Fm, 4 * wh, cudaMemcpyDeviceToHost, s));
     if (MC) {
-        CUDA_TRY(ctx, launch_unpair_cost(a + l.MC, MCnat, W, H, D, s));
+        CUDA_TRY(ctx, launch_unpair_cost(a + l.rec, l.RB, MCnat, W, H, D, s));
         CUDA_TRY(ctx, cudaMemcpyAsync(MC, MCnat, wh * D, cudaMemcpyDeviceToHost, s));
     }
     if (S) CUDA_TRY(ctx, cudaMemcpyAsync(S, Sdev, 2 * wh * D, cudaMemcpyDeviceToHost, s));
@@ -1101,11 +1097,11 @@ cudaError_t enqueue_path_static(const Problem& p, uint8_t* arena, const uint8_t*
     uint32_t* Fm = reinterpret_cast<uint32_t*>(arena + l.Fm);
     cudaError_t e;
     if ((e = launch_census(left, right, Fb, Fm, p.W, p.H, s)) != cudaSuccess) return e;
-    if ((e = launch_cost(Fb, Fm, arena + l.MC, p.W, p.H, p.D, s)) != cudaSuccess) return e;
+    if ((e = launch_cost(Fb, Fm, arena + l.rec, l.RB, p.W, p.H, p.D, s)) != cudaSuccess) return e;
     SweepArgs a{};
-    a.MC = arena + l.MC;
-    a.Lx = arena + l.Lx;
-    a.S = reinterpret_cast<uint32_t*>(arena + l.S);
+    a.rec = arena + l.rec;
+    a.RB = l.RB;
+    a.lx_off = 3 * p.D;  // every pair runs both phases in one launch: field 0 serves them in turn
     a.raw = arena + l.raw;
     a.W = p.W;
     a.H = p.H;

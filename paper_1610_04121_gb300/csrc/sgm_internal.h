@@ -6,13 +6,20 @@
 
 namespace sgm {
 
+// The sweeps keep every per-(pixel, disparity) cube of a pair in one array of
+// per-pixel records [H][W][RB] bytes: the paired costs MC (D bytes, offset 0),
+// the sums S (offset D: D paired bytes when s8, else D/2 packed u16x2 words),
+// then one stored-L_r field (D paired bytes) per pair of opposite paths that
+// needs its own.  One offset then addresses every field of a step's pixel.
+inline int record_bytes(int D, bool s8, int n_lx) { return D + (s8 ? D : 2 * D) + n_lx * D; }
+
 // Arguments of the aggregation sweeps (Eq. 3) over one pair.
 struct SweepArgs {
-    const uint8_t* MC;  // paired costs [H][W][D]
-    uint8_t* Lx;        // scratch: one direction's path costs, paired [H][W][D]
-    uint32_t* S;        // sums: packed u16x2 words [H][W][D/2], or paired bytes [H][W][D] (s8)
+    uint8_t* rec;       // per-pixel records [H][W][RB]
     uint8_t* raw;       // winner-take-all disparity [H][W] (final vertical sweep)
     uint16_t* Sdbg;     // optional natural-order S [H][W][D] (debug)
+    int RB;             // record bytes (W * H * RB < 2^32)
+    int lx_off;         // byte offset of this pair's stored-L_r field in a record
     int W, H, D;
     uint32_t P1x2, P2x2;  // penalties replicated in both u16 halves
     int rx;               // vertical-type sweeps: 0 (vertical), +1 / -1 (diagonals)
@@ -21,7 +28,7 @@ struct SweepArgs {
     int phase;            // vertical-type pairs: 0 = both phases, 1 = first half of each path
                           // (saves the path state), 2 = second half (restores it)
     uint32_t* state;      // path states between phases 1 and 2 (sweep_state_words)
-    int s8;               // pairs: S kept as paired bytes [H][W][D] instead of u16x2 words
+    int s8;               // S kept as paired bytes instead of u16x2 words
 };
 
 // Every sum S held between sweeps fits a byte: with 2 paths S = L_LR <= 31 + P2
@@ -43,8 +50,8 @@ struct CensusJob {
 };
 struct CostJob {
     const uint32_t *Fb, *Fm;
-    uint8_t* MC;
-    int W, H;
+    uint8_t* rec;  // MC is written at offset 0 of each RB-byte record
+    int RB, W, H;
 };
 struct MedianJob {
     const uint8_t* raw;
@@ -62,7 +69,8 @@ struct JobTable {
 // Each launcher enqueues one kernel on `stream` and returns the launch error.
 cudaError_t launch_census(const uint8_t* left, const uint8_t* right, uint32_t* Fb, uint32_t* Fm, int W, int H,
                           cudaStream_t stream);
-cudaError_t launch_cost(const uint32_t* Fb, const uint32_t* Fm, uint8_t* MC, int W, int H, int D,
+// MC goes to offset 0 of the RB-byte record of each pixel.
+cudaError_t launch_cost(const uint32_t* Fb, const uint32_t* Fm, uint8_t* rec, int RB, int W, int H, int D,
                         cudaStream_t stream);
 cudaError_t launch_sweep_h(const SweepArgs& a, cudaStream_t stream);
 // The first sweep stage of a path with pairs (4 or 8 directions): the
@@ -92,8 +100,8 @@ cudaError_t launch_cost_batch(JobTable<CostJob>& t, int D, cudaStream_t stream);
 cudaError_t launch_median_batch(JobTable<MedianJob>& t, cudaStream_t stream);
 cudaError_t launch_sweep_h_batch(JobTable<SweepArgs>& t, cudaStream_t stream);
 cudaError_t launch_sweep_v_batch(JobTable<SweepArgs>& t, cudaStream_t stream);
-// Debug: paired costs -> natural order [H][W][D].
-cudaError_t launch_unpair_cost(const uint8_t* MC, uint8_t* out, int W, int H, int D, cudaStream_t stream);
+// Debug: paired costs (offset 0 of RB-byte records) -> natural order [H][W][D].
+cudaError_t launch_unpair_cost(const uint8_t* rec, int RB, uint8_t* out, int W, int H, int D, cudaStream_t stream);
 
 bool supported_D(int D);
 

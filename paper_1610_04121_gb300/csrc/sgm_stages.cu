@@ -125,7 +125,7 @@ constexpr int kMcSeg = 128, kMcPix = 4, kMcThreads = 128;
 
 template <int D>
 __device__ __forceinline__ void cost_body(const uint32_t* __restrict__ Fb, const uint32_t* __restrict__ Fm,
-                                          uint8_t* __restrict__ MC, int W, int seg, int y) {
+                                          uint8_t* __restrict__ rec, int RB, int W, int seg, int y) {
     constexpr int Q = D / 4, half = D / 2, NF = kMcSeg + D;  // words per pixel; staged match features (even)
     __shared__ __align__(16) uint32_t fm[NF];  // fm[k] = F_match(x0 - D + k)
     __shared__ __align__(16) uint32_t fb[kMcSeg];
@@ -156,7 +156,7 @@ __device__ __forceinline__ void cost_body(const uint32_t* __restrict__ Fb, const
     __syncthreads();
     const int npx = min(kMcSeg, W - x0);
     const int items = ((npx + kMcPix - 1) / kMcPix) * Q;
-    uint32_t* out = reinterpret_cast<uint32_t*>(MC + ((size_t)y * W + x0) * D);
+    uint8_t* out = rec + ((size_t)y * W + x0) * RB;  // MC at offset 0 of each record
     for (int t = threadIdx.x; t < items; t += kMcThreads) {
         const int g = t / Q, wi = t - g * Q, i0 = 2 * wi, px = g * kMcPix;
         // F_match(x - d) for x = x0 + px + p lives at fm[px + p + D - d]
@@ -182,16 +182,17 @@ __device__ __forceinline__ void cost_body(const uint32_t* __restrict__ Fb, const
             const uint32_t c1 = __popc(b ^ rb[p + 2]);  // d = i0 + D/2
             const uint32_t c2 = __popc(b ^ ra[p + 1]);  // d = i0 + 1
             const uint32_t c3 = __popc(b ^ rb[p + 1]);  // d = i0 + 1 + D/2
-            out[(px + p) * Q + wi] = __byte_perm(c0 | (c2 << 16), c1 | (c3 << 16), 0x6240u);  // [c0, c1, c2, c3]
+            reinterpret_cast<uint32_t*>(out + (size_t)(px + p) * RB)[wi] =
+                __byte_perm(c0 | (c2 << 16), c1 | (c3 << 16), 0x6240u);  // [c0, c1, c2, c3]
         }
     }
 }
 
 template <int D>
 __global__ void __launch_bounds__(kMcThreads) cost_kernel(const uint32_t* __restrict__ Fb,
-                                                          const uint32_t* __restrict__ Fm, uint8_t* __restrict__ MC,
-                                                          int W) {
-    cost_body<D>(Fb, Fm, MC, W, blockIdx.x, blockIdx.y);
+                                                          const uint32_t* __restrict__ Fm, uint8_t* __restrict__ rec,
+                                                          int RB, int W) {
+    cost_body<D>(Fb, Fm, rec, RB, W, blockIdx.x, blockIdx.y);
 }
 
 template <int D>
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(kMcThreads) cost_batch_kernel(const __grid_con
     const CostJob& j = t.job[p];
     const int b = blockIdx.x - t.start[p];
     const int segs = (j.W + kMcSeg - 1) / kMcSeg;
-    cost_body<D>(j.Fb, j.Fm, j.MC, j.W, b % segs, b / segs);
+    cost_body<D>(j.Fb, j.Fm, j.rec, j.RB, j.W, b % segs, b / segs);
 }
 
 template <int D>
@@ -226,41 +227,42 @@ cudaError_t launch_cost_batch(JobTable<CostJob>& t, int D, cudaStream_t stream) 
 }
 
 template <int D>
-static cudaError_t launch_cost_t(const uint32_t* Fb, const uint32_t* Fm, uint8_t* MC, int W, int H, cudaStream_t s) {
+static cudaError_t launch_cost_t(const uint32_t* Fb, const uint32_t* Fm, uint8_t* rec, int RB, int W, int H,
+                                 cudaStream_t s) {
     const dim3 grid((W + kMcSeg - 1) / kMcSeg, H);
-    cost_kernel<D><<<grid, kMcThreads, 0, s>>>(Fb, Fm, MC, W);
+    cost_kernel<D><<<grid, kMcThreads, 0, s>>>(Fb, Fm, rec, RB, W);
     return cudaGetLastError();
 }
 
-cudaError_t launch_cost(const uint32_t* Fb, const uint32_t* Fm, uint8_t* MC, int W, int H, int D,
+cudaError_t launch_cost(const uint32_t* Fb, const uint32_t* Fm, uint8_t* rec, int RB, int W, int H, int D,
                         cudaStream_t stream) {
     switch (D) {
-        case 32: return launch_cost_t<32>(Fb, Fm, MC, W, H, stream);
-        case 64: return launch_cost_t<64>(Fb, Fm, MC, W, H, stream);
-        case 96: return launch_cost_t<96>(Fb, Fm, MC, W, H, stream);
-        case 128: return launch_cost_t<128>(Fb, Fm, MC, W, H, stream);
-        case 160: return launch_cost_t<160>(Fb, Fm, MC, W, H, stream);
-        case 192: return launch_cost_t<192>(Fb, Fm, MC, W, H, stream);
-        case 224: return launch_cost_t<224>(Fb, Fm, MC, W, H, stream);
-        case 256: return launch_cost_t<256>(Fb, Fm, MC, W, H, stream);
+        case 32: return launch_cost_t<32>(Fb, Fm, rec, RB, W, H, stream);
+        case 64: return launch_cost_t<64>(Fb, Fm, rec, RB, W, H, stream);
+        case 96: return launch_cost_t<96>(Fb, Fm, rec, RB, W, H, stream);
+        case 128: return launch_cost_t<128>(Fb, Fm, rec, RB, W, H, stream);
+        case 160: return launch_cost_t<160>(Fb, Fm, rec, RB, W, H, stream);
+        case 192: return launch_cost_t<192>(Fb, Fm, rec, RB, W, H, stream);
+        case 224: return launch_cost_t<224>(Fb, Fm, rec, RB, W, H, stream);
+        case 256: return launch_cost_t<256>(Fb, Fm, rec, RB, W, H, stream);
         default: return cudaErrorInvalidValue;
     }
 }
 
-// Paired order -> natural order [H][W][D] (debug only).
-__global__ void unpair_kernel(const uint8_t* __restrict__ MC, uint8_t* __restrict__ out, size_t npix, int D) {
+// Paired order in RB-byte records -> natural order [H][W][D] (debug only).
+__global__ void unpair_kernel(const uint8_t* __restrict__ rec, int RB, uint8_t* __restrict__ out, size_t npix, int D) {
     const size_t n = npix * D;
     const int half = D / 2;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
         const size_t p = t / D;
         const int d = static_cast<int>(t % D);
         const int src = (d < half) ? 2 * d : 2 * (d - half) + 1;
-        out[t] = MC[p * D + src];
+        out[t] = rec[p * RB + src];
     }
 }
 
-cudaError_t launch_unpair_cost(const uint8_t* MC, uint8_t* out, int W, int H, int D, cudaStream_t stream) {
-    unpair_kernel<<<1024, 256, 0, stream>>>(MC, out, (size_t)W * H, D);
+cudaError_t launch_unpair_cost(const uint8_t* rec, int RB, uint8_t* out, int W, int H, int D, cudaStream_t stream) {
+    unpair_kernel<<<1024, 256, 0, stream>>>(rec, RB, out, (size_t)W * H, D);
     return cudaGetLastError();
 }
 

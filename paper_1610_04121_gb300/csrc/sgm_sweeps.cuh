@@ -14,7 +14,10 @@
 // Each lane streams its own bytes of every step's inputs (costs, the other
 // direction's stored L_r, sums) straight from global memory into registers,
 // one chunk of PF steps ahead of the recurrence, and writes its outputs with
-// one coalesced store per step; no shared memory is used.
+// one coalesced store per step; no shared memory is used.  All cubes of a
+// pair live in one array of per-pixel records (sgm_internal.h), so a step's
+// loads and stores share one 32-bit record offset, widened onto per-lane
+// bases with one mad.wide (on the FMA pipe, off the busy integer ALU).
 //
 //   sweep_h : left-to-right with right-to-left, one row per line;
 //             writes S = L_LR + L_RL.
@@ -133,10 +136,34 @@ __device__ __forceinline__ void ldg_words(const uint32_t* p, uint32_t (&w)[K]) {
     }
 }
 
-// One step's inputs for one lane, and their loads at byte offset `off` of the
-// pixel's paired cube entry (the word offset of u16 sums is off / 2).
-template <int K, int MODE, bool S8>
+// 64-bit address base + 32-bit offset in one instruction (IMAD.WIDE.U32).
+__device__ __forceinline__ const uint8_t* at(const uint8_t* base, uint32_t off) {
+    uint64_t r;
+    asm("mad.wide.u32 %0, %1, 1, %2;" : "=l"(r) : "r"(off), "l"(reinterpret_cast<uint64_t>(base)));
+    return reinterpret_cast<const uint8_t*>(r);
+}
+__device__ __forceinline__ uint8_t* at(uint8_t* base, uint32_t off) {
+    return const_cast<uint8_t*>(at(static_cast<const uint8_t*>(base), off));
+}
+
+// A lane's bases into the records: its paired bytes of MC (and, at +D, of
+// byte sums), its u16 sum words, and its bytes of the pair's stored L_r.
+struct LaneBases {
+    uint8_t* pairs;
+    uint8_t* words;
+    uint8_t* lx;
+};
+
+template <int D>
+__device__ __forceinline__ LaneBases lane_bases(const SweepArgs& a, int pl) {
+    constexpr int K = PathShape<D>::K;
+    return LaneBases{a.rec + 2 * K * pl, a.rec + D + 4 * K * pl, a.rec + a.lx_off + 2 * K * pl};
+}
+
+// One step's inputs for one lane, loaded from the record at byte offset `off`.
+template <int D, int MODE, bool S8>
 struct StepIn {
+    static constexpr int K = PathShape<D>::K;
     using M = ModeIO<MODE>;
     static constexpr int PW = (K + 1) / 2;
     static constexpr int REGS = PW + (M::IN_LO ? PW : 0) + (M::IN_S ? (S8 ? PW : K) : 0);
@@ -144,14 +171,15 @@ struct StepIn {
     Regs<M::IN_LO ? PW : 0> lo;
     Regs<M::IN_S ? (S8 ? PW : K) : 0> s;
 
-    __device__ __forceinline__ void load(const SweepArgs& a, size_t off) {
-        ldg_pairs<K, true>(a.MC + off, mc.r);
-        if constexpr (M::IN_LO) ldg_pairs<K, false>(a.Lx + off, lo.r);
+    __device__ __forceinline__ void load(const LaneBases& lb, uint32_t off) {
+        const uint8_t* p = at(lb.pairs, off);
+        ldg_pairs<K, true>(p, mc.r);
+        if constexpr (M::IN_LO) ldg_pairs<K, false>(at(lb.lx, off), lo.r);
         if constexpr (M::IN_S) {
             if constexpr (S8)
-                ldg_pairs<K, false>(reinterpret_cast<const uint8_t*>(a.S) + off, s.r);
+                ldg_pairs<K, false>(p + D, s.r);
             else
-                ldg_words<K>(a.S + off / 2, s.r);
+                ldg_words<K>(reinterpret_cast<const uint32_t*>(at(lb.words, off)), s.r);
         }
     }
 };
@@ -267,23 +295,24 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
                                      int n_other, const SweepArgs& a, int pl) {
     constexpr int G = PathShape<D>::G, K = PathShape<D>::K;
     using M = ModeIO<MODE>;
-    using In = StepIn<K, MODE, S8>;
+    using In = StepIn<D, MODE, S8>;
     constexpr int PF = prefetch_steps(In::REGS);
     const int n_min = min(n_own, n_other), n_max = max(n_own, n_other);
-    const size_t lane_off = static_cast<size_t>(pl) * 2 * K;
+    const uint32_t RB = static_cast<uint32_t>(a.RB);
+    const LaneBases lb = lane_bases<D>(a, pl);
     // Every load is issued unconditionally: past the end of this lane's path it
     // re-reads the path's first pixel (a predicated load would keep the old
     // register value alive and make the step wait for the load).
     In nxt[PF];
     typename Geo::Cursor ld = g.start(), cur = ld;
     const int pix0 = n_own > 0 ? ld.pix : 0;  // an empty path (W or H of 1) may start outside the image
-    auto prefetch = [&](In& b, int i) {
-        const int pix = i < n_own ? ld.pix : pix0;
-        b.load(a, static_cast<size_t>(pix) * D + lane_off);
+    auto prefetch = [&](In& b, int i, bool clamp) {
+        const int pix = (clamp && i >= n_own) ? pix0 : ld.pix;
+        b.load(lb, static_cast<uint32_t>(pix) * RB);
         g.advance(ld);
     };
 #pragma unroll
-    for (int k = 0; k < PF; ++k) prefetch(nxt[k], k);
+    for (int k = 0; k < PF; ++k) prefetch(nxt[k], k, true);
     uint32_t dconst[K];
     if constexpr (M::WTA) wta_consts<K>(pl, D, dconst);
 
@@ -295,9 +324,9 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
         uint32_t mc[K], L[K];
         unpack_regs<K>(in.mc.r, mc);
         ch.step(mc, a.P1x2, a.P2x2, L);
-        const size_t off = static_cast<size_t>(cur.pix) * D + lane_off;
+        const uint32_t off = static_cast<uint32_t>(cur.pix) * RB;
         if constexpr (M::OUT_LX) {
-            if (active) st_pairs<K>(a.Lx + off, pack_pairs<K>(L));
+            if (active) st_pairs<K>(at(lb.lx, off), pack_pairs<K>(L));
         } else {
             uint32_t s[K];
 #pragma unroll
@@ -322,9 +351,9 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
             if constexpr (M::OUT_S) {
                 if (active) {
                     if constexpr (S8)
-                        st_pairs<K>(reinterpret_cast<uint8_t*>(a.S) + off, pack_pairs<K>(s));
+                        st_pairs<K>(at(lb.pairs, off) + D, pack_pairs<K>(s));
                     else
-                        st_words<K>(a.S + off / 2, s);
+                        st_words<K>(reinterpret_cast<uint32_t*>(at(lb.words, off)), s);
                 }
             }
             if constexpr (M::WTA) {
@@ -347,8 +376,13 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
         In in[PF];
 #pragma unroll
         for (int k = 0; k < PF; ++k) in[k] = nxt[k];
+        if (i0 + 2 * PF <= n_min) {
 #pragma unroll
-        for (int k = 0; k < PF; ++k) prefetch(nxt[k], i0 + PF + k);
+            for (int k = 0; k < PF; ++k) prefetch(nxt[k], i0 + PF + k, false);
+        } else {
+#pragma unroll
+            for (int k = 0; k < PF; ++k) prefetch(nxt[k], i0 + PF + k, true);
+        }
         if (n_min - i0 >= PF) {
 #pragma unroll
             for (int k = 0; k < PF; ++k) {
