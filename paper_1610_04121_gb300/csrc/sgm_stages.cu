@@ -16,9 +16,11 @@ namespace sgm {
 // (i-1)*7 + j+3; the i = 0 pairs j = 1..3 give bits 28..30; s(u,v) = u >= v.
 // Each bit costs two instructions: for bytes u, v the value v + ~u = v - u - 1
 // is negative exactly when u >= v, and a funnel shift moves its sign bit in
-// below the bits already collected (highest bit first).
+// below the bits already collected (highest bit first).  The 31 bits are
+// gathered as four independent 8-bit chains joined by byte permutes, which
+// keeps the dependent chain per pixel short.
 // ---------------------------------------------------------------------------
-constexpr int kCtW = 64, kCtH = 16;
+constexpr int kCtW = 64, kCtH = 8;
 
 __device__ __forceinline__ void census_body(const uint8_t* __restrict__ left, const uint8_t* __restrict__ right,
                                             uint32_t* __restrict__ Fb, uint32_t* __restrict__ Fm, int W, int H,
@@ -66,16 +68,26 @@ __device__ __forceinline__ void census_body(const uint8_t* __restrict__ left, co
         for (int c = 0; c < 9; ++c) win[(r + 6) % 7][c] = tile[r + 6][lx + c];
         const int y = y0 + r;
         if (y >= H) break;
-        // window row k (image y - 3 + k) is win[(r + k) % 7]
-        uint32_t f = 0;
+        // window row k (image y - 3 + k) is win[(r + k) % 7]; bit b of the
+        // feature compares the pair given by pair_of(b) below
+        auto diff = [&](int b) -> uint32_t {
+            int i, j;
+            if (b >= 28) {
+                i = 0;
+                j = b - 27;  // bits 28..30: i = 0, j = 1..3
+            } else {
+                i = b / 7 + 1;
+                j = b % 7 - 3;  // bit (i-1)*7 + j+3
+            }
+            return win[(r + 3 - j) % 7][4 - i] + ~win[(r + 3 + j) % 7][4 + i];  // sign: I(x+i,y+j) >= I(x-i,y-j)
+        };
+        uint32_t c[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-        for (int j = 3; j >= 1; --j)  // bits 30..28: i = 0
-            f = __funnelshift_l(win[(r + 3 - j) % 7][4] + ~win[(r + 3 + j) % 7][4], f, 1);
+        for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int i = 4; i >= 1; --i)
-#pragma unroll
-            for (int j = 3; j >= -3; --j)  // bits (i-1)*7 + j+3, highest first
-                f = __funnelshift_l(win[(r + 3 - j) % 7][4 - i] + ~win[(r + 3 + j) % 7][4 + i], f, 1);
+            for (int b = q * 8 + 7; b >= q * 8; --b)  // highest bit of the byte first
+                if (b < 31) c[q] = __funnelshift_l(diff(b), c[q], 1);
+        const uint32_t f = __byte_perm(__byte_perm(c[0], c[1], 0x0040u), __byte_perm(c[2], c[3], 0x0040u), 0x5410u);
         const bool ok = x_ok && y >= 3 && y <= H - 4;
         F[(size_t)y * W + x] = ok ? f : 0u;
     }
