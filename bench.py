@@ -46,10 +46,7 @@ SERVED_OUT_RING = 4  # output buffers per pool pair (a pair can be in flight mor
 # DRAM bytes (read + write) per launch of a kernel, from the ncu capture summarised
 # under profiles/, with the fingerprint of the kernel sources it was taken on;
 # reported as null once those sources have changed since the capture.
-MEASURED_TRAFFIC = {
-    ("sgm_640x480_d128_p4", "sweep_h"): (135506432, "927fe7401ea36edd"),
-    ("sgm_640x480_d128_p4", "sweep_v"): (161556736, "927fe7401ea36edd"),
-}
+MEASURED_TRAFFIC = {}
 KERNEL_SOURCES = ("sgm_sweeps.cuh", "sgm_device.cuh", "sgm_internal.h")
 
 
@@ -508,12 +505,19 @@ def main():
     clocks = clk.summary()
     mean_stage = {k: statistics.mean(v) for k, v in stage_ms.items()}
     # the dominant kernel: each stage is one kernel launch.  Path units per
-    # launch: sweep_h carries the horizontal pair (2) and, with pairs, the first
-    # halves of the (n_paths - 2) / 2 vertical-type pairs (1 each); every later
-    # sweep carries the second halves of one pair (1).  Extra adds per DE: the
-    # stored-L add (+ the S add (+ the winner-take-all minimum)).
+    # launch (one unit = one path over every DE) and extra adds per DE:
+    #   2 paths: sweep_h one path; sweep_v one path, S add and the minimum.
+    #   4 paths: sweep_v+h1 the whole vertical pair (2) and the horizontal
+    #     first halves (1), plus the stored-L add of the vertical second
+    #     halves; sweep_h2 the horizontal second halves (1), the stored-L and
+    #     S adds and the minimum.
+    #   8 paths: sweep_h the horizontal pair (2) and the first halves of three
+    #     vertical-type pairs (3), plus the horizontal stored-L add; every
+    #     later sweep the second halves of one pair (1) with its adds.
     if w.n_paths == 2:
         kernel_stages = {"sweep_h": (1, 0), "sweep_v": (1, 2)}
+    elif w.n_paths == 4:
+        kernel_stages = {"sweep_v+h1": (3, 1), "sweep_h2": (1, 3)}
     else:
         kernel_stages = {"sweep_h": (2 + (w.n_paths - 2) // 2, 1), "sweep_v": (1, 3), "sweep_diag+": (1, 2),
                          "sweep_diag-": (1, 2)}

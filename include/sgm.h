@@ -209,14 +209,22 @@ SGM_API int sgm_debug_stages(sgm_ctx *ctx, const uint8_t *left, const uint8_t *r
  * context created with SGM_FLAG_STAGE_TIMING.  Waits for that path to finish.
  * Writes min(n, stages) values to ms_out and returns the number of stages
  * (5 for 2 or 4 paths, 7 for 8 paths), or a negative sgm_status.  Stage
- * names, in order: census, cost, sweep_h (the horizontal pair; with 4 or 8
- * paths the first halves of the vertical-type pairs run in the same launch),
- * [sweep_diag+, sweep_diag-,] sweep_v, median (sgm_stage_name).
+ * names, in order (sgm_stage_name): census, cost, then the sweeps, then
+ * median.  Sweeps with 2 paths: sweep_h (left to right), sweep_v (top to
+ * bottom with the winner-take-all).  With 4 paths: sweep_v+h1 (the whole
+ * vertical pair beside the first halves of the horizontal pair), sweep_h2
+ * (the horizontal second halves with the winner-take-all).  With 8 paths:
+ * sweep_h (the horizontal pair with the first halves of the three
+ * vertical-type pairs), sweep_diag+, sweep_diag-, sweep_v.
  */
 SGM_API int sgm_stage_times(sgm_ctx *ctx, float *ms_out, int n);
 
 /* Name of stage i of a path with n_paths directions, or NULL. */
 SGM_API const char *sgm_stage_name(int n_paths, int i);
+
+/* Path count (2, 4 or 8) of the path that sgm_stage_times reports on, or 0
+ * when none has been enqueued with SGM_FLAG_STAGE_TIMING. */
+SGM_API int sgm_stage_paths(const sgm_ctx *ctx);
 
 /*
  * Kernel launches issued by this context so far (every launch of this

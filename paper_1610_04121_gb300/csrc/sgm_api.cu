@@ -56,8 +56,10 @@ Layout layout_for(int W, int H, int D_int, int n_paths, bool batched = false) {
     o = align_up(o + wh * static_cast<size_t>(l.RB));
     l.raw = o;
     o = align_up(o + wh);
-    l.state = o;  // path states of the vertical-type pairs between their phases
-    o = align_up(o + (n_paths == 8 ? 3 : 1) * 4 * sweep_state_words(W, static_cast<int>(D)));
+    l.state = o;  // path states between the two phases of a pair: the vertical-type pairs (8 paths), the
+                  // horizontal pair (4 paths)
+    o = align_up(o + 4 * (n_paths == 8 ? 3 * sweep_state_words(W, static_cast<int>(D))
+                                       : sweep_state_words(std::max(W, H), static_cast<int>(D))));
     l.in_left = o;
     o = align_up(o + wh);
     l.in_right = o;
@@ -146,6 +148,7 @@ struct sgm_ctx {
     bool stage_timing = false;
     cudaEvent_t stage_ev[10] = {};
     int last_stages = 0;
+    int last_n_paths = 0;  // path count of the last path enqueued with stage timing
 
     // served requests
     std::mutex mu;
@@ -288,6 +291,23 @@ static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, 
         a.wta = 1;
         if ((e = launch_sweep_v(a, s)) != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
+    } else if (p.n_paths == 4) {
+        // 4 paths: the whole vertical pair (S = L_TB + L_BT) beside the
+        // horizontal first halves, then the horizontal second halves with Eq. 4
+        FirstStageArgs f{};
+        f.h = a;
+        f.h.state = states;
+        f.nv = 1;
+        f.v[0] = a;
+        f.v[0].lx_off = 4 * p.D;  // the vertical pair's stored-L_r field
+        if ((e = launch_sweep_first4(f, s)) != cudaSuccess) return e;
+        if ((e = mark()) != cudaSuccess) return e;
+        SweepArgs b = a;
+        b.state = states;
+        b.wta = 1;
+        b.phase = 2;
+        if ((e = launch_sweep_h2(b, s)) != cudaSuccess) return e;
+        if ((e = mark()) != cudaSuccess) return e;
     } else {
         // the first halves of the vertical-type pairs need only the costs: they
         // run in the same launch as the horizontal pair
@@ -352,6 +372,7 @@ static int enqueue_graph(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const u
     CUDA_TRY(ctx, cudaGraphLaunch(it->second, s));
     ctx->launches += launches_per_path(p);
     ctx->last_stages = ctx->stage_timing ? stages_per_path(p) : 0;
+    ctx->last_n_paths = ctx->stage_timing ? p.n_paths : 0;
     return SGM_OK;
 }
 
@@ -1035,13 +1056,20 @@ int sgm_stage_times(sgm_ctx* ctx, float* ms_out, int n) {
     return k;
 }
 
+int sgm_stage_paths(const sgm_ctx* ctx) { return ctx ? ctx->last_n_paths : 0; }
+
 const char* sgm_stage_name(int n_paths, int i) {
-    // "sweep_h" is the first sweep launch: the horizontal pair, with the
-    // vertical-type first halves in the same launch when there are pairs
-    static const char* five[] = {"census", "cost", "sweep_h", "sweep_v", "median"};
+    // 2 paths: "sweep_h" (left to right), "sweep_v" (top to bottom with Eq. 4).
+    // 4 paths: "sweep_v+h1" (the whole vertical pair beside the horizontal
+    // first halves), "sweep_h2" (the horizontal second halves with Eq. 4).
+    // 8 paths: "sweep_h" (the horizontal pair with the first halves of the
+    // three vertical-type pairs), then one launch per second half.
+    static const char* two[] = {"census", "cost", "sweep_h", "sweep_v", "median"};
+    static const char* four[] = {"census", "cost", "sweep_v+h1", "sweep_h2", "median"};
     static const char* eight[] = {"census", "cost", "sweep_h", "sweep_diag+", "sweep_diag-", "sweep_v", "median"};
     if (n_paths == 8) return (i >= 0 && i < 7) ? eight[i] : nullptr;
-    if (n_paths == 4 || n_paths == 2) return (i >= 0 && i < 5) ? five[i] : nullptr;
+    if (n_paths == 4) return (i >= 0 && i < 5) ? four[i] : nullptr;
+    if (n_paths == 2) return (i >= 0 && i < 5) ? two[i] : nullptr;
     return nullptr;
 }
 

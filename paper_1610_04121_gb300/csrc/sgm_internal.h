@@ -85,6 +85,11 @@ struct FirstStageArgs {
     int start[5];
 };
 cudaError_t launch_sweep_first(FirstStageArgs& f, cudaStream_t stream);
+// 4 paths: the horizontal first halves (saving their state in f.h.state) beside
+// the whole vertical pair f.v[0], which writes S; then the horizontal second
+// halves finish with Eq. 4 (launch_sweep_h2, a.state as in the first stage).
+cudaError_t launch_sweep_first4(FirstStageArgs& f, cudaStream_t stream);
+cudaError_t launch_sweep_h2(const SweepArgs& a, cudaStream_t stream);
 cudaError_t launch_sweep_v(const SweepArgs& a, cudaStream_t stream);
 // Words of saved path state per vertical-type pair between its two phases:
 // per line, 32 lanes x (K + 3) words for each warp carrying it (one warp of

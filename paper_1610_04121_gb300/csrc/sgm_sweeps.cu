@@ -38,6 +38,12 @@ cudaError_t launch_sweep_first(FirstStageArgs& f, cudaStream_t stream) {
     SGM_DISPATCH_D(sweep_launch_first, f.h.D, f, stream)
 }
 
+cudaError_t launch_sweep_first4(FirstStageArgs& f, cudaStream_t stream) {
+    SGM_DISPATCH_D(sweep_launch_first4, f.h.D, f, stream)
+}
+
+cudaError_t launch_sweep_h2(const SweepArgs& a, cudaStream_t stream) { SGM_DISPATCH_D(sweep_launch_h2, a.D, a, stream) }
+
 cudaError_t launch_sweep_h_batch(JobTable<SweepArgs>& t, cudaStream_t stream) {
     if (t.n < 1) return cudaSuccess;
     SGM_DISPATCH_D(sweep_launch_h_batch, t.job[0].D, t, stream)

@@ -407,14 +407,45 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
     }
 }
 
+// Path state of one lane between the two phases of a pair that run in
+// different launches: its K words, the two neighbour words and m, at
+// a.state + ((line * (warps per line) + warp of the line) * 32 + lane) * (K + 3).
+template <int D>
+__device__ __forceinline__ uint32_t* state_slot(const SweepArgs& a, int line, int dir) {
+    constexpr int G = PathShape<D>::G, K = PathShape<D>::K;
+    return a.state + ((static_cast<size_t>(line) * (2 / PathShape<D>::PPW) + (G == 32 ? dir : 0)) * 32 +
+                      (threadIdx.x & 31)) * (K + 3);
+}
+
+template <int G, int K>
+__device__ __forceinline__ void save_state(const Chain<G, K>& ch, uint32_t* st) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) st[j] = ch.w[j];
+    st[K] = ch.up;
+    st[K + 1] = ch.dn;
+    st[K + 2] = ch.mpx2;
+}
+
+template <int G, int K>
+__device__ __forceinline__ void load_state(Chain<G, K>& ch, const uint32_t* st) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) ch.w[j] = __ldcg(st + j);
+    ch.up = __ldcg(st + K);
+    ch.dn = __ldcg(st + K + 1);
+    ch.mpx2 = __ldcg(st + K + 2);
+}
+
 // ---------------------------------------------------------------------------
 // Horizontal axis: one row per line; direction A walks left to right,
 // direction B right to left.  Phase 1: A covers x < W/2, B covers x >= W/2,
-// both storing L in Lx.  Phase 2: each covers the other half and writes
-// S = own L + stored L.  Without `pair` (2-path mode) A covers the whole row
-// and writes S = L_LR.
+// both storing L in the stored-L_r field.  Phase 2: each covers the other
+// half and writes S = own L + stored L (WTA = false) or finishes with Eq. 4,
+// raw = argmin_d (S + own L + stored L), when S already holds the vertical
+// pair (WTA = true).  PH: 0 = both phases in one launch, 1 = phase 1 (saving
+// the path state), 2 = phase 2 (restoring it).  Without `pair` (2-path mode)
+// A covers the whole row and writes S = L_LR.
 // ---------------------------------------------------------------------------
-template <int D, bool PAIR, bool S8>
+template <int D, bool PAIR, bool S8, int PH = 0, bool WTA = false, bool DBG = false>
 __device__ __forceinline__ void sweep_h_body(const SweepArgs& a, int bx) {
     constexpr int G = PathShape<D>::G, K = PathShape<D>::K;
     const LaneRole<D, PAIR> r(bx);
@@ -434,18 +465,31 @@ __device__ __forceinline__ void sweep_h_body(const SweepArgs& a, int bx) {
         walk<D, kSingleH, S8>(ch, g, n, G == 16 ? ((y ^ 1) < a.H ? W : 0) : n, a, r.pl);
     } else {
         const int Wm = W / 2;
-        {
+        if constexpr (PH != 2) {
             const RowGeo g = in_b ? RowGeo{rowbase, W - 1, -1} : RowGeo{rowbase, 0, 1};
             const int nA = Wm, nB = W - Wm;
             walk<D, kStoreL, S8>(ch, g, in_b ? nB : nA, G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
         }
-        pair_barrier<D>();
+        if constexpr (PH == 1) {
+            save_state(ch, state_slot<D>(a, y, r.dir));
+            return;
+        }
+        if constexpr (PH == 2) load_state(ch, state_slot<D>(a, y, r.dir));
+        if constexpr (PH == 0) pair_barrier<D>();
         {
             const RowGeo g = in_b ? RowGeo{rowbase, Wm - 1, -1} : RowGeo{rowbase, Wm, 1};
             const int nA = W - Wm, nB = Wm;
-            walk<D, kSumH, S8>(ch, g, in_b ? nB : nA, G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
+            walk<D, WTA ? kWta2 : kSumH, S8, RowGeo, DBG>(ch, g, in_b ? nB : nA,
+                                                        G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
         }
     }
+}
+
+// Second halves of the horizontal pair with the winner-take-all (4 paths: S
+// holds the vertical pair's sums).
+template <int D, bool S8, bool DBG>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_h2_kernel(SweepArgs a) {
+    sweep_h_body<D, true, S8, 2, true, DBG>(a, blockIdx.x);
 }
 
 template <int D, bool PAIR, bool S8>
@@ -472,7 +516,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_h_batch_kernel(cons
 // PH: 0 = both phases in one launch, 1 = first halves (saving the path state),
 // 2 = second halves (restoring it).  WTA: the pair finishes with Eq. 4
 // instead of adding into S.  PAIR = false is the 2-path top-to-bottom sweep.
-template <int D, int RX, int PH, bool WTA, bool PAIR, bool S8, bool DBG = false>
+// SUMV: a pair that does not finish with Eq. 4 writes S = L + stored L (the
+// first pair to write S) instead of adding into S.
+template <int D, int RX, int PH, bool WTA, bool PAIR, bool S8, bool DBG = false, bool SUMV = false>
 __device__ __forceinline__ void sweep_v_body(const SweepArgs& a, int bx) {
     constexpr int G = PathShape<D>::G, K = PathShape<D>::K;
     const LaneRole<D, PAIR> r(bx);
@@ -491,36 +537,21 @@ __device__ __forceinline__ void sweep_v_body(const SweepArgs& a, int bx) {
                                           G == 16 ? ((c ^ 1) < W ? H : 0) : n, a, r.pl);
     } else {
         const int Hm = H / 2;
-        // saved path state of this lane: K words, the two neighbour words and m
-        uint32_t* st = nullptr;
-        if constexpr (PH != 0)
-            st = a.state + ((static_cast<size_t>(c) * (2 / PathShape<D>::PPW) + (G == 32 ? r.dir : 0)) * 32 + lane) *
-                               (K + 3);
         if constexpr (PH != 2) {
             const Geo g = in_b ? Geo{W, H, c, H - 1, -1} : Geo{W, H, c, 0, 1};
             const int nA = Hm, nB = H - Hm;
             walk<D, kStoreL, S8>(ch, g, in_b ? nB : nA, G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
         }
         if constexpr (PH == 1) {
-#pragma unroll
-            for (int j = 0; j < K; ++j) st[j] = ch.w[j];
-            st[K] = ch.up;
-            st[K + 1] = ch.dn;
-            st[K + 2] = ch.mpx2;
+            save_state(ch, state_slot<D>(a, c, r.dir));
             return;
         }
-        if constexpr (PH == 2) {
-#pragma unroll
-            for (int j = 0; j < K; ++j) ch.w[j] = __ldcg(st + j);
-            ch.up = __ldcg(st + K);
-            ch.dn = __ldcg(st + K + 1);
-            ch.mpx2 = __ldcg(st + K + 2);
-        }
+        if constexpr (PH == 2) load_state(ch, state_slot<D>(a, c, r.dir));
         if constexpr (PH != 1) {
             if constexpr (PH == 0) pair_barrier<D>();
             const Geo g = in_b ? Geo{W, H, c, Hm - 1, -1} : Geo{W, H, c, Hm, 1};
             const int nA = H - Hm, nB = Hm;
-            walk<D, WTA ? kWta2 : kAcc, S8, Geo, DBG>(ch, g, in_b ? nB : nA,
+            walk<D, WTA ? kWta2 : (SUMV ? kSumH : kAcc), S8, Geo, DBG>(ch, g, in_b ? nB : nA,
                                                       G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
         }
     }
@@ -568,6 +599,20 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_first_kernel(const 
     }
 }
 
+// 4 paths, first stage: the horizontal pair's first halves (saving their
+// state) beside the whole vertical pair, which writes S = L_TB + L_BT.  The
+// vertical chains (H steps) are longer than the horizontal first halves (W/2
+// steps at 640x480), so the grid stays busy to the end of the launch; the
+// horizontal second halves then finish with Eq. 4 (sweep_h2_kernel).
+template <int D, bool S8>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_first4_kernel(const __grid_constant__ FirstStageArgs f) {
+    const int b = blockIdx.x;
+    if (b < f.start[1])
+        sweep_h_body<D, true, S8, 1>(f.h, b);
+    else
+        sweep_v_body<D, 0, 0, false, true, S8, false, true>(f.v[0], b - f.start[1]);
+}
+
 // ---------------------------------------------------------------------------
 // Per-D entry points, instantiated one D per translation unit.  The sums are
 // bytes (S8) in 2-path mode always and in 4-path mode when SweepArgs::s8 is
@@ -606,6 +651,31 @@ struct SweepD {
             sweep_first_kernel<D, false, 1><<<grid, block, 0, s>>>(f);
         else
             sweep_first_kernel<D, false, 3><<<grid, block, 0, s>>>(f);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t launch_first4(FirstStageArgs& f, cudaStream_t s) {
+        f.start[0] = 0;
+        f.start[1] = blocks(f.h.H, true);
+        f.start[2] = f.start[1] + blocks(f.v[0].W, true);
+        const dim3 block(32 * kWarpsPerBlock);
+        if (f.h.s8)
+            sweep_first4_kernel<D, true><<<f.start[2], block, 0, s>>>(f);
+        else
+            sweep_first4_kernel<D, false><<<f.start[2], block, 0, s>>>(f);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t launch_h2(const SweepArgs& a, cudaStream_t s) {
+        const dim3 grid(blocks(a.H, true)), block(32 * kWarpsPerBlock);
+        if (a.s8 && a.Sdbg)
+            sweep_h2_kernel<D, true, true><<<grid, block, 0, s>>>(a);
+        else if (a.s8)
+            sweep_h2_kernel<D, true, false><<<grid, block, 0, s>>>(a);
+        else if (a.Sdbg)
+            sweep_h2_kernel<D, false, true><<<grid, block, 0, s>>>(a);
+        else
+            sweep_h2_kernel<D, false, false><<<grid, block, 0, s>>>(a);
         return cudaGetLastError();
     }
 
@@ -685,6 +755,10 @@ SGM_INTERNAL cudaError_t sweep_launch_first(FirstStageArgs& f, cudaStream_t s);
 template <int D>
 SGM_INTERNAL cudaError_t sweep_launch_h_batch(JobTable<SweepArgs>& t, cudaStream_t s);
 template <int D>
+SGM_INTERNAL cudaError_t sweep_launch_first4(FirstStageArgs& f, cudaStream_t s);
+template <int D>
+SGM_INTERNAL cudaError_t sweep_launch_h2(const SweepArgs& a, cudaStream_t s);
+template <int D>
 SGM_INTERNAL cudaError_t sweep_launch_v_batch(JobTable<SweepArgs>& t, cudaStream_t s);
 
 #define SGM_INSTANTIATE_SWEEPS(D)                                                               \
@@ -711,6 +785,14 @@ SGM_INTERNAL cudaError_t sweep_launch_v_batch(JobTable<SweepArgs>& t, cudaStream
     template <>                                                                                 \
     SGM_INTERNAL cudaError_t sweep_launch_v_batch<D>(JobTable<SweepArgs> & t, cudaStream_t s) { \
         return SweepD<D>::launch_v_batch(t, s);                                                 \
+    }                                                                                           \
+    template <>                                                                                 \
+    SGM_INTERNAL cudaError_t sweep_launch_first4<D>(FirstStageArgs & f, cudaStream_t s) {       \
+        return SweepD<D>::launch_first4(f, s);                                                  \
+    }                                                                                           \
+    template <>                                                                                 \
+    SGM_INTERNAL cudaError_t sweep_launch_h2<D>(const SweepArgs& a, cudaStream_t s) {           \
+        return SweepD<D>::launch_h2(a, s);                                                      \
     }
 
 }  // namespace sgm

@@ -64,6 +64,7 @@ _sig("sgm_debug_stages", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _vp, _
 _sig("sgm_kernel_launches", ctypes.c_uint64, [_vp])
 _sig("sgm_stage_times", _i, [_vp, ctypes.POINTER(ctypes.c_float), _i])
 _sig("sgm_stage_name", ctypes.c_char_p, [_i, _i])
+_sig("sgm_stage_paths", _i, [_vp])
 _sig("sgm_version", ctypes.c_char_p, [])
 _sig("sgm_compute_static", _i, [_vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _vp])
 
@@ -169,7 +170,7 @@ def sgm_stage_times(ctx) -> dict:
     n = _lib.sgm_stage_times(ctx, buf, 10)
     if n < 0:
         raise SgmError(n, last_error(ctx))
-    npaths = {7: 8, 5: 4}[n]  # 2 and 4 paths share the five stage names
+    npaths = _lib.sgm_stage_paths(ctx)
     return {_lib.sgm_stage_name(npaths, i).decode(): float(buf[i]) for i in range(n)}
 
 

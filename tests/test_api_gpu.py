@@ -131,7 +131,7 @@ def test_stage_times_inside_graph_replay(sgm):
         R = torch.from_numpy(p.right).cuda()
         out = torch.empty_like(L)
         sgm.sgm_set_stream(c.handle, torch.cuda.current_stream())
-        for n_paths, names in [(4, ["census", "cost", "sweep_h", "sweep_v", "median"]),
+        for n_paths, names in [(4, ["census", "cost", "sweep_v+h1", "sweep_h2", "median"]),
                                (8, ["census", "cost", "sweep_h", "sweep_diag+", "sweep_diag-", "sweep_v", "median"]),
                                (2, ["census", "cost", "sweep_h", "sweep_v", "median"])]:
             for _ in range(2):
