@@ -46,7 +46,10 @@ SERVED_OUT_RING = 4  # output buffers per pool pair (a pair can be in flight mor
 # DRAM bytes (read + write) per launch of a kernel, from the ncu capture summarised
 # under profiles/, with the fingerprint of the kernel sources it was taken on;
 # reported as null once those sources have changed since the capture.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    ("sgm_640x480_d128_p4", "sweep_v+h1"): (149343360, "8015d713dafc5080"),
+    ("sgm_640x480_d128_p4", "sweep_h2"): (119051520, "8015d713dafc5080"),
+}
 KERNEL_SOURCES = ("sgm_sweeps.cuh", "sgm_device.cuh", "sgm_internal.h")
 
 
