@@ -6,12 +6,13 @@
 namespace sgm {
 
 // ---------------------------------------------------------------------------
-// Eq. 1: 9x7 center-symmetric Census transform.  A CTA of kCtW threads covers
-// a kCtW x kCtH tile: the (kCtW+8) x (kCtH+6) bytes around it are staged in
-// shared memory (the read-cooperative 2D tiling of Section 3.1) and each
-// thread walks one column of the tile downwards with the 7 x 9 window in
-// registers, loading one new row of 9 bytes per pixel; blockIdx.z picks the
-// image.  The feature is 0 where the 9x7 window leaves the image.
+// Eq. 1: 9x7 center-symmetric Census transform.  A CTA of kCtT threads covers
+// a kCtW x kCtH tile (kCtW = 2 kCtT): the (kCtW+8) x (kCtH+6) bytes around it
+// are staged in shared memory (the read-cooperative 2D tiling of Section 3.1)
+// and each thread walks two adjacent columns of the tile downwards with the
+// 7 x 10 window they share in registers, loading one new row of 10 bytes per
+// pair of pixels; blockIdx.z picks the image.  The feature is 0 where the 9x7
+// window leaves the image.
 // Bit k follows the printed order of Eq. 1: i = 1..4, j = -3..3 give bit
 // (i-1)*7 + j+3; the i = 0 pairs j = 1..3 give bits 28..30; s(u,v) = u >= v.
 // Each bit costs two instructions: for bytes u, v the value v + ~u = v - u - 1
@@ -20,23 +21,48 @@ namespace sgm {
 // gathered as four independent 8-bit chains joined by byte permutes, which
 // keeps the dependent chain per pixel short.
 // ---------------------------------------------------------------------------
-constexpr int kCtW = 64, kCtH = 8;
+constexpr int kCtT = 32, kCtW = 2 * kCtT, kCtH = 8;
+
+// Census feature of the pixel whose 9 window columns start at column c0 of
+// the window rows; row k of the window (image y - 3 + k) is win[(r + k) % 7].
+template <int NC>
+__device__ __forceinline__ uint32_t census_feature(const uint32_t (&win)[7][NC], int r, int c0) {
+    auto diff = [&](int b) -> uint32_t {
+        int i, j;
+        if (b >= 28) {
+            i = 0;
+            j = b - 27;  // bits 28..30: i = 0, j = 1..3
+        } else {
+            i = b / 7 + 1;
+            j = b % 7 - 3;  // bit (i-1)*7 + j+3
+        }
+        // sign bit set when I(x+i, y+j) >= I(x-i, y-j)
+        return win[(r + 3 - j) % 7][c0 + 4 - i] + ~win[(r + 3 + j) % 7][c0 + 4 + i];
+    };
+    uint32_t c[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int b = q * 8 + 7; b >= q * 8; --b)  // highest bit of the byte first
+            if (b < 31) c[q] = __funnelshift_l(diff(b), c[q], 1);
+    return __byte_perm(__byte_perm(c[0], c[1], 0x0040u), __byte_perm(c[2], c[3], 0x0040u), 0x5410u);
+}
 
 __device__ __forceinline__ void census_body(const uint8_t* __restrict__ left, const uint8_t* __restrict__ right,
                                             uint32_t* __restrict__ Fb, uint32_t* __restrict__ Fm, int W, int H,
                                             int bx, int by, int bz) {
-    constexpr int TW = kCtW + 8, TH = kCtH + 6;
+    constexpr int TW = kCtW + 8, TH = kCtH + 6, NS = (TW + kCtT - 1) / kCtT;
     __shared__ uint8_t tile[TH][TW];
     const uint8_t* img = bz ? right : left;
     uint32_t* F = bz ? Fm : Fb;
     const int x0 = bx * kCtW, y0 = by * kCtH;
-    // Thread t stages tile column t (and t + kCtW for the last 8 columns): all
-    // loads are issued before the first shared-memory store.
+    // Thread t stages tile columns t, t + kCtT, ...: all loads are issued
+    // before the first shared-memory store.
     {
-        uint8_t v[2][TH];
+        uint8_t v[NS][TH];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int tx = threadIdx.x + h * kCtW, gx = x0 - 4 + tx;
+        for (int h = 0; h < NS; ++h) {
+            const int tx = threadIdx.x + h * kCtT, gx = x0 - 4 + tx;
             const bool xin = tx < TW && gx >= 0 && gx < W;
 #pragma unroll
             for (int ty = 0; ty < TH; ++ty) {
@@ -45,8 +71,8 @@ __device__ __forceinline__ void census_body(const uint8_t* __restrict__ left, co
             }
         }
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int tx = threadIdx.x + h * kCtW;
+        for (int h = 0; h < NS; ++h) {
+            const int tx = threadIdx.x + h * kCtT;
             if (tx < TW) {
 #pragma unroll
                 for (int ty = 0; ty < TH; ++ty) tile[ty][tx] = v[h][ty];
@@ -54,52 +80,35 @@ __device__ __forceinline__ void census_body(const uint8_t* __restrict__ left, co
         }
     }
     __syncthreads();
-    const int lx = threadIdx.x, x = x0 + lx;
+    const int lx = 2 * threadIdx.x, x = x0 + lx;
     if (x >= W) return;
-    const bool x_ok = x >= 4 && x <= W - 5;
-    uint32_t win[7][9];  // win[r % 7][c]: tile row r, tile column lx + c (image x - 4 + c)
+    const bool ok0 = x >= 4 && x <= W - 5, ok1 = x + 1 >= 4 && x + 1 <= W - 5, has1 = x + 1 < W;
+    uint32_t win[7][10];  // win[r % 7][c]: tile row r, tile column lx + c (image x - 4 + c)
 #pragma unroll
     for (int r = 0; r < 6; ++r)
 #pragma unroll
-        for (int c = 0; c < 9; ++c) win[r][c] = tile[r][lx + c];
+        for (int c = 0; c < 10; ++c) win[r][c] = tile[r][lx + c];
 #pragma unroll
     for (int r = 0; r < kCtH; ++r) {
 #pragma unroll
-        for (int c = 0; c < 9; ++c) win[(r + 6) % 7][c] = tile[r + 6][lx + c];
+        for (int c = 0; c < 10; ++c) win[(r + 6) % 7][c] = tile[r + 6][lx + c];
         const int y = y0 + r;
         if (y >= H) break;
-        // window row k (image y - 3 + k) is win[(r + k) % 7]; bit b of the
-        // feature compares the pair given by pair_of(b) below
-        auto diff = [&](int b) -> uint32_t {
-            int i, j;
-            if (b >= 28) {
-                i = 0;
-                j = b - 27;  // bits 28..30: i = 0, j = 1..3
-            } else {
-                i = b / 7 + 1;
-                j = b % 7 - 3;  // bit (i-1)*7 + j+3
-            }
-            return win[(r + 3 - j) % 7][4 - i] + ~win[(r + 3 + j) % 7][4 + i];  // sign: I(x+i,y+j) >= I(x-i,y-j)
-        };
-        uint32_t c[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int b = q * 8 + 7; b >= q * 8; --b)  // highest bit of the byte first
-                if (b < 31) c[q] = __funnelshift_l(diff(b), c[q], 1);
-        const uint32_t f = __byte_perm(__byte_perm(c[0], c[1], 0x0040u), __byte_perm(c[2], c[3], 0x0040u), 0x5410u);
-        const bool ok = x_ok && y >= 3 && y <= H - 4;
-        F[(size_t)y * W + x] = ok ? f : 0u;
+        const bool yok = y >= 3 && y <= H - 4;
+        const uint32_t f0 = census_feature(win, r, 0), f1 = census_feature(win, r, 1);
+        uint32_t* row = F + (size_t)y * W + x;
+        row[0] = (ok0 && yok) ? f0 : 0u;
+        if (has1) row[1] = (ok1 && yok) ? f1 : 0u;
     }
 }
 
-__global__ void __launch_bounds__(kCtW) census_kernel(const uint8_t* __restrict__ left, const uint8_t* __restrict__ right,
+__global__ void __launch_bounds__(kCtT) census_kernel(const uint8_t* __restrict__ left, const uint8_t* __restrict__ right,
                                                       uint32_t* __restrict__ Fb, uint32_t* __restrict__ Fm, int W,
                                                       int H) {
     census_body(left, right, Fb, Fm, W, H, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-__global__ void __launch_bounds__(kCtW) census_batch_kernel(const __grid_constant__ JobTable<CensusJob> t) {
+__global__ void __launch_bounds__(kCtT) census_batch_kernel(const __grid_constant__ JobTable<CensusJob> t) {
     const int p = find_job(t, blockIdx.x);
     const CensusJob& j = t.job[p];
     const int b = blockIdx.x - t.start[p];
@@ -111,14 +120,14 @@ cudaError_t launch_census_batch(JobTable<CensusJob>& t, cudaStream_t stream) {
     t.start[0] = 0;
     for (int i = 0; i < t.n; ++i)
         t.start[i + 1] = t.start[i] + 2 * ((t.job[i].W + kCtW - 1) / kCtW) * ((t.job[i].H + kCtH - 1) / kCtH);
-    census_batch_kernel<<<t.start[t.n], kCtW, 0, stream>>>(t);
+    census_batch_kernel<<<t.start[t.n], kCtT, 0, stream>>>(t);
     return cudaGetLastError();
 }
 
 cudaError_t launch_census(const uint8_t* left, const uint8_t* right, uint32_t* Fb, uint32_t* Fm, int W, int H,
                           cudaStream_t stream) {
     dim3 grid((W + kCtW - 1) / kCtW, (H + kCtH - 1) / kCtH, 2);
-    census_kernel<<<grid, kCtW, 0, stream>>>(left, right, Fb, Fm, W, H);
+    census_kernel<<<grid, kCtT, 0, stream>>>(left, right, Fb, Fm, W, H);
     return cudaGetLastError();
 }
 
@@ -298,7 +307,7 @@ __device__ __forceinline__ int med3(int a, int b, int c) { return max(min(a, b),
 // down the tile with its three columns of the 3 x 10 neighbourhood loaded
 // (clamped to the image) into registers up front; each row's three values are
 // sorted once and shared by the three windows that contain the row.
-constexpr int kMedW = 128, kMedH = 8;
+constexpr int kMedW = 128, kMedH = 4;
 
 __device__ __forceinline__ void median_body(const uint8_t* __restrict__ raw, uint8_t* __restrict__ out, int W, int H,
                                             int bx, int by) {
