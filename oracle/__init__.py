@@ -11,6 +11,10 @@ from .oracle import (  # noqa: F401
     csct_at,
     bitcount,
     cost,
+    ct62,
+    ct62_at,
+    bitcount64,
+    cost64,
     aggregate,
     directions,
     wta,

@@ -23,6 +23,7 @@ _lib: Optional[ctypes.CDLL] = None
 
 _u8p = ctypes.POINTER(ctypes.c_uint8)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
 _i32p = ctypes.POINTER(ctypes.c_int32)
 
 
@@ -62,6 +63,16 @@ def load() -> ctypes.CDLL:
             lib.oracle_sgm.restype = ctypes.c_int
             lib.oracle_pixel.argtypes = [_u8p, _u8p] + [ctypes.c_int] * 8 + [_i32p]
             lib.oracle_pixel.restype = ctypes.c_int
+            lib.oracle_ct62_at.argtypes = [_u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            lib.oracle_ct62_at.restype = ctypes.c_uint64
+            lib.oracle_ct62.argtypes = [_u8p, ctypes.c_int, ctypes.c_int, _u64p]
+            lib.oracle_ct62.restype = None
+            lib.oracle_bitcount64.argtypes = [ctypes.c_uint64]
+            lib.oracle_bitcount64.restype = ctypes.c_int
+            lib.oracle_cost64.argtypes = [_u64p, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _u8p]
+            lib.oracle_cost64.restype = None
+            lib.oracle_sgm_ct62.argtypes = [_u8p, _u8p] + [ctypes.c_int] * 6 + [_u8p, _u8p, _u64p, _u64p, _i32p]
+            lib.oracle_sgm_ct62.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -95,6 +106,36 @@ def csct(img: np.ndarray) -> np.ndarray:
 
 def bitcount(v: int) -> int:
     return int(load().oracle_bitcount(v & 0xFFFFFFFF))
+
+
+def ct62_at(img: np.ndarray, x: int, y: int) -> int:
+    """The full 9x7 Census transform (62 bits) at one pixel."""
+    img = _img(img)
+    H, W = img.shape
+    return int(load().oracle_ct62_at(_ptr(img, _u8p), W, H, x, y))
+
+
+def ct62(img: np.ndarray) -> np.ndarray:
+    """The full 9x7 Census transform over an image -> uint64 [H, W]."""
+    img = _img(img)
+    H, W = img.shape
+    F = np.zeros((H, W), dtype=np.uint64)
+    load().oracle_ct62(_ptr(img, _u8p), W, H, _ptr(F, _u64p))
+    return F
+
+
+def bitcount64(v: int) -> int:
+    return int(load().oracle_bitcount64(v & 0xFFFFFFFFFFFFFFFF))
+
+
+def cost64(Fb: np.ndarray, Fm: np.ndarray, D: int) -> np.ndarray:
+    """Eq. 2 on 62-bit Census features -> uint8 [H, W, D]."""
+    Fb = np.ascontiguousarray(Fb, dtype=np.uint64)
+    Fm = np.ascontiguousarray(Fm, dtype=np.uint64)
+    H, W = Fb.shape
+    MC = np.zeros((H, W, D), dtype=np.uint8)
+    load().oracle_cost64(_ptr(Fb, _u64p), _ptr(Fm, _u64p), W, H, D, _ptr(MC, _u8p))
+    return MC
 
 
 def cost(Fb: np.ndarray, Fm: np.ndarray, D: int) -> np.ndarray:
@@ -141,28 +182,34 @@ def median3x3(raw: np.ndarray) -> np.ndarray:
 
 
 def sgm(left: np.ndarray, right: np.ndarray, D: int, P1: int, P2: int, n_paths: int,
-        debug: bool = False):
+        debug: bool = False, census: str = "csct"):
     """Stages 2-4 of Section 2 on one pair.
 
-    Returns the final disparity (uint8 [H, W]); with ``debug`` a dict with
-    ``disp``, ``raw``, ``Fb``, ``Fm`` and ``S`` (int32 [H, W, D]).
+    ``census`` is ``"csct"`` (Eq. 1, 31-bit features) or ``"ct62"`` (the full
+    9x7 Census, 62-bit features).  Returns the final disparity (uint8 [H, W]);
+    with ``debug`` a dict with ``disp``, ``raw``, ``Fb``, ``Fm`` (uint32 or
+    uint64 [H, W]) and ``S`` (int32 [H, W, D]).
     """
+    if census not in ("csct", "ct62"):
+        raise ValueError(f"unknown census {census!r}")
     left, right = _img(left), _img(right)
     H, W = left.shape
     disp = np.zeros((H, W), dtype=np.uint8)
     null = lambda t: ctypes.cast(None, t)  # noqa: E731
+    ftype, fptr = (np.uint32, _u32p) if census == "csct" else (np.uint64, _u64p)
+    fn = load().oracle_sgm if census == "csct" else load().oracle_sgm_ct62
     if debug:
         raw = np.zeros((H, W), dtype=np.uint8)
-        Fb = np.zeros((H, W), dtype=np.uint32)
-        Fm = np.zeros((H, W), dtype=np.uint32)
+        Fb = np.zeros((H, W), dtype=ftype)
+        Fm = np.zeros((H, W), dtype=ftype)
         S = np.zeros((H, W, D), dtype=np.int32)
-        rc = load().oracle_sgm(_ptr(left, _u8p), _ptr(right, _u8p), W, H, D, P1, P2, n_paths, _ptr(disp, _u8p),
-                               _ptr(raw, _u8p), _ptr(Fb, _u32p), _ptr(Fm, _u32p), _ptr(S, _i32p))
+        rc = fn(_ptr(left, _u8p), _ptr(right, _u8p), W, H, D, P1, P2, n_paths, _ptr(disp, _u8p), _ptr(raw, _u8p),
+                _ptr(Fb, fptr), _ptr(Fm, fptr), _ptr(S, _i32p))
     else:
-        rc = load().oracle_sgm(_ptr(left, _u8p), _ptr(right, _u8p), W, H, D, P1, P2, n_paths, _ptr(disp, _u8p),
-                               null(_u8p), null(_u32p), null(_u32p), null(_i32p))
+        rc = fn(_ptr(left, _u8p), _ptr(right, _u8p), W, H, D, P1, P2, n_paths, _ptr(disp, _u8p), null(_u8p),
+                null(fptr), null(fptr), null(_i32p))
     if rc != 0:
-        raise ValueError(f"oracle_sgm failed with {rc}")
+        raise ValueError(f"oracle sgm failed with {rc}")
     if debug:
         return {"disp": disp, "raw": raw, "Fb": Fb, "Fm": Fm, "S": S}
     return disp

@@ -30,6 +30,11 @@
  *  - Path sets: 2 paths = left-to-right and top-to-bottom; 4 paths adds
  *    right-to-left and bottom-to-top; 8 paths adds the four diagonals
  *    (Section 4).
+ *  - The full Census transform the paper compares CSCT against (CT,
+ *    Section 2, related work): every pixel of the 9x7 window but the centre
+ *    against the centre, bit k = s(I(x+i, y+j), I(x, y)) for the k-th
+ *    (j, i) of j = -3..3 (outer), i = -4..4 (inner) with (0, 0) skipped:
+ *    62 bits, LSB first, 0 wherever the window leaves the image.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -70,6 +75,50 @@ ORACLE_EXPORT uint32_t oracle_csct_at(const uint8_t *I, int W, int H, int x, int
 ORACLE_EXPORT void oracle_csct(const uint8_t *I, int W, int H, uint32_t *F) {
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) F[(size_t)y * W + x] = oracle_csct_at(I, W, H, x, y);
+}
+
+/*
+ * The full 9x7 Census transform (CT) of pixel (x, y): the 62 comparisons of a
+ * window pixel against the centre, s(I(neighbour), I(centre)); 0 when the
+ * window leaves the image.
+ */
+ORACLE_EXPORT uint64_t oracle_ct62_at(const uint8_t *I, int W, int H, int x, int y) {
+    uint64_t f = 0;
+    int inside = (x - 4 >= 0) && (x + 4 <= W - 1) && (y - 3 >= 0) && (y + 3 <= H - 1);
+    if (!inside) return 0;
+    int k = 0;
+    for (int j = -3; j <= 3; ++j) {
+        for (int i = -4; i <= 4; ++i) {
+            if (i == 0 && j == 0) continue;
+            int bit = census_s(pixel(I, W, x + i, y + j), pixel(I, W, x, y));
+            f |= (uint64_t)bit << k;
+            ++k;
+        }
+    }
+    return f;
+}
+
+/* CT over the whole image: F[y*W + x] = CT(I, x, y). */
+ORACLE_EXPORT void oracle_ct62(const uint8_t *I, int W, int H, uint64_t *F) {
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) F[(size_t)y * W + x] = oracle_ct62_at(I, W, H, x, y);
+}
+
+/* bitcount of a 64-bit feature difference, a plain loop over the 64 bits. */
+ORACLE_EXPORT int oracle_bitcount64(uint64_t v) {
+    int c = 0;
+    for (int b = 0; b < 64; ++b) c += (int)((v >> b) & 1u);
+    return c;
+}
+
+/* Eq. 2 with CT features: MC = bitcount(F_base(x, y) XOR F_match(x-d, y)). */
+ORACLE_EXPORT void oracle_cost64(const uint64_t *Fb, const uint64_t *Fm, int W, int H, int D, uint8_t *MC) {
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x)
+            for (int d = 0; d < D; ++d) {
+                uint64_t m = (x - d >= 0) ? Fm[(size_t)y * W + (x - d)] : 0;
+                MC[((size_t)y * W + x) * D + d] = (uint8_t)oracle_bitcount64(Fb[(size_t)y * W + x] ^ m);
+            }
 }
 
 /* bitcount of Eq. 2, written as a plain loop over the 32 bit positions. */
@@ -181,6 +230,41 @@ ORACLE_EXPORT void oracle_median3x3(const uint8_t *in, int W, int H, uint8_t *ou
 }
 
 /*
+ * Stages 3-4 of Section 2 on a cost cube MC[y][x][d]: the aggregated paths
+ * (Eq. 3), S, the winner-take-all disparity (Eq. 4) and the 3x3 median.
+ * Optional debug outputs (NULL to skip): S (int32 [H][W][D]), raw disparity
+ * (uint8 [H][W]).  Returns 0, or -2 if memory runs out.
+ */
+static int aggregate_and_select(const uint8_t *MC, int W, int H, int D, int P1, int P2, int npaths, const int *rx,
+                                const int *ry, uint8_t *disp_out, uint8_t *raw_out, int32_t *S_out) {
+    size_t n = (size_t)W * H;
+    int32_t *L = (int32_t *)malloc(n * D * sizeof(int32_t));
+    int32_t *S = (int32_t *)calloc(n * D, sizeof(int32_t));
+    uint8_t *raw = (uint8_t *)malloc(n);
+    int rc = 0;
+    if (!L || !S || !raw) {
+        rc = -2;
+        goto done;
+    }
+    for (int r = 0; r < npaths; ++r) {
+        oracle_aggregate(MC, W, H, D, P1, P2, rx[r], ry[r], L);
+        for (size_t i = 0; i < n * D; ++i) S[i] += L[i];
+    }
+    oracle_wta(S, W, H, D, raw);
+    if (W < 3 || H < 3)
+        memcpy(disp_out, raw, n);
+    else
+        oracle_median3x3(raw, W, H, disp_out);
+    if (raw_out) memcpy(raw_out, raw, n);
+    if (S_out) memcpy(S_out, S, n * D * sizeof(int32_t));
+done:
+    free(L);
+    free(S);
+    free(raw);
+    return rc;
+}
+
+/*
  * The whole path of Section 2, stages 2-4: features, matching cost, the
  * aggregated paths, S, the winner-take-all disparity and the 3x3 median.
  * Optional debug outputs (NULL to skip): Fb/Fm features (uint32 [H][W]),
@@ -198,37 +282,45 @@ ORACLE_EXPORT int oracle_sgm(const uint8_t *left, const uint8_t *right, int W, i
     uint32_t *Fb = (uint32_t *)malloc(n * sizeof(uint32_t));
     uint32_t *Fm = (uint32_t *)malloc(n * sizeof(uint32_t));
     uint8_t *MC = (uint8_t *)malloc(n * D);
-    int32_t *L = (int32_t *)malloc(n * D * sizeof(int32_t));
-    int32_t *S = (int32_t *)calloc(n * D, sizeof(int32_t));
-    uint8_t *raw = (uint8_t *)malloc(n);
-    int rc = 0;
-    if (!Fb || !Fm || !MC || !L || !S || !raw) {
-        rc = -2;
-        goto done;
+    int rc = -2;
+    if (Fb && Fm && MC) {
+        oracle_csct(left, W, H, Fb);
+        oracle_csct(right, W, H, Fm);
+        oracle_cost(Fb, Fm, W, H, D, MC);
+        rc = aggregate_and_select(MC, W, H, D, P1, P2, npaths, rx, ry, disp_out, raw_out, S_out);
+        if (Fb_out) memcpy(Fb_out, Fb, n * sizeof(uint32_t));
+        if (Fm_out) memcpy(Fm_out, Fm, n * sizeof(uint32_t));
     }
-    oracle_csct(left, W, H, Fb);
-    oracle_csct(right, W, H, Fm);
-    oracle_cost(Fb, Fm, W, H, D, MC);
-    for (int r = 0; r < npaths; ++r) {
-        oracle_aggregate(MC, W, H, D, P1, P2, rx[r], ry[r], L);
-        for (size_t i = 0; i < n * D; ++i) S[i] += L[i];
-    }
-    oracle_wta(S, W, H, D, raw);
-    if (W < 3 || H < 3)
-        memcpy(disp_out, raw, n);
-    else
-        oracle_median3x3(raw, W, H, disp_out);
-    if (raw_out) memcpy(raw_out, raw, n);
-    if (Fb_out) memcpy(Fb_out, Fb, n * sizeof(uint32_t));
-    if (Fm_out) memcpy(Fm_out, Fm, n * sizeof(uint32_t));
-    if (S_out) memcpy(S_out, S, n * D * sizeof(int32_t));
-done:
     free(Fb);
     free(Fm);
     free(MC);
-    free(L);
-    free(S);
-    free(raw);
+    return rc;
+}
+
+/* oracle_sgm with the full 9x7 Census (62-bit features, uint64 [H][W]). */
+ORACLE_EXPORT int oracle_sgm_ct62(const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
+                                  int n_paths, uint8_t *disp_out, uint8_t *raw_out, uint64_t *Fb_out,
+                                  uint64_t *Fm_out, int32_t *S_out) {
+    int rx[8], ry[8];
+    if (W < 1 || H < 1 || D < 1 || D > 256 || !left || !right || !disp_out) return -1;
+    int npaths = oracle_directions(n_paths, rx, ry);
+    if (npaths == 0) return -1;
+    size_t n = (size_t)W * H;
+    uint64_t *Fb = (uint64_t *)malloc(n * sizeof(uint64_t));
+    uint64_t *Fm = (uint64_t *)malloc(n * sizeof(uint64_t));
+    uint8_t *MC = (uint8_t *)malloc(n * D);
+    int rc = -2;
+    if (Fb && Fm && MC) {
+        oracle_ct62(left, W, H, Fb);
+        oracle_ct62(right, W, H, Fm);
+        oracle_cost64(Fb, Fm, W, H, D, MC);
+        rc = aggregate_and_select(MC, W, H, D, P1, P2, npaths, rx, ry, disp_out, raw_out, S_out);
+        if (Fb_out) memcpy(Fb_out, Fb, n * sizeof(uint64_t));
+        if (Fm_out) memcpy(Fm_out, Fm, n * sizeof(uint64_t));
+    }
+    free(Fb);
+    free(Fm);
+    free(MC);
     return rc;
 }
 
