@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=SERVED_RATE_HZ, help="served: arrivals per second")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--census", default="csct", choices=["csct", "full"],
+                    help="features: the CSCT of Eq. 1 or the full 9x7 Census (SGM_FLAG_CENSUS_FULL)")
     return ap.parse_args()
 
 
@@ -142,7 +144,11 @@ class ClockSampler:
                                                          .replace('.', '', 1).isdigit()) if rows else None}
 
 
-def oracle_mdes(w, max_seconds: float, rows: int = 0):
+def oracle_census(args):
+    return "ct62" if args.census == "full" else "csct"
+
+
+def oracle_mdes(w, max_seconds: float, rows: int = 0, census: str = "csct"):
     """Time the CPU oracle (single thread, as it stands) on the workload."""
     import oracle
 
@@ -154,7 +160,7 @@ def oracle_mdes(w, max_seconds: float, rows: int = 0):
     H, W = left.shape
     n, t0 = 0, time.perf_counter()
     while True:
-        oracle.sgm(left, right, w.spec.D, w.P1, w.P2, w.n_paths)
+        oracle.sgm(left, right, w.spec.D, w.P1, w.P2, w.n_paths, census=census)
         n += 1
         if time.perf_counter() - t0 >= max_seconds:
             break
@@ -173,11 +179,12 @@ def run_reference(args, w, ws, rank):
     # whole run stays within a few minutes
     rows = min(w.spec.H, max(16, int(96 * 200 / max(args.steps + args.warmup, 1))))
     left, right = pair.left[:rows].copy(), pair.right[:rows].copy()
+    census = oracle_census(args)
     for _ in range(args.warmup):
-        oracle.sgm(left, right, w.spec.D, w.P1, w.P2, w.n_paths)
+        oracle.sgm(left, right, w.spec.D, w.P1, w.P2, w.n_paths, census=census)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.sgm(left, right, w.spec.D, w.P1, w.P2, w.n_paths)
+        oracle.sgm(left, right, w.spec.D, w.P1, w.P2, w.n_paths, census=census)
     dt = time.perf_counter() - t0
     de = w.spec.W * rows * w.spec.D
     value = de * args.steps / dt / 1e6
@@ -187,7 +194,7 @@ def run_reference(args, w, ws, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic (seeded stereo_synth pair)",
-        "config": workload_config(w),
+        "config": workload_config(w, args),
         "cpu_baseline": {"value": value, "unit": "MDE/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "MDE/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -211,9 +218,10 @@ def job_mdes(world_size: int, steps: int, de_per_step: int, max_ms: float) -> fl
     return world_size * steps * de_per_step / (max_ms / 1e3) / 1e6
 
 
-def workload_config(w):
+def workload_config(w, args):
     return {"workload": w.name, "W": w.spec.W, "H": w.spec.H, "D": w.spec.D, "P1": w.P1, "P2": w.P2,
-            "n_paths": w.n_paths, "pairs_per_step": 1}
+            "n_paths": w.n_paths, "pairs_per_step": 1,
+            "census": "full 9x7 (62 bits)" if args.census == "full" else "CSCT (31 bits, Eq. 1)"}
 
 
 def run_batch_bench(args, ws, rank, local):
@@ -454,12 +462,13 @@ def main():
     torch.cuda.synchronize(dev)
     # one explicit stream carries the path, the L2 flush and the timing events
     stream = torch.cuda.Stream(dev)
-    ctx = sgm.Context(local)
+    cflag = sgm.SGM_FLAG_CENSUS_FULL if args.census == "full" else 0
+    ctx = sgm.Context(local, flags=cflag)
     sgm.sgm_set_stream(ctx.handle, stream)
     # Per-kernel durations come from a second context whose captured graph
     # records an event between its kernels; those event nodes lengthen the
     # frame, so that context runs its own timed pass after the headline one.
-    ctx_st = sgm.Context(local, flags=sgm.SGM_FLAG_STAGE_TIMING)
+    ctx_st = sgm.Context(local, flags=sgm.SGM_FLAG_STAGE_TIMING | cflag)
     sgm.sgm_set_stream(ctx_st.handle, stream)
 
     def step(c):
@@ -530,7 +539,7 @@ def main():
     sm_mhz = float(peaks.get("sm_max_mhz", SM_MAX_MHZ_GB300))
     peak_tops = SM_COUNT_GB300 * 128 * 2 * sm_mhz * 1e6 / 1e12
     achieved = ops / (mean_stage[dom] / 1e3) / 1e12
-    traffic = measured_traffic(w.name, dom)
+    traffic = measured_traffic(w.name, dom) if args.census == "csct" else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
                 "frac": achieved / peak_tops, "traffic": traffic,
                 "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
@@ -548,7 +557,7 @@ def main():
         Lh = torch.from_numpy(pair.left).pin_memory()
         Rh = torch.from_numpy(pair.right).pin_memory()
         Oh = torch.empty((H, W), dtype=torch.uint8).pin_memory()
-        ctx2 = sgm.Context(local)
+        ctx2 = sgm.Context(local, flags=cflag)
         for _ in range(3):
             sgm.sgm_compute(ctx2.handle, Lh, Rh, W, H, D, w.P1, w.P2, w.n_paths, Oh)
         if pg:
@@ -563,7 +572,7 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, n, (bw, bh) = oracle_mdes(w, max_seconds=10.0)
+        v, n, (bw, bh) = oracle_mdes(w, max_seconds=10.0, census=oracle_census(args))
         cpu = {"value": v, "unit": "MDE/s", "cores": 1, "kind": "oracle",
                "sample": f"{n} full {bw}x{bh} D={D} {w.n_paths}-path frames, single thread, ~10 s"}
 
@@ -572,7 +581,7 @@ def main():
             "metric": "MDE/s", "value": value, "unit": "MDE/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u16", "data": "synthetic (seeded stereo_synth pair, resident in HBM)",
-            "config": dict(workload_config(w), parallelism=f"replicas x{ws}",
+            "config": dict(workload_config(w, args), parallelism=f"replicas x{ws}",
                            l2="flushed between timed steps (256 MiB write)", fps=1e3 / ms_per_step),
             "roofline": roofline, "frame_roofline": frame_roofline,
             "stage_ms": {k: round(v, 5) for k, v in mean_stage.items()},

@@ -20,7 +20,8 @@
  *  Output   uint8 disparity, row-major, pitch = W (values 0 .. D-1).
  *  W, H     >= 1.
  *  D        one of 32, 64, 96, 128, 160, 192, 224, 256.
- *  P1, P2   penalties of Eq. 3, each in [0, 224] (keeps every L_r <= 255).
+ *  P1, P2   penalties of Eq. 3, each in [0, 224] (keeps every L_r <= 255);
+ *           P2 <= 193 in a context created with SGM_FLAG_CENSUS_FULL.
  *  n_paths  2 (left-to-right, top-to-bottom), 4 (adds right-to-left and
  *           bottom-to-top) or 8 (adds the four diagonals) (Section 4).
  *  Borders  the feature is 0 where the 9x7 window leaves the image, and a
@@ -70,6 +71,9 @@ typedef enum sgm_status {
 
 /* sgm_create flags. */
 #define SGM_FLAG_STAGE_TIMING 1u /* record a CUDA event between the kernels of every path (sgm_stage_times) */
+#define SGM_FLAG_CENSUS_FULL 2u  /* features: the full 9x7 Census (62 bits, every pixel of the window against \
+                                    the centre) in place of the CSCT of Eq. 1; matching costs reach 62, so \
+                                    P2 must not exceed 255 - 62 = 193 */
 
 /* Limits checked by every entry point. */
 #define SGM_MAX_D 256
@@ -87,7 +91,9 @@ typedef struct sgm_pair {
  * Create a context on CUDA device `device` (makes it current for the calling
  * thread).  `mem_cap_bytes` caps the device memory the context may hold for
  * its work arena and served requests (0 = no cap beyond the device's free
- * memory).  `flags` is 0 or SGM_FLAG_STAGE_TIMING.  On success *out
+ * memory).  `flags` is 0 or a combination of SGM_FLAG_STAGE_TIMING and
+ * SGM_FLAG_CENSUS_FULL; the Census type holds for every entry point of the
+ * context (sgm_compute_static always uses the CSCT).  On success *out
  * receives the context.
  * Errors: SGM_EINVAL (null out, bad device, unknown flag), SGM_ECUDA.
  */
@@ -193,7 +199,8 @@ SGM_API int sgm_served_reset_stats(sgm_ctx *ctx);
 /*
  * Debug form of sgm_compute for localising a mismatch stage by stage.  All
  * pointers are host pointers; each optional output may be NULL:
- *   Fb, Fm   uint32 [H][W]    Census features of left and right (Eq. 1)
+ *   Fb, Fm   uint32 [H][W]    Census features of left and right (Eq. 1); uint64 [H][W]
+ *                             in a context created with SGM_FLAG_CENSUS_FULL
  *   MC       uint8  [H][W][D] matching cost (Eq. 2), d fastest
  *   S        uint16 [H][W][D] summed aggregated cost (Eq. 4's sum)
  *   raw      uint8  [H][W]    winner-take-all disparity before the median
@@ -201,7 +208,7 @@ SGM_API int sgm_served_reset_stats(sgm_ctx *ctx);
  * Errors as sgm_compute.
  */
 SGM_API int sgm_debug_stages(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
-                     int n_paths, uint32_t *Fb, uint32_t *Fm, uint8_t *MC, uint16_t *S, uint8_t *raw, uint8_t *disp);
+                     int n_paths, void *Fb, void *Fm, uint8_t *MC, uint16_t *S, uint8_t *raw, uint8_t *disp);
 
 /*
  * Per-kernel device times (milliseconds) of the most recent path this context

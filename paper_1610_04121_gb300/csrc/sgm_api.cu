@@ -41,17 +41,18 @@ struct Layout {
 // state.
 int lx_fields(int n_paths, bool batched) { return n_paths == 2 ? 0 : (batched ? 1 : (n_paths == 8 ? 4 : 2)); }
 
-Layout layout_for(int W, int H, int D_int, int n_paths, bool batched = false) {
+Layout layout_for(int W, int H, int D_int, int n_paths, bool batched = false, bool ct62 = false) {
     const size_t wh = static_cast<size_t>(W) * H;
     const size_t D = static_cast<size_t>(D_int);
+    const size_t fbytes = ct62 ? 8 : 4;
     Layout l{};
     l.n_lx = lx_fields(n_paths, batched);
     l.RB = record_bytes(D_int, false, l.n_lx);
     size_t o = 0;
-    l.Fb = o;
-    o = align_up(o + 4 * wh);
+    l.Fb = o;  // features: uint32 (CSCT) or uint64 (full Census)
+    o = align_up(o + fbytes * wh);
     l.Fm = o;
-    o = align_up(o + 4 * wh);
+    o = align_up(o + fbytes * wh);
     l.rec = o;
     o = align_up(o + wh * static_cast<size_t>(l.RB));
     l.raw = o;
@@ -72,7 +73,15 @@ Layout layout_for(int W, int H, int D_int, int n_paths, bool batched = false) {
 
 struct Problem {
     int W, H, D, P1, P2, n_paths;
+    int ct62 = 0;  // features: 0 = CSCT (Eq. 1), 1 = the full 9x7 Census (SGM_FLAG_CENSUS_FULL)
 };
+
+// Largest matching cost: 31 CSCT bits or 62 full-Census bits.
+inline int mc_max(const Problem& p) { return p.ct62 ? 62 : 31; }
+
+Layout layout_for(const Problem& p, bool batched = false) {
+    return layout_for(p.W, p.H, p.D, p.n_paths, batched, p.ct62 != 0);
+}
 
 bool valid_problem(const Problem& p, std::string* why) {
     char buf[160];
@@ -82,6 +91,9 @@ bool valid_problem(const Problem& p, std::string* why) {
         snprintf(buf, sizeof buf, "D must be a multiple of 32 in [32, %d] (got %d)", SGM_MAX_D, p.D);
     } else if (p.P1 < 0 || p.P1 > SGM_MAX_PENALTY || p.P2 < 0 || p.P2 > SGM_MAX_PENALTY) {
         snprintf(buf, sizeof buf, "P1 and P2 must lie in [0, %d] (got %d, %d)", SGM_MAX_PENALTY, p.P1, p.P2);
+    } else if (p.ct62 && p.P2 > 255 - 62) {
+        snprintf(buf, sizeof buf, "with the full Census P2 must lie in [0, %d] so that path costs fit a byte (got %d)",
+                 255 - 62, p.P2);
     } else if (p.n_paths != 2 && p.n_paths != 4 && p.n_paths != 8) {
         snprintf(buf, sizeof buf, "n_paths must be 2, 4 or 8 (got %d)", p.n_paths);
     } else if (static_cast<double>(p.W) * p.H * record_bytes(p.D, false, lx_fields(p.n_paths, false)) >= 4294967296.0) {
@@ -98,8 +110,8 @@ struct GraphKey {
     Problem p;
     const void *left, *right, *out, *arena;
     bool operator<(const GraphKey& o) const {
-        return std::tie(p.W, p.H, p.D, p.P1, p.P2, p.n_paths, left, right, out, arena) <
-               std::tie(o.p.W, o.p.H, o.p.D, o.p.P1, o.p.P2, o.p.n_paths, o.left, o.right, o.out, o.arena);
+        return std::tie(p.W, p.H, p.D, p.P1, p.P2, p.n_paths, p.ct62, left, right, out, arena) <
+               std::tie(o.p.W, o.p.H, o.p.D, o.p.P1, o.p.P2, o.p.n_paths, o.p.ct62, o.left, o.right, o.out, o.arena);
     }
 };
 
@@ -146,6 +158,7 @@ struct sgm_ctx {
     std::string err;
     std::atomic<uint64_t> launches{0};
     bool stage_timing = false;
+    int ct62 = 0;  // SGM_FLAG_CENSUS_FULL
     cudaEvent_t stage_ev[10] = {};
     int last_stages = 0;
     int last_n_paths = 0;  // path count of the last path enqueued with stage timing
@@ -246,9 +259,9 @@ static int stages_per_path(const Problem& p) { return launches_per_path(p); }
 // and output are device pointers.  Returns a cudaError_t.
 static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const uint8_t* left,
                                 const uint8_t* right, uint8_t* disp, uint16_t* Sdbg, cudaStream_t s, bool timed) {
-    const Layout l = layout_for(p.W, p.H, p.D, p.n_paths);
-    uint32_t* Fb = reinterpret_cast<uint32_t*>(arena + l.Fb);
-    uint32_t* Fm = reinterpret_cast<uint32_t*>(arena + l.Fm);
+    const Layout l = layout_for(p);
+    void* Fb = arena + l.Fb;
+    void* Fm = arena + l.Fm;
     cudaError_t e;
     int stage = 0;
     // with stage timing, event k is recorded before kernel k and after the last
@@ -258,9 +271,9 @@ static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, 
         return cudaEventRecordWithFlags(ctx->stage_ev[stage++], s, cudaEventRecordExternal);
     };
     if ((e = mark()) != cudaSuccess) return e;
-    if ((e = launch_census(left, right, Fb, Fm, p.W, p.H, s)) != cudaSuccess) return e;
+    if ((e = launch_census(left, right, Fb, Fm, p.W, p.H, p.ct62 != 0, s)) != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;
-    if ((e = launch_cost(Fb, Fm, arena + l.rec, l.RB, p.W, p.H, p.D, s)) != cudaSuccess) return e;
+    if ((e = launch_cost(Fb, Fm, arena + l.rec, l.RB, p.W, p.H, p.D, p.ct62 != 0, s)) != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;
     SweepArgs a{};
     a.rec = arena + l.rec;
@@ -274,7 +287,7 @@ static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, 
     a.P1x2 = static_cast<uint32_t>(p.P1) * 0x10001u;
     a.P2x2 = static_cast<uint32_t>(p.P2) * 0x10001u;
     a.pair = p.n_paths >= 4;
-    a.s8 = sum_fits_u8(p.n_paths, p.P2);
+    a.s8 = sum_fits_u8(p.n_paths, p.P2, mc_max(p));
     a.rx = 0;
     a.wta = 0;
     a.phase = 0;
@@ -379,7 +392,7 @@ static int enqueue_graph(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const u
 // Copy-in / path / copy-out for one pair into `arena` (already large enough).
 static int enqueue_pair(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const uint8_t* left, const uint8_t* right,
                         uint8_t* disp, cudaStream_t s, bool use_graph) {
-    const Layout l = layout_for(p.W, p.H, p.D, p.n_paths);
+    const Layout l = layout_for(p);
     const size_t wh = static_cast<size_t>(p.W) * p.H;
     const uint8_t* dl = left;
     const uint8_t* dr = right;
@@ -404,6 +417,13 @@ static int enqueue_pair(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const ui
     return SGM_OK;
 }
 
+// A problem as the context sees it (its Census type).
+static Problem make_problem(const sgm_ctx* ctx, int W, int H, int D, int P1, int P2, int n_paths) {
+    Problem p{W, H, D, P1, P2, n_paths};
+    p.ct62 = ctx ? ctx->ct62 : 0;
+    return p;
+}
+
 static int check_args(sgm_ctx* ctx, const Problem& p, const void* left, const void* right, const void* out) {
     if (!ctx) return fail(nullptr, SGM_EINVAL, "null context");
     if (!left || !right || !out) return fail(ctx, SGM_EINVAL, "null image or output pointer");
@@ -425,9 +445,9 @@ struct BatchItem {
     size_t offset;  // of the pair's region in the arena
 };
 
-// Items launched together share D, the path count and the sum storage.
-static std::tuple<int, int, bool> batch_key(const BatchItem& it) {
-    return std::make_tuple(it.p.D, it.p.n_paths, sum_fits_u8(it.p.n_paths, it.p.P2));
+// Items launched together share D, the path count, the sum storage and the Census type.
+static std::tuple<int, int, bool, int> batch_key(const BatchItem& it) {
+    return std::make_tuple(it.p.D, it.p.n_paths, sum_fits_u8(it.p.n_paths, it.p.P2, mc_max(it.p)), it.p.ct62);
 }
 
 static int launches_per_group(int n_paths) { return 4 + (n_paths == 8 ? 3 : 1); }
@@ -438,7 +458,7 @@ static int enqueue_wave(sgm_ctx* ctx, std::vector<BatchItem>& items, size_t b, s
     // copy-in of host inputs
     for (size_t i = b; i < e; ++i) {
         BatchItem& it = items[i];
-        const Layout l = layout_for(it.p.W, it.p.H, it.p.D, it.p.n_paths, true);
+        const Layout l = layout_for(it.p, true);
         const size_t wh = static_cast<size_t>(it.p.W) * it.p.H;
         uint8_t* base = arena + it.offset;
         if (!is_device_ptr(it.left)) {
@@ -463,10 +483,10 @@ static int enqueue_wave(sgm_ctx* ctx, std::vector<BatchItem>& items, size_t b, s
         ct.n = mt.n = st.n = dt.n = n;
         for (int k = 0; k < n; ++k) {
             const BatchItem& it = items[g0 + k];
-            const Layout l = layout_for(it.p.W, it.p.H, it.p.D, it.p.n_paths, true);
+            const Layout l = layout_for(it.p, true);
             uint8_t* base = arena + it.offset;
-            uint32_t* Fb = reinterpret_cast<uint32_t*>(base + l.Fb);
-            uint32_t* Fm = reinterpret_cast<uint32_t*>(base + l.Fm);
+            void* Fb = base + l.Fb;
+            void* Fm = base + l.Fm;
             ct.job[k] = CensusJob{it.left, it.right, Fb, Fm, it.p.W, it.p.H};
             mt.job[k] = CostJob{Fb, Fm, base + l.rec, l.RB, it.p.W, it.p.H};
             SweepArgs a{};
@@ -480,13 +500,14 @@ static int enqueue_wave(sgm_ctx* ctx, std::vector<BatchItem>& items, size_t b, s
             a.P1x2 = static_cast<uint32_t>(it.p.P1) * 0x10001u;
             a.P2x2 = static_cast<uint32_t>(it.p.P2) * 0x10001u;
             a.pair = it.p.n_paths >= 4;
-            a.s8 = sum_fits_u8(it.p.n_paths, it.p.P2);
+            a.s8 = sum_fits_u8(it.p.n_paths, it.p.P2, mc_max(it.p));
             st.job[k] = a;
             uint8_t* dst = is_device_ptr(it.out) ? it.out : base + l.out;
             dt.job[k] = MedianJob{base + l.raw, dst, it.p.W, it.p.H};
         }
-        CUDA_TRY(ctx, launch_census_batch(ct, s));
-        CUDA_TRY(ctx, launch_cost_batch(mt, D, s));
+        const bool ct62 = items[g0].p.ct62 != 0;
+        CUDA_TRY(ctx, launch_census_batch(ct, ct62, s));
+        CUDA_TRY(ctx, launch_cost_batch(mt, D, ct62, s));
         CUDA_TRY(ctx, launch_sweep_h_batch(st, s));
         const int vrx[3] = {1, -1, 0};
         const int nv = n_paths == 8 ? 3 : 1;
@@ -506,7 +527,7 @@ static int enqueue_wave(sgm_ctx* ctx, std::vector<BatchItem>& items, size_t b, s
     for (size_t i = b; i < e; ++i) {
         const BatchItem& it = items[i];
         if (!is_device_ptr(it.out)) {
-            const Layout l = layout_for(it.p.W, it.p.H, it.p.D, it.p.n_paths, true);
+            const Layout l = layout_for(it.p, true);
             CUDA_TRY(ctx, cudaMemcpyAsync(it.out, arena + it.offset + l.out,
                                           static_cast<size_t>(it.p.W) * it.p.H, cudaMemcpyDeviceToHost, s));
         }
@@ -533,7 +554,7 @@ static int run_batch(sgm_ctx* ctx, std::vector<BatchItem>& items, uint8_t** aren
     while (b < items.size()) {
         size_t e = b, total = 0;
         while (e < items.size()) {
-            const size_t sz = layout_for(items[e].p.W, items[e].p.H, items[e].p.D, items[e].p.n_paths, true).total;
+            const size_t sz = layout_for(items[e].p, true).total;
             if (e > b && total + sz > budget) break;
             items[e].offset = total;
             total += sz;
@@ -664,7 +685,7 @@ static int slot_launch(sgm_ctx* ctx, ServeSlot& sl, size_t budget) {
     size_t total = 0;
     for (BatchItem& it : items) {
         it.offset = total;
-        total += layout_for(it.p.W, it.p.H, it.p.D, it.p.n_paths, true).total;
+        total += layout_for(it.p, true).total;
     }
     int rc = slot_reserve(ctx, sl, total, budget);
     if (rc == SGM_OK) rc = enqueue_wave(ctx, items, 0, items.size(), sl.arena, sl.stream);
@@ -740,7 +761,7 @@ static void serve_loop(sgm_ctx* ctx) {
         size_t used = 0;
         while (rc == SGM_OK && !ctx->queue.empty() && sl->reqs.size() < static_cast<size_t>(kServeMaxPairs)) {
             const Request& r = ctx->queue.front();
-            const size_t sz = layout_for(r.p.W, r.p.H, r.p.D, r.p.n_paths, true).total;
+            const size_t sz = layout_for(r.p, true).total;
             if (used + sz > budget) break;
             used += sz;
             sl->reqs.push_back(r);
@@ -808,7 +829,8 @@ extern "C" {
 int sgm_create(sgm_ctx** out, int device, size_t mem_cap_bytes, unsigned flags) {
     if (!out) return fail(nullptr, SGM_EINVAL, "null output pointer");
     *out = nullptr;
-    if (flags & ~SGM_FLAG_STAGE_TIMING) return fail(nullptr, SGM_EINVAL, "unknown flags %#x", flags);
+    if (flags & ~(SGM_FLAG_STAGE_TIMING | SGM_FLAG_CENSUS_FULL))
+        return fail(nullptr, SGM_EINVAL, "unknown flags %#x", flags);
     int n = 0;
     cudaError_t e = cudaGetDeviceCount(&n);
     if (e != cudaSuccess) return fail(nullptr, SGM_ECUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
@@ -849,6 +871,7 @@ int sgm_create(sgm_ctx** out, int device, size_t mem_cap_bytes, unsigned flags) 
     }
     ctx->stream = ctx->own_stream;
     ctx->stage_timing = (flags & SGM_FLAG_STAGE_TIMING) != 0;
+    ctx->ct62 = (flags & SGM_FLAG_CENSUS_FULL) ? 1 : 0;
     if (ctx->stage_timing) {
         for (auto& ev : ctx->stage_ev) {
             if ((e = cudaEventCreate(&ev)) != cudaSuccess) {
@@ -900,11 +923,11 @@ int sgm_set_stream(sgm_ctx* ctx, void* cuda_stream) {
 
 int sgm_compute(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H, int D, int P1, int P2,
                 int n_paths, uint8_t* disp_out) {
-    const Problem p{W, H, D, P1, P2, n_paths};
+    const Problem p = make_problem(ctx, W, H, D, P1, P2, n_paths);
     int rc = check_args(ctx, p, left, right, disp_out);
     if (rc != SGM_OK) return rc;
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-    rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, layout_for(W, H, D, n_paths).total, true);
+    rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, layout_for(p).total, true);
     if (rc != SGM_OK) return rc;
     rc = enqueue_pair(ctx, p, ctx->arena, left, right, disp_out, ctx->stream, true);
     if (rc != SGM_OK) return rc;
@@ -914,13 +937,13 @@ int sgm_compute(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, 
 
 int sgm_compute_async(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H, int D, int P1, int P2,
                       int n_paths, uint8_t* disp_out) {
-    const Problem p{W, H, D, P1, P2, n_paths};
+    const Problem p = make_problem(ctx, W, H, D, P1, P2, n_paths);
     int rc = check_args(ctx, p, left, right, disp_out);
     if (rc != SGM_OK) return rc;
     if (!is_device_ptr(left) || !is_device_ptr(right) || !is_device_ptr(disp_out))
         return fail(ctx, SGM_EINVAL, "sgm_compute_async takes device pointers only");
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-    rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, layout_for(W, H, D, n_paths).total, true);
+    rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, layout_for(p).total, true);
     if (rc != SGM_OK) return rc;
     return enqueue_graph(ctx, p, ctx->arena, left, right, disp_out, ctx->stream);
 }
@@ -932,7 +955,7 @@ int sgm_compute_batch(sgm_ctx* ctx, int n, const sgm_pair* pairs) {
     items.reserve(n);
     for (int i = 0; i < n; ++i) {
         const sgm_pair& q = pairs[i];
-        const Problem p{q.W, q.H, q.D, q.P1, q.P2, q.n_paths};
+        const Problem p = make_problem(ctx, q.W, q.H, q.D, q.P1, q.P2, q.n_paths);
         int rc = check_args(ctx, p, q.left, q.right, q.disp_out);
         if (rc != SGM_OK) return fail(ctx, rc, "pair %d: %s", i, ctx->err.c_str());
         items.push_back(BatchItem{p, q.left, q.right, q.disp_out, 0});
@@ -946,11 +969,11 @@ int sgm_compute_batch(sgm_ctx* ctx, int n, const sgm_pair* pairs) {
 
 int sgm_submit(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H, int D, int P1, int P2,
                int n_paths, uint8_t* disp_out, uint64_t* ticket) {
-    const Problem p{W, H, D, P1, P2, n_paths};
+    const Problem p = make_problem(ctx, W, H, D, P1, P2, n_paths);
     int rc = check_args(ctx, p, left, right, disp_out);
     if (rc != SGM_OK) return rc;
     if (!ticket) return fail(ctx, SGM_EINVAL, "null ticket pointer");
-    if (ctx->mem_cap && layout_for(W, H, D, n_paths, true).total + ctx->arena_bytes > ctx->mem_cap)
+    if (ctx->mem_cap && layout_for(p, true).total + ctx->arena_bytes > ctx->mem_cap)
         return fail(ctx, SGM_ENOMEM, "pair %dx%d D=%d needs more than the context's memory cap", W, H, D);
     std::lock_guard<std::mutex> lk(ctx->mu);
     if (!ctx->worker_started) {
@@ -1016,12 +1039,12 @@ int sgm_served_reset_stats(sgm_ctx* ctx) {
 }
 
 int sgm_debug_stages(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H, int D, int P1, int P2,
-                     int n_paths, uint32_t* Fb, uint32_t* Fm, uint8_t* MC, uint16_t* S, uint8_t* raw, uint8_t* disp) {
-    const Problem p{W, H, D, P1, P2, n_paths};
+                     int n_paths, void* Fb, void* Fm, uint8_t* MC, uint16_t* S, uint8_t* raw, uint8_t* disp) {
+    const Problem p = make_problem(ctx, W, H, D, P1, P2, n_paths);
     int rc = check_args(ctx, p, left, right, left);
     if (rc != SGM_OK) return rc;
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-    const Layout l = layout_for(W, H, D, n_paths);
+    const Layout l = layout_for(p);
     const size_t wh = static_cast<size_t>(W) * H;
     const size_t extra = align_up(wh * D * 2) + align_up(wh * D);
     rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, l.total + extra, true);
@@ -1033,8 +1056,9 @@ int sgm_debug_stages(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, in
     CUDA_TRY(ctx, cudaMemcpyAsync(a + l.in_left, left, wh, cudaMemcpyHostToDevice, s));
     CUDA_TRY(ctx, cudaMemcpyAsync(a + l.in_right, right, wh, cudaMemcpyHostToDevice, s));
     CUDA_TRY(ctx, enqueue_path(ctx, p, a, a + l.in_left, a + l.in_right, a + l.out, S ? Sdev : nullptr, s, false));
-    if (Fb) CUDA_TRY(ctx, cudaMemcpyAsync(Fb, a + l.Fb, 4 * wh, cudaMemcpyDeviceToHost, s));
-    if (Fm) CUDA_TRY(ctx, cudaMemcpyAsync(Fm, a + l.Fm, 4 * wh, cudaMemcpyDeviceToHost, s));
+    const size_t fbytes = (p.ct62 ? 8 : 4) * wh;
+    if (Fb) CUDA_TRY(ctx, cudaMemcpyAsync(Fb, a + l.Fb, fbytes, cudaMemcpyDeviceToHost, s));
+    if (Fm) CUDA_TRY(ctx, cudaMemcpyAsync(Fm, a + l.Fm, fbytes, cudaMemcpyDeviceToHost, s));
     if (MC) {
         CUDA_TRY(ctx, launch_unpair_cost(a + l.rec, l.RB, MCnat, W, H, D, s));
         CUDA_TRY(ctx, cudaMemcpyAsync(MC, MCnat, wh * D, cudaMemcpyDeviceToHost, s));
@@ -1120,12 +1144,12 @@ cudaError_t static_scratch_for_current_device(uint8_t** out) {
 // The path of Section 2, stages 2-4, with every phase on one stream.
 cudaError_t enqueue_path_static(const Problem& p, uint8_t* arena, const uint8_t* left, const uint8_t* right,
                                 uint8_t* disp, cudaStream_t s) {
-    const Layout l = layout_for(p.W, p.H, p.D, p.n_paths);
-    uint32_t* Fb = reinterpret_cast<uint32_t*>(arena + l.Fb);
-    uint32_t* Fm = reinterpret_cast<uint32_t*>(arena + l.Fm);
+    const Layout l = layout_for(p);
+    void* Fb = arena + l.Fb;
+    void* Fm = arena + l.Fm;
     cudaError_t e;
-    if ((e = launch_census(left, right, Fb, Fm, p.W, p.H, s)) != cudaSuccess) return e;
-    if ((e = launch_cost(Fb, Fm, arena + l.rec, l.RB, p.W, p.H, p.D, s)) != cudaSuccess) return e;
+    if ((e = launch_census(left, right, Fb, Fm, p.W, p.H, false, s)) != cudaSuccess) return e;
+    if ((e = launch_cost(Fb, Fm, arena + l.rec, l.RB, p.W, p.H, p.D, false, s)) != cudaSuccess) return e;
     SweepArgs a{};
     a.rec = arena + l.rec;
     a.RB = l.RB;
@@ -1137,7 +1161,7 @@ cudaError_t enqueue_path_static(const Problem& p, uint8_t* arena, const uint8_t*
     a.P1x2 = static_cast<uint32_t>(p.P1) * 0x10001u;
     a.P2x2 = static_cast<uint32_t>(p.P2) * 0x10001u;
     a.pair = p.n_paths >= 4;
-    a.s8 = sum_fits_u8(p.n_paths, p.P2);
+    a.s8 = sum_fits_u8(p.n_paths, p.P2, mc_max(p));
     if ((e = launch_sweep_h(a, s)) != cudaSuccess) return e;
     if (!a.pair) {
         a.wta = 1;
@@ -1161,13 +1185,13 @@ cudaError_t enqueue_path_static(const Problem& p, uint8_t* arena, const uint8_t*
 
 extern "C" int sgm_compute_static(const uint8_t* left, const uint8_t* right, int W, int H, int D, int P1, int P2,
                                   int n_paths, uint8_t* disp_out, void* cuda_stream) {
-    const Problem p{W, H, D, P1, P2, n_paths};
+    const Problem p{W, H, D, P1, P2, n_paths};  // CSCT features
     if (!left || !right || !disp_out) return fail(nullptr, SGM_EINVAL, "null image or output pointer");
     std::string why;
     if (!valid_problem(p, &why)) return fail(nullptr, SGM_EINVAL, "%s", why.c_str());
     if (!is_device_ptr(left) || !is_device_ptr(right) || !is_device_ptr(disp_out))
         return fail(nullptr, SGM_EINVAL, "sgm_compute_static takes device pointers only");
-    const size_t need = layout_for(W, H, D, n_paths).total;
+    const size_t need = layout_for(p).total;
     if (need > kStaticScratchBytes)
         return fail(nullptr, SGM_EINVAL,
                     "%dx%d D=%d with %d paths needs %zu bytes of scratch; the static scratch holds %zu bytes", W, H, D,

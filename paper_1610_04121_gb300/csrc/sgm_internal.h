@@ -34,7 +34,10 @@ struct SweepArgs {
 // Every sum S held between sweeps fits a byte: with 2 paths S = L_LR <= 31 + P2
 // <= 255 always; with 4 paths S = L_LR + L_RL <= 2 * (31 + P2) before the
 // vertical pair's winner-take-all (L_r - MC <= P2 from Eq. 3, MC <= 31).
-inline bool sum_fits_u8(int n_paths, int P2) { return n_paths == 2 || (n_paths == 4 && 2 * (31 + P2) <= 255); }
+// With the full Census MC <= 62 instead of 31 (mc_max).
+inline bool sum_fits_u8(int n_paths, int P2, int mc_max = 31) {
+    return (n_paths == 2 && mc_max + P2 <= 255) || (n_paths == 4 && 2 * (mc_max + P2) <= 255);
+}
 
 // ---------------------------------------------------------------------------
 // Batched execution: one launch per stage covers many pairs.  A job table is
@@ -43,13 +46,14 @@ inline bool sum_fits_u8(int n_paths, int P2) { return n_paths == 2 || (n_paths =
 // ---------------------------------------------------------------------------
 constexpr int kMaxBatch = 64;
 
+// Features are uint32 (CSCT) or uint64 (full Census) as the table's ct62 flag says.
 struct CensusJob {
     const uint8_t *left, *right;
-    uint32_t *Fb, *Fm;
+    void *Fb, *Fm;
     int W, H;
 };
 struct CostJob {
-    const uint32_t *Fb, *Fm;
+    const void *Fb, *Fm;
     uint8_t* rec;  // MC is written at offset 0 of each RB-byte record
     int RB, W, H;
 };
@@ -67,10 +71,12 @@ struct JobTable {
 };
 
 // Each launcher enqueues one kernel on `stream` and returns the launch error.
-cudaError_t launch_census(const uint8_t* left, const uint8_t* right, uint32_t* Fb, uint32_t* Fm, int W, int H,
+// ct62 = false: the CSCT of Eq. 1, uint32 features; true: the full 9x7
+// Census, uint64 features.
+cudaError_t launch_census(const uint8_t* left, const uint8_t* right, void* Fb, void* Fm, int W, int H, bool ct62,
                           cudaStream_t stream);
 // MC goes to offset 0 of the RB-byte record of each pixel.
-cudaError_t launch_cost(const uint32_t* Fb, const uint32_t* Fm, uint8_t* rec, int RB, int W, int H, int D,
+cudaError_t launch_cost(const void* Fb, const void* Fm, uint8_t* rec, int RB, int W, int H, int D, bool ct62,
                         cudaStream_t stream);
 cudaError_t launch_sweep_h(const SweepArgs& a, cudaStream_t stream);
 // The first sweep stage of a path with pairs (4 or 8 directions): the
@@ -100,8 +106,8 @@ inline size_t sweep_state_words(int W, int D) {
 cudaError_t launch_median(const uint8_t* raw, uint8_t* disp, int W, int H, cudaStream_t stream);
 // Batched forms; every job of a cost or sweep table has the same D (and, for
 // sweeps, the same pair / rx / phase / wta / s8 settings).  `start` is filled in.
-cudaError_t launch_census_batch(JobTable<CensusJob>& t, cudaStream_t stream);
-cudaError_t launch_cost_batch(JobTable<CostJob>& t, int D, cudaStream_t stream);
+cudaError_t launch_census_batch(JobTable<CensusJob>& t, bool ct62, cudaStream_t stream);
+cudaError_t launch_cost_batch(JobTable<CostJob>& t, int D, bool ct62, cudaStream_t stream);
 cudaError_t launch_median_batch(JobTable<MedianJob>& t, cudaStream_t stream);
 cudaError_t launch_sweep_h_batch(JobTable<SweepArgs>& t, cudaStream_t stream);
 cudaError_t launch_sweep_v_batch(JobTable<SweepArgs>& t, cudaStream_t stream);

@@ -1,5 +1,7 @@
 // Census (Eq. 1), matching cost (Eq. 2) and the 3x3 median (Section 2,
 // stage 4) of the SGM path in arXiv 1610.04121, for sm_103a.
+#include <type_traits>
+
 #include "sgm_device.cuh"
 #include "sgm_internal.h"
 
@@ -48,13 +50,42 @@ __device__ __forceinline__ uint32_t census_feature(const uint32_t (&win)[7][NC],
     return __byte_perm(__byte_perm(c[0], c[1], 0x0040u), __byte_perm(c[2], c[3], 0x0040u), 0x5410u);
 }
 
+// The full 9x7 Census (the CT Section 2 contrasts CSCT with): bit k compares
+// the k-th window pixel in row-major order (rows j = -3..3, columns
+// i = -4..4, the centre skipped) with the centre, s(I(x+i, y+j), I(x, y));
+// 62 bits gathered as eight 8-bit chains (the sign of I(x, y) + ~I(x+i, y+j)
+// is set exactly when I(x+i, y+j) >= I(x, y)).
+template <int NC>
+__device__ __forceinline__ uint64_t census62_feature(const uint32_t (&win)[7][NC], int r, int c0) {
+    auto diff = [&](int b) -> uint32_t {
+        const int idx = b < 31 ? b : b + 1;  // window position, the centre (31) skipped
+        const int j = idx / 9 - 3, i = idx % 9 - 4;
+        return win[(r + 3) % 7][c0 + 4] + ~win[(r + 3 + j) % 7][c0 + 4 + i];
+    };
+    uint32_t c[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int b = q * 8 + 7; b >= q * 8; --b)  // highest bit of the byte first
+            if (b < 62) c[q] = __funnelshift_l(diff(b), c[q], 1);
+    const uint32_t lo =
+        __byte_perm(__byte_perm(c[0], c[1], 0x0040u), __byte_perm(c[2], c[3], 0x0040u), 0x5410u);
+    const uint32_t hi =
+        __byte_perm(__byte_perm(c[4], c[5], 0x0040u), __byte_perm(c[6], c[7], 0x0040u), 0x5410u);
+    return static_cast<uint64_t>(hi) << 32 | lo;
+}
+
+// CT = false: the CSCT of Eq. 1 into uint32 features; CT = true: the full
+// 9x7 Census into uint64 features.
+template <bool CT>
 __device__ __forceinline__ void census_body(const uint8_t* __restrict__ left, const uint8_t* __restrict__ right,
-                                            uint32_t* __restrict__ Fb, uint32_t* __restrict__ Fm, int W, int H,
-                                            int bx, int by, int bz) {
+                                            void* __restrict__ Fb, void* __restrict__ Fm, int W, int H, int bx,
+                                            int by, int bz) {
+    using FT = typename std::conditional<CT, uint64_t, uint32_t>::type;
     constexpr int TW = kCtW + 8, TH = kCtH + 6, NS = (TW + kCtT - 1) / kCtT;
     __shared__ uint8_t tile[TH][TW];
     const uint8_t* img = bz ? right : left;
-    uint32_t* F = bz ? Fm : Fb;
+    FT* F = static_cast<FT*>(bz ? Fm : Fb);
     const int x0 = bx * kCtW, y0 = by * kCtH;
     // Thread t stages tile columns t, t + kCtT, ...: all loads are issued
     // before the first shared-memory store.
@@ -95,39 +126,53 @@ __device__ __forceinline__ void census_body(const uint8_t* __restrict__ left, co
         const int y = y0 + r;
         if (y >= H) break;
         const bool yok = y >= 3 && y <= H - 4;
-        const uint32_t f0 = census_feature(win, r, 0), f1 = census_feature(win, r, 1);
-        uint32_t* row = F + (size_t)y * W + x;
-        row[0] = (ok0 && yok) ? f0 : 0u;
-        if (has1) row[1] = (ok1 && yok) ? f1 : 0u;
+        FT f0, f1;
+        if constexpr (CT) {
+            f0 = census62_feature(win, r, 0);
+            f1 = census62_feature(win, r, 1);
+        } else {
+            f0 = census_feature(win, r, 0);
+            f1 = census_feature(win, r, 1);
+        }
+        FT* row = F + (size_t)y * W + x;
+        row[0] = (ok0 && yok) ? f0 : FT(0);
+        if (has1) row[1] = (ok1 && yok) ? f1 : FT(0);
     }
 }
 
+template <bool CT>
 __global__ void __launch_bounds__(kCtT) census_kernel(const uint8_t* __restrict__ left, const uint8_t* __restrict__ right,
-                                                      uint32_t* __restrict__ Fb, uint32_t* __restrict__ Fm, int W,
-                                                      int H) {
-    census_body(left, right, Fb, Fm, W, H, blockIdx.x, blockIdx.y, blockIdx.z);
+                                                      void* __restrict__ Fb, void* __restrict__ Fm, int W, int H) {
+    census_body<CT>(left, right, Fb, Fm, W, H, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
+template <bool CT>
 __global__ void __launch_bounds__(kCtT) census_batch_kernel(const __grid_constant__ JobTable<CensusJob> t) {
     const int p = find_job(t, blockIdx.x);
     const CensusJob& j = t.job[p];
     const int b = blockIdx.x - t.start[p];
     const int tx = (j.W + kCtW - 1) / kCtW, ty = (j.H + kCtH - 1) / kCtH;
-    census_body(j.left, j.right, j.Fb, j.Fm, j.W, j.H, b % tx, (b / tx) % ty, b / (tx * ty));
+    census_body<CT>(j.left, j.right, j.Fb, j.Fm, j.W, j.H, b % tx, (b / tx) % ty, b / (tx * ty));
 }
 
-cudaError_t launch_census_batch(JobTable<CensusJob>& t, cudaStream_t stream) {
+cudaError_t launch_census_batch(JobTable<CensusJob>& t, bool ct62, cudaStream_t stream) {
     t.start[0] = 0;
     for (int i = 0; i < t.n; ++i)
         t.start[i + 1] = t.start[i] + 2 * ((t.job[i].W + kCtW - 1) / kCtW) * ((t.job[i].H + kCtH - 1) / kCtH);
-    census_batch_kernel<<<t.start[t.n], kCtT, 0, stream>>>(t);
+    if (ct62)
+        census_batch_kernel<true><<<t.start[t.n], kCtT, 0, stream>>>(t);
+    else
+        census_batch_kernel<false><<<t.start[t.n], kCtT, 0, stream>>>(t);
     return cudaGetLastError();
 }
 
-cudaError_t launch_census(const uint8_t* left, const uint8_t* right, uint32_t* Fb, uint32_t* Fm, int W, int H,
+cudaError_t launch_census(const uint8_t* left, const uint8_t* right, void* Fb, void* Fm, int W, int H, bool ct62,
                           cudaStream_t stream) {
     dim3 grid((W + kCtW - 1) / kCtW, (H + kCtH - 1) / kCtH, 2);
-    census_kernel<<<grid, kCtT, 0, stream>>>(left, right, Fb, Fm, W, H);
+    if (ct62)
+        census_kernel<true><<<grid, kCtT, 0, stream>>>(left, right, Fb, Fm, W, H);
+    else
+        census_kernel<false><<<grid, kCtT, 0, stream>>>(left, right, Fb, Fm, W, H);
     return cudaGetLastError();
 }
 
@@ -144,27 +189,42 @@ cudaError_t launch_census(const uint8_t* left, const uint8_t* right, uint32_t* F
 // ---------------------------------------------------------------------------
 constexpr int kMcSeg = 128, kMcPix = 4, kMcThreads = 128;
 
-template <int D>
-__device__ __forceinline__ void cost_body(const uint32_t* __restrict__ Fb, const uint32_t* __restrict__ Fm,
+// Two consecutive staged features.
+__device__ __forceinline__ void ld2(const uint32_t* p, uint32_t& a, uint32_t& b) {
+    const uint2 v = *reinterpret_cast<const uint2*>(p);
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void ld2(const uint64_t* p, uint64_t& a, uint64_t& b) {
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(p);
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ uint32_t bitcount(uint32_t v) { return __popc(v); }
+__device__ __forceinline__ uint32_t bitcount(uint64_t v) { return __popcll(v); }
+
+// FT: uint32_t (CSCT features) or uint64_t (full Census features).
+template <int D, class FT>
+__device__ __forceinline__ void cost_body(const FT* __restrict__ Fb, const FT* __restrict__ Fm,
                                           uint8_t* __restrict__ rec, int RB, int W, int seg, int y) {
     constexpr int Q = D / 4, half = D / 2, NF = kMcSeg + D;  // words per pixel; staged match features (even)
-    __shared__ __align__(16) uint32_t fm[NF];  // fm[k] = F_match(x0 - D + k)
-    __shared__ __align__(16) uint32_t fb[kMcSeg];
+    __shared__ __align__(16) FT fm[NF];  // fm[k] = F_match(x0 - D + k)
+    __shared__ __align__(16) FT fb[kMcSeg];
     const int x0 = seg * kMcSeg;
-    const uint32_t* fmrow = Fm + (size_t)y * W;
+    const FT* fmrow = Fm + (size_t)y * W;
     {
         // every load is issued before the first shared-memory store
         constexpr int NI = (NF + kMcThreads - 1) / kMcThreads, NB = kMcSeg / kMcThreads;
-        uint32_t vm[NI], vb[NB];
+        FT vm[NI], vb[NB];
 #pragma unroll
         for (int it = 0; it < NI; ++it) {
             const int i = threadIdx.x + it * kMcThreads, gx = x0 - D + i;
-            vm[it] = (i < NF && gx >= 0 && gx < W) ? __ldg(fmrow + gx) : 0u;
+            vm[it] = (i < NF && gx >= 0 && gx < W) ? __ldg(fmrow + gx) : FT(0);
         }
 #pragma unroll
         for (int it = 0; it < NB; ++it) {
             const int i = threadIdx.x + it * kMcThreads;
-            vb[it] = (x0 + i < W) ? __ldg(Fb + (size_t)y * W + x0 + i) : 0u;
+            vb[it] = (x0 + i < W) ? __ldg(Fb + (size_t)y * W + x0 + i) : FT(0);
         }
 #pragma unroll
         for (int it = 0; it < NI; ++it) {
@@ -183,89 +243,93 @@ __device__ __forceinline__ void cost_body(const uint32_t* __restrict__ Fb, const
         // F_match(x - d) for x = x0 + px + p lives at fm[px + p + D - d]
         const int ba = px + D - i0 - 2;  // d = i0 + 1 - p' ... : fm[ba + p + 1] is d = i0 + 1, fm[ba + p + 2] is d = i0
         const int bb = ba - half;
-        uint32_t ra[kMcPix + 2], rb[kMcPix + 2];
+        FT ra[kMcPix + 2], rb[kMcPix + 2], b4[kMcPix];
 #pragma unroll
         for (int k = 0; k < kMcPix + 2; k += 2) {
-            const uint2 va = *reinterpret_cast<const uint2*>(fm + ba + k);
-            const uint2 vb = *reinterpret_cast<const uint2*>(fm + bb + k);
-            ra[k] = va.x;
-            ra[k + 1] = va.y;
-            rb[k] = vb.x;
-            rb[k + 1] = vb.y;
+            ld2(fm + ba + k, ra[k], ra[k + 1]);
+            ld2(fm + bb + k, rb[k], rb[k + 1]);
         }
-        const uint4 vb4 = *reinterpret_cast<const uint4*>(fb + px);
-        const uint32_t b4[4] = {vb4.x, vb4.y, vb4.z, vb4.w};
+#pragma unroll
+        for (int k = 0; k < kMcPix; k += 2) ld2(fb + px + k, b4[k], b4[k + 1]);
 #pragma unroll
         for (int p = 0; p < kMcPix; ++p) {
             if (px + p >= npx) break;
-            const uint32_t b = b4[p];
-            const uint32_t c0 = __popc(b ^ ra[p + 2]);  // d = i0
-            const uint32_t c1 = __popc(b ^ rb[p + 2]);  // d = i0 + D/2
-            const uint32_t c2 = __popc(b ^ ra[p + 1]);  // d = i0 + 1
-            const uint32_t c3 = __popc(b ^ rb[p + 1]);  // d = i0 + 1 + D/2
+            const FT b = b4[p];
+            const uint32_t c0 = bitcount(b ^ ra[p + 2]);  // d = i0
+            const uint32_t c1 = bitcount(b ^ rb[p + 2]);  // d = i0 + D/2
+            const uint32_t c2 = bitcount(b ^ ra[p + 1]);  // d = i0 + 1
+            const uint32_t c3 = bitcount(b ^ rb[p + 1]);  // d = i0 + 1 + D/2
             reinterpret_cast<uint32_t*>(out + (size_t)(px + p) * RB)[wi] =
                 __byte_perm(c0 | (c2 << 16), c1 | (c3 << 16), 0x6240u);  // [c0, c1, c2, c3]
         }
     }
 }
 
-template <int D>
-__global__ void __launch_bounds__(kMcThreads) cost_kernel(const uint32_t* __restrict__ Fb,
-                                                          const uint32_t* __restrict__ Fm, uint8_t* __restrict__ rec,
-                                                          int RB, int W) {
-    cost_body<D>(Fb, Fm, rec, RB, W, blockIdx.x, blockIdx.y);
+template <int D, class FT>
+__global__ void __launch_bounds__(kMcThreads) cost_kernel(const FT* __restrict__ Fb, const FT* __restrict__ Fm,
+                                                          uint8_t* __restrict__ rec, int RB, int W) {
+    cost_body<D, FT>(Fb, Fm, rec, RB, W, blockIdx.x, blockIdx.y);
 }
 
-template <int D>
+template <int D, class FT>
 __global__ void __launch_bounds__(kMcThreads) cost_batch_kernel(const __grid_constant__ JobTable<CostJob> t) {
     const int p = find_job(t, blockIdx.x);
     const CostJob& j = t.job[p];
     const int b = blockIdx.x - t.start[p];
     const int segs = (j.W + kMcSeg - 1) / kMcSeg;
-    cost_body<D>(j.Fb, j.Fm, j.rec, j.RB, j.W, b % segs, b / segs);
+    cost_body<D, FT>(static_cast<const FT*>(j.Fb), static_cast<const FT*>(j.Fm), j.rec, j.RB, j.W, b % segs,
+                     b / segs);
 }
 
 template <int D>
-static cudaError_t launch_cost_batch_t(JobTable<CostJob>& t, cudaStream_t s) {
+static cudaError_t launch_cost_batch_t(JobTable<CostJob>& t, bool ct62, cudaStream_t s) {
     t.start[0] = 0;
     for (int i = 0; i < t.n; ++i) t.start[i + 1] = t.start[i] + ((t.job[i].W + kMcSeg - 1) / kMcSeg) * t.job[i].H;
-    cost_batch_kernel<D><<<t.start[t.n], kMcThreads, 0, s>>>(t);
+    if (ct62)
+        cost_batch_kernel<D, uint64_t><<<t.start[t.n], kMcThreads, 0, s>>>(t);
+    else
+        cost_batch_kernel<D, uint32_t><<<t.start[t.n], kMcThreads, 0, s>>>(t);
     return cudaGetLastError();
 }
 
-cudaError_t launch_cost_batch(JobTable<CostJob>& t, int D, cudaStream_t stream) {
+cudaError_t launch_cost_batch(JobTable<CostJob>& t, int D, bool ct62, cudaStream_t stream) {
     switch (D) {
-        case 32: return launch_cost_batch_t<32>(t, stream);
-        case 64: return launch_cost_batch_t<64>(t, stream);
-        case 96: return launch_cost_batch_t<96>(t, stream);
-        case 128: return launch_cost_batch_t<128>(t, stream);
-        case 160: return launch_cost_batch_t<160>(t, stream);
-        case 192: return launch_cost_batch_t<192>(t, stream);
-        case 224: return launch_cost_batch_t<224>(t, stream);
-        case 256: return launch_cost_batch_t<256>(t, stream);
+        case 32: return launch_cost_batch_t<32>(t, ct62, stream);
+        case 64: return launch_cost_batch_t<64>(t, ct62, stream);
+        case 96: return launch_cost_batch_t<96>(t, ct62, stream);
+        case 128: return launch_cost_batch_t<128>(t, ct62, stream);
+        case 160: return launch_cost_batch_t<160>(t, ct62, stream);
+        case 192: return launch_cost_batch_t<192>(t, ct62, stream);
+        case 224: return launch_cost_batch_t<224>(t, ct62, stream);
+        case 256: return launch_cost_batch_t<256>(t, ct62, stream);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <int D>
-static cudaError_t launch_cost_t(const uint32_t* Fb, const uint32_t* Fm, uint8_t* rec, int RB, int W, int H,
+static cudaError_t launch_cost_t(const void* Fb, const void* Fm, uint8_t* rec, int RB, int W, int H, bool ct62,
                                  cudaStream_t s) {
     const dim3 grid((W + kMcSeg - 1) / kMcSeg, H);
-    cost_kernel<D><<<grid, kMcThreads, 0, s>>>(Fb, Fm, rec, RB, W);
+    if (ct62)
+        cost_kernel<D, uint64_t><<<grid, kMcThreads, 0, s>>>(static_cast<const uint64_t*>(Fb),
+                                                             static_cast<const uint64_t*>(Fm), rec, RB, W);
+    else
+        cost_kernel<D, uint32_t><<<grid, kMcThreads, 0, s>>>(static_cast<const uint32_t*>(Fb),
+                                                             static_cast<const uint32_t*>(Fm), rec, RB, W);
     return cudaGetLastError();
 }
 
-cudaError_t launch_cost(const uint32_t* Fb, const uint32_t* Fm, uint8_t* rec, int RB, int W, int H, int D,
+cudaError_t launch_cost(const void* Fb, const void* Fm, uint8_t* rec, int RB, int W, int H, int D, bool ct62,
                         cudaStream_t stream) {
     switch (D) {
-        case 32: return launch_cost_t<32>(Fb, Fm, rec, RB, W, H, stream);
-        case 64: return launch_cost_t<64>(Fb, Fm, rec, RB, W, H, stream);
-        case 96: return launch_cost_t<96>(Fb, Fm, rec, RB, W, H, stream);
-        case 128: return launch_cost_t<128>(Fb, Fm, rec, RB, W, H, stream);
-        case 160: return launch_cost_t<160>(Fb, Fm, rec, RB, W, H, stream);
-        case 192: return launch_cost_t<192>(Fb, Fm, rec, RB, W, H, stream);
-        case 224: return launch_cost_t<224>(Fb, Fm, rec, RB, W, H, stream);
-        case 256: return launch_cost_t<256>(Fb, Fm, rec, RB, W, H, stream);
+        case 32: return launch_cost_t<32>(Fb, Fm, rec, RB, W, H, ct62, stream);
+        case 64: return launch_cost_t<64>(Fb, Fm, rec, RB, W, H, ct62, stream);
+        case 96: return launch_cost_t<96>(Fb, Fm, rec, RB, W, H, ct62, stream);
+        case 128: return launch_cost_t<128>(Fb, Fm, rec, RB, W, H, ct62, stream);
+        case 160: return launch_cost_t<160>(Fb, Fm, rec, RB, W, H, ct62, stream);
+        case 192: return launch_cost_t<192>(Fb, Fm, rec, RB, W, H, ct62, stream);
+        case 224: return launch_cost_t<224>(Fb, Fm, rec, RB, W, H, ct62, stream);
+        case 256: return launch_cost_t<256>(Fb, Fm, rec, RB, W, H, ct62, stream);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -29,6 +29,7 @@ SGM_ECUDA, SGM_ETIMEDOUT, SGM_ECANCELED, SGM_EDEVICE = -3, -4, -5, -6
 STATUS_NAMES = {0: "SGM_OK", 1: "SGM_EAGAIN", -1: "SGM_EINVAL", -2: "SGM_ENOMEM", -3: "SGM_ECUDA",
                 -4: "SGM_ETIMEDOUT", -5: "SGM_ECANCELED", -6: "SGM_EDEVICE"}
 SGM_FLAG_STAGE_TIMING = 1
+SGM_FLAG_CENSUS_FULL = 2
 SGM_MAX_D = 256
 SGM_MAX_PENALTY = 224
 
@@ -188,6 +189,7 @@ class Context:
     """Owns one sgm_ctx; a convenience over the functions above."""
 
     def __init__(self, device: int = 0, mem_cap_bytes: int = 0, flags: int = 0):
+        self.flags = flags
         self.handle = sgm_create(device, mem_cap_bytes, flags)
 
     def close(self):
@@ -219,7 +221,8 @@ class Context:
         import numpy as np
 
         H, W = left.shape
-        r = {"Fb": np.zeros((H, W), np.uint32), "Fm": np.zeros((H, W), np.uint32),
+        ft = np.uint64 if self.flags & SGM_FLAG_CENSUS_FULL else np.uint32
+        r = {"Fb": np.zeros((H, W), ft), "Fm": np.zeros((H, W), ft),
              "MC": np.zeros((H, W, D), np.uint8), "S": np.zeros((H, W, D), np.uint16),
              "raw": np.zeros((H, W), np.uint8), "disp": np.zeros((H, W), np.uint8)}
         sgm_debug_stages(self.handle, np.ascontiguousarray(left), np.ascontiguousarray(right), W, H, D, P1, P2,
