@@ -192,7 +192,7 @@ struct Chain {
     uint32_t w[K];
     uint32_t up, dn;  // word pl*K-1 from lane pl-1, word pl*K+K from lane pl+1 (wrapping in the path)
     uint32_t mpx2;    // m(q) in both u16 halves
-    uint32_t sel_up, sel_dn, mask_a, mask_b;
+    uint32_t mul_up, add_up, sel_dn, mask_a, mask_b;
     int src_up, src_dn;
     bool in_b;
 
@@ -200,8 +200,11 @@ struct Chain {
         const int pl = lane & (G - 1), base = lane & (32 - G);
         src_up = base | ((pl + G - 1) & (G - 1));
         src_dn = base | ((pl + 1) & (G - 1));
-        // first lane of a path: d-1 of d=0 is absent, d-1 of d=D/2 is the low half of word D/2-1
-        sel_up = (pl == 0) ? 0x1054u : 0x3210u;
+        // first lane of a path: d-1 of d=0 is absent, d-1 of d=D/2 is the low
+        // half of word D/2-1, so up -> [inf, up.lo] = up * 2^16 + inf (one
+        // multiply-add on the FMA pipe); other lanes take up * 1 + 0
+        mul_up = (pl == 0) ? 0x10000u : 1u;
+        add_up = (pl == 0) ? kInf16 : 0u;
         // last lane of a path: d+1 of d=D-1 is absent, d+1 of d=D/2-1 is the high half of word 0
         sel_dn = (pl == G - 1) ? 0x5432u : 0x3210u;
         in_b = G == 16 && lane >= 16;
@@ -230,7 +233,7 @@ struct Chain {
 
     __device__ __forceinline__ void step(const uint32_t (&mc)[K], uint32_t P1x2, uint32_t P2x2, uint32_t (&L)[K]) {
         const uint32_t inf2 = kInf16 * 0x10001u;
-        const uint32_t u = __byte_perm(up, inf2, sel_up);
+        const uint32_t u = up * mul_up + add_up;
         const uint32_t d = __byte_perm(dn, inf2, sel_dn);
         const uint32_t mp2 = mpx2 + P2x2;
 #pragma unroll
@@ -252,28 +255,47 @@ struct Chain {
     }
 };
 
-// Winner-take-all over one lane's words (Eq. 4): key = S << 8 | d, so the
-// u32 minimum is the smallest S and, among equal S, the lowest d.  dconst[j]
-// holds, for word i = pl*K + j, the bytes [i, i + D/2, 0, 0].
-template <int K>
+// Winner-take-all over one lane's words (Eq. 4).  The key orders by S, then
+// by d, so its minimum over the path is the smallest S with, among equal S,
+// the lowest d.
+//
+// KEY16 (every S below 65536 / D - 1): both u16 halves of word j become
+// S * D + d in one multiply-add on the FMA pipe, d from dconst[j] = [i, i + D/2]
+// for word i = pl*K + j; the lane's minimum key ends in the low half.
+// Otherwise key = S << 8 | d in a u32, built with byte permutes, dconst[j]
+// holding the bytes [i, i + D/2, 0, 0].
+template <int K, bool KEY16>
 __device__ __forceinline__ void wta_consts(int pl, int D, uint32_t (&dconst)[K]) {
 #pragma unroll
     for (int j = 0; j < K; ++j) {
         const uint32_t i = static_cast<uint32_t>(pl * K + j);
-        dconst[j] = i | ((i + static_cast<uint32_t>(D / 2)) << 8);
+        dconst[j] = i | ((i + static_cast<uint32_t>(D / 2)) << (KEY16 ? 16 : 8));
     }
 }
 
-template <int K>
+template <int K, int D, bool KEY16>
 __device__ __forceinline__ uint32_t wta_key(const uint32_t (&s)[K], const uint32_t (&dconst)[K]) {
-    uint32_t best = 0xffffffffu;
+    if constexpr (KEY16) {
+        uint32_t best = s[0] * static_cast<uint32_t>(D) + dconst[0];
 #pragma unroll
-    for (int j = 0; j < K; ++j) {
-        const uint32_t klo = __byte_perm(s[j], dconst[j], 0x6104u);  // [d_lo, S_lo.b0, S_lo.b1, 0]
-        const uint32_t khi = __byte_perm(s[j], dconst[j], 0x6325u);  // [d_hi, S_hi.b0, S_hi.b1, 0]
-        best = min(best, min(klo, khi));
+        for (int j = 1; j < K; ++j) best = vmin2(best, s[j] * static_cast<uint32_t>(D) + dconst[j]);
+        return vmin2(best, __umulhi(best, 0x10000u));
+    } else {
+        uint32_t best = 0xffffffffu;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const uint32_t klo = __byte_perm(s[j], dconst[j], 0x6104u);  // [d_lo, S_lo.b0, S_lo.b1, 0]
+            const uint32_t khi = __byte_perm(s[j], dconst[j], 0x6325u);  // [d_hi, S_hi.b0, S_hi.b1, 0]
+            best = min(best, min(klo, khi));
+        }
+        return best;
     }
-    return best;
+}
+
+// The disparity of a path's minimum key.
+template <int D, bool KEY16>
+__device__ __forceinline__ uint8_t wta_disparity(uint32_t key) {
+    return static_cast<uint8_t>(KEY16 ? key % static_cast<uint32_t>(D) : key & 0xffu);
 }
 
 // Index of the job that owns block b in a job table (start[] ascending).

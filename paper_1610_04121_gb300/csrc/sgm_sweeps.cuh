@@ -191,7 +191,9 @@ struct StepIn {
 // Pixels of a row walk: x = x0 + dx * i in row y.
 struct RowGeo {
     static constexpr bool kResets = false;
+    static constexpr bool kLinear = true;  // consecutive pixels are step_pix() apart
     int rowbase, x0, dx;
+    __device__ __forceinline__ int step_pix() const { return dx; }
     struct Cursor {
         int pix;
     };
@@ -204,7 +206,9 @@ struct RowGeo {
 template <int RX>
 struct ColGeo {
     static constexpr bool kResets = RX != 0;
+    static constexpr bool kLinear = RX == 0;
     int W, H, c, y0, dy;
+    __device__ __forceinline__ int step_pix() const { return dy * W; }
     struct Cursor {
         int pix, x, y;
     };
@@ -306,15 +310,28 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
     In nxt[PF];
     typename Geo::Cursor ld = g.start(), cur = ld;
     const int pix0 = n_own > 0 ? ld.pix : 0;  // an empty path (W or H of 1) may start outside the image
+    // Walks with a constant pixel stride advance 32-bit record offsets
+    // directly (one add per step instead of an index update and a multiply).
+    const uint32_t off0 = static_cast<uint32_t>(pix0) * RB;
+    const uint32_t doff = Geo::kLinear ? static_cast<uint32_t>(g.step_pix()) * RB : 0u;
+    uint32_t off_ld = static_cast<uint32_t>(ld.pix) * RB, off_cur = off_ld;
     auto prefetch = [&](In& b, int i, bool clamp) {
-        const int pix = (clamp && i >= n_own) ? pix0 : ld.pix;
-        b.load(lb, static_cast<uint32_t>(pix) * RB);
-        g.advance(ld);
+        if constexpr (Geo::kLinear) {
+            b.load(lb, (clamp && i >= n_own) ? off0 : off_ld);
+            off_ld += doff;
+        } else {
+            const int pix = (clamp && i >= n_own) ? pix0 : ld.pix;
+            b.load(lb, static_cast<uint32_t>(pix) * RB);
+            g.advance(ld);
+        }
     };
 #pragma unroll
     for (int k = 0; k < PF; ++k) prefetch(nxt[k], k, true);
+    // 16-bit keys: byte sums of 2 or 4 paths stay below 511, so S * D + d
+    // fits 16 bits for D <= 128
+    constexpr bool KEY16 = S8 && D <= 128;
     uint32_t dconst[K];
-    if constexpr (M::WTA) wta_consts<K>(pl, D, dconst);
+    if constexpr (M::WTA) wta_consts<K, KEY16>(pl, D, dconst);
 
     // one step of the recurrence at `cur` and its outputs
     auto body = [&](const In& in, bool active) {
@@ -324,9 +341,16 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
         uint32_t mc[K], L[K];
         unpack_regs<K>(in.mc.r, mc);
         ch.step(mc, a.P1x2, a.P2x2, L);
-        const uint32_t off = static_cast<uint32_t>(cur.pix) * RB;
+        const uint32_t off = Geo::kLinear ? off_cur : static_cast<uint32_t>(cur.pix) * RB;
         if constexpr (M::OUT_LX) {
             if (active) st_pairs<K>(at(lb.lx, off), pack_pairs<K>(L));
+        } else if constexpr (MODE == kSumH && S8) {
+            // byte sums: every L_r <= 127 here (sum_fits_u8), so the paired
+            // bytes of L and of the stored L_r add without carries
+            U8Pairs<K> o = pack_pairs<K>(L);
+#pragma unroll
+            for (int q = 0; q < (K + 1) / 2; ++q) o.r[q] += in.lo.r[q];
+            if (active) st_pairs<K>(at(lb.pairs, off) + D, o);
         } else {
             uint32_t s[K];
 #pragma unroll
@@ -357,8 +381,8 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
                 }
             }
             if constexpr (M::WTA) {
-                const uint32_t key = ch.path_min(wta_key<K>(s, dconst));
-                if (active && pl == 0) a.raw[cur.pix] = static_cast<uint8_t>(key & 0xffu);
+                const uint32_t key = ch.path_min(wta_key<K, D, KEY16>(s, dconst));
+                if (active && pl == 0) a.raw[cur.pix] = wta_disparity<D, KEY16>(key);
                 if (DBG && active) {  // debug: natural-order S
                     const size_t p = static_cast<size_t>(cur.pix);
 #pragma unroll
@@ -388,6 +412,7 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
             for (int k = 0; k < PF; ++k) {
                 body(in[k], true);
                 g.advance(cur);
+                off_cur += doff;
             }
         } else {
             // last steps: a path with fewer steps keeps its state through the extra ones
@@ -401,6 +426,7 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
                     body(in[k], i < n_own);
                     if (i >= n_own) ch = saved;
                     g.advance(cur);
+                    off_cur += doff;
                 }
             }
         }
