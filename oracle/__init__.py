@@ -20,6 +20,14 @@ from .oracle import (  # noqa: F401
     wta,
     median3x3,
     sgm,
+    sgm_ex,
+    aggregate_ex,
+    subpixel,
+    median3x3_u16,
+    POST_SUBPIXEL,
+    POST_LR_CHECK,
+    POST_ADAPTIVE_P2,
+    DISP16_INVALID,
     pixel,
     disp_at,
 )

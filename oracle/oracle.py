@@ -25,6 +25,13 @@ _u8p = ctypes.POINTER(ctypes.c_uint8)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
 _i32p = ctypes.POINTER(ctypes.c_int32)
+_u16p = ctypes.POINTER(ctypes.c_uint16)
+
+# post-filter flags of sgm_ex (values of the C ABI's SGM_POST_* flags)
+POST_SUBPIXEL = 1
+POST_LR_CHECK = 2
+POST_ADAPTIVE_P2 = 4
+DISP16_INVALID = 0xFFFF
 
 
 def build(force: bool = False) -> str:
@@ -73,6 +80,14 @@ def load() -> ctypes.CDLL:
             lib.oracle_cost64.restype = None
             lib.oracle_sgm_ct62.argtypes = [_u8p, _u8p] + [ctypes.c_int] * 6 + [_u8p, _u8p, _u64p, _u64p, _i32p]
             lib.oracle_sgm_ct62.restype = ctypes.c_int
+            lib.oracle_aggregate_ex.argtypes = [_u8p, _u8p] + [ctypes.c_int] * 7 + [_i32p]
+            lib.oracle_aggregate_ex.restype = None
+            lib.oracle_subpixel.argtypes = [_i32p, ctypes.c_int, ctypes.c_int]
+            lib.oracle_subpixel.restype = ctypes.c_int
+            lib.oracle_median3x3_u16.argtypes = [_u16p, ctypes.c_int, ctypes.c_int, _u16p]
+            lib.oracle_median3x3_u16.restype = None
+            lib.oracle_sgm_ex.argtypes = [_u8p, _u8p] + [ctypes.c_int] * 7 + [ctypes.c_uint, _u16p, _u8p, _u8p]
+            lib.oracle_sgm_ex.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -155,6 +170,54 @@ def aggregate(MC: np.ndarray, P1: int, P2: int, rx: int, ry: int) -> np.ndarray:
     L = np.zeros((H, W, D), dtype=np.int32)
     load().oracle_aggregate(_ptr(MC, _u8p), W, H, D, P1, P2, rx, ry, _ptr(L, _i32p))
     return L
+
+
+def aggregate_ex(MC: np.ndarray, Ib: Optional[np.ndarray], P1: int, P2: int, rx: int, ry: int) -> np.ndarray:
+    """Eq. 3 along r with adaptive P2 from the base image Ib (None: constant P2)."""
+    MC = np.ascontiguousarray(MC, dtype=np.uint8)
+    H, W, D = MC.shape
+    L = np.zeros((H, W, D), dtype=np.int32)
+    ib = ctypes.cast(None, _u8p) if Ib is None else _ptr(_img(Ib), _u8p)
+    load().oracle_aggregate_ex(_ptr(MC, _u8p), ib, W, H, D, P1, P2, rx, ry, _ptr(L, _i32p))
+    return L
+
+
+def subpixel(S: np.ndarray, d: int) -> int:
+    """Sub-pixel disparity (1/16 pixel) at the winner d of one pixel's S."""
+    S = np.ascontiguousarray(S, dtype=np.int32)
+    return int(load().oracle_subpixel(_ptr(S, _i32p), S.shape[0], d))
+
+
+def median3x3_u16(v: np.ndarray) -> np.ndarray:
+    v = np.ascontiguousarray(v, dtype=np.uint16)
+    H, W = v.shape
+    out = np.zeros_like(v)
+    load().oracle_median3x3_u16(_ptr(v, _u16p), W, H, _ptr(out, _u16p))
+    return out
+
+
+def sgm_ex(left: np.ndarray, right: np.ndarray, D: int, P1: int, P2: int, n_paths: int, post: int = 0,
+           census: str = "csct", debug: bool = False):
+    """The path with the post-filters (sub-pixel, LR check, adaptive P2).
+
+    Returns uint16 [H, W] in 1/16 pixel, DISP16_INVALID where the LR check
+    fails; with ``debug`` a dict with ``out``, ``dL`` and ``dR`` (the integer
+    winner-take-all disparities of the left and right passes).
+    """
+    if census not in ("csct", "ct62"):
+        raise ValueError(f"unknown census {census!r}")
+    left, right = _img(left), _img(right)
+    H, W = left.shape
+    out = np.zeros((H, W), dtype=np.uint16)
+    dL = np.zeros((H, W), dtype=np.uint8)
+    dR = np.zeros((H, W), dtype=np.uint8)
+    rc = load().oracle_sgm_ex(_ptr(left, _u8p), _ptr(right, _u8p), W, H, D, P1, P2, n_paths,
+                              1 if census == "ct62" else 0, post, _ptr(out, _u16p), _ptr(dL, _u8p), _ptr(dR, _u8p))
+    if rc != 0:
+        raise ValueError(f"oracle sgm_ex failed with {rc}")
+    if debug:
+        return {"out": out, "dL": dL, "dR": dR}
+    return out
 
 
 def directions(n_paths: int):

@@ -35,6 +35,10 @@
  *    against the centre, bit k = s(I(x+i, y+j), I(x, y)) for the k-th
  *    (j, i) of j = -3..3 (outer), i = -4..4 (inner) with (0, 0) skipped:
  *    62 bits, LSB first, 0 wherever the window leaves the image.
+ *  - The post-filters the paper announces for later work (Section 6:
+ *    left-right consistency check, sub-pixel disparity, adaptive P2) are
+ *    named there without a definition; oracle_sgm_ex states the readings
+ *    taken here, each from the standard SGM formulation.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -148,12 +152,27 @@ ORACLE_EXPORT void oracle_cost(const uint32_t *Fb, const uint32_t *Fm, int W, in
 }
 
 /*
+ * Adaptive P2 (announced in Section 6; reading): for the step from q to p
+ * the jump penalty is P2(p, q) = max(P1, P2 / (1 + |I_b(p) - I_b(q)|)), integer
+ * division, I_b the base image: a large intensity step along the path makes
+ * a disparity jump cheaper, never cheaper than P1.
+ */
+static int adaptive_p2(const uint8_t *Ib, int W, int x, int y, int qx, int qy, int P1, int P2) {
+    int g = pixel(Ib, W, x, y) - pixel(Ib, W, qx, qy);
+    if (g < 0) g = -g;
+    int v = P2 / (1 + g);
+    return v > P1 ? v : P1;
+}
+
+/*
  * Eq. 3 (Section 3.2) along one direction r = (rx, ry), rx, ry in {-1, 0, 1}.
  * The predecessor of p = (x, y) is q = (x - rx, y - ry).  Pixels are visited
  * so that q is always finished before p.  L[y][x][d] (int32) receives L_r.
+ * Ib = NULL: the constant P2 of Eq. 3; otherwise P2 at each step is
+ * adaptive_p2 of the base image Ib.
  */
-ORACLE_EXPORT void oracle_aggregate(const uint8_t *MC, int W, int H, int D, int P1, int P2, int rx, int ry,
-                                    int32_t *L) {
+ORACLE_EXPORT void oracle_aggregate_ex(const uint8_t *MC, const uint8_t *Ib, int W, int H, int D, int P1, int P2,
+                                       int rx, int ry, int32_t *L) {
     int y0 = (ry >= 0) ? 0 : H - 1, y1 = (ry >= 0) ? H : -1, sy = (ry >= 0) ? 1 : -1;
     int x0 = (rx >= 0) ? 0 : W - 1, x1 = (rx >= 0) ? W : -1, sx = (rx >= 0) ? 1 : -1;
     for (int y = y0; y != y1; y += sy) {
@@ -165,6 +184,7 @@ ORACLE_EXPORT void oracle_aggregate(const uint8_t *MC, int W, int H, int D, int 
                 for (int d = 0; d < D; ++d) out[d] = mc[d];
                 continue;
             }
+            const int p2 = Ib ? adaptive_p2(Ib, W, x, y, qx, qy, P1, P2) : P2;
             const int32_t *prev = L + ((size_t)qy * W + qx) * D;
             int32_t mprev = prev[0];
             for (int k = 1; k < D; ++k)
@@ -173,11 +193,17 @@ ORACLE_EXPORT void oracle_aggregate(const uint8_t *MC, int W, int H, int D, int 
                 int32_t best = prev[d];
                 if (d - 1 >= 0 && prev[d - 1] + P1 < best) best = prev[d - 1] + P1;
                 if (d + 1 < D && prev[d + 1] + P1 < best) best = prev[d + 1] + P1;
-                if (mprev + P2 < best) best = mprev + P2;
+                if (mprev + p2 < best) best = mprev + p2;
                 out[d] = (int32_t)mc[d] + best - mprev;
             }
         }
     }
+}
+
+/* Eq. 3 with the constant P2. */
+ORACLE_EXPORT void oracle_aggregate(const uint8_t *MC, int W, int H, int D, int P1, int P2, int rx, int ry,
+                                    int32_t *L) {
+    oracle_aggregate_ex(MC, NULL, W, H, D, P1, P2, rx, ry, L);
 }
 
 /* The direction set for n_paths in {2, 4, 8}; returns the count, or 0. */
@@ -389,4 +415,169 @@ done:
     free(Lprev);
     free(Lcur);
     return result;
+}
+
+/* floor(n / d) for d > 0. */
+static long floor_div(long n, long d) {
+    long q = n / d;
+    if (n % d != 0 && n < 0) q -= 1;
+    return q;
+}
+
+/*
+ * Sub-pixel disparity (announced in Section 6; reading): the vertex of the
+ * parabola through (d-1, S(d-1)), (d, S(d)), (d+1, S(d+1)) at the winner d
+ * of Eq. 4, in 1/16 pixel: 16 d + round(16 * (S(d-1) - S(d+1)) /
+ * (2 (S(d-1) + S(d+1) - 2 S(d)))), halves rounded up, i.e.
+ * 16 d + floor((16 num + den) / (2 den)).  At d = 0 and d = D-1 the value is
+ * 16 d.  Because ties of Eq. 4 go to the lowest d, S(d-1) > S(d) and the
+ * denominator is positive; the offset lies in [-8, 8].
+ */
+ORACLE_EXPORT int oracle_subpixel(const int32_t *S, int D, int d) {
+    if (d <= 0 || d >= D - 1) return 16 * d;
+    const long num = (long)S[d - 1] - S[d + 1];
+    const long den = (long)S[d - 1] + S[d + 1] - 2L * S[d];
+    return 16 * d + (int)floor_div(16 * num + den, 2 * den);
+}
+
+/* The 3x3 median of stage 4 on 16-bit values (same border reading). */
+ORACLE_EXPORT void oracle_median3x3_u16(const uint16_t *in, int W, int H, uint16_t *out) {
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            size_t p = (size_t)y * W + x;
+            if (x == 0 || y == 0 || x == W - 1 || y == H - 1) {
+                out[p] = in[p];
+                continue;
+            }
+            int v[9], n = 0;
+            for (int j = -1; j <= 1; ++j)
+                for (int i = -1; i <= 1; ++i) v[n++] = in[(size_t)(y + j) * W + (x + i)];
+            for (int a = 1; a < 9; ++a) {
+                int t = v[a], b = a - 1;
+                while (b >= 0 && v[b] > t) {
+                    v[b + 1] = v[b];
+                    --b;
+                }
+                v[b + 1] = t;
+            }
+            out[p] = (uint16_t)v[4];
+        }
+    }
+}
+
+/*
+ * One matching pass: features (CSCT of Eq. 1, or the full Census when
+ * census_full), costs (Eq. 2), the aggregated paths (Eq. 3, adaptive P2 from
+ * the base image when ap2), S and the winner-take-all disparity (Eq. 4).
+ * S (int32 [H][W][D]) and raw (uint8 [H][W]) are outputs.  Returns 0 or -2.
+ */
+static int matching_pass(const uint8_t *base, const uint8_t *match, int W, int H, int D, int P1, int P2, int npaths,
+                         const int *rx, const int *ry, int census_full, int ap2, int32_t *S, uint8_t *raw) {
+    size_t n = (size_t)W * H;
+    uint8_t *MC = (uint8_t *)malloc(n * D);
+    int32_t *L = (int32_t *)malloc(n * D * sizeof(int32_t));
+    void *Fb = malloc(n * 8), *Fm = malloc(n * 8);
+    int rc = -2;
+    if (MC && L && Fb && Fm) {
+        if (census_full) {
+            oracle_ct62(base, W, H, (uint64_t *)Fb);
+            oracle_ct62(match, W, H, (uint64_t *)Fm);
+            oracle_cost64((const uint64_t *)Fb, (const uint64_t *)Fm, W, H, D, MC);
+        } else {
+            oracle_csct(base, W, H, (uint32_t *)Fb);
+            oracle_csct(match, W, H, (uint32_t *)Fm);
+            oracle_cost((const uint32_t *)Fb, (const uint32_t *)Fm, W, H, D, MC);
+        }
+        memset(S, 0, n * D * sizeof(int32_t));
+        for (int r = 0; r < npaths; ++r) {
+            oracle_aggregate_ex(MC, ap2 ? base : NULL, W, H, D, P1, P2, rx[r], ry[r], L);
+            for (size_t i = 0; i < n * D; ++i) S[i] += L[i];
+        }
+        oracle_wta(S, W, H, D, raw);
+        rc = 0;
+    }
+    free(MC);
+    free(L);
+    free(Fb);
+    free(Fm);
+    return rc;
+}
+
+static void mirror_rows(const uint8_t *in, int W, int H, uint8_t *out) {
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) out[(size_t)y * W + x] = in[(size_t)y * W + (W - 1 - x)];
+}
+
+#define ORACLE_POST_SUBPIXEL 1u
+#define ORACLE_POST_LR_CHECK 2u
+#define ORACLE_POST_ADAPTIVE_P2 4u
+#define ORACLE_DISP16_INVALID 0xFFFFu
+
+/*
+ * The path with the post-filters announced in Section 6, output in 1/16
+ * pixel (uint16 [H][W]):
+ *  1. the left pass (base = left, match = right) gives S and the
+ *     winner-take-all disparity d_L (Eq. 4), with adaptive P2 when asked;
+ *  2. v = oracle_subpixel(S, d_L) with SUBPIXEL, else 16 d_L;
+ *  3. out = the 3x3 median of v (the border ring copied);
+ *  4. with LR_CHECK (reading): the right image's disparity d_R is the same
+ *     pass on the mirrored pair (base = mirrored right, match = mirrored
+ *     left; adaptive P2 from its own base), mirrored back, so that right
+ *     pixel x matches left pixel x + d_R(x); a left pixel x is consistent
+ *     when x - d_L(x) >= 0 and |d_L(x) - d_R(x - d_L(x))| <= 1 (integer
+ *     winner-take-all disparities of both passes); out = 0xFFFF elsewhere.
+ * Without post-filters out = 16 * the output of oracle_sgm.  Optional debug
+ * outputs: d_L and d_R (uint8 [H][W], original coordinates).
+ * Returns 0, -1 on bad arguments, -2 if memory runs out.
+ */
+ORACLE_EXPORT int oracle_sgm_ex(const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
+                                int n_paths, int census_full, unsigned post, uint16_t *out16, uint8_t *dL_out,
+                                uint8_t *dR_out) {
+    int rx[8], ry[8];
+    if (W < 1 || H < 1 || D < 1 || D > 256 || !left || !right || !out16) return -1;
+    int npaths = oracle_directions(n_paths, rx, ry);
+    if (npaths == 0) return -1;
+    const int ap2 = (post & ORACLE_POST_ADAPTIVE_P2) != 0;
+    size_t n = (size_t)W * H;
+    int32_t *S = (int32_t *)malloc(n * D * sizeof(int32_t));
+    uint8_t *dL = (uint8_t *)malloc(n), *dRm = (uint8_t *)malloc(n);
+    uint8_t *mb = (uint8_t *)malloc(n), *mm = (uint8_t *)malloc(n);
+    uint16_t *v = (uint16_t *)malloc(n * sizeof(uint16_t));
+    int rc = -2;
+    if (!S || !dL || !dRm || !mb || !mm || !v) goto done;
+    if ((rc = matching_pass(left, right, W, H, D, P1, P2, npaths, rx, ry, census_full, ap2, S, dL)) != 0) goto done;
+    for (size_t p = 0; p < n; ++p)
+        v[p] = (uint16_t)((post & ORACLE_POST_SUBPIXEL) ? oracle_subpixel(S + p * D, D, dL[p]) : 16 * dL[p]);
+    if (W < 3 || H < 3)
+        memcpy(out16, v, n * sizeof(uint16_t));
+    else
+        oracle_median3x3_u16(v, W, H, out16);
+    if (post & ORACLE_POST_LR_CHECK) {
+        mirror_rows(right, W, H, mb);
+        mirror_rows(left, W, H, mm);
+        if ((rc = matching_pass(mb, mm, W, H, D, P1, P2, npaths, rx, ry, census_full, ap2, S, dRm)) != 0) goto done;
+        for (int y = 0; y < H; ++y) {
+            for (int x = 0; x < W; ++x) {
+                const int d = dL[(size_t)y * W + x], xr = x - d;
+                int ok = xr >= 0;
+                if (ok) {
+                    const int dr = dRm[(size_t)y * W + (W - 1 - xr)];
+                    ok = (d - dr <= 1) && (dr - d <= 1);
+                }
+                if (!ok) out16[(size_t)y * W + x] = (uint16_t)ORACLE_DISP16_INVALID;
+            }
+        }
+        if (dR_out) mirror_rows(dRm, W, H, dR_out);
+    } else if (dR_out) {
+        memset(dR_out, 0, n);
+    }
+    if (dL_out) memcpy(dL_out, dL, n);
+done:
+    free(S);
+    free(dL);
+    free(dRm);
+    free(mb);
+    free(mm);
+    free(v);
+    return rc;
 }
