@@ -128,6 +128,39 @@ SGM_API int sgm_set_stream(sgm_ctx *ctx, void *cuda_stream);
 SGM_API int sgm_compute(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
                 int n_paths, uint8_t *disp_out);
 
+/* Post-filter flags of sgm_compute_ex (the post-filters Section 6 of the
+ * paper announces; the paper gives no definition, these are the readings). */
+#define SGM_POST_SUBPIXEL 1u    /* parabola vertex through S(d-1), S(d), S(d+1) at the winner d */
+#define SGM_POST_LR_CHECK 2u    /* left-right consistency check */
+#define SGM_POST_ADAPTIVE_P2 4u /* P2 per step from the base image's intensity step */
+#define SGM_DISP16_INVALID 0xFFFFu
+
+/*
+ * sgm_compute with post-filters; `post` is 0 or a combination of the
+ * SGM_POST_* flags; disp16_out is uint16 [H][W] in 1/16 pixel.  Pointers as
+ * sgm_compute (host or device); blocking.
+ *   - ADAPTIVE_P2: the step q -> p of every path uses
+ *     P2(p, q) = max(P1, P2 / (1 + |I(p) - I(q)|)) (integer division, I the
+ *     base image) in place of P2 in Eq. 3; needs max(P1, P2) <= 255 - 31
+ *     (255 - 62 with SGM_FLAG_CENSUS_FULL).
+ *   - SUBPIXEL: at the winner d of Eq. 4 with 0 < d < D-1 the value is
+ *     16 d + floor((16 (S(d-1) - S(d+1)) + den) / (2 den)),
+ *     den = S(d-1) + S(d+1) - 2 S(d) (the vertex offset rounded to 1/16,
+ *     halves up; within [-8, 8]); else 16 d.
+ *   - the 3x3 median (Section 2) then runs on these values (border ring
+ *     copied);
+ *   - LR_CHECK: the right image's disparity d_R is the same matching pass on
+ *     the mirrored pair (base = mirrored right, match = mirrored left), read
+ *     back in original columns; left pixel x with winner d is kept when
+ *     x - d >= 0 and |d - d_R(x - d)| <= 1, else the output is
+ *     SGM_DISP16_INVALID.
+ * With post = 0 the output is 16 x that of sgm_compute.  Stage timing does
+ * not cover this entry point.  Errors as sgm_compute (SGM_EINVAL also for
+ * unknown flags and the adaptive P2 bound).
+ */
+SGM_API int sgm_compute_ex(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1,
+                           int P2, int n_paths, unsigned post, uint16_t *disp16_out);
+
 /*
  * Non-blocking form for device pointers only: enqueues the whole path on the
  * context's stream and returns at once.  `left`, `right` and `disp_out` must

@@ -30,6 +30,7 @@ inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 // Offsets of one pair's buffers inside a work arena.
 struct Layout {
     size_t Fb, Fm, rec, raw, state, in_left, in_right, out, total;
+    size_t sub, rawR, ml, mr;  // post-filters (sgm_compute_ex) only
     int RB;    // bytes per pixel record (sgm_internal.h): MC, S (room for u16 words), stored L_r fields
     int n_lx;  // stored-L_r fields per record
 };
@@ -41,7 +42,7 @@ struct Layout {
 // state.
 int lx_fields(int n_paths, bool batched) { return n_paths == 2 ? 0 : (batched ? 1 : (n_paths == 8 ? 4 : 2)); }
 
-Layout layout_for(int W, int H, int D_int, int n_paths, bool batched = false, bool ct62 = false) {
+Layout layout_for(int W, int H, int D_int, int n_paths, bool batched = false, bool ct62 = false, bool post = false) {
     const size_t wh = static_cast<size_t>(W) * H;
     const size_t D = static_cast<size_t>(D_int);
     const size_t fbytes = ct62 ? 8 : 4;
@@ -66,7 +67,17 @@ Layout layout_for(int W, int H, int D_int, int n_paths, bool batched = false, bo
     l.in_right = o;
     o = align_up(o + wh);
     l.out = o;
-    o = align_up(o + wh);
+    o = align_up(o + (post ? 2 : 1) * wh);  // u16 output with post-filters
+    if (post) {
+        l.sub = o;  // per pixel S(d-1) - S(d) | (S(d+1) - S(d)) << 16 at the winner
+        o = align_up(o + 4 * wh);
+        l.rawR = o;  // the right pass's disparity, mirrored columns
+        o = align_up(o + wh);
+        l.ml = o;  // mirrored left and right images
+        o = align_up(o + wh);
+        l.mr = o;
+        o = align_up(o + wh);
+    }
     l.total = o;
     return l;
 }
@@ -74,13 +85,24 @@ Layout layout_for(int W, int H, int D_int, int n_paths, bool batched = false, bo
 struct Problem {
     int W, H, D, P1, P2, n_paths;
     int ct62 = 0;  // features: 0 = CSCT (Eq. 1), 1 = the full 9x7 Census (SGM_FLAG_CENSUS_FULL)
+    int post = 0;  // 0: the plain path (u8 output); else kPostOut16 | the SGM_POST_* flags of sgm_compute_ex
 };
+
+// Set on every sgm_compute_ex problem: the post form with uint16 output, even
+// without post-filters.
+constexpr int kPostOut16 = 0x100;
 
 // Largest matching cost: 31 CSCT bits or 62 full-Census bits.
 inline int mc_max(const Problem& p) { return p.ct62 ? 62 : 31; }
 
+// Largest jump penalty of a step: P2, or max(P1, P2) with adaptive P2.
+inline int p2_max(const Problem& p) { return (p.post & SGM_POST_ADAPTIVE_P2) ? std::max(p.P1, p.P2) : p.P2; }
+
+// S kept as bytes between the sweeps (sum_fits_u8 for this problem).
+inline bool s8_for(const Problem& p) { return sum_fits_u8(p.n_paths, p2_max(p), mc_max(p)); }
+
 Layout layout_for(const Problem& p, bool batched = false) {
-    return layout_for(p.W, p.H, p.D, p.n_paths, batched, p.ct62 != 0);
+    return layout_for(p.W, p.H, p.D, p.n_paths, batched, p.ct62 != 0, p.post != 0);
 }
 
 bool valid_problem(const Problem& p, std::string* why) {
@@ -96,6 +118,11 @@ bool valid_problem(const Problem& p, std::string* why) {
                  255 - 62, p.P2);
     } else if (p.n_paths != 2 && p.n_paths != 4 && p.n_paths != 8) {
         snprintf(buf, sizeof buf, "n_paths must be 2, 4 or 8 (got %d)", p.n_paths);
+    } else if (p.post & ~(kPostOut16 | SGM_POST_SUBPIXEL | SGM_POST_LR_CHECK | SGM_POST_ADAPTIVE_P2)) {
+        snprintf(buf, sizeof buf, "unknown post-filter flags %#x", static_cast<unsigned>(p.post & ~kPostOut16));
+    } else if ((p.post & SGM_POST_ADAPTIVE_P2) && p2_max(p) > 255 - mc_max(p)) {
+        snprintf(buf, sizeof buf, "with adaptive P2, max(P1, P2) must not exceed %d (got %d)", 255 - mc_max(p),
+                 p2_max(p));
     } else if (static_cast<double>(p.W) * p.H * record_bytes(p.D, false, lx_fields(p.n_paths, false)) >= 4294967296.0) {
         snprintf(buf, sizeof buf, "W*H*D too large (%d x %d x %d): the per-pixel records must stay below 4 GiB", p.W,
                  p.H, p.D);
@@ -110,8 +137,9 @@ struct GraphKey {
     Problem p;
     const void *left, *right, *out, *arena;
     bool operator<(const GraphKey& o) const {
-        return std::tie(p.W, p.H, p.D, p.P1, p.P2, p.n_paths, p.ct62, left, right, out, arena) <
-               std::tie(o.p.W, o.p.H, o.p.D, o.p.P1, o.p.P2, o.p.n_paths, o.p.ct62, o.left, o.right, o.out, o.arena);
+        return std::tie(p.W, p.H, p.D, p.P1, p.P2, p.n_paths, p.ct62, p.post, left, right, out, arena) <
+               std::tie(o.p.W, o.p.H, o.p.D, o.p.P1, o.p.P2, o.p.n_paths, o.p.ct62, o.p.post, o.left, o.right, o.out,
+                        o.arena);
     }
 };
 
@@ -250,28 +278,28 @@ static bool is_device_ptr(const void* p) {
 // Kernels per path: census, cost, the first sweep stage (horizontal pair and
 // vertical-type first halves), the second halves of each vertical-type pair
 // (sweep_diag+, sweep_diag-, sweep_v), median; with 2 paths: census, cost,
-// sweep_h, sweep_v, median.  Each kernel is one timed stage.
-static int launches_per_path(const Problem& p) { return p.n_paths == 8 ? 7 : 5; }
+// sweep_h, sweep_v, median.  Each kernel is one timed stage.  With
+// post-filters: one matching pass (census, cost, sweeps) for the left image,
+// with the LR check a mirror kernel and a second pass, then the post kernel.
+static int launches_per_match(const Problem& p) { return p.n_paths == 8 ? 6 : 4; }
+static int launches_per_path(const Problem& p) {
+    if (!p.post) return launches_per_match(p) + 1;
+    return launches_per_match(p) * ((p.post & SGM_POST_LR_CHECK) ? 2 : 1) + ((p.post & SGM_POST_LR_CHECK) ? 1 : 0) + 1;
+}
 static int stages_per_path(const Problem& p) { return launches_per_path(p); }
 
-// Bytes of one [H][W][D] u8 scratch cube of path costs.
-// Enqueue the whole path (Section 2, stages 2-4) for one pair whose inputs
-// and output are device pointers.  Returns a cudaError_t.
-static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const uint8_t* left,
-                                const uint8_t* right, uint8_t* disp, uint16_t* Sdbg, cudaStream_t s, bool timed) {
-    const Layout l = layout_for(p);
+// One matching pass (Section 2, stages 2-3 and Eq. 4) of the pair
+// (base, match): census, cost and the sweeps; the winner-take-all disparity
+// goes to raw.  In the post form the sweeps take their jump penalties from
+// base's intensities and, with sub, write the winner's neighbour sums.
+template <class Mark>
+static cudaError_t enqueue_match(const Problem& p, const Layout& l, uint8_t* arena, const uint8_t* base,
+                                 const uint8_t* match, uint8_t* raw, uint32_t* sub, uint16_t* Sdbg, cudaStream_t s,
+                                 Mark&& mark) {
     void* Fb = arena + l.Fb;
     void* Fm = arena + l.Fm;
     cudaError_t e;
-    int stage = 0;
-    // with stage timing, event k is recorded before kernel k and after the last
-    auto mark = [&]() -> cudaError_t {
-        if (!timed) return cudaSuccess;
-        // External: inside a stream capture this becomes an event-record node of the graph
-        return cudaEventRecordWithFlags(ctx->stage_ev[stage++], s, cudaEventRecordExternal);
-    };
-    if ((e = mark()) != cudaSuccess) return e;
-    if ((e = launch_census(left, right, Fb, Fm, p.W, p.H, p.ct62 != 0, s)) != cudaSuccess) return e;
+    if ((e = launch_census(base, match, Fb, Fm, p.W, p.H, p.ct62 != 0, s)) != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;
     if ((e = launch_cost(Fb, Fm, arena + l.rec, l.RB, p.W, p.H, p.D, p.ct62 != 0, s)) != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;
@@ -279,7 +307,7 @@ static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, 
     a.rec = arena + l.rec;
     a.RB = l.RB;
     a.lx_off = 3 * p.D;  // stored-L_r field k at 3D + kD: the horizontal pair takes field 0
-    a.raw = arena + l.raw;
+    a.raw = raw;
     a.Sdbg = Sdbg;
     a.W = p.W;
     a.H = p.H;
@@ -287,10 +315,14 @@ static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, 
     a.P1x2 = static_cast<uint32_t>(p.P1) * 0x10001u;
     a.P2x2 = static_cast<uint32_t>(p.P2) * 0x10001u;
     a.pair = p.n_paths >= 4;
-    a.s8 = sum_fits_u8(p.n_paths, p.P2, mc_max(p));
+    a.s8 = s8_for(p);
     a.rx = 0;
     a.wta = 0;
     a.phase = 0;
+    a.post = p.post ? 1 : 0;
+    a.img = base;
+    a.ap2 = (p.post & SGM_POST_ADAPTIVE_P2) ? 1 : 0;
+    a.sub = sub;
     uint32_t* states = reinterpret_cast<uint32_t*>(arena + l.state);
     const size_t sw = sweep_state_words(p.W, p.D);
     // vertical-type pairs: (rx, wta) in the order their second halves run
@@ -349,8 +381,48 @@ static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, 
             if ((e = mark()) != cudaSuccess) return e;
         }
     }
-    if ((e = launch_median(a.raw, disp, p.W, p.H, s)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+// Enqueue the whole path (Section 2, stages 2-4) for one pair whose inputs
+// and output are device pointers: disp is uint8 [H][W], or uint16 [H][W] in
+// 1/16 pixel with post-filters (p.post).  Returns a cudaError_t.
+static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const uint8_t* left,
+                                const uint8_t* right, uint8_t* disp, uint16_t* Sdbg, cudaStream_t s, bool timed) {
+    const Layout l = layout_for(p);
+    cudaError_t e;
+    int stage = 0;
+    // with stage timing, event k is recorded before kernel k and after the last
+    auto mark = [&]() -> cudaError_t {
+        if (!timed) return cudaSuccess;
+        // External: inside a stream capture this becomes an event-record node of the graph
+        return cudaEventRecordWithFlags(ctx->stage_ev[stage++], s, cudaEventRecordExternal);
+    };
     if ((e = mark()) != cudaSuccess) return e;
+    if (!p.post) {
+        if ((e = enqueue_match(p, l, arena, left, right, arena + l.raw, nullptr, Sdbg, s, mark)) != cudaSuccess)
+            return e;
+        if ((e = launch_median(arena + l.raw, disp, p.W, p.H, s)) != cudaSuccess) return e;
+        if ((e = mark()) != cudaSuccess) return e;
+    } else {
+        uint32_t* sub = (p.post & SGM_POST_SUBPIXEL) ? reinterpret_cast<uint32_t*>(arena + l.sub) : nullptr;
+        if ((e = enqueue_match(p, l, arena, left, right, arena + l.raw, sub, nullptr, s, mark)) != cudaSuccess)
+            return e;
+        const uint8_t* rawR = nullptr;
+        if (p.post & SGM_POST_LR_CHECK) {
+            // the right image's disparity: the same pass on the mirrored pair
+            if ((e = launch_mirror(left, right, arena + l.ml, arena + l.mr, p.W, p.H, s)) != cudaSuccess) return e;
+            if ((e = mark()) != cudaSuccess) return e;
+            if ((e = enqueue_match(p, l, arena, arena + l.mr, arena + l.ml, arena + l.rawR, nullptr, nullptr, s,
+                                   mark)) != cudaSuccess)
+                return e;
+            rawR = arena + l.rawR;
+        }
+        if ((e = launch_post(arena + l.raw, sub, rawR, reinterpret_cast<uint16_t*>(disp), p.W, p.H, p.D, s)) !=
+            cudaSuccess)
+            return e;
+        if ((e = mark()) != cudaSuccess) return e;
+    }
     ctx->launches += launches_per_path(p);
     return cudaSuccess;
 }
@@ -368,7 +440,9 @@ static int enqueue_graph(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const u
         cudaGraph_t g = nullptr;
         CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
         const uint64_t before = ctx->launches.load();
-        cudaError_t e = enqueue_path(ctx, p, arena, left, right, disp, nullptr, ctx->capture_stream, ctx->stage_timing);
+        // paths with post-filters are never stage-timed (sgm_stage_times names the plain path's kernels)
+        cudaError_t e = enqueue_path(ctx, p, arena, left, right, disp, nullptr, ctx->capture_stream,
+                                     ctx->stage_timing && !p.post);
         ctx->launches = before;  // captured, not launched
         cudaError_t e2 = cudaStreamEndCapture(ctx->capture_stream, &g);
         if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -384,8 +458,8 @@ static int enqueue_graph(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const u
     }
     CUDA_TRY(ctx, cudaGraphLaunch(it->second, s));
     ctx->launches += launches_per_path(p);
-    ctx->last_stages = ctx->stage_timing ? stages_per_path(p) : 0;
-    ctx->last_n_paths = ctx->stage_timing ? p.n_paths : 0;
+    ctx->last_stages = (ctx->stage_timing && !p.post) ? stages_per_path(p) : 0;
+    ctx->last_n_paths = (ctx->stage_timing && !p.post) ? p.n_paths : 0;
     return SGM_OK;
 }
 
@@ -413,7 +487,7 @@ static int enqueue_pair(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const ui
     } else {
         CUDA_TRY(ctx, enqueue_path(ctx, p, arena, dl, dr, dout, nullptr, s, false));
     }
-    if (out_host) CUDA_TRY(ctx, cudaMemcpyAsync(disp, dout, wh, cudaMemcpyDeviceToHost, s));
+    if (out_host) CUDA_TRY(ctx, cudaMemcpyAsync(disp, dout, (p.post ? 2 : 1) * wh, cudaMemcpyDeviceToHost, s));
     return SGM_OK;
 }
 
@@ -447,7 +521,7 @@ struct BatchItem {
 
 // Items launched together share D, the path count, the sum storage and the Census type.
 static std::tuple<int, int, bool, int> batch_key(const BatchItem& it) {
-    return std::make_tuple(it.p.D, it.p.n_paths, sum_fits_u8(it.p.n_paths, it.p.P2, mc_max(it.p)), it.p.ct62);
+    return std::make_tuple(it.p.D, it.p.n_paths, s8_for(it.p), it.p.ct62);
 }
 
 static int launches_per_group(int n_paths) { return 4 + (n_paths == 8 ? 3 : 1); }
@@ -500,7 +574,7 @@ static int enqueue_wave(sgm_ctx* ctx, std::vector<BatchItem>& items, size_t b, s
             a.P1x2 = static_cast<uint32_t>(it.p.P1) * 0x10001u;
             a.P2x2 = static_cast<uint32_t>(it.p.P2) * 0x10001u;
             a.pair = it.p.n_paths >= 4;
-            a.s8 = sum_fits_u8(it.p.n_paths, it.p.P2, mc_max(it.p));
+            a.s8 = s8_for(it.p);
             st.job[k] = a;
             uint8_t* dst = is_device_ptr(it.out) ? it.out : base + l.out;
             dt.job[k] = MedianJob{base + l.raw, dst, it.p.W, it.p.H};
@@ -935,6 +1009,21 @@ int sgm_compute(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, 
     return SGM_OK;
 }
 
+int sgm_compute_ex(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H, int D, int P1, int P2,
+                   int n_paths, unsigned post, uint16_t* disp16_out) {
+    Problem p = make_problem(ctx, W, H, D, P1, P2, n_paths);
+    p.post = (post & ~static_cast<unsigned>(kPostOut16)) == post ? static_cast<int>(post) | kPostOut16 : -1;
+    int rc = check_args(ctx, p, left, right, disp16_out);
+    if (rc != SGM_OK) return rc;
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, layout_for(p).total, true);
+    if (rc != SGM_OK) return rc;
+    rc = enqueue_pair(ctx, p, ctx->arena, left, right, reinterpret_cast<uint8_t*>(disp16_out), ctx->stream, true);
+    if (rc != SGM_OK) return rc;
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return SGM_OK;
+}
+
 int sgm_compute_async(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H, int D, int P1, int P2,
                       int n_paths, uint8_t* disp_out) {
     const Problem p = make_problem(ctx, W, H, D, P1, P2, n_paths);
@@ -1161,7 +1250,7 @@ cudaError_t enqueue_path_static(const Problem& p, uint8_t* arena, const uint8_t*
     a.P1x2 = static_cast<uint32_t>(p.P1) * 0x10001u;
     a.P2x2 = static_cast<uint32_t>(p.P2) * 0x10001u;
     a.pair = p.n_paths >= 4;
-    a.s8 = sum_fits_u8(p.n_paths, p.P2, mc_max(p));
+    a.s8 = s8_for(p);
     if ((e = launch_sweep_h(a, s)) != cudaSuccess) return e;
     if (!a.pair) {
         a.wta = 1;

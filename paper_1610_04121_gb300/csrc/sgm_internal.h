@@ -29,6 +29,16 @@ struct SweepArgs {
                           // (saves the path state), 2 = second half (restores it)
     uint32_t* state;      // path states between phases 1 and 2 (sweep_state_words)
     int s8;               // S kept as paired bytes instead of u16x2 words
+    // Post-filter form of the sweeps (sgm_compute_ex): post = 1 selects it.
+    // Every step q -> p then takes its jump penalty from a per-block table
+    // indexed by |I(p) - I(q)| of the base image img (max(P1, P2 / (1 + g))
+    // with ap2, else P2 throughout), and a winner-take-all sweep with
+    // sub != nullptr also writes, per pixel, S(d-1) - S(d) | (S(d+1) - S(d)) << 16
+    // at the winner d (each half 0 when that neighbour is outside [0, D)).
+    int post;
+    const uint8_t* img;   // base image [H][W] (post form)
+    int ap2;              // adaptive P2: P2(g) = max(P1, P2 / (1 + g)); else P2
+    uint32_t* sub;        // [H][W] (post form, winner-take-all sweeps; optional)
 };
 
 // Every sum S held between sweeps fits a byte: with 2 paths S = L_LR <= 31 + P2
@@ -104,6 +114,16 @@ inline size_t sweep_state_words(int W, int D) {
     return (D % 64 == 0) ? static_cast<size_t>(W) * 64 * (D / 64 + 3) : static_cast<size_t>(W) * 32 * (D / 32 + 3);
 }
 cudaError_t launch_median(const uint8_t* raw, uint8_t* disp, int W, int H, cudaStream_t stream);
+// Post-filters (sgm_compute_ex).  Mirror: mr[y][x] = right[y][W-1-x],
+// ml[y][x] = left[y][W-1-x].
+cudaError_t launch_mirror(const uint8_t* left, const uint8_t* right, uint8_t* ml, uint8_t* mr, int W, int H,
+                          cudaStream_t stream);
+// out16 = 3x3 median of v, v = 16 d + the sub-pixel offset from sub (when
+// sub != nullptr) with d = rawL; then, when rawRm != nullptr (the right
+// pass's disparity in mirrored columns), 0xFFFF where the left-right check
+// fails.
+cudaError_t launch_post(const uint8_t* rawL, const uint32_t* sub, const uint8_t* rawRm, uint16_t* out16, int W,
+                        int H, int D, cudaStream_t stream);
 // Batched forms; every job of a cost or sweep table has the same D (and, for
 // sweeps, the same pair / rx / phase / wta / s8 settings).  `start` is filled in.
 cudaError_t launch_census_batch(JobTable<CensusJob>& t, bool ct62, cudaStream_t stream);

@@ -435,6 +435,100 @@ cudaError_t launch_median(const uint8_t* raw, uint8_t* disp, int W, int H, cudaS
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Post-filters (announced in Section 6; the readings are those of
+// sgm_compute_ex in sgm.h).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) mirror_kernel(const uint8_t* __restrict__ left,
+                                                     const uint8_t* __restrict__ right, uint8_t* __restrict__ ml,
+                                                     uint8_t* __restrict__ mr, int W, int H) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= W || y >= H) return;
+    const size_t src = static_cast<size_t>(y) * W + (W - 1 - x), dst = static_cast<size_t>(y) * W + x;
+    ml[dst] = __ldg(left + src);
+    mr[dst] = __ldg(right + src);
+}
+
+cudaError_t launch_mirror(const uint8_t* left, const uint8_t* right, uint8_t* ml, uint8_t* mr, int W, int H,
+                          cudaStream_t stream) {
+    dim3 grid((W + 255) / 256, H);
+    mirror_kernel<<<grid, 256, 0, stream>>>(left, right, ml, mr, W, H);
+    return cudaGetLastError();
+}
+
+// The value in 1/16 pixel at one pixel: 16 d, plus the rounded vertex offset
+// of the parabola through S(d-1), S(d), S(d+1) (alpha = S(d-1) - S(d) > 0,
+// gamma = S(d+1) - S(d) >= 0): floor((16 (alpha - gamma) + (alpha + gamma)) /
+// (2 (alpha + gamma))), none at d = 0 or D-1.
+__device__ __forceinline__ int subpixel_value(int d, uint32_t ag, int D) {
+    if (d <= 0 || d >= D - 1) return 16 * d;
+    const int al = static_cast<int>(ag & 0xffffu), ga = static_cast<int>(ag >> 16);
+    const int n = 16 * (al - ga) + (al + ga), den = 2 * (al + ga);
+    int q = n / den;
+    if (n % den != 0 && n < 0) --q;  // floor
+    return 16 * d + q;
+}
+
+constexpr int kPostW = 32, kPostH = 8;
+
+// v = the sub-pixel (or 16 d) value of each pixel of a 34 x 10 tile in shared
+// memory, then the 3x3 median (border ring copied), then the left-right check.
+__global__ void __launch_bounds__(kPostW* kPostH) post_kernel(const uint8_t* __restrict__ rawL,
+                                                              const uint32_t* __restrict__ sub,
+                                                              const uint8_t* __restrict__ rawRm,
+                                                              uint16_t* __restrict__ out16, int W, int H, int D) {
+    __shared__ int v[kPostH + 2][kPostW + 2];
+    const int x0 = blockIdx.x * kPostW, y0 = blockIdx.y * kPostH;
+    const int t = threadIdx.y * kPostW + threadIdx.x;
+    for (int c = t; c < (kPostH + 2) * (kPostW + 2); c += kPostW * kPostH) {
+        const int cy = c / (kPostW + 2), cx = c - cy * (kPostW + 2);
+        const int gx = x0 - 1 + cx, gy = y0 - 1 + cy;
+        int val = 0;
+        if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+            const size_t p = static_cast<size_t>(gy) * W + gx;
+            const int d = rawL[p];
+            val = sub ? subpixel_value(d, sub[p], D) : 16 * d;
+        }
+        v[cy][cx] = val;
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= W || y >= H) return;
+    const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
+    int out;
+    if (x == 0 || y == 0 || x == W - 1 || y == H - 1) {
+        out = v[ty][tx];
+    } else {
+        // median of 9: sort each row, then the median of (largest row
+        // minimum, median of the row medians, smallest row maximum)
+        int a0 = v[ty - 1][tx - 1], a1 = v[ty - 1][tx], a2 = v[ty - 1][tx + 1];
+        int b0 = v[ty][tx - 1], b1 = v[ty][tx], b2 = v[ty][tx + 1];
+        int c0 = v[ty + 1][tx - 1], c1 = v[ty + 1][tx], c2 = v[ty + 1][tx + 1];
+        sort3(a0, a1, a2);
+        sort3(b0, b1, b2);
+        sort3(c0, c1, c2);
+        out = med3(max(max(a0, b0), c0), med3(a1, b1, c1), min(min(a2, b2), c2));
+    }
+    const size_t p = static_cast<size_t>(y) * W + x;
+    if (rawRm) {
+        const int d = rawL[p], xr = x - d;
+        bool ok = xr >= 0;
+        if (ok) {
+            const int dr = rawRm[static_cast<size_t>(y) * W + (W - 1 - xr)];
+            ok = d - dr <= 1 && dr - d <= 1;
+        }
+        if (!ok) out = 0xffff;
+    }
+    out16[p] = static_cast<uint16_t>(out);
+}
+
+cudaError_t launch_post(const uint8_t* rawL, const uint32_t* sub, const uint8_t* rawRm, uint16_t* out16, int W,
+                        int H, int D, cudaStream_t stream) {
+    dim3 grid((W + kPostW - 1) / kPostW, (H + kPostH - 1) / kPostH), block(kPostW, kPostH);
+    post_kernel<<<grid, block, 0, stream>>>(rawL, sub, rawRm, out16, W, H, D);
+    return cudaGetLastError();
+}
+
 bool supported_D(int D) { return D >= 32 && D <= 256 && D % 32 == 0; }
 
 }  // namespace sgm

@@ -160,16 +160,19 @@ __device__ __forceinline__ LaneBases lane_bases(const SweepArgs& a, int pl) {
     return LaneBases{a.rec + 2 * K * pl, a.rec + D + 4 * K * pl, a.rec + a.lx_off + 2 * K * pl};
 }
 
-// One step's inputs for one lane, loaded from the record at byte offset `off`.
-template <int D, int MODE, bool S8>
+// One step's inputs for one lane, loaded from the record at byte offset `off`;
+// in the post form also the base image at the step's pixel and at its
+// predecessor on the path (low and high half of im).
+template <int D, int MODE, bool S8, int POST = 0>
 struct StepIn {
     static constexpr int K = PathShape<D>::K;
     using M = ModeIO<MODE>;
     static constexpr int PW = (K + 1) / 2;
-    static constexpr int REGS = PW + (M::IN_LO ? PW : 0) + (M::IN_S ? (S8 ? PW : K) : 0);
+    static constexpr int REGS = PW + (M::IN_LO ? PW : 0) + (M::IN_S ? (S8 ? PW : K) : 0) + (POST ? 1 : 0);
     Regs<PW> mc;
     Regs<M::IN_LO ? PW : 0> lo;
     Regs<M::IN_S ? (S8 ? PW : K) : 0> s;
+    Regs<POST ? 1 : 0> im;
 
     __device__ __forceinline__ void load(const LaneBases& lb, uint32_t off) {
         const uint8_t* p = at(lb.pairs, off);
@@ -182,7 +185,34 @@ struct StepIn {
                 ldg_words<K>(reinterpret_cast<const uint32_t*>(at(lb.words, off)), s.r);
         }
     }
+    __device__ __forceinline__ void load_img(const uint8_t* img, int pix, int ppix) {
+        if constexpr (POST) im.r[0] = static_cast<uint32_t>(__ldg(img + pix)) | static_cast<uint32_t>(__ldg(img + ppix)) << 16;
+    }
 };
+
+// Jump penalties of the post form, P2x2 by |I(p) - I(q)| (see SweepArgs).
+__device__ __forceinline__ uint32_t* post_p2_table() {
+    __shared__ uint32_t tab[256];
+    return tab;
+}
+
+// Fills the table; every thread of the block calls it before any early exit.
+template <int POST>
+__device__ __forceinline__ void post_init(const SweepArgs& a) {
+    if constexpr (POST != 0) {
+        uint32_t* tab = post_p2_table();
+        const int P1 = static_cast<int>(a.P1x2 & 0xffffu), P2 = static_cast<int>(a.P2x2 & 0xffffu);
+        for (int g = threadIdx.x; g < 256; g += blockDim.x) {
+            int v = P2;
+            if (a.ap2) {
+                v = P2 / (1 + g);
+                v = v > P1 ? v : P1;
+            }
+            tab[g] = static_cast<uint32_t>(v) * 0x10001u;
+        }
+        __syncthreads();
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Walk geometry.  A cursor names the pixel of one step; `advance` moves it to
@@ -199,6 +229,8 @@ struct RowGeo {
     };
     __device__ __forceinline__ Cursor start() const { return Cursor{rowbase + x0}; }
     __device__ __forceinline__ void advance(Cursor& c) const { c.pix += dx; }
+    // the pixel before the start on the path (unclamped; may lie outside)
+    __device__ __forceinline__ int before_start() const { return rowbase + x0 - dx; }
 };
 
 // Pixels of a column (RX = 0) or wrapped-diagonal (RX = +1/-1) walk:
@@ -223,6 +255,12 @@ struct ColGeo {
     __device__ __forceinline__ Cursor start() const {
         const int x = x_at(y0);
         return Cursor{y0 * W + x, x, y0};
+    }
+    // the pixel before the start on the path (its row may lie outside)
+    __device__ __forceinline__ int before_start() const {
+        const int y = y0 - dy;
+        if (y < 0 || y >= H) return y0 * W + x_at(y0);  // a path start: any pixel will do
+        return y * W + x_at(y);
     }
     __device__ __forceinline__ void advance(Cursor& k) const {
         if constexpr (RX == 0) {
@@ -294,12 +332,12 @@ struct LaneRole {
 // count; n_other: the step count of the warp's other path (G = 16), else
 // n_own.  DBG: a winner-take-all walk also writes S in natural order to
 // a.Sdbg.
-template <int D, int MODE, bool S8, class Geo, bool DBG = false>
+template <int D, int MODE, bool S8, class Geo, bool DBG = false, int POST = 0>
 __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch, const Geo& g, int n_own,
                                      int n_other, const SweepArgs& a, int pl) {
     constexpr int G = PathShape<D>::G, K = PathShape<D>::K;
     using M = ModeIO<MODE>;
-    using In = StepIn<D, MODE, S8>;
+    using In = StepIn<D, MODE, S8, POST>;
     constexpr int PF = prefetch_steps(In::REGS);
     const int n_min = min(n_own, n_other), n_max = max(n_own, n_other);
     const uint32_t RB = static_cast<uint32_t>(a.RB);
@@ -315,14 +353,25 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
     const uint32_t off0 = static_cast<uint32_t>(pix0) * RB;
     const uint32_t doff = Geo::kLinear ? static_cast<uint32_t>(g.step_pix()) * RB : 0u;
     uint32_t off_ld = static_cast<uint32_t>(ld.pix) * RB, off_cur = off_ld;
+    // post form: the pixel of the step being prefetched and of its predecessor
+    int pix_ld = ld.pix;
+    int pprev = min(max(g.before_start(), 0), a.W * a.H - 1);
     auto prefetch = [&](In& b, int i, bool clamp) {
+        const bool past = clamp && i >= n_own;
+        int pix;
         if constexpr (Geo::kLinear) {
-            b.load(lb, (clamp && i >= n_own) ? off0 : off_ld);
+            b.load(lb, past ? off0 : off_ld);
             off_ld += doff;
+            pix = pix_ld;
+            pix_ld += g.step_pix();
         } else {
-            const int pix = (clamp && i >= n_own) ? pix0 : ld.pix;
-            b.load(lb, static_cast<uint32_t>(pix) * RB);
+            pix = ld.pix;
+            b.load(lb, static_cast<uint32_t>(past ? pix0 : pix) * RB);
             g.advance(ld);
+        }
+        if constexpr (POST != 0) {
+            b.load_img(a.img, past ? pix0 : pix, past ? pix0 : pprev);
+            pprev = pix;
         }
     };
 #pragma unroll
@@ -340,7 +389,13 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
         }
         uint32_t mc[K], L[K];
         unpack_regs<K>(in.mc.r, mc);
-        ch.step(mc, a.P1x2, a.P2x2, L);
+        uint32_t p2x2 = a.P2x2;
+        if constexpr (POST != 0) {  // the jump penalty of this step from the base image
+            const uint32_t v = in.im.r[0];
+            const int gdiff = abs(static_cast<int>(v & 0xffffu) - static_cast<int>(v >> 16));
+            p2x2 = post_p2_table()[gdiff];
+        }
+        ch.step(mc, a.P1x2, p2x2, L);
         const uint32_t off = Geo::kLinear ? off_cur : static_cast<uint32_t>(cur.pix) * RB;
         if constexpr (M::OUT_LX) {
             if (active) st_pairs<K>(at(lb.lx, off), pack_pairs<K>(L));
@@ -383,6 +438,26 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
             if constexpr (M::WTA) {
                 const uint32_t key = ch.path_min(wta_key<K, D, KEY16>(s, dconst));
                 if (active && pl == 0) a.raw[cur.pix] = wta_disparity<D, KEY16>(key);
+                if constexpr (POST != 0) {
+                    if (a.sub) {  // uniform: S at the winner's neighbours for the sub-pixel step
+                        const int d = wta_disparity<D, KEY16>(key);
+                        const uint32_t Sd = KEY16 ? key / static_cast<uint32_t>(D) : key >> 8;
+                        uint32_t v = 0;  // S(d-1) in the low half, S(d+1) in the high half
+#pragma unroll
+                        for (int j = 0; j < K; ++j) {
+                            const int i = pl * K + j;
+                            const uint32_t lo = s[j] & 0xffffu, hi = s[j] >> 16;
+                            v |= (i + 1 == d) ? lo : 0u;
+                            v |= (i + D / 2 + 1 == d) ? hi : 0u;
+                            v |= (i == d + 1) ? lo << 16 : 0u;
+                            v |= (i + D / 2 == d + 1) ? hi << 16 : 0u;
+                        }
+                        v = ch.path_sum(v);  // one lane of the path holds each neighbour
+                        const uint32_t al = d > 0 ? (v & 0xffffu) - Sd : 0u;
+                        const uint32_t ga = d + 1 < D ? (v >> 16) - Sd : 0u;
+                        if (active && pl == 0) a.sub[cur.pix] = al | ga << 16;
+                    }
+                }
                 if (DBG && active) {  // debug: natural-order S
                     const size_t p = static_cast<size_t>(cur.pix);
 #pragma unroll
@@ -471,7 +546,7 @@ __device__ __forceinline__ void load_state(Chain<G, K>& ch, const uint32_t* st) 
 // the path state), 2 = phase 2 (restoring it).  Without `pair` (2-path mode)
 // A covers the whole row and writes S = L_LR.
 // ---------------------------------------------------------------------------
-template <int D, bool PAIR, bool S8, int PH = 0, bool WTA = false, bool DBG = false>
+template <int D, bool PAIR, bool S8, int PH = 0, bool WTA = false, bool DBG = false, int POST = 0>
 __device__ __forceinline__ void sweep_h_body(const SweepArgs& a, int bx) {
     constexpr int G = PathShape<D>::G, K = PathShape<D>::K;
     const LaneRole<D, PAIR> r(bx);
@@ -488,13 +563,14 @@ __device__ __forceinline__ void sweep_h_body(const SweepArgs& a, int bx) {
         const bool valid = y < a.H;
         const RowGeo g{valid ? rowbase : 0, 0, 1};
         const int n = valid ? W : 0;
-        walk<D, kSingleH, S8>(ch, g, n, G == 16 ? ((y ^ 1) < a.H ? W : 0) : n, a, r.pl);
+        walk<D, kSingleH, S8, RowGeo, false, POST>(ch, g, n, G == 16 ? ((y ^ 1) < a.H ? W : 0) : n, a, r.pl);
     } else {
         const int Wm = W / 2;
         if constexpr (PH != 2) {
             const RowGeo g = in_b ? RowGeo{rowbase, W - 1, -1} : RowGeo{rowbase, 0, 1};
             const int nA = Wm, nB = W - Wm;
-            walk<D, kStoreL, S8>(ch, g, in_b ? nB : nA, G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
+            walk<D, kStoreL, S8, RowGeo, false, POST>(ch, g, in_b ? nB : nA,
+                                                      G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
         }
         if constexpr (PH == 1) {
             save_state(ch, state_slot<D>(a, y, r.dir));
@@ -505,22 +581,24 @@ __device__ __forceinline__ void sweep_h_body(const SweepArgs& a, int bx) {
         {
             const RowGeo g = in_b ? RowGeo{rowbase, Wm - 1, -1} : RowGeo{rowbase, Wm, 1};
             const int nA = W - Wm, nB = Wm;
-            walk<D, WTA ? kWta2 : kSumH, S8, RowGeo, DBG>(ch, g, in_b ? nB : nA,
-                                                        G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
+            walk<D, WTA ? kWta2 : kSumH, S8, RowGeo, DBG, POST>(ch, g, in_b ? nB : nA,
+                                                              G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
         }
     }
 }
 
 // Second halves of the horizontal pair with the winner-take-all (4 paths: S
 // holds the vertical pair's sums).
-template <int D, bool S8, bool DBG>
+template <int D, bool S8, bool DBG, int POST = 0>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_h2_kernel(SweepArgs a) {
-    sweep_h_body<D, true, S8, 2, true, DBG>(a, blockIdx.x);
+    post_init<POST>(a);
+    sweep_h_body<D, true, S8, 2, true, DBG, POST>(a, blockIdx.x);
 }
 
-template <int D, bool PAIR, bool S8>
+template <int D, bool PAIR, bool S8, int POST = 0>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_h_kernel(SweepArgs a) {
-    sweep_h_body<D, PAIR, S8>(a, blockIdx.x);
+    post_init<POST>(a);
+    sweep_h_body<D, PAIR, S8, 0, false, false, POST>(a, blockIdx.x);
 }
 
 template <int D, bool PAIR, bool S8>
@@ -544,7 +622,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_h_batch_kernel(cons
 // instead of adding into S.  PAIR = false is the 2-path top-to-bottom sweep.
 // SUMV: a pair that does not finish with Eq. 4 writes S = L + stored L (the
 // first pair to write S) instead of adding into S.
-template <int D, int RX, int PH, bool WTA, bool PAIR, bool S8, bool DBG = false, bool SUMV = false>
+template <int D, int RX, int PH, bool WTA, bool PAIR, bool S8, bool DBG = false, bool SUMV = false, int POST = 0>
 __device__ __forceinline__ void sweep_v_body(const SweepArgs& a, int bx) {
     constexpr int G = PathShape<D>::G, K = PathShape<D>::K;
     const LaneRole<D, PAIR> r(bx);
@@ -559,14 +637,15 @@ __device__ __forceinline__ void sweep_v_body(const SweepArgs& a, int bx) {
     if constexpr (!PAIR) {
         const bool valid = c < W;
         const int n = valid ? H : 0;
-        walk<D, kSingleWta, S8, Geo, DBG>(ch, Geo{W, H, valid ? c : 0, 0, 1}, n,
-                                          G == 16 ? ((c ^ 1) < W ? H : 0) : n, a, r.pl);
+        walk<D, kSingleWta, S8, Geo, DBG, POST>(ch, Geo{W, H, valid ? c : 0, 0, 1}, n,
+                                                G == 16 ? ((c ^ 1) < W ? H : 0) : n, a, r.pl);
     } else {
         const int Hm = H / 2;
         if constexpr (PH != 2) {
             const Geo g = in_b ? Geo{W, H, c, H - 1, -1} : Geo{W, H, c, 0, 1};
             const int nA = Hm, nB = H - Hm;
-            walk<D, kStoreL, S8>(ch, g, in_b ? nB : nA, G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
+            walk<D, kStoreL, S8, Geo, false, POST>(ch, g, in_b ? nB : nA,
+                                                   G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
         }
         if constexpr (PH == 1) {
             save_state(ch, state_slot<D>(a, c, r.dir));
@@ -577,15 +656,16 @@ __device__ __forceinline__ void sweep_v_body(const SweepArgs& a, int bx) {
             if constexpr (PH == 0) pair_barrier<D>();
             const Geo g = in_b ? Geo{W, H, c, Hm - 1, -1} : Geo{W, H, c, Hm, 1};
             const int nA = H - Hm, nB = Hm;
-            walk<D, WTA ? kWta2 : (SUMV ? kSumH : kAcc), S8, Geo, DBG>(ch, g, in_b ? nB : nA,
-                                                      G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
+            walk<D, WTA ? kWta2 : (SUMV ? kSumH : kAcc), S8, Geo, DBG, POST>(
+                ch, g, in_b ? nB : nA, G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
         }
     }
 }
 
-template <int D, int RX, int PH, bool WTA, bool PAIR, bool S8, bool DBG = false>
+template <int D, int RX, int PH, bool WTA, bool PAIR, bool S8, bool DBG = false, int POST = 0>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_v_kernel(SweepArgs a) {
-    sweep_v_body<D, RX, PH, WTA, PAIR, S8, DBG>(a, blockIdx.x);
+    post_init<POST>(a);
+    sweep_v_body<D, RX, PH, WTA, PAIR, S8, DBG, false, POST>(a, blockIdx.x);
 }
 
 // Batched form: both phases in one launch (PH = 0).
@@ -599,26 +679,27 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_v_batch_kernel(cons
 // block distribution over the SMs for all of them (two kernels sharing the
 // SMs through concurrent streams ran far slower than either alone).  NV = 1
 // (4 paths: the vertical pair only) keeps the diagonal code out of the kernel.
-template <int D, bool S8, int NV>
+template <int D, bool S8, int NV, int POST = 0>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_first_kernel(const __grid_constant__ FirstStageArgs f) {
+    post_init<POST>(f.h);
     const int b = blockIdx.x;
     if (b < f.start[1]) {
-        sweep_h_body<D, true, S8>(f.h, b);
+        sweep_h_body<D, true, S8, 0, false, false, POST>(f.h, b);
         return;
     }
     if constexpr (NV == 1) {
-        sweep_v_body<D, 0, 1, false, true, S8>(f.v[0], b - f.start[1]);
+        sweep_v_body<D, 0, 1, false, true, S8, false, false, POST>(f.v[0], b - f.start[1]);
     } else {
         for (int k = 0; k < NV; ++k) {
             if (b < f.start[k + 2]) {
                 const SweepArgs& v = f.v[k];
                 const int bx = b - f.start[k + 1];
                 if (v.rx == 0)
-                    sweep_v_body<D, 0, 1, false, true, S8>(v, bx);
+                    sweep_v_body<D, 0, 1, false, true, S8, false, false, POST>(v, bx);
                 else if (v.rx > 0)
-                    sweep_v_body<D, 1, 1, false, true, S8>(v, bx);
+                    sweep_v_body<D, 1, 1, false, true, S8, false, false, POST>(v, bx);
                 else
-                    sweep_v_body<D, -1, 1, false, true, S8>(v, bx);
+                    sweep_v_body<D, -1, 1, false, true, S8, false, false, POST>(v, bx);
                 return;
             }
         }
@@ -630,13 +711,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_first_kernel(const 
 // vertical chains (H steps) are longer than the horizontal first halves (W/2
 // steps at 640x480), so the grid stays busy to the end of the launch; the
 // horizontal second halves then finish with Eq. 4 (sweep_h2_kernel).
-template <int D, bool S8>
+template <int D, bool S8, int POST = 0>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_first4_kernel(const __grid_constant__ FirstStageArgs f) {
+    post_init<POST>(f.h);
     const int b = blockIdx.x;
     if (b < f.start[1])
-        sweep_h_body<D, true, S8, 1>(f.h, b);
+        sweep_h_body<D, true, S8, 1, false, false, POST>(f.h, b);
     else
-        sweep_v_body<D, 0, 0, false, true, S8, false, true>(f.v[0], b - f.start[1]);
+        sweep_v_body<D, 0, 0, false, true, S8, false, true, POST>(f.v[0], b - f.start[1]);
 }
 
 // ---------------------------------------------------------------------------
@@ -656,6 +738,11 @@ struct SweepD {
 
     static cudaError_t launch_h(const SweepArgs& a, cudaStream_t s) {
         const dim3 grid(blocks(a.H, a.pair)), block(32 * kWarpsPerBlock);
+        if (a.post) {  // post form: 2-path left-to-right only
+            if (a.pair) return cudaErrorInvalidValue;
+            sweep_h_kernel<D, false, true, 1><<<grid, block, 0, s>>>(a);
+            return cudaGetLastError();
+        }
         if (!a.pair)
             sweep_h_kernel<D, false, true><<<grid, block, 0, s>>>(a);
         else if (a.s8)
@@ -671,6 +758,11 @@ struct SweepD {
         for (int k = 0; k < f.nv; ++k) f.start[k + 2] = f.start[k + 1] + blocks(f.v[k].W, true);
         const dim3 block(32 * kWarpsPerBlock);
         const int grid = f.start[f.nv + 1];
+        if (f.h.post) {  // post form: 8 paths only
+            if (f.nv != 3 || f.h.s8) return cudaErrorInvalidValue;
+            sweep_first_kernel<D, false, 3, 1><<<grid, block, 0, s>>>(f);
+            return cudaGetLastError();
+        }
         if (f.nv == 1 && f.h.s8)
             sweep_first_kernel<D, true, 1><<<grid, block, 0, s>>>(f);
         else if (f.nv == 1)
@@ -685,7 +777,11 @@ struct SweepD {
         f.start[1] = blocks(f.h.H, true);
         f.start[2] = f.start[1] + blocks(f.v[0].W, true);
         const dim3 block(32 * kWarpsPerBlock);
-        if (f.h.s8)
+        if (f.h.post && f.h.s8)
+            sweep_first4_kernel<D, true, 1><<<f.start[2], block, 0, s>>>(f);
+        else if (f.h.post)
+            sweep_first4_kernel<D, false, 1><<<f.start[2], block, 0, s>>>(f);
+        else if (f.h.s8)
             sweep_first4_kernel<D, true><<<f.start[2], block, 0, s>>>(f);
         else
             sweep_first4_kernel<D, false><<<f.start[2], block, 0, s>>>(f);
@@ -694,7 +790,11 @@ struct SweepD {
 
     static cudaError_t launch_h2(const SweepArgs& a, cudaStream_t s) {
         const dim3 grid(blocks(a.H, true)), block(32 * kWarpsPerBlock);
-        if (a.s8 && a.Sdbg)
+        if (a.post && a.s8)
+            sweep_h2_kernel<D, true, false, 1><<<grid, block, 0, s>>>(a);
+        else if (a.post)
+            sweep_h2_kernel<D, false, false, 1><<<grid, block, 0, s>>>(a);
+        else if (a.s8 && a.Sdbg)
             sweep_h2_kernel<D, true, true><<<grid, block, 0, s>>>(a);
         else if (a.s8)
             sweep_h2_kernel<D, true, false><<<grid, block, 0, s>>>(a);
@@ -752,6 +852,21 @@ struct SweepD {
 
     static cudaError_t launch_v(const SweepArgs& a, cudaStream_t s) {
         const dim3 grid(blocks(a.W, a.pair)), block(32 * kWarpsPerBlock);
+        if (a.post) {
+            // post form: the 2-path top-to-bottom sweep, and the second halves
+            // of the three vertical-type pairs of 8 paths (u16 sums)
+            if (!a.pair)
+                sweep_v_kernel<D, 0, 0, true, false, true, false, 1><<<grid, block, 0, s>>>(a);
+            else if (a.phase != 2 || a.s8)
+                return cudaErrorInvalidValue;
+            else if (a.rx == 0)
+                sweep_v_kernel<D, 0, 2, true, true, false, false, 1><<<grid, block, 0, s>>>(a);
+            else if (a.rx > 0)
+                sweep_v_kernel<D, 1, 2, false, true, false, false, 1><<<grid, block, 0, s>>>(a);
+            else
+                sweep_v_kernel<D, -1, 2, false, true, false, false, 1><<<grid, block, 0, s>>>(a);
+            return cudaGetLastError();
+        }
         if (!a.pair && a.Sdbg)
             sweep_v_kernel<D, 0, 0, true, false, true, true><<<grid, block, 0, s>>>(a);
         else if (!a.pair)

@@ -30,6 +30,10 @@ STATUS_NAMES = {0: "SGM_OK", 1: "SGM_EAGAIN", -1: "SGM_EINVAL", -2: "SGM_ENOMEM"
                 -4: "SGM_ETIMEDOUT", -5: "SGM_ECANCELED", -6: "SGM_EDEVICE"}
 SGM_FLAG_STAGE_TIMING = 1
 SGM_FLAG_CENSUS_FULL = 2
+SGM_POST_SUBPIXEL = 1
+SGM_POST_LR_CHECK = 2
+SGM_POST_ADAPTIVE_P2 = 4
+SGM_DISP16_INVALID = 0xFFFF
 SGM_MAX_D = 256
 SGM_MAX_PENALTY = 224
 
@@ -56,6 +60,7 @@ _sig("sgm_last_error", ctypes.c_char_p, [_vp])
 _sig("sgm_set_stream", _i, [_vp, _vp])
 _sig("sgm_compute", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp])
 _sig("sgm_compute_async", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp])
+_sig("sgm_compute_ex", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, ctypes.c_uint, _vp])
 _sig("sgm_compute_batch", _i, [_vp, _i, ctypes.POINTER(sgm_pair)])
 _sig("sgm_submit", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, ctypes.POINTER(ctypes.c_uint64)])
 _sig("sgm_poll", _i, [_vp, ctypes.c_uint64, ctypes.c_int64])
@@ -122,6 +127,11 @@ def sgm_set_stream(ctx, stream) -> None:
 
 def sgm_compute(ctx, left, right, W, H, D, P1, P2, n_paths, disp_out) -> None:
     _check(ctx, _lib.sgm_compute(ctx, addr(left), addr(right), W, H, D, P1, P2, n_paths, addr(disp_out)))
+
+
+def sgm_compute_ex(ctx, left, right, W, H, D, P1, P2, n_paths, post, disp16_out) -> None:
+    _check(ctx, _lib.sgm_compute_ex(ctx, addr(left), addr(right), W, H, D, P1, P2, n_paths, post,
+                                    addr(disp16_out)))
 
 
 def sgm_compute_async(ctx, left, right, W, H, D, P1, P2, n_paths, disp_out) -> None:
@@ -215,6 +225,21 @@ class Context:
         if out is None:
             out = _empty_like_u8(left)
         sgm_compute(self.handle, left, right, W, H, D, P1, P2, n_paths, out)
+        return out
+
+    def compute_ex(self, left, right, D, P1, P2, n_paths, post=0, out=None):
+        """Disparity in 1/16 pixel with post-filters (uint16; numpy or torch)."""
+        H, W = left.shape
+        if out is None:
+            if hasattr(left, "data_ptr") and hasattr(left, "device"):
+                import torch
+
+                out = torch.empty((H, W), dtype=torch.int16, device=left.device)
+            else:
+                import numpy as np
+
+                out = np.empty((H, W), np.uint16)
+        sgm_compute_ex(self.handle, left, right, W, H, D, P1, P2, n_paths, post, out)
         return out
 
     def debug(self, left, right, D, P1, P2, n_paths):
