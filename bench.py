@@ -80,6 +80,9 @@ def parse():
     ap.add_argument("--rate", type=float, default=SERVED_RATE_HZ, help="served: arrivals per second")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--post", type=int, default=0,
+                    help="post-filters of sgm_compute_ex (1 sub-pixel | 2 LR check | 4 adaptive P2); "
+                         "times that entry point instead of the plain path")
     ap.add_argument("--census", default="csct", choices=["csct", "full"],
                     help="features: the CSCT of Eq. 1 or the full 9x7 Census (SGM_FLAG_CENSUS_FULL)")
     return ap.parse_args()
@@ -222,6 +225,99 @@ def workload_config(w, args):
     return {"workload": w.name, "W": w.spec.W, "H": w.spec.H, "D": w.spec.D, "P1": w.P1, "P2": w.P2,
             "n_paths": w.n_paths, "pairs_per_step": 1,
             "census": "full 9x7 (62 bits)" if args.census == "full" else "CSCT (31 bits, Eq. 1)"}
+
+
+def run_post_bench(args, w, ws, rank, local):
+    """The path with post-filters (sgm_compute_ex_async, the captured graph)
+    on the workload's pair, resident in HBM."""
+    import torch
+    from paper_1610_04121_gb300 import sgm
+
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+        pg = dist
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W, H, D = w.spec.W, w.spec.H, w.spec.D
+    pair = synth.make_pair(w.spec, synth.BASE_SEED + synth.WORKLOAD_INDEX[w.name] + 7919 * rank)
+    L = torch.from_numpy(pair.left).to(dev)
+    R = torch.from_numpy(pair.right).to(dev)
+    out = torch.empty((H, W), dtype=torch.int16, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(dev)
+    cflag = sgm.SGM_FLAG_CENSUS_FULL if args.census == "full" else 0
+    ctx = sgm.Context(local, flags=cflag)
+    sgm.sgm_set_stream(ctx.handle, stream)
+
+    def step():
+        sgm.sgm_compute_ex_async(ctx.handle, L, R, W, H, D, w.P1, w.P2, w.n_paths, args.post, out)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches0 = ctx.launches
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)
+            ev0[k].record(stream)
+            step()
+            ev1[k].record(stream)
+        torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    launches = ctx.launches - launches0
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)), pg, dev)
+    ms_per_step = total_ms / args.steps
+    de = W * H * D
+    value = job_mdes(ws, args.steps, de, total_ms)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        census = oracle_census(args)
+        n, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < 10.0:
+            oracle.sgm_ex(pair.left, pair.right, D, w.P1, w.P2, w.n_paths, args.post, census)
+            n += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": de * n / dt / 1e6, "unit": "MDE/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n} full {W}x{H} D={D} {w.n_paths}-path frames with post={args.post}, single thread"}
+    if rank == 0:
+        peaks, peak_kind = load_peaks()
+        hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+        passes = 2 if args.post & 2 else 1
+        frame_bytes = passes * (2 * W * H + W * H + 4 * de) + 2 * W * H
+        frame_gbs = frame_bytes / (ms_per_step / 1e3) / 1e9
+        line = {
+            "metric": "MDE/s", "value": value, "unit": "MDE/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u16", "data": "synthetic (seeded stereo_synth pair, resident in HBM)",
+            "config": dict(workload_config(w, args), parallelism=f"replicas x{ws}", post=args.post,
+                           post_names=[n for b, n in ((1, "subpixel"), (2, "lr_check"), (4, "adaptive_p2"))
+                                       if args.post & b],
+                           l2="flushed between timed steps (256 MiB write)", fps=1e3 / ms_per_step,
+                           de_counts="W*H*D once per frame, although the LR check runs a second matching pass"),
+            "roofline": None,
+            "frame_roofline": {"bound": "hbm", "achieved": frame_gbs, "peak": hbm, "unit": "GB/s",
+                               "frac": frame_gbs / hbm, "algorithmic_bytes_per_frame": frame_bytes,
+                               "peak_source": f"{peak_kind} hbm_gbs"},
+            "cpu_baseline": cpu, "e2e": None, "gpu_launches": launches, "clocks": clk.summary(),
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
 
 
 def run_batch_bench(args, ws, rank, local):
@@ -440,6 +536,8 @@ def main():
     w = synth.WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w, ws, rank)
+    if args.post:
+        return run_post_bench(args, w, ws, rank, local)
 
     import torch
 

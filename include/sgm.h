@@ -113,8 +113,10 @@ SGM_API const char *sgm_last_error(const sgm_ctx *ctx);
 
 /*
  * Make the context enqueue its work on `cuda_stream` (a cudaStream_t of the
- * context's device, or NULL for the context's own stream).  The caller keeps
- * the stream alive while the context uses it.
+ * context's device, or NULL for the context's own stream; the default
+ * stream, whose handle is NULL, is selected with cudaStreamLegacy or
+ * cudaStreamPerThread).  The caller keeps the stream alive while the context
+ * uses it.
  */
 SGM_API int sgm_set_stream(sgm_ctx *ctx, void *cuda_stream);
 
@@ -160,6 +162,10 @@ SGM_API int sgm_compute(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right,
  */
 SGM_API int sgm_compute_ex(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1,
                            int P2, int n_paths, unsigned post, uint16_t *disp16_out);
+
+/* Non-blocking sgm_compute_ex for device pointers only (as sgm_compute_async). */
+SGM_API int sgm_compute_ex_async(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, int W, int H, int D,
+                                 int P1, int P2, int n_paths, unsigned post, uint16_t *disp16_out);
 
 /*
  * Non-blocking form for device pointers only: enqueues the whole path on the

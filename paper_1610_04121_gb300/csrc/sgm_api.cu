@@ -1037,6 +1037,20 @@ int sgm_compute_async(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, i
     return enqueue_graph(ctx, p, ctx->arena, left, right, disp_out, ctx->stream);
 }
 
+int sgm_compute_ex_async(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H, int D, int P1,
+                         int P2, int n_paths, unsigned post, uint16_t* disp16_out) {
+    Problem p = make_problem(ctx, W, H, D, P1, P2, n_paths);
+    p.post = (post & ~static_cast<unsigned>(kPostOut16)) == post ? static_cast<int>(post) | kPostOut16 : -1;
+    int rc = check_args(ctx, p, left, right, disp16_out);
+    if (rc != SGM_OK) return rc;
+    if (!is_device_ptr(left) || !is_device_ptr(right) || !is_device_ptr(disp16_out))
+        return fail(ctx, SGM_EINVAL, "sgm_compute_ex_async takes device pointers only");
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, layout_for(p).total, true);
+    if (rc != SGM_OK) return rc;
+    return enqueue_graph(ctx, p, ctx->arena, left, right, reinterpret_cast<uint8_t*>(disp16_out), ctx->stream);
+}
+
 int sgm_compute_batch(sgm_ctx* ctx, int n, const sgm_pair* pairs) {
     if (!ctx) return fail(nullptr, SGM_EINVAL, "null context");
     if (n < 0 || (n > 0 && !pairs)) return fail(ctx, SGM_EINVAL, "bad batch (n=%d, pairs=%p)", n, (const void*)pairs);

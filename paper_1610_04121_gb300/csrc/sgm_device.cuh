@@ -231,17 +231,6 @@ struct Chain {
         }
     }
 
-    // the sum of v over this lane's path
-    __device__ __forceinline__ uint32_t path_sum(uint32_t v) const {
-        if constexpr (G == 32) {
-            return __reduce_add_sync(0xffffffffu, v);
-        } else {
-            const uint32_t a = __reduce_add_sync(0xffffffffu, in_b ? 0u : v);
-            const uint32_t b = __reduce_add_sync(0xffffffffu, in_b ? v : 0u);
-            return in_b ? b : a;
-        }
-    }
-
     __device__ __forceinline__ void step(const uint32_t (&mc)[K], uint32_t P1x2, uint32_t P2x2, uint32_t (&L)[K]) {
         const uint32_t inf2 = kInf16 * 0x10001u;
         const uint32_t u = up * mul_up + add_up;

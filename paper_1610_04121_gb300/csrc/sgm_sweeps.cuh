@@ -160,19 +160,16 @@ __device__ __forceinline__ LaneBases lane_bases(const SweepArgs& a, int pl) {
     return LaneBases{a.rec + 2 * K * pl, a.rec + D + 4 * K * pl, a.rec + a.lx_off + 2 * K * pl};
 }
 
-// One step's inputs for one lane, loaded from the record at byte offset `off`;
-// in the post form also the base image at the step's pixel and at its
-// predecessor on the path (low and high half of im).
-template <int D, int MODE, bool S8, int POST = 0>
+// One step's inputs for one lane, loaded from the record at byte offset `off`.
+template <int D, int MODE, bool S8>
 struct StepIn {
     static constexpr int K = PathShape<D>::K;
     using M = ModeIO<MODE>;
     static constexpr int PW = (K + 1) / 2;
-    static constexpr int REGS = PW + (M::IN_LO ? PW : 0) + (M::IN_S ? (S8 ? PW : K) : 0) + (POST ? 1 : 0);
+    static constexpr int REGS = PW + (M::IN_LO ? PW : 0) + (M::IN_S ? (S8 ? PW : K) : 0);
     Regs<PW> mc;
     Regs<M::IN_LO ? PW : 0> lo;
     Regs<M::IN_S ? (S8 ? PW : K) : 0> s;
-    Regs<POST ? 1 : 0> im;
 
     __device__ __forceinline__ void load(const LaneBases& lb, uint32_t off) {
         const uint8_t* p = at(lb.pairs, off);
@@ -184,9 +181,6 @@ struct StepIn {
             else
                 ldg_words<K>(reinterpret_cast<const uint32_t*>(at(lb.words, off)), s.r);
         }
-    }
-    __device__ __forceinline__ void load_img(const uint8_t* img, int pix, int ppix) {
-        if constexpr (POST) im.r[0] = static_cast<uint32_t>(__ldg(img + pix)) | static_cast<uint32_t>(__ldg(img + ppix)) << 16;
     }
 };
 
@@ -231,6 +225,8 @@ struct RowGeo {
     __device__ __forceinline__ void advance(Cursor& c) const { c.pix += dx; }
     // the pixel before the start on the path (unclamped; may lie outside)
     __device__ __forceinline__ int before_start() const { return rowbase + x0 - dx; }
+    // the pixel of step i
+    __device__ __forceinline__ int pix_at(int i) const { return rowbase + x0 + dx * i; }
 };
 
 // Pixels of a column (RX = 0) or wrapped-diagonal (RX = +1/-1) walk:
@@ -255,6 +251,11 @@ struct ColGeo {
     __device__ __forceinline__ Cursor start() const {
         const int x = x_at(y0);
         return Cursor{y0 * W + x, x, y0};
+    }
+    // the pixel of step i
+    __device__ __forceinline__ int pix_at(int i) const {
+        const int y = y0 + dy * i;
+        return y * W + x_at(y);
     }
     // the pixel before the start on the path (its row may lie outside)
     __device__ __forceinline__ int before_start() const {
@@ -337,7 +338,7 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
                                      int n_other, const SweepArgs& a, int pl) {
     constexpr int G = PathShape<D>::G, K = PathShape<D>::K;
     using M = ModeIO<MODE>;
-    using In = StepIn<D, MODE, S8, POST>;
+    using In = StepIn<D, MODE, S8>;
     constexpr int PF = prefetch_steps(In::REGS);
     const int n_min = min(n_own, n_other), n_max = max(n_own, n_other);
     const uint32_t RB = static_cast<uint32_t>(a.RB);
@@ -353,27 +354,28 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
     const uint32_t off0 = static_cast<uint32_t>(pix0) * RB;
     const uint32_t doff = Geo::kLinear ? static_cast<uint32_t>(g.step_pix()) * RB : 0u;
     uint32_t off_ld = static_cast<uint32_t>(ld.pix) * RB, off_cur = off_ld;
-    // post form: the pixel of the step being prefetched and of its predecessor
-    int pix_ld = ld.pix;
-    int pprev = min(max(g.before_start(), 0), a.W * a.H - 1);
     auto prefetch = [&](In& b, int i, bool clamp) {
-        const bool past = clamp && i >= n_own;
-        int pix;
         if constexpr (Geo::kLinear) {
-            b.load(lb, past ? off0 : off_ld);
+            b.load(lb, (clamp && i >= n_own) ? off0 : off_ld);
             off_ld += doff;
-            pix = pix_ld;
-            pix_ld += g.step_pix();
         } else {
-            pix = ld.pix;
-            b.load(lb, static_cast<uint32_t>(past ? pix0 : pix) * RB);
+            const int pix = (clamp && i >= n_own) ? pix0 : ld.pix;
+            b.load(lb, static_cast<uint32_t>(pix) * RB);
             g.advance(ld);
         }
-        if constexpr (POST != 0) {
-            b.load_img(a.img, past ? pix0 : pix, past ? pix0 : pprev);
-            pprev = pix;
-        }
     };
+    // Post form: the jump penalty of every step comes from the base image.
+    // Lane pl of a path loads the intensity of step i0 + pl of each chunk
+    // (one chunk ahead, like the records) and turns it into that step's
+    // penalty at the chunk's start; step k then takes lane k's penalty with
+    // one shuffle.  im_last carries the intensity of the step before the chunk.
+    static_assert(PF <= G, "one lane per step of a chunk");
+    auto img_at_step = [&](int i) -> uint32_t { return __ldg(a.img + (i < n_own ? g.pix_at(i) : pix0)); };
+    uint32_t im_nxt = 0, im_last = 0, p2_lane = 0;
+    if constexpr (POST != 0) {
+        im_nxt = img_at_step(pl);
+        im_last = __ldg(a.img + min(max(g.before_start(), 0), a.W * a.H - 1));
+    }
 #pragma unroll
     for (int k = 0; k < PF; ++k) prefetch(nxt[k], k, true);
     // 16-bit keys: byte sums of 2 or 4 paths stay below 511, so S * D + d
@@ -383,18 +385,13 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
     if constexpr (M::WTA) wta_consts<K, KEY16>(pl, D, dconst);
 
     // one step of the recurrence at `cur` and its outputs
-    auto body = [&](const In& in, bool active) {
+    auto body = [&](const In& in, bool active, int k) {
         if constexpr (Geo::kResets) {
             if (g.starts(cur)) ch.reset();
         }
         uint32_t mc[K], L[K];
         unpack_regs<K>(in.mc.r, mc);
-        uint32_t p2x2 = a.P2x2;
-        if constexpr (POST != 0) {  // the jump penalty of this step from the base image
-            const uint32_t v = in.im.r[0];
-            const int gdiff = abs(static_cast<int>(v & 0xffffu) - static_cast<int>(v >> 16));
-            p2x2 = post_p2_table()[gdiff];
-        }
+        const uint32_t p2x2 = POST != 0 ? __shfl_sync(0xffffffffu, p2_lane, k, G) : a.P2x2;
         ch.step(mc, a.P1x2, p2x2, L);
         const uint32_t off = Geo::kLinear ? off_cur : static_cast<uint32_t>(cur.pix) * RB;
         if constexpr (M::OUT_LX) {
@@ -442,19 +439,19 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
                     if (a.sub) {  // uniform: S at the winner's neighbours for the sub-pixel step
                         const int d = wta_disparity<D, KEY16>(key);
                         const uint32_t Sd = KEY16 ? key / static_cast<uint32_t>(D) : key >> 8;
-                        uint32_t v = 0;  // S(d-1) in the low half, S(d+1) in the high half
+                        // S(e) from the lane holding disparity e: word i = e mod D/2 in
+                        // lane i / K, slot i % K, the high half for e >= D/2
+                        auto s_at = [&](int e) -> uint32_t {
+                            const int i = e < D / 2 ? e : e - D / 2, src = i / K, jj = i - src * K;
+                            uint32_t w = s[0];
 #pragma unroll
-                        for (int j = 0; j < K; ++j) {
-                            const int i = pl * K + j;
-                            const uint32_t lo = s[j] & 0xffffu, hi = s[j] >> 16;
-                            v |= (i + 1 == d) ? lo : 0u;
-                            v |= (i + D / 2 + 1 == d) ? hi : 0u;
-                            v |= (i == d + 1) ? lo << 16 : 0u;
-                            v |= (i + D / 2 == d + 1) ? hi << 16 : 0u;
-                        }
-                        v = ch.path_sum(v);  // one lane of the path holds each neighbour
-                        const uint32_t al = d > 0 ? (v & 0xffffu) - Sd : 0u;
-                        const uint32_t ga = d + 1 < D ? (v >> 16) - Sd : 0u;
+                            for (int j = 1; j < K; ++j) w = (jj == j) ? s[j] : w;
+                            w = __shfl_sync(0xffffffffu, w, src, G);
+                            return e < D / 2 ? (w & 0xffffu) : (w >> 16);
+                        };
+                        const uint32_t sm = s_at(d > 0 ? d - 1 : 0), sp = s_at(d + 1 < D ? d + 1 : d);
+                        const uint32_t al = d > 0 ? sm - Sd : 0u;
+                        const uint32_t ga = d + 1 < D ? sp - Sd : 0u;
                         if (active && pl == 0) a.sub[cur.pix] = al | ga << 16;
                     }
                 }
@@ -475,6 +472,14 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
         In in[PF];
 #pragma unroll
         for (int k = 0; k < PF; ++k) in[k] = nxt[k];
+        if constexpr (POST != 0) {
+            const uint32_t im = im_nxt;
+            im_nxt = img_at_step(i0 + PF + pl);
+            uint32_t prev = __shfl_up_sync(0xffffffffu, im, 1, G);
+            if (pl == 0) prev = im_last;
+            p2_lane = post_p2_table()[abs(static_cast<int>(im) - static_cast<int>(prev))];
+            im_last = __shfl_sync(0xffffffffu, im, PF - 1, G);
+        }
         if (i0 + 2 * PF <= n_min) {
 #pragma unroll
             for (int k = 0; k < PF; ++k) prefetch(nxt[k], i0 + PF + k, false);
@@ -485,7 +490,7 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
         if (n_min - i0 >= PF) {
 #pragma unroll
             for (int k = 0; k < PF; ++k) {
-                body(in[k], true);
+                body(in[k], true, k);
                 g.advance(cur);
                 off_cur += doff;
             }
@@ -498,7 +503,7 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
                     // every lane runs the step (it holds warp-synchronous
                     // exchanges); a finished path then takes its state back
                     const Chain<G, K> saved = ch;
-                    body(in[k], i < n_own);
+                    body(in[k], i < n_own, k);
                     if (i >= n_own) ch = saved;
                     g.advance(cur);
                     off_cur += doff;

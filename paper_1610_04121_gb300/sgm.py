@@ -61,6 +61,7 @@ _sig("sgm_set_stream", _i, [_vp, _vp])
 _sig("sgm_compute", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp])
 _sig("sgm_compute_async", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp])
 _sig("sgm_compute_ex", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, ctypes.c_uint, _vp])
+_sig("sgm_compute_ex_async", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, ctypes.c_uint, _vp])
 _sig("sgm_compute_batch", _i, [_vp, _i, ctypes.POINTER(sgm_pair)])
 _sig("sgm_submit", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, ctypes.POINTER(ctypes.c_uint64)])
 _sig("sgm_poll", _i, [_vp, ctypes.c_uint64, ctypes.c_int64])
@@ -119,9 +120,16 @@ def sgm_destroy(ctx) -> None:
     _lib.sgm_destroy(ctx)
 
 
+CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy: the legacy default stream as an explicit handle
+
+
 def sgm_set_stream(ctx, stream) -> None:
-    """`stream`: a torch.cuda.Stream, an integer cudaStream_t, or None."""
+    """`stream`: a torch.cuda.Stream, an integer cudaStream_t, or None (the
+    context's own stream).  torch's default stream has the handle 0, which
+    the library reads as None, so it is passed as cudaStreamLegacy."""
     handle = getattr(stream, "cuda_stream", stream)
+    if handle == 0 and stream is not None and hasattr(stream, "cuda_stream"):
+        handle = CUDA_STREAM_LEGACY
     _check(ctx, _lib.sgm_set_stream(ctx, handle))
 
 
@@ -132,6 +140,11 @@ def sgm_compute(ctx, left, right, W, H, D, P1, P2, n_paths, disp_out) -> None:
 def sgm_compute_ex(ctx, left, right, W, H, D, P1, P2, n_paths, post, disp16_out) -> None:
     _check(ctx, _lib.sgm_compute_ex(ctx, addr(left), addr(right), W, H, D, P1, P2, n_paths, post,
                                     addr(disp16_out)))
+
+
+def sgm_compute_ex_async(ctx, left, right, W, H, D, P1, P2, n_paths, post, disp16_out) -> None:
+    _check(ctx, _lib.sgm_compute_ex_async(ctx, addr(left), addr(right), W, H, D, P1, P2, n_paths, post,
+                                          addr(disp16_out)))
 
 
 def sgm_compute_async(ctx, left, right, W, H, D, P1, P2, n_paths, disp_out) -> None:

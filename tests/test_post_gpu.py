@@ -110,3 +110,24 @@ def test_device_pointers_and_repeat_calls(sgm, ctx):
 def test_full_size_frame(ctx, n_paths):
     pair = synth.make_pair(synth.PairSpec(640, 480, 128, 4, 2, 100), 31)
     _check(ctx, pair.left, pair.right, 128, 7, 84, n_paths, SUB | LR | AP2)
+
+
+def test_async_form_on_the_context_stream(sgm):
+    import torch
+
+    pair = synth.make_pair(synth.PairSpec(130, 66, 64, 4, 2, 40), 23)
+    ref = oracle.sgm_ex(pair.left, pair.right, 64, 10, 120, 8, SUB | LR | AP2)
+    L = torch.from_numpy(pair.left).cuda()
+    R = torch.from_numpy(pair.right).cuda()
+    out = torch.zeros((66, 130), dtype=torch.int16, device="cuda")
+    with sgm.Context(0) as c:
+        sgm.sgm_set_stream(c.handle, torch.cuda.current_stream())
+        sgm.sgm_compute_ex_async(c.handle, L, R, 130, 66, 64, 10, 120, 8, SUB | LR | AP2, out)
+        torch.cuda.current_stream().synchronize()
+        sgm.sgm_set_stream(c.handle, None)
+        got = out.cpu().numpy().view(np.uint16)
+        bad = np.argwhere(got != ref)
+        assert bad.size == 0, f"{len(bad)} differ, e.g. {[(y, x, int(got[y, x]), int(ref[y, x])) for y, x in bad[:6]]}"
+        with pytest.raises(sgm.SgmError):  # host pointers are refused
+            sgm.sgm_compute_ex_async(c.handle, pair.left, pair.right, 130, 66, 64, 10, 120, 8, SUB,
+                                     np.zeros((66, 130), np.uint16))
