@@ -244,7 +244,8 @@ SGM_API int sgm_served_reset_stats(sgm_ctx *ctx);
  *   S        uint16 [H][W][D] summed aggregated cost (Eq. 4's sum)
  *   raw      uint8  [H][W]    winner-take-all disparity before the median
  *   disp     uint8  [H][W]    final disparity
- * Errors as sgm_compute.
+ * A 4-path problem runs the schedule forced by sgm_set_schedule, else
+ * SGM_SCHED_V_THEN_H (it is not autotuned).  Errors as sgm_compute.
  */
 SGM_API int sgm_debug_stages(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
                      int n_paths, void *Fb, void *Fm, uint8_t *MC, uint16_t *S, uint8_t *raw, uint8_t *disp);
@@ -271,6 +272,35 @@ SGM_API const char *sgm_stage_name(int n_paths, int i);
 /* Path count (2, 4 or 8) of the path that sgm_stage_times reports on, or 0
  * when none has been enqueued with SGM_FLAG_STAGE_TIMING. */
 SGM_API int sgm_stage_paths(const sgm_ctx *ctx);
+
+/* Name of stage i of the path that sgm_stage_times reports on (it follows
+ * that path's sweep schedule: with SGM_SCHED_H_THEN_V the 4-path sweeps are
+ * sweep_h+v1, sweep_v2), or NULL. */
+SGM_API const char *sgm_stage_label(const sgm_ctx *ctx, int i);
+
+/*
+ * Sweep schedules of the 4-path plain path (sgm_compute, sgm_compute_async):
+ *   SGM_SCHED_V_THEN_H  the whole vertical pair (writing S) beside the first
+ *                       halves of the horizontal pair, then the horizontal
+ *                       second halves with the winner-take-all;
+ *   SGM_SCHED_H_THEN_V  the whole horizontal pair beside the vertical first
+ *                       halves, then the vertical second halves with the
+ *                       winner-take-all.
+ * Both give bit-identical results.  By default the context autotunes: the
+ * first call for a new (W, H, D, Census type, byte-sum) key runs the path
+ * with each schedule (once to warm up, twice timed with CUDA events on the
+ * context's stream; that call blocks meanwhile) and keeps the faster one for
+ * the key; a stream under capture is not tuned (the first schedule is used).
+ * sgm_set_schedule(ctx, s) forces schedule s; -1 restores autotuning.
+ * Errors: SGM_EINVAL (null context, unknown schedule).
+ */
+#define SGM_SCHED_V_THEN_H 0
+#define SGM_SCHED_H_THEN_V 1
+SGM_API int sgm_set_schedule(sgm_ctx *ctx, int schedule);
+
+/* The schedule the context uses for this problem: the forced one, the tuned
+ * one, SGM_SCHED_V_THEN_H for 2 and 8 paths, or -1 when not tuned yet. */
+SGM_API int sgm_schedule_for(const sgm_ctx *ctx, int W, int H, int D, int P1, int P2, int n_paths);
 
 /*
  * Kernel launches issued by this context so far (every launch of this

@@ -86,6 +86,7 @@ struct Problem {
     int W, H, D, P1, P2, n_paths;
     int ct62 = 0;  // features: 0 = CSCT (Eq. 1), 1 = the full 9x7 Census (SGM_FLAG_CENSUS_FULL)
     int post = 0;  // 0: the plain path (u8 output); else kPostOut16 | the SGM_POST_* flags of sgm_compute_ex
+    int sched = 0;  // 4-path sweep schedule (SGM_SCHED_*)
 };
 
 // Set on every sgm_compute_ex problem: the post form with uint16 output, even
@@ -137,9 +138,9 @@ struct GraphKey {
     Problem p;
     const void *left, *right, *out, *arena;
     bool operator<(const GraphKey& o) const {
-        return std::tie(p.W, p.H, p.D, p.P1, p.P2, p.n_paths, p.ct62, p.post, left, right, out, arena) <
-               std::tie(o.p.W, o.p.H, o.p.D, o.p.P1, o.p.P2, o.p.n_paths, o.p.ct62, o.p.post, o.left, o.right, o.out,
-                        o.arena);
+        return std::tie(p.W, p.H, p.D, p.P1, p.P2, p.n_paths, p.ct62, p.post, p.sched, left, right, out, arena) <
+               std::tie(o.p.W, o.p.H, o.p.D, o.p.P1, o.p.P2, o.p.n_paths, o.p.ct62, o.p.post, o.p.sched, o.left,
+                        o.right, o.out, o.arena);
     }
 };
 
@@ -190,6 +191,11 @@ struct sgm_ctx {
     cudaEvent_t stage_ev[10] = {};
     int last_stages = 0;
     int last_n_paths = 0;  // path count of the last path enqueued with stage timing
+    int last_sched = 0;    // its sweep schedule
+    // 4-path schedule: forced (>= 0) or autotuned per key (-1)
+    int forced_sched = -1;
+    std::map<std::tuple<int, int, int, int, int, bool>, int> tuned;  // (W, H, D, n_paths, ct62, s8) -> schedule
+    cudaEvent_t tune_ev[2] = {};
 
     // served requests
     std::mutex mu;
@@ -336,6 +342,26 @@ static cudaError_t enqueue_match(const Problem& p, const Layout& l, uint8_t* are
         a.wta = 1;
         if ((e = launch_sweep_v(a, s)) != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
+    } else if (p.n_paths == 4 && p.sched == SGM_SCHED_H_THEN_V) {
+        // 4 paths, the other schedule: the whole horizontal pair
+        // (S = L_LR + L_RL) beside the vertical first halves, then the
+        // vertical second halves with Eq. 4
+        FirstStageArgs f{};
+        f.h = a;
+        f.nv = 1;
+        f.v[0] = a;
+        f.v[0].phase = 1;
+        f.v[0].state = states;
+        f.v[0].lx_off = 4 * p.D;
+        if ((e = launch_sweep_first(f, s)) != cudaSuccess) return e;
+        if ((e = mark()) != cudaSuccess) return e;
+        SweepArgs b = a;
+        b.phase = 2;
+        b.wta = 1;
+        b.state = states;
+        b.lx_off = 4 * p.D;
+        if ((e = launch_sweep_v(b, s)) != cudaSuccess) return e;
+        if ((e = mark()) != cudaSuccess) return e;
     } else if (p.n_paths == 4) {
         // 4 paths: the whole vertical pair (S = L_TB + L_BT) beside the
         // horizontal first halves, then the horizontal second halves with Eq. 4
@@ -460,6 +486,53 @@ static int enqueue_graph(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const u
     ctx->launches += launches_per_path(p);
     ctx->last_stages = (ctx->stage_timing && !p.post) ? stages_per_path(p) : 0;
     ctx->last_n_paths = (ctx->stage_timing && !p.post) ? p.n_paths : 0;
+    ctx->last_sched = p.sched;
+    return SGM_OK;
+}
+
+// The 4-path sweep schedule of a plain-path problem: forced, or the faster of
+// the two measured on the first use of its (W, H, D, Census, byte sums) key.
+// Tuning runs the whole path (into the caller's output, which every schedule
+// computes bit-identically) once per schedule to warm up and twice timed with
+// events on `s`; the minimum decides.  A stream under capture cannot be
+// timed: there the default schedule is used untuned.
+static int choose_schedule(sgm_ctx* ctx, Problem& p, uint8_t* arena, const uint8_t* left, const uint8_t* right,
+                           uint8_t* disp, cudaStream_t s) {
+    p.sched = SGM_SCHED_V_THEN_H;
+    if (p.n_paths != 4 || p.post) return SGM_OK;
+    if (ctx->forced_sched >= 0) {
+        p.sched = ctx->forced_sched;
+        return SGM_OK;
+    }
+    const auto key = std::make_tuple(p.W, p.H, p.D, p.n_paths, p.ct62, s8_for(p));
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end()) {
+        p.sched = it->second;
+        return SGM_OK;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CUDA_TRY(ctx, cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return SGM_OK;
+    float best_ms[2] = {0.f, 0.f};
+    for (int sched = 0; sched < 2; ++sched) {
+        Problem q = p;
+        q.sched = sched;
+        int rc = enqueue_graph(ctx, q, arena, left, right, disp, s);  // captures the graph; warm-up
+        if (rc != SGM_OK) return rc;
+        float best = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            CUDA_TRY(ctx, cudaEventRecord(ctx->tune_ev[0], s));
+            if ((rc = enqueue_graph(ctx, q, arena, left, right, disp, s)) != SGM_OK) return rc;
+            CUDA_TRY(ctx, cudaEventRecord(ctx->tune_ev[1], s));
+            CUDA_TRY(ctx, cudaEventSynchronize(ctx->tune_ev[1]));
+            float ms = 0.f;
+            CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->tune_ev[0], ctx->tune_ev[1]));
+            best = std::min(best, ms);
+        }
+        best_ms[sched] = best;
+    }
+    p.sched = best_ms[1] < best_ms[0] ? SGM_SCHED_H_THEN_V : SGM_SCHED_V_THEN_H;
+    ctx->tuned.emplace(key, p.sched);
     return SGM_OK;
 }
 
@@ -482,7 +555,10 @@ static int enqueue_pair(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const ui
     const bool out_host = !is_device_ptr(disp);
     if (out_host) dout = arena + l.out;
     if (use_graph) {
-        int rc = enqueue_graph(ctx, p, arena, dl, dr, dout, s);
+        Problem q = p;
+        int rc = choose_schedule(ctx, q, arena, dl, dr, dout, s);
+        if (rc != SGM_OK) return rc;
+        rc = enqueue_graph(ctx, q, arena, dl, dr, dout, s);
         if (rc != SGM_OK) return rc;
     } else {
         CUDA_TRY(ctx, enqueue_path(ctx, p, arena, dl, dr, dout, nullptr, s, false));
@@ -954,6 +1030,12 @@ int sgm_create(sgm_ctx** out, int device, size_t mem_cap_bytes, unsigned flags) 
             }
         }
     }
+    for (auto& ev : ctx->tune_ev) {
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) {
+            sgm_destroy(ctx);
+            return fail(nullptr, SGM_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
+        }
+    }
     *out = ctx;
     return SGM_OK;
 }
@@ -982,6 +1064,8 @@ int sgm_destroy(sgm_ctx* ctx) {
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     for (auto& ev : ctx->stage_ev)
+        if (ev) cudaEventDestroy(ev);
+    for (auto& ev : ctx->tune_ev)
         if (ev) cudaEventDestroy(ev);
     delete ctx;
     return SGM_OK;
@@ -1034,7 +1118,10 @@ int sgm_compute_async(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, i
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, layout_for(p).total, true);
     if (rc != SGM_OK) return rc;
-    return enqueue_graph(ctx, p, ctx->arena, left, right, disp_out, ctx->stream);
+    Problem q = p;
+    rc = choose_schedule(ctx, q, ctx->arena, left, right, disp_out, ctx->stream);
+    if (rc != SGM_OK) return rc;
+    return enqueue_graph(ctx, q, ctx->arena, left, right, disp_out, ctx->stream);
 }
 
 int sgm_compute_ex_async(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H, int D, int P1,
@@ -1143,7 +1230,8 @@ int sgm_served_reset_stats(sgm_ctx* ctx) {
 
 int sgm_debug_stages(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H, int D, int P1, int P2,
                      int n_paths, void* Fb, void* Fm, uint8_t* MC, uint16_t* S, uint8_t* raw, uint8_t* disp) {
-    const Problem p = make_problem(ctx, W, H, D, P1, P2, n_paths);
+    Problem p = make_problem(ctx, W, H, D, P1, P2, n_paths);
+    if (ctx && n_paths == 4 && ctx->forced_sched >= 0) p.sched = ctx->forced_sched;  // else the first schedule
     int rc = check_args(ctx, p, left, right, left);
     if (rc != SGM_OK) return rc;
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
@@ -1184,6 +1272,31 @@ int sgm_stage_times(sgm_ctx* ctx, float* ms_out, int n) {
 }
 
 int sgm_stage_paths(const sgm_ctx* ctx) { return ctx ? ctx->last_n_paths : 0; }
+
+const char* sgm_stage_label(const sgm_ctx* ctx, int i) {
+    if (!ctx || ctx->last_n_paths == 0) return nullptr;
+    if (ctx->last_n_paths == 4 && ctx->last_sched == SGM_SCHED_H_THEN_V) {
+        static const char* four_hv[] = {"census", "cost", "sweep_h+v1", "sweep_v2", "median"};
+        return (i >= 0 && i < 5) ? four_hv[i] : nullptr;
+    }
+    return sgm_stage_name(ctx->last_n_paths, i);
+}
+
+int sgm_set_schedule(sgm_ctx* ctx, int schedule) {
+    if (!ctx) return fail(nullptr, SGM_EINVAL, "null context");
+    if (schedule < -1 || schedule > SGM_SCHED_H_THEN_V) return fail(ctx, SGM_EINVAL, "unknown schedule %d", schedule);
+    ctx->forced_sched = schedule;
+    return SGM_OK;
+}
+
+int sgm_schedule_for(const sgm_ctx* ctx, int W, int H, int D, int P1, int P2, int n_paths) {
+    if (!ctx) return SGM_EINVAL;
+    if (n_paths != 4) return SGM_SCHED_V_THEN_H;
+    if (ctx->forced_sched >= 0) return ctx->forced_sched;
+    Problem p = make_problem(ctx, W, H, D, P1, P2, n_paths);
+    auto it = ctx->tuned.find(std::make_tuple(p.W, p.H, p.D, p.n_paths, p.ct62, s8_for(p)));
+    return it == ctx->tuned.end() ? -1 : it->second;
+}
 
 const char* sgm_stage_name(int n_paths, int i) {
     // 2 paths: "sweep_h" (left to right), "sweep_v" (top to bottom with Eq. 4).

@@ -34,6 +34,8 @@ SGM_POST_SUBPIXEL = 1
 SGM_POST_LR_CHECK = 2
 SGM_POST_ADAPTIVE_P2 = 4
 SGM_DISP16_INVALID = 0xFFFF
+SGM_SCHED_V_THEN_H = 0
+SGM_SCHED_H_THEN_V = 1
 SGM_MAX_D = 256
 SGM_MAX_PENALTY = 224
 
@@ -72,6 +74,9 @@ _sig("sgm_kernel_launches", ctypes.c_uint64, [_vp])
 _sig("sgm_stage_times", _i, [_vp, ctypes.POINTER(ctypes.c_float), _i])
 _sig("sgm_stage_name", ctypes.c_char_p, [_i, _i])
 _sig("sgm_stage_paths", _i, [_vp])
+_sig("sgm_stage_label", ctypes.c_char_p, [_vp, _i])
+_sig("sgm_set_schedule", _i, [_vp, _i])
+_sig("sgm_schedule_for", _i, [_vp, _i, _i, _i, _i, _i, _i])
 _sig("sgm_version", ctypes.c_char_p, [])
 _sig("sgm_compute_static", _i, [_vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _vp])
 
@@ -194,8 +199,17 @@ def sgm_stage_times(ctx) -> dict:
     n = _lib.sgm_stage_times(ctx, buf, 10)
     if n < 0:
         raise SgmError(n, last_error(ctx))
-    npaths = _lib.sgm_stage_paths(ctx)
-    return {_lib.sgm_stage_name(npaths, i).decode(): float(buf[i]) for i in range(n)}
+    return {_lib.sgm_stage_label(ctx, i).decode(): float(buf[i]) for i in range(n)}
+
+
+def sgm_set_schedule(ctx, schedule: int) -> None:
+    """Force a 4-path sweep schedule (SGM_SCHED_*), or -1 to autotune."""
+    _check(ctx, _lib.sgm_set_schedule(ctx, schedule))
+
+
+def sgm_schedule_for(ctx, W, H, D, P1, P2, n_paths) -> int:
+    """The schedule used for this problem, or -1 when not tuned yet."""
+    return _lib.sgm_schedule_for(ctx, W, H, D, P1, P2, n_paths)
 
 
 def sgm_compute_static(left, right, W, H, D, P1, P2, n_paths, disp_out, stream=None) -> None:
