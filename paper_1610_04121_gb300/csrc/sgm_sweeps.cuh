@@ -68,8 +68,8 @@ struct ModeIO {
 // chunk the loads of the next chunk are issued, so every load has at least one
 // chunk (PF steps of the recurrence) to arrive.  PF is chosen so that the two
 // chunks of inputs held in registers stay near 96 registers.
-__host__ __device__ constexpr int prefetch_steps(int regs_per_step) {
-    return 48 / regs_per_step > 16 ? 16 : (48 / regs_per_step < 4 ? 4 : 48 / regs_per_step);
+__host__ __device__ constexpr int prefetch_steps(int regs_per_step, int budget = 48) {
+    return budget / regs_per_step > 16 ? 16 : (budget / regs_per_step < 4 ? 4 : budget / regs_per_step);
 }
 
 template <int N>
@@ -333,13 +333,14 @@ struct LaneRole {
 // count; n_other: the step count of the warp's other path (G = 16), else
 // n_own.  DBG: a winner-take-all walk also writes S in natural order to
 // a.Sdbg.
-template <int D, int MODE, bool S8, class Geo, bool DBG = false, int POST = 0>
+// PFB: the registers one chunk of prefetched inputs may take (prefetch_steps).
+template <int D, int MODE, bool S8, class Geo, bool DBG = false, int POST = 0, int PFB = 48>
 __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch, const Geo& g, int n_own,
                                      int n_other, const SweepArgs& a, int pl) {
     constexpr int G = PathShape<D>::G, K = PathShape<D>::K;
     using M = ModeIO<MODE>;
     using In = StepIn<D, MODE, S8>;
-    constexpr int PF = prefetch_steps(In::REGS);
+    constexpr int PF = prefetch_steps(In::REGS, PFB);
     const int n_min = min(n_own, n_other), n_max = max(n_own, n_other);
     const uint32_t RB = static_cast<uint32_t>(a.RB);
     const LaneBases lb = lane_bases<D>(a, pl);
@@ -551,7 +552,7 @@ __device__ __forceinline__ void load_state(Chain<G, K>& ch, const uint32_t* st) 
 // the path state), 2 = phase 2 (restoring it).  Without `pair` (2-path mode)
 // A covers the whole row and writes S = L_LR.
 // ---------------------------------------------------------------------------
-template <int D, bool PAIR, bool S8, int PH = 0, bool WTA = false, bool DBG = false, int POST = 0>
+template <int D, bool PAIR, bool S8, int PH = 0, bool WTA = false, bool DBG = false, int POST = 0, int PFB = 48>
 __device__ __forceinline__ void sweep_h_body(const SweepArgs& a, int bx) {
     constexpr int G = PathShape<D>::G, K = PathShape<D>::K;
     const LaneRole<D, PAIR> r(bx);
@@ -568,14 +569,14 @@ __device__ __forceinline__ void sweep_h_body(const SweepArgs& a, int bx) {
         const bool valid = y < a.H;
         const RowGeo g{valid ? rowbase : 0, 0, 1};
         const int n = valid ? W : 0;
-        walk<D, kSingleH, S8, RowGeo, false, POST>(ch, g, n, G == 16 ? ((y ^ 1) < a.H ? W : 0) : n, a, r.pl);
+        walk<D, kSingleH, S8, RowGeo, false, POST, PFB>(ch, g, n, G == 16 ? ((y ^ 1) < a.H ? W : 0) : n, a, r.pl);
     } else {
         const int Wm = W / 2;
         if constexpr (PH != 2) {
             const RowGeo g = in_b ? RowGeo{rowbase, W - 1, -1} : RowGeo{rowbase, 0, 1};
             const int nA = Wm, nB = W - Wm;
-            walk<D, kStoreL, S8, RowGeo, false, POST>(ch, g, in_b ? nB : nA,
-                                                      G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
+            walk<D, kStoreL, S8, RowGeo, false, POST, PFB>(ch, g, in_b ? nB : nA,
+                                                           G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
         }
         if constexpr (PH == 1) {
             save_state(ch, state_slot<D>(a, y, r.dir));
@@ -586,8 +587,8 @@ __device__ __forceinline__ void sweep_h_body(const SweepArgs& a, int bx) {
         {
             const RowGeo g = in_b ? RowGeo{rowbase, Wm - 1, -1} : RowGeo{rowbase, Wm, 1};
             const int nA = W - Wm, nB = Wm;
-            walk<D, WTA ? kWta2 : kSumH, S8, RowGeo, DBG, POST>(ch, g, in_b ? nB : nA,
-                                                              G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
+            walk<D, WTA ? kWta2 : kSumH, S8, RowGeo, DBG, POST, PFB>(
+                ch, g, in_b ? nB : nA, G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
         }
     }
 }
@@ -606,10 +607,15 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_h_kernel(SweepArgs 
     sweep_h_body<D, PAIR, S8, 0, false, false, POST>(a, blockIdx.x);
 }
 
+// Batched forms: many chains in flight, so more warps per SM (5 blocks) with
+// half the prefetch registers serve better than deep prefetch.
+constexpr int kBatchBlocksPerSM = 5, kBatchPrefetchBudget = 24;
+
 template <int D, bool PAIR, bool S8>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_h_batch_kernel(const __grid_constant__ JobTable<SweepArgs> t) {
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, kBatchBlocksPerSM)
+    sweep_h_batch_kernel(const __grid_constant__ JobTable<SweepArgs> t) {
     const int p = find_job(t, blockIdx.x);
-    sweep_h_body<D, PAIR, S8>(t.job[p], blockIdx.x - t.start[p]);
+    sweep_h_body<D, PAIR, S8, 0, false, false, 0, kBatchPrefetchBudget>(t.job[p], blockIdx.x - t.start[p]);
 }
 
 // ---------------------------------------------------------------------------
@@ -627,7 +633,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_h_batch_kernel(cons
 // instead of adding into S.  PAIR = false is the 2-path top-to-bottom sweep.
 // SUMV: a pair that does not finish with Eq. 4 writes S = L + stored L (the
 // first pair to write S) instead of adding into S.
-template <int D, int RX, int PH, bool WTA, bool PAIR, bool S8, bool DBG = false, bool SUMV = false, int POST = 0>
+template <int D, int RX, int PH, bool WTA, bool PAIR, bool S8, bool DBG = false, bool SUMV = false, int POST = 0,
+          int PFB = 48>
 __device__ __forceinline__ void sweep_v_body(const SweepArgs& a, int bx) {
     constexpr int G = PathShape<D>::G, K = PathShape<D>::K;
     const LaneRole<D, PAIR> r(bx);
@@ -642,15 +649,15 @@ __device__ __forceinline__ void sweep_v_body(const SweepArgs& a, int bx) {
     if constexpr (!PAIR) {
         const bool valid = c < W;
         const int n = valid ? H : 0;
-        walk<D, kSingleWta, S8, Geo, DBG, POST>(ch, Geo{W, H, valid ? c : 0, 0, 1}, n,
-                                                G == 16 ? ((c ^ 1) < W ? H : 0) : n, a, r.pl);
+        walk<D, kSingleWta, S8, Geo, DBG, POST, PFB>(ch, Geo{W, H, valid ? c : 0, 0, 1}, n,
+                                                     G == 16 ? ((c ^ 1) < W ? H : 0) : n, a, r.pl);
     } else {
         const int Hm = H / 2;
         if constexpr (PH != 2) {
             const Geo g = in_b ? Geo{W, H, c, H - 1, -1} : Geo{W, H, c, 0, 1};
             const int nA = Hm, nB = H - Hm;
-            walk<D, kStoreL, S8, Geo, false, POST>(ch, g, in_b ? nB : nA,
-                                                   G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
+            walk<D, kStoreL, S8, Geo, false, POST, PFB>(ch, g, in_b ? nB : nA,
+                                                        G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
         }
         if constexpr (PH == 1) {
             save_state(ch, state_slot<D>(a, c, r.dir));
@@ -661,7 +668,7 @@ __device__ __forceinline__ void sweep_v_body(const SweepArgs& a, int bx) {
             if constexpr (PH == 0) pair_barrier<D>();
             const Geo g = in_b ? Geo{W, H, c, Hm - 1, -1} : Geo{W, H, c, Hm, 1};
             const int nA = H - Hm, nB = Hm;
-            walk<D, WTA ? kWta2 : (SUMV ? kSumH : kAcc), S8, Geo, DBG, POST>(
+            walk<D, WTA ? kWta2 : (SUMV ? kSumH : kAcc), S8, Geo, DBG, POST, PFB>(
                 ch, g, in_b ? nB : nA, G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
         }
     }
@@ -675,9 +682,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_v_kernel(SweepArgs 
 
 // Batched form: both phases in one launch (PH = 0).
 template <int D, int RX, bool WTA, bool PAIR, bool S8>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_v_batch_kernel(const __grid_constant__ JobTable<SweepArgs> t) {
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, kBatchBlocksPerSM)
+    sweep_v_batch_kernel(const __grid_constant__ JobTable<SweepArgs> t) {
     const int p = find_job(t, blockIdx.x);
-    sweep_v_body<D, RX, 0, WTA, PAIR, S8>(t.job[p], blockIdx.x - t.start[p]);
+    sweep_v_body<D, RX, 0, WTA, PAIR, S8, false, false, 0, kBatchPrefetchBudget>(t.job[p], blockIdx.x - t.start[p]);
 }
 
 // The horizontal pair and the vertical-type first halves in one grid: one
