@@ -28,8 +28,10 @@
  *           match column x-d < 0 uses the feature 0; the first pixel of each
  *           path takes L_r = MC; the median copies the one-pixel border ring.
  *  Pointers "host or device": the library asks the CUDA runtime which kind a
- *           pointer is.  Host memory may be pageable or pinned (pinned is
- *           faster).  Device pointers must be on the context's device.
+ *           pointer is.  Host memory may be pageable (copied through the
+ *           context's arena) or pinned (read and written in place by the
+ *           kernels, with no separate copy).  Device pointers must be on the
+ *           context's device.
  *  Ownership the caller owns every buffer it passes; the library never frees
  *           or keeps a caller pointer beyond the call, except for
  *           sgm_submit (see there).  The library owns its context, its device

@@ -537,23 +537,32 @@ static int choose_schedule(sgm_ctx* ctx, Problem& p, uint8_t* arena, const uint8
 }
 
 // Copy-in / path / copy-out for one pair into `arena` (already large enough).
+// Device memory and pinned host memory are read and written in place by the
+// kernels (pinned host memory is mapped into the device's address space, so
+// the census reads the images and the last kernel writes the output over the
+// host link with no separate copy); pageable host memory is staged through
+// the arena with copies.
 static int enqueue_pair(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const uint8_t* left, const uint8_t* right,
                         uint8_t* disp, cudaStream_t s, bool use_graph) {
     const Layout l = layout_for(p);
     const size_t wh = static_cast<size_t>(p.W) * p.H;
+    auto in_place = [](const void* q) {
+        const cudaMemoryType t = pointer_kind(q);
+        return t == cudaMemoryTypeDevice || t == cudaMemoryTypeManaged || t == cudaMemoryTypeHost;
+    };
     const uint8_t* dl = left;
     const uint8_t* dr = right;
     uint8_t* dout = disp;
-    if (!is_device_ptr(left)) {
+    if (!in_place(left)) {
         CUDA_TRY(ctx, cudaMemcpyAsync(arena + l.in_left, left, wh, cudaMemcpyHostToDevice, s));
         dl = arena + l.in_left;
     }
-    if (!is_device_ptr(right)) {
+    if (!in_place(right)) {
         CUDA_TRY(ctx, cudaMemcpyAsync(arena + l.in_right, right, wh, cudaMemcpyHostToDevice, s));
         dr = arena + l.in_right;
     }
-    const bool out_host = !is_device_ptr(disp);
-    if (out_host) dout = arena + l.out;
+    const bool out_staged = !in_place(disp);
+    if (out_staged) dout = arena + l.out;
     if (use_graph) {
         Problem q = p;
         int rc = choose_schedule(ctx, q, arena, dl, dr, dout, s);
@@ -563,7 +572,7 @@ static int enqueue_pair(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const ui
     } else {
         CUDA_TRY(ctx, enqueue_path(ctx, p, arena, dl, dr, dout, nullptr, s, false));
     }
-    if (out_host) CUDA_TRY(ctx, cudaMemcpyAsync(disp, dout, (p.post ? 2 : 1) * wh, cudaMemcpyDeviceToHost, s));
+    if (out_staged) CUDA_TRY(ctx, cudaMemcpyAsync(disp, dout, (p.post ? 2 : 1) * wh, cudaMemcpyDeviceToHost, s));
     return SGM_OK;
 }
 

@@ -207,3 +207,39 @@ def test_batch_rejects_a_pair_over_the_cap(sgm):
         assert e.value.code == sgm.SGM_ENOMEM
     finally:
         c.close()
+
+
+def test_pinned_buffers_used_in_place(sgm):
+    import torch
+
+    # pinned host buffers are read and written in place by the kernels; a
+    # fresh context tunes first, then replays; pageable buffers beside them
+    # are staged through copies
+    p = _pair(160, 96, 64, seed=41)
+    ref = oracle.sgm(p.left, p.right, 64, 7, 84, 4)
+    Lp, Rp = torch.from_numpy(p.left).pin_memory(), torch.from_numpy(p.right).pin_memory()
+    c = sgm.Context(0)
+    try:
+        for _ in range(3):
+            op = torch.zeros((96, 160), dtype=torch.uint8).pin_memory()
+            sgm.sgm_compute(c.handle, Lp, Rp, 160, 96, 64, 7, 84, 4, op)
+            assert (op.numpy() == ref).all()
+        op = torch.zeros((96, 160), dtype=torch.uint8).pin_memory()
+        for _ in range(2):  # the same pointers twice: the second call replays the graph
+            op.zero_()
+            sgm.sgm_compute(c.handle, Lp, Rp, 160, 96, 64, 7, 84, 4, op)
+            assert (op.numpy() == ref).all()
+        out = np.zeros((96, 160), np.uint8)  # pageable output beside pinned inputs
+        sgm.sgm_compute(c.handle, Lp, Rp, 160, 96, 64, 7, 84, 4, out)
+        assert (out == ref).all()
+        Ld = torch.from_numpy(p.left).cuda()
+        sgm.sgm_compute(c.handle, Ld, Rp, 160, 96, 64, 7, 84, 4, op)  # device input beside pinned ones
+        assert (op.numpy() == ref).all()
+        ref16 = oracle.sgm_ex(p.left, p.right, 64, 7, 84, 4, oracle.POST_SUBPIXEL | oracle.POST_LR_CHECK)
+        o16 = torch.zeros((96, 160), dtype=torch.int16).pin_memory()
+        for _ in range(2):
+            sgm.sgm_compute_ex(c.handle, Lp, Rp, 160, 96, 64, 7, 84, 4,
+                               oracle.POST_SUBPIXEL | oracle.POST_LR_CHECK, o16)
+            assert (o16.numpy().view(np.uint16) == ref16).all()
+    finally:
+        c.close()
