@@ -281,6 +281,14 @@ static bool is_device_ptr(const void* p) {
     return t == cudaMemoryTypeDevice || t == cudaMemoryTypeManaged;
 }
 
+// Memory the kernels may read or write in place: device memory, and pinned
+// host memory (mapped into the device's address space); pageable host memory
+// goes through copies.
+static bool kernel_accessible(const void* p) {
+    const cudaMemoryType t = pointer_kind(p);
+    return t == cudaMemoryTypeDevice || t == cudaMemoryTypeManaged || t == cudaMemoryTypeHost;
+}
+
 // Kernels per path: census, cost, the first sweep stage (horizontal pair and
 // vertical-type first halves), the second halves of each vertical-type pair
 // (sweep_diag+, sweep_diag-, sweep_v), median; with 2 paths: census, cost,
@@ -546,10 +554,7 @@ static int enqueue_pair(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const ui
                         uint8_t* disp, cudaStream_t s, bool use_graph) {
     const Layout l = layout_for(p);
     const size_t wh = static_cast<size_t>(p.W) * p.H;
-    auto in_place = [](const void* q) {
-        const cudaMemoryType t = pointer_kind(q);
-        return t == cudaMemoryTypeDevice || t == cudaMemoryTypeManaged || t == cudaMemoryTypeHost;
-    };
+    auto in_place = kernel_accessible;
     const uint8_t* dl = left;
     const uint8_t* dr = right;
     uint8_t* dout = disp;
@@ -620,11 +625,11 @@ static int enqueue_wave(sgm_ctx* ctx, std::vector<BatchItem>& items, size_t b, s
         const Layout l = layout_for(it.p, true);
         const size_t wh = static_cast<size_t>(it.p.W) * it.p.H;
         uint8_t* base = arena + it.offset;
-        if (!is_device_ptr(it.left)) {
+        if (!kernel_accessible(it.left)) {
             CUDA_TRY(ctx, cudaMemcpyAsync(base + l.in_left, it.left, wh, cudaMemcpyHostToDevice, s));
             it.left = base + l.in_left;
         }
-        if (!is_device_ptr(it.right)) {
+        if (!kernel_accessible(it.right)) {
             CUDA_TRY(ctx, cudaMemcpyAsync(base + l.in_right, it.right, wh, cudaMemcpyHostToDevice, s));
             it.right = base + l.in_right;
         }
@@ -661,7 +666,7 @@ static int enqueue_wave(sgm_ctx* ctx, std::vector<BatchItem>& items, size_t b, s
             a.pair = it.p.n_paths >= 4;
             a.s8 = s8_for(it.p);
             st.job[k] = a;
-            uint8_t* dst = is_device_ptr(it.out) ? it.out : base + l.out;
+            uint8_t* dst = kernel_accessible(it.out) ? it.out : base + l.out;
             dt.job[k] = MedianJob{base + l.raw, dst, it.p.W, it.p.H};
         }
         const bool ct62 = items[g0].p.ct62 != 0;
@@ -685,7 +690,7 @@ static int enqueue_wave(sgm_ctx* ctx, std::vector<BatchItem>& items, size_t b, s
     // copy-out of host outputs
     for (size_t i = b; i < e; ++i) {
         const BatchItem& it = items[i];
-        if (!is_device_ptr(it.out)) {
+        if (!kernel_accessible(it.out)) {
             const Layout l = layout_for(it.p, true);
             CUDA_TRY(ctx, cudaMemcpyAsync(it.out, arena + it.offset + l.out,
                                           static_cast<size_t>(it.p.W) * it.p.H, cudaMemcpyDeviceToHost, s));
