@@ -48,49 +48,6 @@ struct U8Pairs {
     uint32_t r[(K + 1) / 2];
 };
 
-template <int K>
-__device__ __forceinline__ U8Pairs<K> ld_pairs(const uint8_t* p) {
-    U8Pairs<K> o;
-    if constexpr (K == 1) {
-        o.r[0] = *reinterpret_cast<const uint16_t*>(p);
-    } else if constexpr (K == 2) {
-        o.r[0] = *reinterpret_cast<const uint32_t*>(p);
-    } else if constexpr (K == 4) {
-        const uint2 v = *reinterpret_cast<const uint2*>(p);
-        o.r[0] = v.x;
-        o.r[1] = v.y;
-    } else if constexpr (K == 8) {
-        const uint4 v = *reinterpret_cast<const uint4*>(p);
-        o.r[0] = v.x;
-        o.r[1] = v.y;
-        o.r[2] = v.z;
-        o.r[3] = v.w;
-    } else if constexpr (K == 6) {
-        const uint32_t* q = reinterpret_cast<const uint32_t*>(p);  // 12 bytes, 4-byte aligned
-        o.r[0] = q[0];
-        o.r[1] = q[1];
-        o.r[2] = q[2];
-    } else {
-        const uint16_t* h = reinterpret_cast<const uint16_t*>(p);
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const uint32_t v = h[j];
-            if (j & 1)
-                o.r[j >> 1] |= v << 16;
-            else
-                o.r[j >> 1] = v;
-        }
-    }
-    return o;
-}
-
-// Paired bytes -> packed u16x2 words.
-template <int K>
-__device__ __forceinline__ void unpack_pairs(const U8Pairs<K>& b, uint32_t (&w)[K]) {
-#pragma unroll
-    for (int j = 0; j < K; ++j) w[j] = __byte_perm(b.r[j >> 1], 0u, (j & 1) ? 0x4342u : 0x4140u);
-}
-
 // Packed u16x2 words (each lane <= 255) -> paired bytes.
 template <int K>
 __device__ __forceinline__ U8Pairs<K> pack_pairs(const uint32_t (&w)[K]) {
@@ -124,32 +81,6 @@ __device__ __forceinline__ void st_pairs(uint8_t* p, const U8Pairs<K>& o) {
         uint16_t* h = reinterpret_cast<uint16_t*>(p);
 #pragma unroll
         for (int j = 0; j < K; ++j) h[j] = static_cast<uint16_t>((j & 1) ? (o.r[j >> 1] >> 16) : o.r[j >> 1]);
-    }
-}
-
-template <int K>
-__device__ __forceinline__ void ld_words(const uint32_t* p, uint32_t (&w)[K]) {
-    if constexpr (K == 1) {
-        w[0] = p[0];
-    } else if constexpr (K % 4 == 0) {
-#pragma unroll
-        for (int j = 0; j < K; j += 4) {
-            const uint4 v = *reinterpret_cast<const uint4*>(p + j);
-            w[j] = v.x;
-            w[j + 1] = v.y;
-            w[j + 2] = v.z;
-            w[j + 3] = v.w;
-        }
-    } else if constexpr (K % 2 == 0) {
-#pragma unroll
-        for (int j = 0; j < K; j += 2) {
-            const uint2 v = *reinterpret_cast<const uint2*>(p + j);
-            w[j] = v.x;
-            w[j + 1] = v.y;
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < K; ++j) w[j] = p[j];
     }
 }
 
