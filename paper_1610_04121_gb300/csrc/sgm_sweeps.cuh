@@ -14,7 +14,8 @@
 // Each lane streams its own bytes of every step's inputs (costs, the other
 // direction's stored L_r, sums) straight from global memory into registers,
 // one chunk of PF steps ahead of the recurrence, and writes its outputs with
-// one coalesced store per step; no shared memory is used.  All cubes of a
+// one coalesced store per step; no shared memory is used (but for the post
+// form's 256-entry penalty table).  All cubes of a
 // pair live in one array of per-pixel records (sgm_internal.h), so a step's
 // loads and stores share one 32-bit record offset, widened onto per-lane
 // bases with one mad.wide (on the FMA pipe, off the busy integer ALU).
@@ -24,11 +25,17 @@
 //   sweep_v : top-to-bottom with bottom-to-top along columns (RX = 0) or along
 //             the wrapped diagonals of Section 3.2 (RX = +1 / -1); either adds
 //             its pair sum into S or, for the last axis, finishes with Eq. 4.
+//   sweep_first4 / sweep_h2 : the 4-path schedule that runs the whole
+//             vertical pair beside the horizontal first halves, then the
+//             horizontal second halves with Eq. 4.
+//   post form (POST = 1): every step takes its jump penalty from the base
+//             image (adaptive P2), and the winner-take-all walks also write
+//             the sums beside the winner for the sub-pixel step.
 //
 // S is kept either as packed u16x2 words [H][W][D/2] or, when every value it
 // holds before the winner-take-all fits a byte (2 or 4 paths with
-// 2 * (31 + P2) <= 255, see sum_fits_u8), as paired bytes [H][W][D] like the
-// costs (template flag S8).
+// 2 * (MC_max + P2) <= 255, see sum_fits_u8), as paired bytes [H][W][D] like
+// the costs (template flag S8).
 #pragma once
 
 #include "sgm_device.cuh"
