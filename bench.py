@@ -83,6 +83,9 @@ def parse():
     ap.add_argument("--post", type=int, default=0,
                     help="post-filters of sgm_compute_ex (1 sub-pixel | 2 LR check | 4 adaptive P2); "
                          "times that entry point instead of the plain path")
+    ap.add_argument("--inflight", type=int, default=1,
+                    help="frames in flight: N contexts on N streams take the steps in turn (a video stream's "
+                         "throughput); 1 is the headline, one frame at a time")
     ap.add_argument("--schedule", type=int, default=-1,
                     help="4-path sweep schedule (0 vertical pair first, 1 horizontal pair first); "
                          "-1 lets the library autotune it (the default)")
@@ -323,6 +326,84 @@ def run_post_bench(args, w, ws, rank, local):
     return 0
 
 
+def run_inflight_bench(args, w, ws, rank, local):
+    """Frames of one shape in flight together: context i (own stream, own
+    arena, own pair) takes steps i, i + N, ...; the K steps are timed as one
+    region from the first stream's start to the last stream's end.  Each
+    frame's records (about 200 MB at 640x480x128) exceed L2, and the frames
+    in flight use different pairs and arenas."""
+    import torch
+    from paper_1610_04121_gb300 import sgm
+
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+        pg = dist
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W, H, D, N = w.spec.W, w.spec.H, w.spec.D, args.inflight
+    lanes = []
+    for i in range(N):
+        pair = synth.make_pair(w.spec, synth.BASE_SEED + synth.WORKLOAD_INDEX[w.name] + 7919 * rank + 101 * i)
+        L = torch.from_numpy(pair.left).to(dev)
+        R = torch.from_numpy(pair.right).to(dev)
+        out = torch.empty((H, W), dtype=torch.uint8, device=dev)
+        st = torch.cuda.Stream(dev)
+        c = sgm.Context(local)
+        sgm.sgm_set_stream(c.handle, st)
+        if args.schedule >= 0:
+            sgm.sgm_set_schedule(c.handle, args.schedule)
+        lanes.append((c, st, L, R, out))
+
+    def step(k):
+        c, st, L, R, out = lanes[k % N]
+        sgm.sgm_compute_async(c.handle, L, R, W, H, D, w.P1, w.P2, w.n_paths, out)
+
+    for k in range(max(args.warmup, 3) * N):
+        step(k)
+    torch.cuda.synchronize(dev)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(N)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(N)]
+    launches0 = sum(l[0].launches for l in lanes)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for i in range(N):
+            ev0[i].record(lanes[i][1])
+        for k in range(args.steps):
+            step(k)
+        for i in range(N):
+            ev1[i].record(lanes[i][1])
+        torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    launches = sum(l[0].launches for l in lanes) - launches0
+    # the region from the earliest start to the latest end over the streams
+    t_ms = max(ev0[0].elapsed_time(ev1[i]) for i in range(N)) - min(ev0[0].elapsed_time(ev0[i]) for i in range(N))
+    total_ms = max_over_ranks(t_ms, pg, dev)
+    ms_per_step = total_ms / args.steps
+    value = job_mdes(ws, args.steps, W * H * D, total_ms)
+    if rank == 0:
+        line = {
+            "metric": "MDE/s", "value": value, "unit": "MDE/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u16", "data": "synthetic (seeded stereo_synth pairs, resident in HBM)",
+            "config": dict(workload_config(w, args), parallelism=f"replicas x{ws}", frames_in_flight=N,
+                           l2="records of each frame (~200 MB at 640x480x128) exceed L2; frames in flight use "
+                              "different pairs and arenas", fps=1e3 / ms_per_step),
+            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clk.summary(),
+        }
+        print(json.dumps(line))
+    for l in lanes:
+        l[0].close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
 def run_batch_bench(args, ws, rank, local):
     """64 uneven pairs per step through sgm_compute_batch, against the same
     pairs as plain per-pair launches (sgm_compute_async, one after another)."""
@@ -541,6 +622,8 @@ def main():
         return run_reference(args, w, ws, rank)
     if args.post:
         return run_post_bench(args, w, ws, rank, local)
+    if args.inflight > 1:
+        return run_inflight_bench(args, w, ws, rank, local)
 
     import torch
 
