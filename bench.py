@@ -524,7 +524,8 @@ def run_served_bench(args, ws, rank, local):
         pg = dist
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    recipe = synth.batch_recipe(64, config=4)
+    # sizes and D as the batch; 8 paths with P1 = 10, P2 = 120 ("up to 1920x1080 with D up to 256 and 8 paths")
+    recipe = synth.batch_recipe(64, config=4, paths=(8,), P1=10, P2=120)
     pool = []
     for i, w in enumerate(recipe):
         p = synth.make_pair(w.spec, synth.BASE_SEED + 4000 + i + 7919 * rank)
@@ -589,7 +590,8 @@ def run_served_bench(args, ws, rank, local):
             "ms_per_step": wall * 1e3 / max(n, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u16", "data": "synthetic (seeded stereo_synth pairs, pinned host buffers)",
             "config": {"workload": "served", "arrival_rate_hz": args.rate, "duration_s": args.duration,
-                       "requests": n, "pool": "64 pairs: 320x240/640x480/1242x375/1920x1080, D 64/128/256, 4 or 8 paths",
+                       "requests": n,
+                       "pool": "64 pairs: 320x240/640x480/1242x375/1920x1080, D 64/128/256, 8 paths, P1 = 10, P2 = 120",
                        "offered_mdes": de / args.duration / 1e6, "step": "one request",
                        "parallelism": f"replicas x{ws}", "l2": "inputs and buffers far exceed L2",
                        "plain_per_pair_mdes": plain, "served_over_plain": value / plain if plain else None},
