@@ -49,6 +49,9 @@ SERVED_OUT_RING = 4  # output buffers per pool pair (a pair can be in flight mor
 MEASURED_TRAFFIC = {
     ("sgm_640x480_d128_p4", "sweep_v+h1"): (148489984, "491a94ead9f28c1f"),
     ("sgm_640x480_d128_p4", "sweep_h2"): (119061120, "491a94ead9f28c1f"),
+    ("sgm_1242x375_d128_p8", "sweep_h"): (586146816, "491a94ead9f28c1f"),
+    ("sgm_1242x375_d128_p8", "sweep_diag+"): (311648768, "491a94ead9f28c1f"),
+    ("sgm_1242x375_d128_p8", "sweep_v"): (241617152, "491a94ead9f28c1f"),
 }
 KERNEL_SOURCES = ("sgm_sweeps.cuh", "sgm_device.cuh", "sgm_internal.h")
 
@@ -744,6 +747,20 @@ def main():
                 "ops_per_launch": ops}
     frame_bytes = 2 * W * H + W * H + 4 * de
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    if w.n_paths == 8:
+        # u16 sums: the sweeps move more bytes than their arithmetic can hide.
+        # Algorithmic bytes per DE of each launch: the first stage reads MC
+        # twice for the horizontal pair and once per vertical-type pair, stores
+        # and reloads the horizontal stored L_r, stores the three vertical-type
+        # ones and writes S (u16); each diagonal second half reads MC and its
+        # stored L_r and reads and writes S; the vertical one reads all three.
+        bytes_per_de = {"sweep_h": 12, "sweep_diag+": 6, "sweep_diag-": 6, "sweep_v": 4}
+        alg = de * bytes_per_de[dom]
+        gbs = alg / (mean_stage[dom] / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                    "traffic": traffic,
+                    "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+                    "algorithmic_bytes_per_launch": alg, "peak_source": f"{peak_kind} hbm_gbs"}
     frame_gbs = frame_bytes / (ms_per_step / 1e3) / 1e9
     frame_roofline = {"bound": "hbm", "achieved": frame_gbs, "peak": hbm, "unit": "GB/s", "frac": frame_gbs / hbm,
                       "algorithmic_bytes_per_frame": frame_bytes, "peak_source": f"{peak_kind} hbm_gbs"}
