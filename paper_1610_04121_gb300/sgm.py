@@ -255,7 +255,9 @@ class Context:
         return out
 
     def compute_ex(self, left, right, D, P1, P2, n_paths, post=0, out=None):
-        """Disparity in 1/16 pixel with post-filters (uint16; numpy or torch)."""
+        """Disparity in 1/16 pixel with post-filters: numpy in -> uint16 out;
+        torch in -> an int16 tensor holding the uint16 values (SGM_DISP16_INVALID
+        reads as -1; view it as uint16 through numpy)."""
         H, W = left.shape
         if out is None:
             if hasattr(left, "data_ptr") and hasattr(left, "device"):
