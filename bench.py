@@ -90,7 +90,7 @@ def parse():
                     help="frames in flight: N contexts on N streams take the steps in turn (a video stream's "
                          "throughput); 1 is the headline, one frame at a time")
     ap.add_argument("--schedule", type=int, default=-1,
-                    help="4-path sweep schedule (0 vertical pair first, 1 horizontal pair first); "
+                    help="4-path sweep schedule (0 vertical pair first, 1 horizontal pair first, 2 paired lines); "
                          "-1 lets the library autotune it (the default)")
     ap.add_argument("--census", default="csct", choices=["csct", "full"],
                     help="features: the CSCT of Eq. 1 or the full 9x7 Census (SGM_FLAG_CENSUS_FULL)")
@@ -727,9 +727,15 @@ def main():
     if w.n_paths == 2:
         kernel_stages = {"sweep_h": (1, 0), "sweep_v": (1, 2)}
     elif w.n_paths == 4:
-        # either schedule: the whole first pair beside the other pair's first
-        # halves, then that pair's second halves with the winner-take-all
-        kernel_stages = {"sweep_v+h1": (3, 1), "sweep_h2": (1, 3), "sweep_h+v1": (3, 1), "sweep_v2": (1, 3)}
+        # the first two schedules: the whole first pair beside the other pair's
+        # first halves, then that pair's second halves with the winner-take-all;
+        # the paired-line schedule: the whole vertical pair beside n1 = min(W2, H2)
+        # steps of each horizontal direction, then the rest of the horizontal
+        # directions, and the sums and the minimum of every pixel
+        W2, H2 = W + (W & 1), H + (H & 1)
+        f1 = min(W2, H2) / W2
+        kernel_stages = {"sweep_v+h1": (3, 1), "sweep_h2": (1, 3), "sweep_h+v1": (3, 1), "sweep_v2": (1, 3),
+                         "pairs_vh": (2 + 2 * f1, 1), "pairs_h_wta": (2 * (1 - f1), 3)}
     else:
         kernel_stages = {"sweep_h": (2 + (w.n_paths - 2) // 2, 1), "sweep_v": (1, 3), "sweep_diag+": (1, 2),
                          "sweep_diag-": (1, 2)}
@@ -798,7 +804,7 @@ def main():
             "vs_baseline": None, "dtype": "u16", "data": "synthetic (seeded stereo_synth pair, resident in HBM)",
             "config": dict(workload_config(w, args), parallelism=f"replicas x{ws}",
                            l2="flushed between timed steps (256 MiB write)", fps=1e3 / ms_per_step,
-                           sweep_schedule={0: "V_THEN_H", 1: "H_THEN_V"}.get(sched, str(sched))
+                           sweep_schedule={0: "V_THEN_H", 1: "H_THEN_V", 2: "PAIRS"}.get(sched, str(sched))
                            + (" (autotuned)" if w.n_paths == 4 and args.schedule < 0 else "")),
             "roofline": roofline, "frame_roofline": frame_roofline,
             "stage_ms": {k: round(v, 5) for k, v in mean_stage.items()},

@@ -277,27 +277,38 @@ SGM_API int sgm_stage_paths(const sgm_ctx *ctx);
 
 /* Name of stage i of the path that sgm_stage_times reports on (it follows
  * that path's sweep schedule: with SGM_SCHED_H_THEN_V the 4-path sweeps are
- * sweep_h+v1, sweep_v2), or NULL. */
+ * sweep_h+v1, sweep_v2; with SGM_SCHED_PAIRS pairs_vh, pairs_h_wta), or NULL. */
 SGM_API const char *sgm_stage_label(const sgm_ctx *ctx, int i);
 
 /*
- * Sweep schedules of the 4-path plain path (sgm_compute, sgm_compute_async):
+ * Sweep schedules of the 4-path plain path (sgm_compute, sgm_compute_async;
+ * Eq. 3 along the four paths of Section 4, then Eq. 4):
  *   SGM_SCHED_V_THEN_H  the whole vertical pair (writing S) beside the first
  *                       halves of the horizontal pair, then the horizontal
  *                       second halves with the winner-take-all;
  *   SGM_SCHED_H_THEN_V  the whole horizontal pair beside the vertical first
  *                       halves, then the vertical second halves with the
- *                       winner-take-all.
- * Both give bit-identical results.  By default the context autotunes: the
+ *                       winner-take-all;
+ *   SGM_SCHED_PAIRS     two lines per warp over 2 x 2 pixel quads: the whole
+ *                       vertical pair beside min(W, H) steps of each
+ *                       horizontal direction, then the rest of the
+ *                       horizontal directions with the winner-take-all
+ *                       beside a parallel winner-take-all over the columns
+ *                       both horizontal directions passed (the longest
+ *                       chain is max(W, H) steps).  Not offered when its
+ *                       quad records would pass 4 GiB.
+ * All give bit-identical results.  By default the context autotunes: the
  * first call for a new (W, H, D, Census type, byte-sum) key runs the path
- * with each schedule (once to warm up, twice timed with CUDA events on the
- * context's stream; that call blocks meanwhile) and keeps the faster one for
- * the key; a stream under capture is not tuned (the first schedule is used).
- * sgm_set_schedule(ctx, s) forces schedule s; -1 restores autotuning.
+ * with each schedule (once to warm up, then five times timed with CUDA
+ * events on the context's stream; that call blocks meanwhile) and keeps the
+ * one with the lowest median for the key; a stream under capture is not
+ * tuned (the first schedule is used).  sgm_set_schedule(ctx, s) forces
+ * schedule s; -1 restores autotuning.
  * Errors: SGM_EINVAL (null context, unknown schedule).
  */
 #define SGM_SCHED_V_THEN_H 0
 #define SGM_SCHED_H_THEN_V 1
+#define SGM_SCHED_PAIRS 2
 SGM_API int sgm_set_schedule(sgm_ctx *ctx, int schedule);
 
 /* The schedule the context uses for this problem: the forced one, the tuned

@@ -31,8 +31,10 @@ inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 struct Layout {
     size_t Fb, Fm, rec, raw, state, in_left, in_right, out, total;
     size_t sub, rawR, ml, mr;  // post-filters (sgm_compute_ex) only
-    int RB;    // bytes per pixel record (sgm_internal.h): MC, S (room for u16 words), stored L_r fields
+    int RB;    // bytes per pixel record (sgm_internal.h): MC, S (room for u16 words), stored L_r fields;
+               // the paired-line schedule: bytes of one quad in a cube (4D)
     int n_lx;  // stored-L_r fields per record
+    size_t fs = 0;  // the paired-line schedule: bytes of one cube array
 };
 
 // Stored-L_r fields: one per pair of opposite paths whose first halves run
@@ -87,6 +89,7 @@ struct Problem {
     int ct62 = 0;  // features: 0 = CSCT (Eq. 1), 1 = the full 9x7 Census (SGM_FLAG_CENSUS_FULL)
     int post = 0;  // 0: the plain path (u8 output); else kPostOut16 | the SGM_POST_* flags of sgm_compute_ex
     int sched = 0;  // 4-path sweep schedule (SGM_SCHED_*)
+    int n1 = -1;    // SGM_SCHED_PAIRS: horizontal steps in the first launch (-1: the default)
 };
 
 // Set on every sgm_compute_ex problem: the post form with uint16 output, even
@@ -102,9 +105,74 @@ inline int p2_max(const Problem& p) { return (p.post & SGM_POST_ADAPTIVE_P2) ? s
 // S kept as bytes between the sweeps (sum_fits_u8 for this problem).
 inline bool s8_for(const Problem& p) { return sum_fits_u8(p.n_paths, p2_max(p), mc_max(p)); }
 
-Layout layout_for(const Problem& p, bool batched = false) {
+// The paired-line schedule (SGM_SCHED_PAIRS) of a 4-path plain problem.
+inline bool pairs_sched(const Problem& p) { return p.n_paths == 4 && !p.post && p.sched == SGM_SCHED_PAIRS; }
+
+// Its 32-bit quad offsets (q * 4D) must stay below 4 GiB.
+inline bool pairs_fit(const Problem& p) {
+    const double W2 = p.W + (p.W & 1), H2 = p.H + (p.H & 1);
+    return W2 * H2 * p.D < 4294967296.0;
+}
+
+// The quad cubes (one array of FS bytes per field), the quad raw disparity
+// and the horizontal chains' state (sgm_internal.h); `RB` holds the bytes of
+// one quad in a field (4D).
+Layout layout_pairs(const Problem& p) {
+    const PairsArgs g = pairs_geometry(p.W, p.H, p.D, p.n1);
+    const size_t wh = static_cast<size_t>(p.W) * p.H, quads = static_cast<size_t>(g.QW) * g.QH;
+    const size_t fbytes = p.ct62 ? 8 : 4;
+    Layout l{};
+    l.RB = 4 * p.D;
+    l.fs = align_up(quads * static_cast<size_t>(l.RB));
+    l.n_lx = 0;
+    size_t o = 0;
+    l.Fb = o;
+    o = align_up(o + fbytes * wh);
+    l.Fm = o;
+    o = align_up(o + fbytes * wh);
+    l.rec = o;
+    o = align_up(o + pairs_fields(s8_for(p)) * l.fs);
+    l.raw = o;
+    o = align_up(o + 4 * quads);
+    l.state = o;
+    o = align_up(o + 4 * static_cast<size_t>(g.QH) * 2 * 32 * (p.D / 32 + 1));
+    l.in_left = o;
+    o = align_up(o + wh);
+    l.in_right = o;
+    o = align_up(o + wh);
+    l.out = o;
+    o = align_up(o + wh);
+    l.total = o;
+    return l;
+}
+
+Layout schedule_layout(const Problem& p, bool batched) {
+    if (!batched && pairs_sched(p)) return layout_pairs(p);
     return layout_for(p.W, p.H, p.D, p.n_paths, batched, p.ct62 != 0, p.post != 0);
 }
+
+// A 4-path plain problem may run any schedule (the tuner tries each on the
+// same staged inputs): its staging buffers (in_left, in_right, out) sit past
+// the working region of every schedule, so one arena serves them all.
+Layout layout_for(const Problem& p, bool batched = false) {
+    Layout l = schedule_layout(p, batched);
+    if (batched || p.n_paths != 4 || p.post) return l;
+    size_t base = 0;
+    for (int s = 0; s <= SGM_SCHED_PAIRS; ++s) {
+        Problem q = p;
+        q.sched = s;
+        if (s == SGM_SCHED_PAIRS && !pairs_fit(q)) continue;
+        base = std::max(base, schedule_layout(q, false).in_left);
+    }
+    const size_t wh = static_cast<size_t>(p.W) * p.H;
+    l.in_left = base;
+    l.in_right = align_up(base + wh);
+    l.out = align_up(l.in_right + wh);
+    l.total = align_up(l.out + wh);
+    return l;
+}
+
+size_t arena_need(const Problem& p) { return layout_for(p).total; }
 
 bool valid_problem(const Problem& p, std::string* why) {
     char buf[160];
@@ -138,8 +206,8 @@ struct GraphKey {
     Problem p;
     const void *left, *right, *out, *arena;
     bool operator<(const GraphKey& o) const {
-        return std::tie(p.W, p.H, p.D, p.P1, p.P2, p.n_paths, p.ct62, p.post, p.sched, left, right, out, arena) <
-               std::tie(o.p.W, o.p.H, o.p.D, o.p.P1, o.p.P2, o.p.n_paths, o.p.ct62, o.p.post, o.p.sched, o.left,
+        return std::tie(p.W, p.H, p.D, p.P1, p.P2, p.n_paths, p.ct62, p.post, p.sched, p.n1, left, right, out, arena) <
+               std::tie(o.p.W, o.p.H, o.p.D, o.p.P1, o.p.P2, o.p.n_paths, o.p.ct62, o.p.post, o.p.sched, o.p.n1, o.left,
                         o.right, o.out, o.arena);
     }
 };
@@ -315,6 +383,29 @@ static cudaError_t enqueue_match(const Problem& p, const Layout& l, uint8_t* are
     cudaError_t e;
     if ((e = launch_census(base, match, Fb, Fm, p.W, p.H, p.ct62 != 0, s)) != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;
+    if (pairs_sched(p)) {
+        // two lines per warp over quad records: the vertical pair beside the
+        // first n1 steps of each horizontal direction, then the horizontal
+        // rest with Eq. 4 beside the parallel winner-take-all; raw in quads
+        if ((e = launch_cost_quads(Fb, Fm, arena + l.rec, l.RB, p.W, p.H, p.D, p.ct62 != 0, s)) != cudaSuccess)
+            return e;
+        if ((e = mark()) != cudaSuccess) return e;
+        PairsArgs g = pairs_geometry(p.W, p.H, p.D, p.n1);
+        g.rec = arena + l.rec;
+        g.rawq = raw;
+        g.Sdbg = Sdbg;
+        g.state = reinterpret_cast<uint32_t*>(arena + l.state);
+        g.QB = l.RB;
+        g.FS = l.fs;
+        g.P1x2 = static_cast<uint32_t>(p.P1) * 0x10001u;
+        g.P2x2 = static_cast<uint32_t>(p.P2) * 0x10001u;
+        g.s8 = s8_for(p) ? 1 : 0;
+        g.mc_max = mc_max(p);
+        if ((e = launch_pairs_stage1(g, s)) != cudaSuccess) return e;
+        if ((e = mark()) != cudaSuccess) return e;
+        if ((e = launch_pairs_stage2(g, s)) != cudaSuccess) return e;
+        return mark();
+    }
     if ((e = launch_cost(Fb, Fm, arena + l.rec, l.RB, p.W, p.H, p.D, p.ct62 != 0, s)) != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;
     SweepArgs a{};
@@ -436,7 +527,9 @@ static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, 
     if (!p.post) {
         if ((e = enqueue_match(p, l, arena, left, right, arena + l.raw, nullptr, Sdbg, s, mark)) != cudaSuccess)
             return e;
-        if ((e = launch_median(arena + l.raw, disp, p.W, p.H, s)) != cudaSuccess) return e;
+        e = pairs_sched(p) ? launch_median_quads(arena + l.raw, disp, p.W, p.H, s)
+                           : launch_median(arena + l.raw, disp, p.W, p.H, s);
+        if (e != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
     } else {
         uint32_t* sub = (p.post & SGM_POST_SUBPIXEL) ? reinterpret_cast<uint32_t*>(arena + l.sub) : nullptr;
@@ -498,18 +591,20 @@ static int enqueue_graph(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const u
     return SGM_OK;
 }
 
-// The 4-path sweep schedule of a plain-path problem: forced, or the faster of
-// the two measured on the first use of its (W, H, D, Census, byte sums) key.
-// Tuning runs the whole path (into the caller's output, which every schedule
-// computes bit-identically) once per schedule to warm up and twice timed with
-// events on `s`; the minimum decides.  A stream under capture cannot be
-// timed: there the default schedule is used untuned.
+// The 4-path sweep schedule of a plain-path problem: forced, or the fastest of
+// the kSchedules measured on the first use of its (W, H, D, Census, byte sums)
+// key.  Tuning runs the whole path (into the caller's output, which every
+// schedule computes bit-identically) once per schedule to warm up and
+// kTuneReps times timed with events on `s`; the median decides.  A stream
+// under capture cannot be timed: there the default schedule is used untuned.
+constexpr int kSchedules = 3, kTuneReps = 5;
 static int choose_schedule(sgm_ctx* ctx, Problem& p, uint8_t* arena, const uint8_t* left, const uint8_t* right,
                            uint8_t* disp, cudaStream_t s) {
     p.sched = SGM_SCHED_V_THEN_H;
     if (p.n_paths != 4 || p.post) return SGM_OK;
     if (ctx->forced_sched >= 0) {
         p.sched = ctx->forced_sched;
+        if (pairs_sched(p) && !pairs_fit(p)) p.sched = SGM_SCHED_V_THEN_H;  // quad records would pass 4 GiB
         return SGM_OK;
     }
     const auto key = std::make_tuple(p.W, p.H, p.D, p.n_paths, p.ct62, s8_for(p));
@@ -521,25 +616,30 @@ static int choose_schedule(sgm_ctx* ctx, Problem& p, uint8_t* arena, const uint8
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CUDA_TRY(ctx, cudaStreamIsCapturing(s, &cs));
     if (cs != cudaStreamCaptureStatusNone) return SGM_OK;
-    float best_ms[2] = {0.f, 0.f};
-    for (int sched = 0; sched < 2; ++sched) {
+    float best_ms = 0.f;
+    int best = -1;
+    for (int sched = 0; sched < kSchedules; ++sched) {
         Problem q = p;
         q.sched = sched;
+        if (sched == SGM_SCHED_PAIRS && !pairs_fit(q)) continue;
         int rc = enqueue_graph(ctx, q, arena, left, right, disp, s);  // captures the graph; warm-up
         if (rc != SGM_OK) return rc;
-        float best = 1e30f;
-        for (int rep = 0; rep < 2; ++rep) {
+        float ms[kTuneReps];
+        for (int rep = 0; rep < kTuneReps; ++rep) {
             CUDA_TRY(ctx, cudaEventRecord(ctx->tune_ev[0], s));
             if ((rc = enqueue_graph(ctx, q, arena, left, right, disp, s)) != SGM_OK) return rc;
             CUDA_TRY(ctx, cudaEventRecord(ctx->tune_ev[1], s));
             CUDA_TRY(ctx, cudaEventSynchronize(ctx->tune_ev[1]));
-            float ms = 0.f;
-            CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->tune_ev[0], ctx->tune_ev[1]));
-            best = std::min(best, ms);
+            CUDA_TRY(ctx, cudaEventElapsedTime(&ms[rep], ctx->tune_ev[0], ctx->tune_ev[1]));
         }
-        best_ms[sched] = best;
+        std::sort(ms, ms + kTuneReps);
+        const float med = ms[kTuneReps / 2];
+        if (best < 0 || med < best_ms) {
+            best = sched;
+            best_ms = med;
+        }
     }
-    p.sched = best_ms[1] < best_ms[0] ? SGM_SCHED_H_THEN_V : SGM_SCHED_V_THEN_H;
+    p.sched = best;
     ctx->tuned.emplace(key, p.sched);
     return SGM_OK;
 }
@@ -1099,7 +1199,7 @@ int sgm_compute(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, 
     int rc = check_args(ctx, p, left, right, disp_out);
     if (rc != SGM_OK) return rc;
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-    rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, layout_for(p).total, true);
+    rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, arena_need(p), true);
     if (rc != SGM_OK) return rc;
     rc = enqueue_pair(ctx, p, ctx->arena, left, right, disp_out, ctx->stream, true);
     if (rc != SGM_OK) return rc;
@@ -1130,7 +1230,7 @@ int sgm_compute_async(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, i
     if (!is_device_ptr(left) || !is_device_ptr(right) || !is_device_ptr(disp_out))
         return fail(ctx, SGM_EINVAL, "sgm_compute_async takes device pointers only");
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-    rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, layout_for(p).total, true);
+    rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, arena_need(p), true);
     if (rc != SGM_OK) return rc;
     Problem q = p;
     rc = choose_schedule(ctx, q, ctx->arena, left, right, disp_out, ctx->stream);
@@ -1249,14 +1349,16 @@ int sgm_debug_stages(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, in
     int rc = check_args(ctx, p, left, right, left);
     if (rc != SGM_OK) return rc;
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    if (pairs_sched(p) && !pairs_fit(p)) return fail(ctx, SGM_EINVAL, "problem too large for the paired schedule");
     const Layout l = layout_for(p);
     const size_t wh = static_cast<size_t>(W) * H;
-    const size_t extra = align_up(wh * D * 2) + align_up(wh * D);
+    const size_t extra = align_up(wh * D * 2) + align_up(wh * D) + align_up(wh);
     rc = ensure_arena(ctx, &ctx->arena, &ctx->arena_bytes, l.total + extra, true);
     if (rc != SGM_OK) return rc;
     uint8_t* a = ctx->arena;
     uint16_t* Sdev = reinterpret_cast<uint16_t*>(a + l.total);
     uint8_t* MCnat = a + l.total + align_up(wh * D * 2);
+    uint8_t* rawnat = MCnat + align_up(wh * D);
     cudaStream_t s = ctx->stream;
     CUDA_TRY(ctx, cudaMemcpyAsync(a + l.in_left, left, wh, cudaMemcpyHostToDevice, s));
     CUDA_TRY(ctx, cudaMemcpyAsync(a + l.in_right, right, wh, cudaMemcpyHostToDevice, s));
@@ -1265,11 +1367,20 @@ int sgm_debug_stages(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, in
     if (Fb) CUDA_TRY(ctx, cudaMemcpyAsync(Fb, a + l.Fb, fbytes, cudaMemcpyDeviceToHost, s));
     if (Fm) CUDA_TRY(ctx, cudaMemcpyAsync(Fm, a + l.Fm, fbytes, cudaMemcpyDeviceToHost, s));
     if (MC) {
-        CUDA_TRY(ctx, launch_unpair_cost(a + l.rec, l.RB, MCnat, W, H, D, s));
+        if (pairs_sched(p))
+            CUDA_TRY(ctx, launch_unquad_cost(a + l.rec, l.RB, MCnat, W, H, D, s));
+        else
+            CUDA_TRY(ctx, launch_unpair_cost(a + l.rec, l.RB, MCnat, W, H, D, s));
         CUDA_TRY(ctx, cudaMemcpyAsync(MC, MCnat, wh * D, cudaMemcpyDeviceToHost, s));
     }
     if (S) CUDA_TRY(ctx, cudaMemcpyAsync(S, Sdev, 2 * wh * D, cudaMemcpyDeviceToHost, s));
-    if (raw) CUDA_TRY(ctx, cudaMemcpyAsync(raw, a + l.raw, wh, cudaMemcpyDeviceToHost, s));
+    if (raw && pairs_sched(p)) {
+        // quads of bytes: the cost unquad with one "disparity" per pixel
+        CUDA_TRY(ctx, launch_unquad_cost(a + l.raw, 4, rawnat, W, H, 1, s));
+        CUDA_TRY(ctx, cudaMemcpyAsync(raw, rawnat, wh, cudaMemcpyDeviceToHost, s));
+    } else if (raw) {
+        CUDA_TRY(ctx, cudaMemcpyAsync(raw, a + l.raw, wh, cudaMemcpyDeviceToHost, s));
+    }
     if (disp) CUDA_TRY(ctx, cudaMemcpyAsync(disp, a + l.out, wh, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(ctx, cudaStreamSynchronize(s));
     return SGM_OK;
@@ -1293,12 +1404,16 @@ const char* sgm_stage_label(const sgm_ctx* ctx, int i) {
         static const char* four_hv[] = {"census", "cost", "sweep_h+v1", "sweep_v2", "median"};
         return (i >= 0 && i < 5) ? four_hv[i] : nullptr;
     }
+    if (ctx->last_n_paths == 4 && ctx->last_sched == SGM_SCHED_PAIRS) {
+        static const char* four_pairs[] = {"census", "cost", "pairs_vh", "pairs_h_wta", "median"};
+        return (i >= 0 && i < 5) ? four_pairs[i] : nullptr;
+    }
     return sgm_stage_name(ctx->last_n_paths, i);
 }
 
 int sgm_set_schedule(sgm_ctx* ctx, int schedule) {
     if (!ctx) return fail(nullptr, SGM_EINVAL, "null context");
-    if (schedule < -1 || schedule > SGM_SCHED_H_THEN_V) return fail(ctx, SGM_EINVAL, "unknown schedule %d", schedule);
+    if (schedule < -1 || schedule > SGM_SCHED_PAIRS) return fail(ctx, SGM_EINVAL, "unknown schedule %d", schedule);
     ctx->forced_sched = schedule;
     return SGM_OK;
 }
@@ -1371,10 +1486,30 @@ cudaError_t static_scratch_for_current_device(uint8_t** out) {
     return cudaSuccess;
 }
 
+// What the allocation-free path touches: features, records with one stored-L_r
+// field (every pair runs both phases in one launch) and the raw disparity.
+Layout static_layout(const Problem& p) {
+    const size_t wh = static_cast<size_t>(p.W) * p.H;
+    Layout l{};
+    l.n_lx = p.n_paths == 2 ? 0 : 1;
+    l.RB = record_bytes(p.D, false, l.n_lx);
+    size_t o = 0;
+    l.Fb = o;
+    o = align_up(o + 4 * wh);
+    l.Fm = o;
+    o = align_up(o + 4 * wh);
+    l.rec = o;
+    o = align_up(o + wh * static_cast<size_t>(l.RB));
+    l.raw = o;
+    o = align_up(o + wh);
+    l.total = o;
+    return l;
+}
+
 // The path of Section 2, stages 2-4, with every phase on one stream.
 cudaError_t enqueue_path_static(const Problem& p, uint8_t* arena, const uint8_t* left, const uint8_t* right,
                                 uint8_t* disp, cudaStream_t s) {
-    const Layout l = layout_for(p);
+    const Layout l = static_layout(p);
     void* Fb = arena + l.Fb;
     void* Fm = arena + l.Fm;
     cudaError_t e;
@@ -1421,7 +1556,7 @@ extern "C" int sgm_compute_static(const uint8_t* left, const uint8_t* right, int
     if (!valid_problem(p, &why)) return fail(nullptr, SGM_EINVAL, "%s", why.c_str());
     if (!is_device_ptr(left) || !is_device_ptr(right) || !is_device_ptr(disp_out))
         return fail(nullptr, SGM_EINVAL, "sgm_compute_static takes device pointers only");
-    const size_t need = layout_for(p).total;
+    const size_t need = static_layout(p).total;
     if (need > kStaticScratchBytes)
         return fail(nullptr, SGM_EINVAL,
                     "%dx%d D=%d with %d paths needs %zu bytes of scratch; the static scratch holds %zu bytes", W, H, D,

@@ -334,6 +334,137 @@ cudaError_t launch_cost(const void* Fb, const void* Fm, uint8_t* rec, int RB, in
     }
 }
 
+// ---------------------------------------------------------------------------
+// Eq. 2 into the quad cube of the paired-line schedule (sgm_internal.h): per
+// quad of 2 x 2 pixels and disparity d, the four costs at byte i + 2j of a
+// 32-bit word (pixel (2qx + i, 2qy + j)); padding pixels (x >= W or y >= H)
+// get MC = 0.  A CTA covers kQcSeg quads of one quad row: the two rows' base
+// features and the match features x0 - D .. x0 + 2 kQcSeg - 1 are staged in
+// shared memory.  A thread computes four consecutive disparities of one quad
+// (16 bytes, one store); consecutive threads take consecutive disparity
+// groups, so a warp's stores cover 512 contiguous bytes.
+// ---------------------------------------------------------------------------
+constexpr int kQcSeg = 32, kQcThreads = 128;
+
+template <int D, class FT>
+__device__ __forceinline__ void cost_quads_body(const FT* __restrict__ Fb, const FT* __restrict__ Fm,
+                                                uint8_t* __restrict__ mc, int QB, int W, int H, int bx, int qy) {
+    constexpr int NG = D / 4, SW = 2 * kQcSeg, NF = SW + D;
+    __shared__ __align__(16) FT fm[2][NF];  // fm[j][k] = F_match(x0 - D + k, 2 qy + j)
+    __shared__ __align__(16) FT fb[2][SW];  // fb[j][k] = F_base(x0 + k, 2 qy + j)
+    const int qx0 = bx * kQcSeg, x0 = 2 * qx0, QW = (W + 1) / 2;
+    {
+        constexpr int NI = (2 * NF + kQcThreads - 1) / kQcThreads, NB = (2 * SW + kQcThreads - 1) / kQcThreads;
+        FT vm[NI], vb[NB];
+#pragma unroll
+        for (int it = 0; it < NI; ++it) {
+            const int i = threadIdx.x + it * kQcThreads, j = i / NF, k = i - j * NF, gx = x0 - D + k, y = 2 * qy + j;
+            vm[it] = (i < 2 * NF && gx >= 0 && gx < W && y < H) ? __ldg(Fm + (size_t)y * W + gx) : FT(0);
+        }
+#pragma unroll
+        for (int it = 0; it < NB; ++it) {
+            const int i = threadIdx.x + it * kQcThreads, j = i / SW, k = i - j * SW, gx = x0 + k, y = 2 * qy + j;
+            vb[it] = (i < 2 * SW && gx < W && y < H) ? __ldg(Fb + (size_t)y * W + gx) : FT(0);
+        }
+#pragma unroll
+        for (int it = 0; it < NI; ++it) {
+            const int i = threadIdx.x + it * kQcThreads;
+            if (i < 2 * NF) fm[i / NF][i % NF] = vm[it];
+        }
+#pragma unroll
+        for (int it = 0; it < NB; ++it) {
+            const int i = threadIdx.x + it * kQcThreads;
+            if (i < 2 * SW) fb[i / SW][i % SW] = vb[it];
+        }
+    }
+    __syncthreads();
+    const int nq = min(kQcSeg, QW - qx0);
+    const int items = nq * NG;
+    // padding: column 2qx + 1 beyond the image only in the last quad column
+    // (odd W), row 2qy + 1 only in the last quad row (odd H)
+    const bool row1 = 2 * qy + 1 < H;
+    for (int t = threadIdx.x; t < items; t += kQcThreads) {
+        const int g = t % NG, ql = t / NG, xl = 2 * ql, d0 = 4 * g;
+        const bool col1 = x0 + xl + 1 < W;
+        uint32_t c[2][2][4];  // c[i][j][e]: pixel (x0 + xl + i, 2qy + j), d = d0 + e
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            // match features of pixels xl, xl + 1 at d0 .. d0 + 3: fm[j][xl + i - d + D]
+            const int kb = xl + D - d0 - 4;  // even: six values kb .. kb + 5 cover them
+            FT m[6];
+#pragma unroll
+            for (int k = 0; k < 6; k += 2) ld2(&fm[j][kb + k], m[k], m[k + 1]);
+            FT b0, b1;
+            ld2(&fb[j][xl], b0, b1);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                c[0][j][e] = bitcount(b0 ^ m[4 - e]);  // fm[j][xl - (d0 + e) + D] = m[4 - e]
+                c[1][j][e] = bitcount(b1 ^ m[5 - e]);
+            }
+        }
+        uint32_t q[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const uint32_t c01 = row1 ? c[0][1][e] : 0u, c10 = col1 ? c[1][0][e] : 0u,
+                           c11 = (row1 && col1) ? c[1][1][e] : 0u;
+            // bytes [c(0,0), c(1,0), c(0,1), c(1,1)]
+            q[e] = __byte_perm(c[0][0][e] | (c01 << 16), c10 | (c11 << 16), 0x6240u);
+        }
+        *reinterpret_cast<uint4*>(mc + ((size_t)qy * QW + qx0 + ql) * QB + 4 * d0) = make_uint4(q[0], q[1], q[2], q[3]);
+    }
+}
+
+template <int D, class FT>
+__global__ void __launch_bounds__(kQcThreads) cost_quads_kernel(const FT* __restrict__ Fb, const FT* __restrict__ Fm,
+                                                                uint8_t* __restrict__ mc, int QB, int W, int H) {
+    cost_quads_body<D, FT>(Fb, Fm, mc, QB, W, H, blockIdx.x, blockIdx.y);
+}
+
+template <int D>
+static cudaError_t launch_cost_quads_t(const void* Fb, const void* Fm, uint8_t* mc, int QB, int W, int H, bool ct62,
+                                       cudaStream_t s) {
+    const int QW = (W + 1) / 2, QH = (H + 1) / 2;
+    const dim3 grid((QW + kQcSeg - 1) / kQcSeg, QH);
+    if (ct62)
+        cost_quads_kernel<D, uint64_t><<<grid, kQcThreads, 0, s>>>(static_cast<const uint64_t*>(Fb),
+                                                                   static_cast<const uint64_t*>(Fm), mc, QB, W, H);
+    else
+        cost_quads_kernel<D, uint32_t><<<grid, kQcThreads, 0, s>>>(static_cast<const uint32_t*>(Fb),
+                                                                   static_cast<const uint32_t*>(Fm), mc, QB, W, H);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cost_quads(const void* Fb, const void* Fm, uint8_t* mc, int QB, int W, int H, int D, bool ct62,
+                              cudaStream_t stream) {
+    switch (D) {
+        case 32: return launch_cost_quads_t<32>(Fb, Fm, mc, QB, W, H, ct62, stream);
+        case 64: return launch_cost_quads_t<64>(Fb, Fm, mc, QB, W, H, ct62, stream);
+        case 96: return launch_cost_quads_t<96>(Fb, Fm, mc, QB, W, H, ct62, stream);
+        case 128: return launch_cost_quads_t<128>(Fb, Fm, mc, QB, W, H, ct62, stream);
+        case 160: return launch_cost_quads_t<160>(Fb, Fm, mc, QB, W, H, ct62, stream);
+        case 192: return launch_cost_quads_t<192>(Fb, Fm, mc, QB, W, H, ct62, stream);
+        case 224: return launch_cost_quads_t<224>(Fb, Fm, mc, QB, W, H, ct62, stream);
+        case 256: return launch_cost_quads_t<256>(Fb, Fm, mc, QB, W, H, ct62, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// A quad-layout cube -> natural order [H][W][D] (debug only).
+__global__ void unquad_kernel(const uint8_t* __restrict__ cube, int QB, uint8_t* __restrict__ out, int W, int H, int D) {
+    const size_t n = (size_t)W * H * D;
+    const int QW = (W + 1) / 2;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t p = t / D;
+        const int d = static_cast<int>(t % D), x = static_cast<int>(p % W), y = static_cast<int>(p / W);
+        out[t] = cube[((size_t)(y >> 1) * QW + (x >> 1)) * QB + 4 * d + (x & 1) + 2 * (y & 1)];
+    }
+}
+
+cudaError_t launch_unquad_cost(const uint8_t* cube, int QB, uint8_t* out, int W, int H, int D, cudaStream_t stream) {
+    unquad_kernel<<<1024, 256, 0, stream>>>(cube, QB, out, W, H, D);
+    return cudaGetLastError();
+}
+
 // Paired order in RB-byte records -> natural order [H][W][D] (debug only).
 __global__ void unpair_kernel(const uint8_t* __restrict__ rec, int RB, uint8_t* __restrict__ out, size_t npix, int D) {
     const size_t n = npix * D;
@@ -373,6 +504,17 @@ __device__ __forceinline__ int med3(int a, int b, int c) { return max(min(a, b),
 // sorted once and shared by the three windows that contain the row.
 constexpr int kMedW = 128, kMedH = 4;
 
+// QUAD: raw in quads of 2 x 2 pixels ([ceil(H/2)][ceil(W/2)][4], pixel (x, y)
+// at byte (x & 1) + 2 (y & 1) of its quad), else row-major [H][W].
+template <bool QUAD = false>
+__device__ __forceinline__ int raw_at(const uint8_t* __restrict__ raw, int W, int x, int y) {
+    if constexpr (QUAD)
+        return __ldg(raw + ((size_t)(y >> 1) * ((W + 1) >> 1) + (x >> 1)) * 4 + (x & 1) + 2 * (y & 1));
+    else
+        return __ldg(raw + (size_t)y * W + x);
+}
+
+template <bool QUAD = false>
 __device__ __forceinline__ void median_body(const uint8_t* __restrict__ raw, uint8_t* __restrict__ out, int W, int H,
                                             int bx, int by) {
     const int x = bx * kMedW + threadIdx.x, y0 = by * kMedH;
@@ -382,10 +524,9 @@ __device__ __forceinline__ void median_body(const uint8_t* __restrict__ raw, uin
 #pragma unroll
     for (int r = 0; r < kMedH + 2; ++r) {
         const int gy = min(max(y0 - 1 + r, 0), H - 1);
-        const uint8_t* row = raw + (size_t)gy * W;
-        lo[r] = __ldg(row + xl);
-        mid[r] = __ldg(row + x);
-        hi[r] = __ldg(row + xr);
+        lo[r] = raw_at<QUAD>(raw, W, xl, gy);
+        mid[r] = raw_at<QUAD>(raw, W, x, gy);
+        hi[r] = raw_at<QUAD>(raw, W, xr, gy);
     }
     int c[kMedH];  // raw centre values: the border ring keeps them
 #pragma unroll
@@ -432,6 +573,17 @@ cudaError_t launch_median_batch(JobTable<MedianJob>& t, cudaStream_t stream) {
 cudaError_t launch_median(const uint8_t* raw, uint8_t* disp, int W, int H, cudaStream_t stream) {
     dim3 grid((W + kMedW - 1) / kMedW, (H + kMedH - 1) / kMedH);
     median_kernel<<<grid, kMedW, 0, stream>>>(raw, disp, W, H);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kMedW) median_quads_kernel(const uint8_t* __restrict__ rawq,
+                                                           uint8_t* __restrict__ out, int W, int H) {
+    median_body<true>(rawq, out, W, H, blockIdx.x, blockIdx.y);
+}
+
+cudaError_t launch_median_quads(const uint8_t* rawq, uint8_t* disp, int W, int H, cudaStream_t stream) {
+    dim3 grid((W + kMedW - 1) / kMedW, (H + kMedH - 1) / kMedH);
+    median_quads_kernel<<<grid, kMedW, 0, stream>>>(rawq, disp, W, H);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,9 @@
 // Dispatch of the aggregation sweeps (Eq. 3, Eq. 4) by disparity count; the
 // kernels themselves are in sgm_sweeps.cuh, instantiated per D in
 // sgm_sweeps_d<D>.cu so that the translation units compile in parallel.
+#include <algorithm>
+
+#include "sgm_pairs.cuh"
 #include "sgm_sweeps.cuh"
 
 namespace sgm {
@@ -52,6 +55,43 @@ cudaError_t launch_sweep_h_batch(JobTable<SweepArgs>& t, cudaStream_t stream) {
 cudaError_t launch_sweep_v_batch(JobTable<SweepArgs>& t, cudaStream_t stream) {
     if (t.n < 1) return cudaSuccess;
     SGM_DISPATCH_D(sweep_launch_v_batch, t.job[0].D, t, stream)
+}
+
+// The paired-line 4-path schedule: n1 steps of each horizontal direction
+// beside the vertical pair in the first launch (default min(W2, H2), which
+// ends both at the same step), the vertical pair meeting at row Hm.
+PairsArgs pairs_geometry(int W, int H, int D, int n1_req) {
+    PairsArgs a{};
+    a.W = W;
+    a.H = H;
+    a.D = D;
+    a.W2 = W + (W & 1);
+    a.H2 = H + (H & 1);
+    a.QW = a.W2 / 2;
+    a.QH = a.H2 / 2;
+    int n1 = n1_req < 0 ? std::min(a.W2, a.H2) : n1_req;
+    a.n1 = std::max(0, std::min(a.W2, n1 & ~1));
+    a.Hm = (a.H2 / 2) & ~1;
+    if (a.W2 > 2 * a.n1) {
+        a.a = a.b = (a.W2 / 2) & ~1;  // the horizontal pair meets in the middle in the second launch
+    } else {
+        a.a = a.n1;  // columns [W2 - n1, n1) were passed by both directions in the first launch
+        a.b = a.W2 - a.n1;
+    }
+    a.nvb = a.QW;
+    a.nhb = a.QH;
+    a.nh2 = a.W2 > a.n1 ? a.QH : 0;
+    const int par = (a.a - a.b) / 2 * a.QH;  // quads of the parallel winner-take-all
+    a.npw = par > 0 ? (par + 1) / 2 : 0;      // one quad per warp, two warps per block
+    return a;
+}
+
+cudaError_t launch_pairs_stage1(const PairsArgs& a, cudaStream_t stream) {
+    SGM_DISPATCH_D(pairs_launch1, a.D, a, stream)
+}
+
+cudaError_t launch_pairs_stage2(const PairsArgs& a, cudaStream_t stream) {
+    SGM_DISPATCH_D(pairs_launch2, a.D, a, stream)
 }
 
 }  // namespace sgm

@@ -36,6 +36,7 @@ SGM_POST_ADAPTIVE_P2 = 4
 SGM_DISP16_INVALID = 0xFFFF
 SGM_SCHED_V_THEN_H = 0
 SGM_SCHED_H_THEN_V = 1
+SGM_SCHED_PAIRS = 2
 SGM_MAX_D = 256
 SGM_MAX_PENALTY = 224
 

@@ -1,6 +1,6 @@
-"""The two 4-path sweep schedules and their autotuner, through the C ABI.
+"""The three 4-path sweep schedules and their autotuner, through the C ABI.
 
-Both schedules compute Eq. 3 and Eq. 4 over the same paths, so each must
+All schedules compute Eq. 3 and Eq. 4 over the same paths, so each must
 match the oracle bit for bit on its own; the tuner only decides which runs.
 """
 import numpy as np
@@ -19,7 +19,7 @@ def sgm():
     return m
 
 
-@pytest.mark.parametrize("sched", [0, 1])
+@pytest.mark.parametrize("sched", [0, 1, 2])
 @pytest.mark.parametrize("D", [32, 64, 96, 128, 160, 256])
 def test_each_schedule_matches_the_oracle(sgm, sched, D):
     pair = synth.make_pair(synth.PairSpec(77, 45, D, 4, 2, min(48, D - 1)), 7000 + D)
@@ -33,7 +33,7 @@ def test_each_schedule_matches_the_oracle(sgm, sched, D):
     assert (dbg["S"].astype(np.int32) == ref["S"]).all() and (dbg["raw"] == ref["raw"]).all()
 
 
-@pytest.mark.parametrize("sched", [0, 1])
+@pytest.mark.parametrize("sched", [0, 1, 2])
 @pytest.mark.parametrize("W,H", [(1, 1), (1, 9), (9, 1), (2, 33), (33, 2), (17, 23), (200, 31), (31, 200)])
 @pytest.mark.parametrize("P2", [84, 96, 97])  # byte sums hold up to 2 * (31 + P2) <= 255
 def test_schedules_on_edge_sizes_and_sum_widths(sgm, sched, W, H, P2):
@@ -53,10 +53,10 @@ def test_autotuner_picks_one_and_keeps_it(sgm):
         assert sgm.sgm_schedule_for(c.handle, 160, 96, 64, 7, 84, 4) == -1  # not tuned yet
         before = c.launches
         assert (c.compute(pair.left, pair.right, 64, 7, 84, 4) == ref).all()
-        # tuning: per schedule one warm-up and two timed runs, then the chosen run
-        assert c.launches - before == 5 * (2 * 3 + 1)
+        # tuning: per schedule one warm-up and five timed runs, then the chosen run
+        assert c.launches - before == 5 * (3 * 6 + 1)
         chosen = sgm.sgm_schedule_for(c.handle, 160, 96, 64, 7, 84, 4)
-        assert chosen in (0, 1)
+        assert chosen in (0, 1, 2)
         before = c.launches
         assert (c.compute(pair.left, pair.right, 64, 7, 84, 4) == ref).all()
         assert c.launches - before == 5
@@ -64,7 +64,7 @@ def test_autotuner_picks_one_and_keeps_it(sgm):
         # other path counts have one schedule
         assert sgm.sgm_schedule_for(c.handle, 160, 96, 64, 7, 84, 8) == 0
         with pytest.raises(sgm.SgmError):
-            sgm.sgm_set_schedule(c.handle, 2)
+            sgm.sgm_set_schedule(c.handle, 3)
 
 
 def test_stage_labels_follow_the_schedule(sgm):
@@ -78,6 +78,7 @@ def test_stage_labels_follow_the_schedule(sgm):
     try:
         sgm.sgm_set_stream(c.handle, torch.cuda.current_stream())
         for sched, names in [(1, ["census", "cost", "sweep_h+v1", "sweep_v2", "median"]),
+                             (2, ["census", "cost", "pairs_vh", "pairs_h_wta", "median"]),
                              (0, ["census", "cost", "sweep_v+h1", "sweep_h2", "median"])]:
             sgm.sgm_set_schedule(c.handle, sched)
             sgm.sgm_compute_async(c.handle, L, R, 128, 80, 128, 7, 84, 4, out)
@@ -93,6 +94,6 @@ def test_full_frame_both_schedules(sgm):
     pair = synth.make_pair(synth.PairSpec(640, 480, 128, 12, 2, 120), 17)
     ref = oracle.sgm(pair.left, pair.right, 128, 7, 84, 4)
     with sgm.Context(0) as c:
-        for sched in (0, 1):
+        for sched in (0, 1, 2):
             sgm.sgm_set_schedule(c.handle, sched)
             assert (c.compute(pair.left, pair.right, 128, 7, 84, 4) == ref).all()
