@@ -131,7 +131,7 @@ Layout layout_pairs(const Problem& p) {
     l.Fm = o;
     o = align_up(o + fbytes * wh);
     l.rec = o;
-    o = align_up(o + pairs_fields(s8_for(p)) * l.fs);
+    o = align_up(o + kPairsFields * l.fs);
     l.raw = o;
     o = align_up(o + 4 * quads);
     l.state = o;
@@ -248,6 +248,10 @@ struct sgm_ctx {
     cudaStream_t own_stream = nullptr;
     cudaStream_t stream = nullptr;
     cudaStream_t capture_stream = nullptr;
+    // a second stream and two events that fork and join two kernels of one
+    // path (the paired schedule's second launch), in and outside graph capture
+    cudaStream_t aux_stream = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     size_t mem_cap = 0;
     uint8_t* arena = nullptr;
     size_t arena_bytes = 0;
@@ -363,12 +367,21 @@ static bool kernel_accessible(const void* p) {
 // sweep_h, sweep_v, median.  Each kernel is one timed stage.  With
 // post-filters: one matching pass (census, cost, sweeps) for the left image,
 // with the LR check a mirror kernel and a second pass, then the post kernel.
-static int launches_per_match(const Problem& p) { return p.n_paths == 8 ? 6 : 4; }
+// The paired schedule runs its second launch as two kernels side by side (one
+// timed stage).
+static int launches_per_match(const Problem& p) { return p.n_paths == 8 ? 6 : (pairs_sched(p) ? 5 : 4); }
 static int launches_per_path(const Problem& p) {
     if (!p.post) return launches_per_match(p) + 1;
     return launches_per_match(p) * ((p.post & SGM_POST_LR_CHECK) ? 2 : 1) + ((p.post & SGM_POST_LR_CHECK) ? 1 : 0) + 1;
 }
-static int stages_per_path(const Problem& p) { return launches_per_path(p); }
+static int stages_per_path(const Problem& p) { return launches_per_path(p) - (pairs_sched(p) ? 1 : 0); }
+
+// Two kernels of one path side by side: `aux` waits for `fork` recorded on
+// the path's stream, the path's stream waits for `join` recorded on `aux`.
+struct ForkJoin {
+    cudaStream_t aux;
+    cudaEvent_t fork, join;
+};
 
 // One matching pass (Section 2, stages 2-3 and Eq. 4) of the pair
 // (base, match): census, cost and the sweeps; the winner-take-all disparity
@@ -377,7 +390,7 @@ static int stages_per_path(const Problem& p) { return launches_per_path(p); }
 template <class Mark>
 static cudaError_t enqueue_match(const Problem& p, const Layout& l, uint8_t* arena, const uint8_t* base,
                                  const uint8_t* match, uint8_t* raw, uint32_t* sub, uint16_t* Sdbg, cudaStream_t s,
-                                 Mark&& mark) {
+                                 const ForkJoin& fj, Mark&& mark) {
     void* Fb = arena + l.Fb;
     void* Fm = arena + l.Fm;
     cudaError_t e;
@@ -403,7 +416,14 @@ static cudaError_t enqueue_match(const Problem& p, const Layout& l, uint8_t* are
         g.mc_max = mc_max(p);
         if ((e = launch_pairs_stage1(g, s)) != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
-        if ((e = launch_pairs_stage2(g, s)) != cudaSuccess) return e;
+        // the horizontal chains (the long pole: enqueued first) and the
+        // parallel winner-take-all side by side
+        if ((e = cudaEventRecord(fj.fork, s)) != cudaSuccess) return e;
+        if ((e = launch_pairs_chain2(g, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(fj.aux, fj.fork, 0)) != cudaSuccess) return e;
+        if ((e = launch_pairs_par(g, fj.aux)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(fj.join, fj.aux)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s, fj.join, 0)) != cudaSuccess) return e;
         return mark();
     }
     if ((e = launch_cost(Fb, Fm, arena + l.rec, l.RB, p.W, p.H, p.D, p.ct62 != 0, s)) != cudaSuccess) return e;
@@ -515,6 +535,7 @@ static cudaError_t enqueue_match(const Problem& p, const Layout& l, uint8_t* are
 static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const uint8_t* left,
                                 const uint8_t* right, uint8_t* disp, uint16_t* Sdbg, cudaStream_t s, bool timed) {
     const Layout l = layout_for(p);
+    const ForkJoin fj{ctx->aux_stream, ctx->fork_ev, ctx->join_ev};
     cudaError_t e;
     int stage = 0;
     // with stage timing, event k is recorded before kernel k and after the last
@@ -525,7 +546,7 @@ static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, 
     };
     if ((e = mark()) != cudaSuccess) return e;
     if (!p.post) {
-        if ((e = enqueue_match(p, l, arena, left, right, arena + l.raw, nullptr, Sdbg, s, mark)) != cudaSuccess)
+        if ((e = enqueue_match(p, l, arena, left, right, arena + l.raw, nullptr, Sdbg, s, fj, mark)) != cudaSuccess)
             return e;
         e = pairs_sched(p) ? launch_median_quads(arena + l.raw, disp, p.W, p.H, s)
                            : launch_median(arena + l.raw, disp, p.W, p.H, s);
@@ -533,14 +554,14 @@ static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, 
         if ((e = mark()) != cudaSuccess) return e;
     } else {
         uint32_t* sub = (p.post & SGM_POST_SUBPIXEL) ? reinterpret_cast<uint32_t*>(arena + l.sub) : nullptr;
-        if ((e = enqueue_match(p, l, arena, left, right, arena + l.raw, sub, nullptr, s, mark)) != cudaSuccess)
+        if ((e = enqueue_match(p, l, arena, left, right, arena + l.raw, sub, nullptr, s, fj, mark)) != cudaSuccess)
             return e;
         const uint8_t* rawR = nullptr;
         if (p.post & SGM_POST_LR_CHECK) {
             // the right image's disparity: the same pass on the mirrored pair
             if ((e = launch_mirror(left, right, arena + l.ml, arena + l.mr, p.W, p.H, s)) != cudaSuccess) return e;
             if ((e = mark()) != cudaSuccess) return e;
-            if ((e = enqueue_match(p, l, arena, arena + l.mr, arena + l.ml, arena + l.rawR, nullptr, nullptr, s,
+            if ((e = enqueue_match(p, l, arena, arena + l.mr, arena + l.ml, arena + l.rawR, nullptr, nullptr, s, fj,
                                    mark)) != cudaSuccess)
                 return e;
             rawR = arena + l.rawR;
@@ -1105,7 +1126,10 @@ int sgm_create(sgm_ctx** out, int device, size_t mem_cap_bytes, unsigned flags) 
     ctx->device = device;
     ctx->mem_cap = mem_cap_bytes;
     if ((e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        (e = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming)) != cudaSuccess) {
         sgm_destroy(ctx);
         return fail(nullptr, SGM_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
     }
@@ -1177,6 +1201,12 @@ int sgm_destroy(sgm_ctx* ctx) {
     if (ctx->serve_pool) cudaMemPoolDestroy(ctx->serve_pool);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    if (ctx->aux_stream) {
+        cudaStreamSynchronize(ctx->aux_stream);
+        cudaStreamDestroy(ctx->aux_stream);
+    }
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+    if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
     for (auto& ev : ctx->stage_ev)
         if (ev) cudaEventDestroy(ev);
     for (auto& ev : ctx->tune_ev)

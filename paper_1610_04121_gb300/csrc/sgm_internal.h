@@ -143,18 +143,16 @@ cudaError_t launch_unpair_cost(const uint8_t* rec, int RB, uint8_t* out, int W, 
 // quad takes QB = 4D bytes of a cube.  Each cube is its own array of
 // [QH][QW] quads (FS bytes), at rec + f FS for field f:
 //   0 MC    matching costs (Eq. 2); 0 at padding pixels
-//   1 Lv    the vertical pair's stored L_r (meet in the middle)
-//   2 Lh0   stored L_r of the left-to-right path
-//   3 Lh1   stored L_r of the right-to-left path
-//   4 Sv    S of the vertical pair in bytes when they fit (s8); else 4 and 5
-//   5       hold it in u16, rows 2qy (field 4) and 2qy + 1 (field 5) of each
-//           quad, as the pairs (S(2qx, y), S(2qx + 1, y))
+//   1 LvT   stored L_r of the top-to-bottom path
+//   2 LvB   stored L_r of the bottom-to-top path
+//   3 Lh0   stored L_r of the left-to-right path
+//   4 Lh1   stored L_r of the right-to-left path
 // One 32-bit offset q QB then addresses quad q in every field.
 // ---------------------------------------------------------------------------
-inline int pairs_fields(bool s8) { return s8 ? 5 : 6; }
+constexpr int kPairsFields = 5;
 
 struct PairsArgs {
-    uint8_t* rec;     // the field arrays (pairs_fields of FS bytes each)
+    uint8_t* rec;     // the field arrays (kPairsFields of FS bytes each)
     uint8_t* rawq;    // winner-take-all disparity in quads [QH][QW][4]
     uint16_t* Sdbg;   // optional natural-order S [H][W][D] (debug)
     uint32_t* state;  // horizontal chains between the launches: [QH][2][32][K + 1]
@@ -162,16 +160,15 @@ struct PairsArgs {
     size_t FS;        // bytes of one field array (QH * QW * QB, rounded up)
     int QB;           // bytes of one quad in a field: 4D (W2 * H2 * D < 2^32)
     int n1;           // steps of each horizontal direction in the first launch (even)
-    int Hm;           // vertical meeting row (even): top-to-bottom stores rows [0, Hm)
     // second launch: left-to-right stores [n1, a) then finishes [a, W2) with
     // Eq. 4; right-to-left stores [b, W2 - n1) then finishes [0, b); columns
     // [b, a) are finished by the parallel winner-take-all
     int a, b;
     uint32_t P1x2, P2x2;
-    int s8;           // S of the vertical pair in bytes
+    int s8;           // two stored L_r sum in a byte: 2 (MC_max + P2) <= 255
     int mc_max;       // largest matching cost: 31 (CSCT) or 62 (full Census)
     int nvb, nhb;     // first launch: vertical / horizontal blocks (64 threads each)
-    int nh2, npw;     // second launch: chain blocks, parallel winner-take-all blocks
+    int nh2, npw;     // second launch: chain blocks; parallel winner-take-all blocks (beside them)
 };
 // Geometry and block counts for a W x H problem (n1 < 0: the default split).
 PairsArgs pairs_geometry(int W, int H, int D, int n1);
@@ -179,7 +176,10 @@ PairsArgs pairs_geometry(int W, int H, int D, int n1);
 cudaError_t launch_cost_quads(const void* Fb, const void* Fm, uint8_t* mc, int QB, int W, int H, int D, bool ct62,
                               cudaStream_t stream);
 cudaError_t launch_pairs_stage1(const PairsArgs& a, cudaStream_t stream);
-cudaError_t launch_pairs_stage2(const PairsArgs& a, cudaStream_t stream);
+// The second launch is two kernels that may run side by side: the chains and
+// the parallel winner-take-all.
+cudaError_t launch_pairs_chain2(const PairsArgs& a, cudaStream_t stream);
+cudaError_t launch_pairs_par(const PairsArgs& a, cudaStream_t stream);
 // 3x3 median of a quad-layout raw disparity.
 cudaError_t launch_median_quads(const uint8_t* rawq, uint8_t* disp, int W, int H, cudaStream_t stream);
 // Debug: a quad-layout cube (quad q at cube + q QB) -> natural order [H][W][D].

@@ -23,13 +23,13 @@
 //
 // Schedule (4 paths: left-to-right, right-to-left, top-to-bottom,
 // bottom-to-top):
-//   launch 1  the vertical pair, meeting in the middle (the first halves
-//             store L_r, the second halves write S_v = L_TB + L_BT), beside
-//             n1 steps of each horizontal direction (storing L_r);
+//   launch 1  every walker stores its own L_r: the vertical pair walks every
+//             row, each horizontal direction n1 columns; nothing is read but
+//             the costs, so no walker waits for another;
 //   launch 2  the rest of each horizontal direction, finishing its pixels
-//             with Eq. 4 (S = S_v + L_LR + L_RL), beside a parallel
-//             winner-take-all over the columns both horizontal directions
-//             passed in launch 1.
+//             with Eq. 4 (S = its own L_r + the three stored ones), beside a
+//             parallel winner-take-all over the columns both horizontal
+//             directions passed in launch 1.
 // With n1 = min(W, H) the longest chain is max(W, H) steps, against H + W / 2
 // for a schedule that finishes one pair before the other starts.
 #pragma once
@@ -44,7 +44,7 @@ constexpr uint32_t kInf2 = kInf16 * 0x10001u;
 constexpr unsigned kFull = 0xffffffffu;
 
 // Field arrays (sgm_internal.h).
-enum Field { kMC = 0, kLV = 1, kLH0 = 2, kLH1 = 3, kSV = 4, kSV1 = 5 };
+enum Field { kMC = 0, kLVT = 1, kLVB = 2, kLH0 = 3, kLH1 = 4 };
 
 // One quad register [x0y0, x1y0, x0y1, x1y1] -> the u16x2 word of one step:
 // the column pair at row h (vertical walks) or the row pair at column h
@@ -60,10 +60,33 @@ __device__ __forceinline__ uint32_t toq(uint32_t w0, uint32_t w1) {
     return __byte_perm(w0, w1, VERT ? 0x6420u : 0x6240u);
 }
 
-// N registers from 4N bytes at p (16-byte aligned when N % 4 == 0, 8-byte when N is even).
-template <int N, bool NC>
+// L2 eviction priority of a cube's loads and stores: kL2Normal, or kL2Last
+// (kept over normal and first lines; the costs, read by four walkers) or
+// kL2First (streamed through; stored costs read much later).
+enum L2Hint { kL2Normal = 0, kL2Last = 1, kL2First = 2 };
+
+template <int HINT>
+__device__ __forceinline__ uint64_t l2_policy() {
+    uint64_t pol;
+    if constexpr (HINT == kL2Last)
+        asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    else
+        asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// N registers from 4N bytes at p (16-byte aligned when N % 4 == 0, 8-byte when
+// N is even), through L2 only.
+template <int N, bool NC, int HINT = kL2Normal>
 __device__ __forceinline__ void ldv(const uint8_t* p, uint32_t (&r)[N]) {
-    if constexpr (N % 4 == 0) {
+    if constexpr (N % 4 == 0 && HINT != kL2Normal) {
+        const uint64_t pol = l2_policy<HINT>();
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i)
+            asm volatile("ld.global.cg.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                         : "=r"(r[4 * i]), "=r"(r[4 * i + 1]), "=r"(r[4 * i + 2]), "=r"(r[4 * i + 3])
+                         : "l"(p + 16 * i), "l"(pol));
+    } else if constexpr (N % 4 == 0) {
 #pragma unroll
         for (int i = 0; i < N / 4; ++i) {
             const uint4* q = reinterpret_cast<const uint4*>(p) + i;
@@ -90,9 +113,16 @@ __device__ __forceinline__ void ldv(const uint8_t* p, uint32_t (&r)[N]) {
     }
 }
 
-template <int N>
+template <int N, int HINT = kL2Normal>
 __device__ __forceinline__ void stv(uint8_t* p, const uint32_t (&r)[N]) {
-    if constexpr (N % 4 == 0) {
+    if constexpr (N % 4 == 0 && HINT != kL2Normal) {
+        const uint64_t pol = l2_policy<HINT>();
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i)
+            asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p + 16 * i),
+                         "r"(r[4 * i]), "r"(r[4 * i + 1]), "r"(r[4 * i + 2]), "r"(r[4 * i + 3]), "l"(pol)
+                         : "memory");
+    } else if constexpr (N % 4 == 0) {
 #pragma unroll
         for (int i = 0; i < N / 4; ++i)
             reinterpret_cast<uint4*>(p)[i] = make_uint4(r[4 * i], r[4 * i + 1], r[4 * i + 2], r[4 * i + 3]);
@@ -104,6 +134,16 @@ __device__ __forceinline__ void stv(uint8_t* p, const uint32_t (&r)[N]) {
         for (int i = 0; i < N; ++i) reinterpret_cast<unsigned*>(p)[i] = r[i];
     }
 }
+
+// Launch 2: input registers of the chains' prefetch, and quads per warp of the
+// parallel winner-take-all.
+constexpr int kChainPrefetchRegs = 192, kParItems = 4;
+
+// Cache policy of the walks' traffic (measured on the 640x480 D=128 frame):
+// the stored costs, written in the first launch and read in the second, go
+// through L2 as evict-first, so that they do not push out the costs the other
+// walkers are about to read (first launch 51 -> 43 us, second 41 -> 35 us).
+constexpr int kHintMcLoad = kL2Normal, kHintLStore = kL2First, kHintLLoad = kL2First;
 
 // 64-bit base + 32-bit record offset in one instruction.
 __device__ __forceinline__ uint8_t* at(uint8_t* base, uint32_t off) {
@@ -210,33 +250,30 @@ __device__ __forceinline__ void wta_dconst(int lane, uint32_t (&dc)[K]) {
 }
 
 enum Mode {
-    kStore = 0,  // store L_r in a field (first halves)
-    kSumV = 1,   // vertical second halves: S_v = L + the other direction's stored L_r
-    kWta = 2     // horizontal last steps: S = L + the other direction's stored L_r + S_v, then Eq. 4
+    kStore = 0,  // store L_r in this direction's field
+    kWta = 1     // horizontal last steps: S = L + the three stored L_r, then Eq. 4
 };
 
-// Inputs of one unit (two steps: one quad) of a walk; with u16 sums S_v
-// takes K registers from each of its two arrays (s, s1).
-template <int D, int MODE, bool S8>
+// Inputs of one unit (two steps: one quad) of a walk: MC, and for kWta the
+// other horizontal direction's stored L_r and the two vertical ones.
+template <int D, int MODE>
 struct UnitIn {
     static constexpr int K = D / 32;
-    static constexpr int NO = MODE == kStore ? 0 : K;
-    static constexpr int NS = MODE == kWta ? K : 0;
-    static constexpr int NS1 = MODE == kWta && !S8 ? K : 0;
-    static constexpr int REGS = K + NO + NS + NS1;
+    static constexpr int NO = MODE == kWta ? K : 0;
+    static constexpr int REGS = K + 3 * NO;
     uint32_t mc[K];
     uint32_t o[NO > 0 ? NO : 1];
-    uint32_t s[NS > 0 ? NS : 1];
-    uint32_t s1[NS1 > 0 ? NS1 : 1];
+    uint32_t v0[NO > 0 ? NO : 1];
+    uint32_t v1[NO > 0 ? NO : 1];
 };
 
 // Per-lane field bases of a walk.
 struct Bases {
     uint8_t* mc;   // MC
-    uint8_t* o;    // the other direction's stored L_r (kSumV, kWta)
-    uint8_t* out;  // this direction's stored L_r (kStore) or S_v (kSumV; u16 sums: row 2qy)
-    uint8_t* sv;   // S_v (kWta; u16 sums: row 2qy)
-    uint8_t* sv1;  // u16 sums: row 2qy + 1 of S_v (kSumV, kWta)
+    uint8_t* out;  // this direction's stored L_r (kStore)
+    uint8_t* o;    // the other horizontal direction's stored L_r (kWta)
+    uint8_t* v0;   // top-to-bottom stored L_r (kWta)
+    uint8_t* v1;   // bottom-to-top stored L_r (kWta)
 };
 
 // A walk over `nu` units: unit k at record offset off0 + k * dstride (a
@@ -252,10 +289,9 @@ struct Walk {
 // Byte selectors of a walk, held in registers so that one body of code serves
 // every axis and direction: the two steps of a unit take halves h0 then h1
 // (0 then 1 for ascending rows or columns); un[t] turns a quad register into
-// the word of step t, cq turns the words of steps 0 and 1 into a quad, and
-// s16[t] picks step t's u16 pair out of a u16 quad (horizontal walks).
+// the word of step t and cq turns the words of steps 0 and 1 into a quad.
 struct Sel {
-    uint32_t un[2], cq, s16[2];
+    uint32_t un[2], cq;
     int h0;
 };
 
@@ -267,25 +303,34 @@ __device__ __forceinline__ Sel walk_sel(bool vert, bool asc) {
     // words w0 (half 0), w1 (half 1): vertical [w0.b0, w0.b2, w1.b0, w1.b2],
     // horizontal [w0.b0, w1.b0, w0.b2, w1.b2]; descending walks pass (w1, w0)
     s.cq = vert ? (asc ? 0x6420u : 0x2064u) : (asc ? 0x6240u : 0x2604u);
-    s.s16[0] = asc ? 0x5410u : 0x7632u;
-    s.s16[1] = asc ? 0x7632u : 0x5410u;
     s.h0 = asc ? 0 : 1;
     return s;
 }
 
 // Units prefetched ahead of the recurrence for `regs_per_unit` input registers.
 __host__ __device__ constexpr int units_ahead(int regs_per_unit, int budget) {
-    return budget / regs_per_unit > 6 ? 6 : (budget / regs_per_unit < 2 ? 2 : budget / regs_per_unit);
+    return budget / regs_per_unit > 12 ? 12 : (budget / regs_per_unit < 2 ? 2 : budget / regs_per_unit);
+}
+
+// Sum of the three stored L_r of a pixel pair in one step's u16 words: the
+// other horizontal direction (o) and the two vertical ones (v0, v1).  S8:
+// the two vertical costs add as bytes (L_TB + L_BT <= 2 (MC_max + P2) <= 255).
+template <bool S8>
+__device__ __forceinline__ uint32_t stored3(uint32_t o, uint32_t v0, uint32_t v1, uint32_t sel) {
+    if constexpr (S8)
+        return __byte_perm(o, 0u, sel) + __byte_perm(v0 + v1, 0u, sel);
+    else
+        return __byte_perm(o, 0u, sel) + __byte_perm(v0, 0u, sel) + __byte_perm(v1, 0u, sel);
 }
 
 // One walk.  The inputs of unit k + PU are loaded into unit k's registers as
 // soon as unit k is done, so every load has PU units of the recurrence to
 // arrive, and the loop body is PU units long.
-template <int D, int MODE, bool S8, bool KEY16 = true, bool DBG = false, int PFB = 48>
+template <int D, int MODE, bool S8 = true, bool KEY16 = true, bool DBG = false, int PFB = 48>
 __device__ __forceinline__ void walk(Chain2<D / 32>& ch, const PairsArgs& a, const Bases& bs, const Walk& wk,
                                      const Sel& sel) {
     constexpr int K = D / 32;
-    using In = UnitIn<D, MODE, S8>;
+    using In = UnitIn<D, MODE>;
     constexpr int PU = units_ahead(In::REGS, PFB);
     const int nu = wk.nu;
     if (nu <= 0) return;
@@ -294,23 +339,20 @@ __device__ __forceinline__ void walk(Chain2<D / 32>& ch, const PairsArgs& a, con
     // run is never re-read by the same SM (measured: the L1 path made the
     // first launch 1.7x slower)
     auto load = [&](In& in, uint32_t off) {
-        ldv<K, false>(at(bs.mc, off), in.mc);
-        if constexpr (MODE != kStore) ldv<K, false>(at(bs.o, off), in.o);
+        ldv<K, false, kHintMcLoad>(at(bs.mc, off), in.mc);
         if constexpr (MODE == kWta) {
-            ldv<K, false>(at(bs.sv, off), in.s);
-            if constexpr (!S8) ldv<K, false>(at(bs.sv1, off), in.s1);
+            ldv<K, false, kHintLLoad>(at(bs.o, off), in.o);
+            ldv<K, false, kHintLLoad>(at(bs.v0, off), in.v0);
+            ldv<K, false, kHintLLoad>(at(bs.v1, off), in.v1);
         }
     };
     uint32_t dc[K];
     if constexpr (MODE == kWta) wta_dconst<K, KEY16>(lane, dc);
     uint32_t off_cur = wk.off0, off_ld = wk.off0;
     int qc = wk.qc0;
-    // u16 sums of the vertical pair: step t writes its row's array
-    uint8_t* const sv_first = sel.h0 ? bs.sv1 : bs.out;
-    uint8_t* const sv_second = sel.h0 ? bs.out : bs.sv1;
 
     auto unit = [&](const In& in) {
-        uint32_t first[K];    // kStore / kSumV with byte sums: L of the unit's first step
+        uint32_t first[K];    // kStore: L of the unit's first step
         uint32_t dfirst = 0;  // kWta: disparities of the first step
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
@@ -318,33 +360,20 @@ __device__ __forceinline__ void walk(Chain2<D / 32>& ch, const PairsArgs& a, con
 #pragma unroll
             for (int j = 0; j < K; ++j) m[j] = __byte_perm(in.mc[j], 0u, sel.un[t]);
             ch.step(m, a.P1x2, a.P2x2);
-            if constexpr (MODE == kStore || (MODE == kSumV && S8)) {
+            if constexpr (MODE == kStore) {
                 if (t == 0) {
 #pragma unroll
                     for (int j = 0; j < K; ++j) first[j] = ch.w[j];
                 } else {
                     uint32_t q[K];
 #pragma unroll
-                    for (int j = 0; j < K; ++j) {
-                        q[j] = __byte_perm(first[j], ch.w[j], sel.cq);
-                        // byte sums: both terms and their sum stay below 256 (no carries)
-                        if constexpr (MODE == kSumV) q[j] += in.o[j];
-                    }
-                    stv<K>(at(bs.out, off_cur), q);
+                    for (int j = 0; j < K; ++j) q[j] = __byte_perm(first[j], ch.w[j], sel.cq);
+                    stv<K, kHintLStore>(at(bs.out, off_cur), q);
                 }
-            } else if constexpr (MODE == kSumV) {  // vertical, u16 sums: (S(x0, y), S(x1, y)) per row array
-                uint32_t s[K];
-#pragma unroll
-                for (int j = 0; j < K; ++j) s[j] = ch.w[j] + __byte_perm(in.o[j], 0u, sel.un[t]);
-                stv<K>(at(t == 0 ? sv_first : sv_second, off_cur), s);
             } else {  // kWta (horizontal)
                 uint32_t S[K];
 #pragma unroll
-                for (int j = 0; j < K; ++j) {
-                    const uint32_t sv = S8 ? __byte_perm(in.s[j], 0u, sel.un[t])
-                                           : __byte_perm(in.s[j], in.s1[j], sel.s16[t]);
-                    S[j] = ch.w[j] + __byte_perm(in.o[j], 0u, sel.un[t]) + sv;
-                }
+                for (int j = 0; j < K; ++j) S[j] = ch.w[j] + stored3<S8>(in.o[j], in.v0[j], in.v1[j], sel.un[t]);
                 const uint32_t dd = wta2<K, D, KEY16>(S, dc);
                 if constexpr (DBG) {
                     const int x = 2 * qc + (t == 0 ? sel.h0 : 1 - sel.h0), y0 = 2 * wk.r;
@@ -400,16 +429,17 @@ __device__ __forceinline__ uint32_t* state_slot(const PairsArgs& a, int r, int d
 
 // A lane's 4 K bytes of every quad sit at 4 K lane in each field array.
 template <int D>
-__device__ __forceinline__ Bases lane_bases(const PairsArgs& a, int o_field, int out_field) {
+__device__ __forceinline__ Bases lane_bases(const PairsArgs& a, int out_field, int o_field = kMC) {
     constexpr int K = D / 32;
     uint8_t* const l = a.rec + 4 * K * (threadIdx.x & 31);
-    return Bases{l, l + o_field * a.FS, l + out_field * a.FS, l + kSV * a.FS, l + kSV1 * a.FS};
+    return Bases{l, l + out_field * a.FS, l + o_field * a.FS, l + kLVT * a.FS, l + kLVB * a.FS};
 }
 
-// Launch 1: blocks alternate between vertical line pairs (warp 0 top-to-bottom,
-// warp 1 bottom-to-top) and horizontal line pairs (warp 0 left-to-right,
-// warp 1 right-to-left) while both last.
-template <int D, bool S8>
+// Launch 1: every walker stores its own L_r.  Blocks alternate between
+// vertical line pairs (warp 0 top-to-bottom, warp 1 bottom-to-top, every row)
+// and horizontal line pairs (warp 0 left-to-right over columns [0, n1),
+// warp 1 right-to-left over [W2 - n1, W2)) while both last.
+template <int D>
 __global__ void __launch_bounds__(64) pairs_stage1_kernel(const __grid_constant__ PairsArgs a) {
     constexpr int K = D / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -429,25 +459,18 @@ __global__ void __launch_bounds__(64) pairs_stage1_kernel(const __grid_constant_
     if (vert) {
         const int c = idx;  // columns 2c, 2c + 1
         const uint32_t us = static_cast<uint32_t>(a.QW) * QB, off0 = static_cast<uint32_t>(c) * QB;
-        const int hu = a.Hm / 2;
-        const Bases st = lane_bases<D>(a, 0, kLV);
-        const Bases sm = lane_bases<D>(a, kLV, kSV);
-        // warp 0 walks down (rows [0, Hm) then [Hm, H2)), warp 1 up
         const bool down = warp == 0;
-        const Sel sel = walk_sel(true, down);
-        const Walk w1 = down ? Walk{off0, us, hu, 0, 0, 0} : Walk{off0 + (a.QH - 1) * us, 0u - us, a.QH - hu, 0, 0, 0};
-        const Walk w2 = down ? Walk{off0 + hu * us, us, a.QH - hu, 0, 0, 0} : Walk{off0 + (hu - 1) * us, 0u - us, hu, 0, 0, 0};
-        walk<D, kStore, S8>(ch, a, st, w1, sel);
-        pair_sync();
-        walk<D, kSumV, S8>(ch, a, sm, w2, sel);
+        walk<D, kStore>(ch, a, lane_bases<D>(a, down ? kLVT : kLVB),
+                        down ? Walk{off0, us, a.QH, 0, 0, 0} : Walk{off0 + (a.QH - 1) * us, 0u - us, a.QH, 0, 0, 0},
+                        walk_sel(true, down));
     } else {
         const int r = idx;  // rows 2r, 2r + 1
         const uint32_t off0 = static_cast<uint32_t>(r) * a.QW * QB;
         const int n = a.n1 / 2;
         const bool right = warp == 0;  // warp 0 walks left to right, warp 1 right to left
-        walk<D, kStore, S8>(ch, a, lane_bases<D>(a, 0, right ? kLH0 : kLH1),
-                            right ? Walk{off0, QB, n, 0, 0, r} : Walk{off0 + (a.QW - 1) * QB, 0u - QB, n, 0, 0, r},
-                            walk_sel(false, right));
+        walk<D, kStore>(ch, a, lane_bases<D>(a, right ? kLH0 : kLH1),
+                        right ? Walk{off0, QB, n, 0, 0, r} : Walk{off0 + (a.QW - 1) * QB, 0u - QB, n, 0, 0, r},
+                        walk_sel(false, right));
         if (a.nh2 > 0) {
             uint32_t* st = state_slot<K>(a, r, warp);
 #pragma unroll
@@ -457,65 +480,78 @@ __global__ void __launch_bounds__(64) pairs_stage1_kernel(const __grid_constant_
     }
 }
 
-// Launch 2: blocks [0, nh2) finish the horizontal pairs (one row pair per
-// block); the others run the parallel winner-take-all over columns [b, a).
+// Launch 2a: the rest of the horizontal pairs, one row pair per block (warp 0
+// left to right, warp 1 right to left), finishing their pixels with Eq. 4.
+// Few warps walk long chains here, so they prefetch deep.
 template <int D, bool S8, bool KEY16, bool DBG>
-__global__ void __launch_bounds__(64) pairs_stage2_kernel(const __grid_constant__ PairsArgs a) {
+__global__ void __launch_bounds__(64) pairs_chain2_kernel(const __grid_constant__ PairsArgs a) {
     constexpr int K = D / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t QB = static_cast<uint32_t>(a.QB);
-    if (static_cast<int>(blockIdx.x) < a.nh2) {
-        const int r = blockIdx.x;
-        Chain2<K> ch;
-        ch.init(lane);
-        {
-            const uint32_t* st = state_slot<K>(a, r, warp);
+    const int r = blockIdx.x;
+    Chain2<K> ch;
+    ch.init(lane);
+    {
+        const uint32_t* st = state_slot<K>(a, r, warp);
 #pragma unroll
-            for (int j = 0; j < K; ++j) ch.w[j] = __ldcg(st + j);
-            ch.mpx2 = __ldcg(st + K);
-            ch.exchange();
-        }
-        const uint32_t off0 = static_cast<uint32_t>(r) * a.QW * QB;
-        const int n1u = a.n1 / 2, au = a.a / 2, bu = a.b / 2, ru = (a.W2 - a.n1) / 2;
-        const bool right = warp == 0;  // warp 0 walks left to right, warp 1 right to left
-        const Sel sel = walk_sel(false, right);
-        walk<D, kStore, S8>(ch, a, lane_bases<D>(a, 0, right ? kLH0 : kLH1),
-                            right ? Walk{off0 + n1u * QB, QB, au - n1u, 0, 0, r}
-                                  : Walk{off0 + (ru - 1) * QB, 0u - QB, ru - bu, 0, 0, r},
-                            sel);
-        if (a.a > a.n1) pair_sync();  // the other direction's stores of this launch
-        walk<D, kWta, S8, KEY16, DBG, 72>(ch, a, lane_bases<D>(a, right ? kLH1 : kLH0, 0),
-                                          right ? Walk{off0 + au * QB, QB, a.QW - au, au, 1, r}
-                                                : Walk{off0 + (bu - 1) * QB, 0u - QB, bu, bu - 1, -1, r},
-                                          sel);
-        return;
+        for (int j = 0; j < K; ++j) ch.w[j] = __ldcg(st + j);
+        ch.mpx2 = __ldcg(st + K);
+        ch.exchange();
     }
-    // parallel winner-take-all: one quad per warp (its loads wait for DRAM
-    // once; many warps keep many quads in flight)
+    const uint32_t off0 = static_cast<uint32_t>(r) * a.QW * QB;
+    const int n1u = a.n1 / 2, au = a.a / 2, bu = a.b / 2, ru = (a.W2 - a.n1) / 2;
+    const bool right = warp == 0;
+    const Sel sel = walk_sel(false, right);
+    walk<D, kStore>(ch, a, lane_bases<D>(a, right ? kLH0 : kLH1),
+                    right ? Walk{off0 + n1u * QB, QB, au - n1u, 0, 0, r}
+                          : Walk{off0 + (ru - 1) * QB, 0u - QB, ru - bu, 0, 0, r},
+                    sel);
+    if (a.a > a.n1) pair_sync();  // the other direction's stores of this launch
+    walk<D, kWta, S8, KEY16, DBG, kChainPrefetchRegs>(ch, a, lane_bases<D>(a, kMC, right ? kLH1 : kLH0),
+                                                      right ? Walk{off0 + au * QB, QB, a.QW - au, au, 1, r}
+                                                            : Walk{off0 + (bu - 1) * QB, 0u - QB, bu, bu - 1, -1, r},
+                                                      sel);
+}
+
+// Launch 2b (beside 2a): the winner-take-all of the quads in columns [b, a),
+// which both horizontal directions passed in launch 1.  Each warp takes
+// kParItems quads and issues all their loads before the first sum, so many
+// quads are in flight.
+template <int D, bool S8, bool KEY16, bool DBG>
+__global__ void __launch_bounds__(64) pairs_par_kernel(const __grid_constant__ PairsArgs a) {
+    constexpr int K = D / 32, NI = kParItems;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cols = (a.a - a.b) / 2, items = cols * a.QH;
-    if (cols <= 0) return;
     uint32_t dc[K];
     wta_dconst<K, KEY16>(lane, dc);
-    const int nw = 2 * a.npw;
     const int lb = 4 * K * lane;
-    for (int it = (blockIdx.x - a.nh2) * 2 + warp; it < items; it += nw) {
+    const int it0 = (blockIdx.x * 2 + warp) * NI;
+    uint32_t l0[NI][K], l1[NI][K], v0[NI][K], v1[NI][K];
+#pragma unroll
+    for (int n = 0; n < NI; ++n) {
+        const int it = min(it0 + n, items - 1);  // past the end: re-read the last quad
+        const uint8_t* q = a.rec + (static_cast<size_t>(it / cols) * a.QW + a.b / 2 + it % cols) * a.QB + lb;
+        ldv<K, false, kHintLLoad>(q + kLH0 * a.FS, l0[n]);
+        ldv<K, false, kHintLLoad>(q + kLH1 * a.FS, l1[n]);
+        ldv<K, false, kHintLLoad>(q + kLVT * a.FS, v0[n]);
+        ldv<K, false, kHintLLoad>(q + kLVB * a.FS, v1[n]);
+    }
+#pragma unroll
+    for (int n = 0; n < NI; ++n) {
+        const int it = it0 + n;
+        if (it >= items) return;
         const int r = it / cols, qx = a.b / 2 + it % cols;
-        const uint8_t* q = a.rec + (static_cast<size_t>(r) * a.QW + qx) * a.QB + lb;
-        uint32_t l0[K], l1[K], sv[K], sv1[K];
-        ldv<K, false>(q + kLH0 * a.FS, l0);
-        ldv<K, false>(q + kLH1 * a.FS, l1);
-        ldv<K, false>(q + kSV * a.FS, sv);
-        if constexpr (!S8) ldv<K, false>(q + kSV1 * a.FS, sv1);
         uint32_t dd[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {  // rows 2r and 2r + 1
             uint32_t S[K];
 #pragma unroll
             for (int j = 0; j < K; ++j) {
-                if constexpr (S8)  // both stored costs in a byte: l0 + l1 <= 2 (MC_max + P2) <= 255
-                    S[j] = unq<true>(l0[j] + l1[j], h) + unq<true>(sv[j], h);
+                if constexpr (S8)  // pairs of stored costs in a byte: each pair <= 2 (MC_max + P2) <= 255
+                    S[j] = unq<true>(l0[n][j] + l1[n][j], h) + unq<true>(v0[n][j] + v1[n][j], h);
                 else
-                    S[j] = unq<true>(l0[j], h) + unq<true>(l1[j], h) + (h ? sv1[j] : sv[j]);
+                    S[j] = unq<true>(l0[n][j], h) + unq<true>(l1[n][j], h) + unq<true>(v0[n][j], h) +
+                           unq<true>(v1[n][j], h);
             }
             dd[h] = wta2<K, D, KEY16>(S, dc);
             if constexpr (DBG) {
@@ -549,31 +585,47 @@ struct PairsD {
     static cudaError_t stage1(const PairsArgs& a, cudaStream_t s) {
         const int grid = a.nvb + a.nhb;
         if (grid <= 0) return cudaSuccess;
-        if (a.s8)
-            pairs_stage1_kernel<D, true><<<grid, 64, 0, s>>>(a);
-        else
-            pairs_stage1_kernel<D, false><<<grid, 64, 0, s>>>(a);
+        pairs_stage1_kernel<D><<<grid, 64, 0, s>>>(a);
         return cudaGetLastError();
     }
     template <bool S8, bool KEY16>
-    static void stage2_t(const PairsArgs& a, int grid, cudaStream_t s) {
+    static void chain_t(const PairsArgs& a, cudaStream_t s) {
         if (a.Sdbg)
-            pairs_stage2_kernel<D, S8, KEY16, true><<<grid, 64, 0, s>>>(a);
+            pairs_chain2_kernel<D, S8, KEY16, true><<<a.nh2, 64, 0, s>>>(a);
         else
-            pairs_stage2_kernel<D, S8, KEY16, false><<<grid, 64, 0, s>>>(a);
+            pairs_chain2_kernel<D, S8, KEY16, false><<<a.nh2, 64, 0, s>>>(a);
     }
-    static cudaError_t stage2(const PairsArgs& a, cudaStream_t s) {
-        const int grid = a.nh2 + a.npw;
-        if (grid <= 0) return cudaSuccess;
+    template <bool S8, bool KEY16>
+    static void par_t(const PairsArgs& a, cudaStream_t s) {
+        if (a.Sdbg)
+            pairs_par_kernel<D, S8, KEY16, true><<<a.npw, 64, 0, s>>>(a);
+        else
+            pairs_par_kernel<D, S8, KEY16, false><<<a.npw, 64, 0, s>>>(a);
+    }
+    static cudaError_t chain2(const PairsArgs& a, cudaStream_t s) {
+        if (a.nh2 <= 0) return cudaSuccess;
         const bool k16 = key16(a);
         if (a.s8 && k16)
-            stage2_t<true, true>(a, grid, s);
+            chain_t<true, true>(a, s);
         else if (a.s8)
-            stage2_t<true, false>(a, grid, s);
+            chain_t<true, false>(a, s);
         else if (k16)
-            stage2_t<false, true>(a, grid, s);
+            chain_t<false, true>(a, s);
         else
-            stage2_t<false, false>(a, grid, s);
+            chain_t<false, false>(a, s);
+        return cudaGetLastError();
+    }
+    static cudaError_t par(const PairsArgs& a, cudaStream_t s) {
+        if (a.npw <= 0) return cudaSuccess;
+        const bool k16 = key16(a);
+        if (a.s8 && k16)
+            par_t<true, true>(a, s);
+        else if (a.s8)
+            par_t<true, false>(a, s);
+        else if (k16)
+            par_t<false, true>(a, s);
+        else
+            par_t<false, false>(a, s);
         return cudaGetLastError();
     }
 };
@@ -585,16 +637,22 @@ struct PairsD {
 template <int D>
 SGM_INTERNAL_P cudaError_t pairs_launch1(const PairsArgs& a, cudaStream_t s);
 template <int D>
-SGM_INTERNAL_P cudaError_t pairs_launch2(const PairsArgs& a, cudaStream_t s);
+SGM_INTERNAL_P cudaError_t pairs_launch_chain2(const PairsArgs& a, cudaStream_t s);
+template <int D>
+SGM_INTERNAL_P cudaError_t pairs_launch_par(const PairsArgs& a, cudaStream_t s);
 
-#define SGM_INSTANTIATE_PAIRS(D)                                                      \
-    template <>                                                                       \
-    SGM_INTERNAL_P cudaError_t pairs_launch1<D>(const PairsArgs& a, cudaStream_t s) { \
-        return pairs::PairsD<D>::stage1(a, s);                                        \
-    }                                                                                 \
-    template <>                                                                       \
-    SGM_INTERNAL_P cudaError_t pairs_launch2<D>(const PairsArgs& a, cudaStream_t s) { \
-        return pairs::PairsD<D>::stage2(a, s);                                        \
+#define SGM_INSTANTIATE_PAIRS(D)                                                            \
+    template <>                                                                             \
+    SGM_INTERNAL_P cudaError_t pairs_launch1<D>(const PairsArgs& a, cudaStream_t s) {       \
+        return pairs::PairsD<D>::stage1(a, s);                                              \
+    }                                                                                       \
+    template <>                                                                             \
+    SGM_INTERNAL_P cudaError_t pairs_launch_chain2<D>(const PairsArgs& a, cudaStream_t s) { \
+        return pairs::PairsD<D>::chain2(a, s);                                              \
+    }                                                                                       \
+    template <>                                                                             \
+    SGM_INTERNAL_P cudaError_t pairs_launch_par<D>(const PairsArgs& a, cudaStream_t s) {    \
+        return pairs::PairsD<D>::par(a, s);                                                 \
     }
 
 }  // namespace sgm

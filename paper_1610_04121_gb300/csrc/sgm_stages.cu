@@ -345,6 +345,7 @@ cudaError_t launch_cost(const void* Fb, const void* Fm, uint8_t* rec, int RB, in
 // groups, so a warp's stores cover 512 contiguous bytes.
 // ---------------------------------------------------------------------------
 constexpr int kQcSeg = 32, kQcThreads = 128;
+constexpr bool kQuadCostKeepInL2 = false;
 
 template <int D, class FT>
 __device__ __forceinline__ void cost_quads_body(const FT* __restrict__ Fb, const FT* __restrict__ Fm,
@@ -410,7 +411,17 @@ __device__ __forceinline__ void cost_quads_body(const FT* __restrict__ Fb, const
             // bytes [c(0,0), c(1,0), c(0,1), c(1,1)]
             q[e] = __byte_perm(c[0][0][e] | (c01 << 16), c10 | (c11 << 16), 0x6240u);
         }
-        *reinterpret_cast<uint4*>(mc + ((size_t)qy * QW + qx0 + ql) * QB + 4 * d0) = make_uint4(q[0], q[1], q[2], q[3]);
+        uint8_t* dst = mc + ((size_t)qy * QW + qx0 + ql) * QB + 4 * d0;
+        if constexpr (kQuadCostKeepInL2) {
+            // the four walkers read these costs again: keep them in L2 over the streamed cubes
+            uint64_t pol;
+            asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+            asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(dst), "r"(q[0]), "r"(q[1]),
+                         "r"(q[2]), "r"(q[3]), "l"(pol)
+                         : "memory");
+        } else {
+            *reinterpret_cast<uint4*>(dst) = make_uint4(q[0], q[1], q[2], q[3]);
+        }
     }
 }
 

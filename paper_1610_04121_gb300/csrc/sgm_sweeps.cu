@@ -59,7 +59,7 @@ cudaError_t launch_sweep_v_batch(JobTable<SweepArgs>& t, cudaStream_t stream) {
 
 // The paired-line 4-path schedule: n1 steps of each horizontal direction
 // beside the vertical pair in the first launch (default min(W2, H2), which
-// ends both at the same step), the vertical pair meeting at row Hm.
+// ends both at the same step).
 PairsArgs pairs_geometry(int W, int H, int D, int n1_req) {
     PairsArgs a{};
     a.W = W;
@@ -71,7 +71,6 @@ PairsArgs pairs_geometry(int W, int H, int D, int n1_req) {
     a.QH = a.H2 / 2;
     int n1 = n1_req < 0 ? std::min(a.W2, a.H2) : n1_req;
     a.n1 = std::max(0, std::min(a.W2, n1 & ~1));
-    a.Hm = (a.H2 / 2) & ~1;
     if (a.W2 > 2 * a.n1) {
         a.a = a.b = (a.W2 / 2) & ~1;  // the horizontal pair meets in the middle in the second launch
     } else {
@@ -82,7 +81,8 @@ PairsArgs pairs_geometry(int W, int H, int D, int n1_req) {
     a.nhb = a.QH;
     a.nh2 = a.W2 > a.n1 ? a.QH : 0;
     const int par = (a.a - a.b) / 2 * a.QH;  // quads of the parallel winner-take-all
-    a.npw = par > 0 ? (par + 1) / 2 : 0;      // one quad per warp, two warps per block
+    const int per_block = 2 * pairs::kParItems;
+    a.npw = par > 0 ? (par + per_block - 1) / per_block : 0;
     return a;
 }
 
@@ -90,8 +90,12 @@ cudaError_t launch_pairs_stage1(const PairsArgs& a, cudaStream_t stream) {
     SGM_DISPATCH_D(pairs_launch1, a.D, a, stream)
 }
 
-cudaError_t launch_pairs_stage2(const PairsArgs& a, cudaStream_t stream) {
-    SGM_DISPATCH_D(pairs_launch2, a.D, a, stream)
+cudaError_t launch_pairs_chain2(const PairsArgs& a, cudaStream_t stream) {
+    SGM_DISPATCH_D(pairs_launch_chain2, a.D, a, stream)
+}
+
+cudaError_t launch_pairs_par(const PairsArgs& a, cudaStream_t stream) {
+    SGM_DISPATCH_D(pairs_launch_par, a.D, a, stream)
 }
 
 }  // namespace sgm

@@ -53,13 +53,16 @@ def test_autotuner_picks_one_and_keeps_it(sgm):
         assert sgm.sgm_schedule_for(c.handle, 160, 96, 64, 7, 84, 4) == -1  # not tuned yet
         before = c.launches
         assert (c.compute(pair.left, pair.right, 64, 7, 84, 4) == ref).all()
-        # tuning: per schedule one warm-up and five timed runs, then the chosen run
-        assert c.launches - before == 5 * (3 * 6 + 1)
+        # tuning: per schedule one warm-up and five timed runs, then the chosen
+        # run; a path is 5 kernels, 6 with the paired schedule (its second
+        # launch is two kernels side by side)
+        per_path = {0: 5, 1: 5, 2: 6}
         chosen = sgm.sgm_schedule_for(c.handle, 160, 96, 64, 7, 84, 4)
         assert chosen in (0, 1, 2)
+        assert c.launches - before == 6 * sum(per_path.values()) + per_path[chosen]
         before = c.launches
         assert (c.compute(pair.left, pair.right, 64, 7, 84, 4) == ref).all()
-        assert c.launches - before == 5
+        assert c.launches - before == per_path[chosen]
         assert sgm.sgm_schedule_for(c.handle, 160, 96, 64, 7, 84, 4) == chosen
         # other path counts have one schedule
         assert sgm.sgm_schedule_for(c.handle, 160, 96, 64, 7, 84, 8) == 0
