@@ -20,6 +20,7 @@ from .oracle import (  # noqa: F401
     wta,
     median3x3,
     sgm,
+    sgm_threads,
     sgm_ex,
     aggregate_ex,
     subpixel,

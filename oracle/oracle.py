@@ -39,8 +39,8 @@ def build(force: bool = False) -> str:
     os.makedirs(_OUT_DIR, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.run(["gcc", "-O2", "-std=c11", "-Wall", "-Wextra", "-shared", "-fPIC", "-o", tmp, _SRC],
-                       check=True)
+        subprocess.run(["gcc", "-O2", "-std=c11", "-Wall", "-Wextra", "-shared", "-fPIC", "-pthread", "-o", tmp,
+                        _SRC], check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -88,6 +88,8 @@ def load() -> ctypes.CDLL:
             lib.oracle_median3x3_u16.restype = None
             lib.oracle_sgm_ex.argtypes = [_u8p, _u8p] + [ctypes.c_int] * 7 + [ctypes.c_uint, _u16p, _u8p, _u8p]
             lib.oracle_sgm_ex.restype = ctypes.c_int
+            lib.oracle_sgm_threads.argtypes = [_u8p, _u8p] + [ctypes.c_int] * 6 + [_u8p, ctypes.c_int]
+            lib.oracle_sgm_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -276,6 +278,20 @@ def sgm(left: np.ndarray, right: np.ndarray, D: int, P1: int, P2: int, n_paths: 
     if debug:
         return {"disp": disp, "raw": raw, "Fb": Fb, "Fm": Fm, "S": S}
     return disp
+
+
+def sgm_threads(left: np.ndarray, right: np.ndarray, D: int, P1: int, P2: int, n_paths: int,
+                nthreads: int) -> np.ndarray:
+    """oracle_sgm's disparity with its independent parts on ``nthreads`` threads
+    (the CPU baseline's all-core timing; ``sgm`` stays the parity reference)."""
+    left, right = _img(left), _img(right)
+    H, W = left.shape
+    out = np.zeros((H, W), dtype=np.uint8)
+    rc = load().oracle_sgm_threads(_ptr(left, _u8p), _ptr(right, _u8p), W, H, D, P1, P2, n_paths, _ptr(out, _u8p),
+                                   nthreads)
+    if rc != 0:
+        raise RuntimeError(f"oracle_sgm_threads failed ({rc})")
+    return out
 
 
 def pixel(left: np.ndarray, right: np.ndarray, D: int, P1: int, P2: int, n_paths: int, x: int, y: int

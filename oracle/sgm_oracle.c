@@ -581,3 +581,223 @@ done:
     free(v);
     return rc;
 }
+
+/*
+ * The same computation as oracle_sgm (CSCT features), with its independent
+ * parts spread over `nthreads` POSIX threads.  It exists to time the CPU
+ * baseline on every host core; the parity reference stays oracle_sgm, and a
+ * test checks that both give identical disparities.  The work splits along
+ * what the definitions leave independent: rows of the Census (Eq. 1), of the
+ * matching cost (Eq. 2), of the sum and the winner-take-all (Eq. 4) and of the
+ * median; and, for Eq. 3, whole directions, each one's rows (horizontal
+ * paths, whose predecessors lie in the same row) or columns (vertical paths)
+ * in bands.  Diagonal directions run whole on one thread each.
+ */
+#include <pthread.h>
+
+typedef struct {
+    int kind; /* 0 census rows, 1 cost rows, 2 aggregation band, 3 sum and WTA rows, 4 median rows */
+    int a0, a1; /* rows (kinds 0, 1, 3, 4) or the band's rows / columns (kind 2) */
+    int img, r; /* census: 0 left, 1 right; aggregation: direction index */
+} oracle_task;
+
+typedef struct {
+    const uint8_t *left, *right;
+    int W, H, D, P1, P2, npaths, rx[8], ry[8];
+    uint32_t *Fb, *Fm;
+    uint8_t *MC, *raw, *disp;
+    int32_t *L; /* npaths cubes */
+    oracle_task *tasks;
+    int ntasks;
+    int next; /* next task, taken under the lock */
+    pthread_mutex_t lock;
+} oracle_job;
+
+/* Eq. 3 for direction r over the pixels x in [x0, x1), y in [y0, y1) of a band
+ * that holds every predecessor of its pixels; the loop is oracle_aggregate_ex's. */
+static void aggregate_band(const oracle_job *J, int r, int x0b, int x1b, int y0b, int y1b) {
+    const int W = J->W, H = J->H, D = J->D, rx = J->rx[r], ry = J->ry[r];
+    int32_t *L = J->L + (size_t)r * W * H * D;
+    int y0 = (ry >= 0) ? y0b : y1b - 1, y1 = (ry >= 0) ? y1b : y0b - 1, sy = (ry >= 0) ? 1 : -1;
+    int x0 = (rx >= 0) ? x0b : x1b - 1, x1 = (rx >= 0) ? x1b : x0b - 1, sx = (rx >= 0) ? 1 : -1;
+    for (int y = y0; y != y1; y += sy) {
+        for (int x = x0; x != x1; x += sx) {
+            const uint8_t *mc = J->MC + ((size_t)y * W + x) * D;
+            int32_t *out = L + ((size_t)y * W + x) * D;
+            int qx = x - rx, qy = y - ry;
+            if (qx < 0 || qx >= W || qy < 0 || qy >= H) {
+                for (int d = 0; d < D; ++d) out[d] = mc[d];
+                continue;
+            }
+            const int32_t *prev = L + ((size_t)qy * W + qx) * D;
+            int32_t mprev = prev[0];
+            for (int k = 1; k < D; ++k)
+                if (prev[k] < mprev) mprev = prev[k];
+            for (int d = 0; d < D; ++d) {
+                int32_t best = prev[d];
+                if (d - 1 >= 0 && prev[d - 1] + J->P1 < best) best = prev[d - 1] + J->P1;
+                if (d + 1 < D && prev[d + 1] + J->P1 < best) best = prev[d + 1] + J->P1;
+                if (mprev + J->P2 < best) best = mprev + J->P2;
+                out[d] = (int32_t)mc[d] + best - mprev;
+            }
+        }
+    }
+}
+
+static void run_task(oracle_job *J, const oracle_task *t) {
+    const int W = J->W, H = J->H, D = J->D;
+    if (t->kind == 0) {
+        const uint8_t *I = t->img ? J->right : J->left;
+        uint32_t *F = t->img ? J->Fm : J->Fb;
+        for (int y = t->a0; y < t->a1; ++y)
+            for (int x = 0; x < W; ++x) F[(size_t)y * W + x] = oracle_csct_at(I, W, H, x, y);
+    } else if (t->kind == 1) {
+        for (int y = t->a0; y < t->a1; ++y)
+            for (int x = 0; x < W; ++x)
+                for (int d = 0; d < D; ++d) {
+                    uint32_t v = J->Fb[(size_t)y * W + x] ^ match_feature(J->Fm, W, x - d, y);
+                    J->MC[((size_t)y * W + x) * D + d] = (uint8_t)oracle_bitcount(v);
+                }
+    } else if (t->kind == 2) {
+        const int r = t->r;
+        if (J->ry[r] == 0)
+            aggregate_band(J, r, 0, W, t->a0, t->a1); /* horizontal: rows */
+        else if (J->rx[r] == 0)
+            aggregate_band(J, r, t->a0, t->a1, 0, H); /* vertical: columns */
+        else
+            aggregate_band(J, r, 0, W, 0, H); /* diagonal: whole */
+    } else if (t->kind == 3) {
+        for (size_t p = (size_t)t->a0 * W; p < (size_t)t->a1 * W; ++p) {
+            int best = 0;
+            int32_t sbest = 0;
+            for (int d = 0; d < D; ++d) {
+                int32_t s = 0;
+                for (int r = 0; r < J->npaths; ++r) s += J->L[((size_t)r * W * H + p) * D + d];
+                if (d == 0 || s < sbest) {
+                    sbest = s;
+                    best = d;
+                }
+            }
+            J->raw[p] = (uint8_t)best;
+        }
+    } else {
+        for (int y = t->a0; y < t->a1; ++y) {
+            for (int x = 0; x < W; ++x) {
+                size_t p = (size_t)y * W + x;
+                if (W < 3 || H < 3 || x == 0 || y == 0 || x == W - 1 || y == H - 1) {
+                    J->disp[p] = J->raw[p];
+                    continue;
+                }
+                int v[9], n = 0;
+                for (int j = -1; j <= 1; ++j)
+                    for (int i = -1; i <= 1; ++i) v[n++] = J->raw[(size_t)(y + j) * W + (x + i)];
+                for (int a = 1; a < 9; ++a) {
+                    int tv = v[a], b = a - 1;
+                    while (b >= 0 && v[b] > tv) {
+                        v[b + 1] = v[b];
+                        --b;
+                    }
+                    v[b + 1] = tv;
+                }
+                J->disp[p] = (uint8_t)v[4];
+            }
+        }
+    }
+}
+
+static void *worker(void *arg) {
+    oracle_job *J = (oracle_job *)arg;
+    for (;;) {
+        pthread_mutex_lock(&J->lock);
+        int i = J->next++;
+        pthread_mutex_unlock(&J->lock);
+        if (i >= J->ntasks) return NULL;
+        run_task(J, &J->tasks[i]);
+    }
+}
+
+/* Runs J->tasks on nthreads threads (the calling thread included) and waits. */
+static void run_phase(oracle_job *J, int nthreads) {
+    pthread_t th[256];
+    int started = 0;
+    J->next = 0;
+    for (int i = 1; i < nthreads && i < 256; ++i)
+        if (pthread_create(&th[started], NULL, worker, J) == 0) ++started;
+    worker(J);
+    for (int i = 0; i < started; ++i) pthread_join(th[i], NULL);
+}
+
+/* Tasks of rows [0, n) in bands of about n / (4 nthreads) rows. */
+static int add_bands(oracle_task *t, int k, int kind, int n, int nthreads, int img, int r) {
+    int bands = 4 * nthreads;
+    if (bands > n) bands = n;
+    for (int b = 0; b < bands; ++b) {
+        t[k].kind = kind;
+        t[k].a0 = (int)((long)n * b / bands);
+        t[k].a1 = (int)((long)n * (b + 1) / bands);
+        t[k].img = img;
+        t[k].r = r;
+        ++k;
+    }
+    return k;
+}
+
+ORACLE_EXPORT int oracle_sgm_threads(const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
+                                     int n_paths, uint8_t *disp_out, int nthreads) {
+    oracle_job J;
+    memset(&J, 0, sizeof J);
+    if (W < 1 || H < 1 || D < 1 || D > 256 || !left || !right || !disp_out) return -1;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    J.npaths = oracle_directions(n_paths, J.rx, J.ry);
+    if (J.npaths == 0) return -1;
+    J.left = left;
+    J.right = right;
+    J.W = W;
+    J.H = H;
+    J.D = D;
+    J.P1 = P1;
+    J.P2 = P2;
+    J.disp = disp_out;
+    size_t n = (size_t)W * H;
+    J.Fb = (uint32_t *)malloc(n * sizeof(uint32_t));
+    J.Fm = (uint32_t *)malloc(n * sizeof(uint32_t));
+    J.MC = (uint8_t *)malloc(n * D);
+    J.raw = (uint8_t *)malloc(n);
+    J.L = (int32_t *)malloc((size_t)J.npaths * n * D * sizeof(int32_t));
+    int maxt = 8 * nthreads * (J.npaths + 2) + 16;
+    J.tasks = (oracle_task *)malloc((size_t)maxt * sizeof(oracle_task));
+    int rc = -2;
+    if (J.Fb && J.Fm && J.MC && J.raw && J.L && J.tasks) {
+        pthread_mutex_init(&J.lock, NULL);
+        int k = add_bands(J.tasks, 0, 0, H, nthreads, 0, 0);
+        J.ntasks = add_bands(J.tasks, k, 0, H, nthreads, 1, 0);
+        run_phase(&J, nthreads);
+        J.ntasks = add_bands(J.tasks, 0, 1, H, nthreads, 0, 0);
+        run_phase(&J, nthreads);
+        k = 0;
+        for (int r = 0; r < J.npaths; ++r) {
+            if (J.ry[r] == 0)
+                k = add_bands(J.tasks, k, 2, H, nthreads, 0, r);
+            else if (J.rx[r] == 0)
+                k = add_bands(J.tasks, k, 2, W, nthreads, 0, r);
+            else
+                k = add_bands(J.tasks, k, 2, 1, nthreads, 0, r);
+        }
+        J.ntasks = k;
+        run_phase(&J, nthreads);
+        J.ntasks = add_bands(J.tasks, 0, 3, H, nthreads, 0, 0);
+        run_phase(&J, nthreads);
+        J.ntasks = add_bands(J.tasks, 0, 4, H, nthreads, 0, 0);
+        run_phase(&J, nthreads);
+        pthread_mutex_destroy(&J.lock);
+        rc = 0;
+    }
+    free(J.Fb);
+    free(J.Fm);
+    free(J.MC);
+    free(J.raw);
+    free(J.L);
+    free(J.tasks);
+    return rc;
+}
