@@ -337,9 +337,11 @@ SGM_API const char *sgm_version(void);
  * stream) and returns without waiting.  It needs no context and calls no
  * cudaMalloc, cudaFree or other allocating routine: every intermediate lives
  * in one static device array of 48 MiB that each GPU which loads the library
- * keeps until the process exits.  Sizes whose intermediates do not fit are
- * rejected with SGM_EINVAL (320x240 with D = 64 and 8 paths fits; 640x480
- * with D = 128 does not).
+ * keeps until the process exits.  The intermediates take 8 W H bytes for the
+ * features, W H (3 D) bytes (2 paths) or W H (4 D) bytes (4 or 8 paths) for
+ * the per-pixel records and W H for the raw disparity; sizes that do not fit
+ * are rejected with SGM_EINVAL (320x240 with D = 128 and 8 paths fits, about
+ * 40 MB; 640x480 with D = 128 does not).
  *
  * The first call on a device looks up the array's device address and sets
  * kernel attributes; make that first call before any stream capture.  Every

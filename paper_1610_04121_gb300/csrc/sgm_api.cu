@@ -397,9 +397,9 @@ static cudaError_t enqueue_match(const Problem& p, const Layout& l, uint8_t* are
     if ((e = launch_census(base, match, Fb, Fm, p.W, p.H, p.ct62 != 0, s)) != cudaSuccess) return e;
     if ((e = mark()) != cudaSuccess) return e;
     if (pairs_sched(p)) {
-        // two lines per warp over quad records: the vertical pair beside the
-        // first n1 steps of each horizontal direction, then the horizontal
-        // rest with Eq. 4 beside the parallel winner-take-all; raw in quads
+        // two lines per warp over quad cubes: the costs, then every walker
+        // storing its L_r beside the others, then the horizontal rest with
+        // Eq. 4 beside the parallel winner-take-all; raw in quads
         if ((e = launch_cost_quads(Fb, Fm, arena + l.rec, l.RB, p.W, p.H, p.D, p.ct62 != 0, s)) != cudaSuccess)
             return e;
         if ((e = mark()) != cudaSuccess) return e;

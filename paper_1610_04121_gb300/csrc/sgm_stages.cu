@@ -23,7 +23,7 @@ namespace sgm {
 // gathered as four independent 8-bit chains joined by byte permutes, which
 // keeps the dependent chain per pixel short.
 // ---------------------------------------------------------------------------
-constexpr int kCtT = 32, kCtW = 2 * kCtT, kCtH = 8;
+constexpr int kCtT = 32, kCtW = 2 * kCtT, kCtH = 4;
 
 // Census feature of the pixel whose 9 window columns start at column c0 of
 // the window rows; row k of the window (image y - 3 + k) is win[(r + k) % 7].
@@ -340,17 +340,17 @@ cudaError_t launch_cost(const void* Fb, const void* Fm, uint8_t* rec, int RB, in
 // 32-bit word (pixel (2qx + i, 2qy + j)); padding pixels (x >= W or y >= H)
 // get MC = 0.  A CTA covers kQcSeg quads of one quad row: the two rows' base
 // features and the match features x0 - D .. x0 + 2 kQcSeg - 1 are staged in
-// shared memory.  A thread computes four consecutive disparities of one quad
-// (16 bytes, one store); consecutive threads take consecutive disparity
-// groups, so a warp's stores cover 512 contiguous bytes.
+// shared memory.  A thread computes kQcDisp = 8 consecutive disparities of
+// one quad (one 32-byte store; the quad cube is 256-byte aligned and a quad
+// takes 4D bytes) from nine match features of each row; the 32 threads of a
+// warp take 8 quads x 4 disparity groups.
 // ---------------------------------------------------------------------------
-constexpr int kQcSeg = 32, kQcThreads = 128;
-constexpr bool kQuadCostKeepInL2 = false;
+constexpr int kQcSeg = 32, kQcThreads = 128, kQcDisp = 8;
 
 template <int D, class FT>
 __device__ __forceinline__ void cost_quads_body(const FT* __restrict__ Fb, const FT* __restrict__ Fm,
                                                 uint8_t* __restrict__ mc, int QB, int W, int H, int bx, int qy) {
-    constexpr int NG = D / 4, SW = 2 * kQcSeg, NF = SW + D;
+    constexpr int NG = D / kQcDisp, SW = 2 * kQcSeg, NF = SW + D;
     __shared__ __align__(16) FT fm[2][NF];  // fm[j][k] = F_match(x0 - D + k, 2 qy + j)
     __shared__ __align__(16) FT fb[2][SW];  // fb[j][k] = F_base(x0 + k, 2 qy + j)
     const int qx0 = bx * kQcSeg, x0 = 2 * qx0, QW = (W + 1) / 2;
@@ -380,48 +380,43 @@ __device__ __forceinline__ void cost_quads_body(const FT* __restrict__ Fb, const
     }
     __syncthreads();
     const int nq = min(kQcSeg, QW - qx0);
-    const int items = nq * NG;
+    // a warp takes 8 quads x 4 disparity groups: its feature loads span 40
+    // words of shared memory (few bank conflicts) and its stores 8 runs of
+    // 128 contiguous bytes
+    const int items = ((nq + 7) / 8) * 8 * NG;
     // padding: column 2qx + 1 beyond the image only in the last quad column
     // (odd W), row 2qy + 1 only in the last quad row (odd H)
     const bool row1 = 2 * qy + 1 < H;
     for (int t = threadIdx.x; t < items; t += kQcThreads) {
-        const int g = t % NG, ql = t / NG, xl = 2 * ql, d0 = 4 * g;
+        const int lane = t % 32, blk = t / 32, go = blk % (NG / 4), qo = blk / (NG / 4);
+        const int ql = 8 * qo + lane % 8, g = 4 * go + lane / 8, xl = 2 * ql, d0 = kQcDisp * g;
+        if (ql >= nq) continue;
         const bool col1 = x0 + xl + 1 < W;
-        uint32_t c[2][2][4];  // c[i][j][e]: pixel (x0 + xl + i, 2qy + j), d = d0 + e
+        // byte weights of pixels (1, 0), (0, 1), (1, 1) in a quad word (0 at
+        // padding pixels): the word is built by multiply-adds
+        const uint32_t w10 = col1 ? 0x100u : 0u, w01 = row1 ? 0x10000u : 0u, w11 = (row1 && col1) ? 0x1000000u : 0u;
+        uint32_t q[kQcDisp];
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            // match features of pixels xl, xl + 1 at d0 .. d0 + 3: fm[j][xl + i - d + D]
-            const int kb = xl + D - d0 - 4;  // even: six values kb .. kb + 5 cover them
-            FT m[6];
+            // match features of pixels xl, xl + 1 at d0 .. d0 + kQcDisp - 1:
+            // fm[j][xl + i - d + D] = m[kQcDisp + i - e] for d = d0 + e
+            const int kb = xl + D - d0 - kQcDisp;  // even
+            FT m[kQcDisp + 2];
 #pragma unroll
-            for (int k = 0; k < 6; k += 2) ld2(&fm[j][kb + k], m[k], m[k + 1]);
+            for (int k = 0; k < kQcDisp + 2; k += 2) ld2(&fm[j][kb + k], m[k], m[k + 1]);
             FT b0, b1;
             ld2(&fb[j][xl], b0, b1);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                c[0][j][e] = bitcount(b0 ^ m[4 - e]);  // fm[j][xl - (d0 + e) + D] = m[4 - e]
-                c[1][j][e] = bitcount(b1 ^ m[5 - e]);
+            for (int e = 0; e < kQcDisp; ++e) {
+                const uint32_t c0 = bitcount(b0 ^ m[kQcDisp - e]), c1 = bitcount(b1 ^ m[kQcDisp + 1 - e]);
+                q[e] = j == 0 ? c0 + c1 * w10 : q[e] + c0 * w01 + c1 * w11;
             }
         }
-        uint32_t q[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const uint32_t c01 = row1 ? c[0][1][e] : 0u, c10 = col1 ? c[1][0][e] : 0u,
-                           c11 = (row1 && col1) ? c[1][1][e] : 0u;
-            // bytes [c(0,0), c(1,0), c(0,1), c(1,1)]
-            q[e] = __byte_perm(c[0][0][e] | (c01 << 16), c10 | (c11 << 16), 0x6240u);
-        }
+        // one 32-byte store
         uint8_t* dst = mc + ((size_t)qy * QW + qx0 + ql) * QB + 4 * d0;
-        if constexpr (kQuadCostKeepInL2) {
-            // the four walkers read these costs again: keep them in L2 over the streamed cubes
-            uint64_t pol;
-            asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-            asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(dst), "r"(q[0]), "r"(q[1]),
-                         "r"(q[2]), "r"(q[3]), "l"(pol)
-                         : "memory");
-        } else {
-            *reinterpret_cast<uint4*>(dst) = make_uint4(q[0], q[1], q[2], q[3]);
-        }
+        asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst), "r"(q[0]), "r"(q[1]),
+                     "r"(q[2]), "r"(q[3]), "r"(q[4]), "r"(q[5]), "r"(q[6]), "r"(q[7])
+                     : "memory");
     }
 }
 

@@ -108,12 +108,16 @@ def test_served_results_match_and_tickets_retire(sgm):
         c.close()
 
 
-def test_launch_counter_counts_kernels(ctx):
+def test_launch_counter_counts_kernels(sgm, ctx):
     p = _pair()
     ctx.compute(p.left, p.right, 64, 7, 84, 4)  # the first call of a 4-path key also tunes its schedule
     before = ctx.launches
     ctx.compute(p.left, p.right, 64, 7, 84, 4)
-    assert ctx.launches - before == 5  # census, cost, horizontal + vertical first halves, vertical rest, median
+    H, W = p.left.shape
+    # census, cost, the two sweep stages, median; the paired schedule runs its
+    # second sweep stage as two kernels side by side
+    paired = sgm.sgm_schedule_for(ctx.handle, W, H, 64, 7, 84, 4) == sgm.SGM_SCHED_PAIRS
+    assert ctx.launches - before == (6 if paired else 5)
     before = ctx.launches
     ctx.compute(p.left, p.right, 64, 7, 84, 8)
     assert ctx.launches - before == 7  # the second halves of three vertical-type pairs

@@ -89,6 +89,16 @@ def test_full_census(ctx62, D, P2):
     _compare(ctx62, pair.left, pair.right, D, 7, P2, census="ct62")
 
 
+@pytest.mark.parametrize("D", [64, 256])
+@pytest.mark.parametrize("census", ["csct", "ct62"])
+def test_census_cost_tiles(ctx, ctx62, D, census):
+    # Census tiles of 64 x 4 pixels, cost segments of 32 quads (64 columns)
+    # with the match features of D columns to their left: ragged last tiles
+    # and segments in both directions
+    pair = synth.make_pair(synth.PairSpec(301, 21, D, 3, 1, min(60, D - 1)), 9300 + D)
+    _compare(ctx62 if census == "ct62" else ctx, pair.left, pair.right, D, 7, 84, census)
+
+
 def test_identical_images_give_zero(ctx):
     pair = synth.make_pair(synth.PairSpec(64, 40, 64, 3, 2, 40), 5)
     _compare(ctx, pair.left, pair.left, 64, 7, 84)

@@ -17,9 +17,11 @@ import stereo_synth as synth
 pytestmark = pytest.mark.gpu
 
 CASES = [
-    (320, 240, 64, 7, 84, 4, 11),    # the small single-pair workload's shape
-    (160, 120, 96, 10, 120, 8, 12),  # 8 paths, D not a multiple of 64
-    (97, 61, 32, 7, 84, 2, 13),      # 2 paths, ragged sizes
+    (320, 240, 64, 7, 84, 4, 11),     # the small single-pair workload's shape
+    (160, 120, 96, 10, 120, 8, 12),   # 8 paths, D not a multiple of 64
+    (97, 61, 32, 7, 84, 2, 13),       # 2 paths, ragged sizes
+    (200, 100, 128, 10, 120, 4, 14),  # 4 paths whose sums need 16 bits (P2 > 96)
+    (320, 240, 128, 10, 120, 8, 15),  # about 40 MB of intermediates: near the array's size
 ]
 
 
@@ -35,12 +37,18 @@ def test_static_entry_matches_compute_on_two_calls(W, H, D, P1, P2, n_paths, see
     left = torch.from_numpy(pair.left).cuda()
     right = torch.from_numpy(pair.right).cuda()
     stream = torch.cuda.current_stream()
-    for _ in range(2):
-        out = torch.full((H, W), 255, dtype=torch.uint8, device="cuda")
+    outs = [torch.full((H, W), 255, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    torch.cuda.synchronize()
+    free_before = None
+    for k, out in enumerate(outs):
         sgm.sgm_compute_static(left, right, W, H, D, P1, P2, n_paths, out, stream)
         stream.synchronize()
         got = out.cpu().numpy()
         assert np.array_equal(got, expected), f"{int((got != expected).sum())} pixels differ"
+        if k == 0:
+            free_before = torch.cuda.mem_get_info()[0]  # after the first call's set-up
+    # the second call took no device memory
+    assert torch.cuda.mem_get_info()[0] == free_before
 
 
 def test_static_entry_rejects_what_it_cannot_hold():
