@@ -62,13 +62,13 @@ typedef struct sgm_ctx sgm_ctx;
 
 typedef enum sgm_status {
     SGM_OK = 0,
-    SGM_EAGAIN = 1,      /* sgm_poll: the request is still running */
+    SGM_EAGAIN = 1,      /* sgm_poll: the request is still running; sgm_submit: shed by the admission bound */
     SGM_EINVAL = -1,     /* bad argument (sizes, D, penalties, paths, null pointer, unknown ticket) */
     SGM_ENOMEM = -2,     /* device memory (or the context's memory cap) exhausted */
     SGM_ECUDA = -3,      /* a CUDA runtime call failed; see sgm_last_error */
     SGM_ETIMEDOUT = -4,  /* sgm_poll: the timeout elapsed */
     SGM_ECANCELED = -5,  /* the request was cancelled by sgm_destroy */
-    SGM_EDEVICE = -6     /* a kernel reported an error through the device status word */
+    SGM_EDEVICE = -6     /* a batched kernel rejected a work-list descriptor (the device status word) */
 } sgm_status;
 
 /* sgm_create flags. */
@@ -97,7 +97,15 @@ typedef struct sgm_pair {
  * SGM_FLAG_CENSUS_FULL; the Census type holds for every entry point of the
  * context (sgm_compute_static always uses the CSCT).  On success *out
  * receives the context.
- * Errors: SGM_EINVAL (null out, bad device, unknown flag), SGM_ECUDA.
+ * Test hooks, read from the environment here (host side only; no kernel is
+ * made to fault): SGM_TEST_FAIL_ALLOC=n makes the context's n-th device or
+ * pinned-host allocation fail as if memory were exhausted (the call that
+ * needed it returns SGM_ENOMEM, or sgm_create itself for its own first
+ * allocations, and the context stays usable); SGM_TEST_BAD_JOB=n gives the
+ * first n batched waves one sweep descriptor with a wrong D, which its kernel
+ * skips and reports through the device status word (SGM_EDEVICE).
+ * Errors: SGM_EINVAL (null out, bad device, unknown flag), SGM_ENOMEM,
+ * SGM_ECUDA.
  */
 SGM_API int sgm_create(sgm_ctx **out, int device, size_t mem_cap_bytes, unsigned flags);
 
@@ -183,12 +191,21 @@ SGM_API int sgm_compute_async(sgm_ctx *ctx, const uint8_t *left, const uint8_t *
 /*
  * Batched computation of `n` independent pairs of possibly different sizes,
  * D, penalties and path counts (the paper's scaling argument, Section 4,
- * applied to many pairs at once).  Each stage runs as one launch over a
- * device work list covering every pair.  Pointers of each pair as in
+ * applied to many pairs at once).  Pairs are grouped by (D, path count, sum
+ * width); every stage of a group is one persistent grid whose blocks take
+ * units (tiles, row segments, blocks of sweep lines) from a device work list
+ * covering the group's pairs, longest chains first.  A wave (the pairs whose
+ * buffers fit the memory budget at once, at most 16 groups) is one CUDA
+ * graph launch, the groups on concurrent branches; the graph is captured
+ * once per wave shape and replayed with the lists rewritten.  The first wave
+ * of a new set of pair shapes autotunes the sweep grid (persistent blocks per
+ * SM from {2, 3, 4, 5}: one warm-up and five timed runs each, the lowest
+ * median wins; the call blocks meanwhile).  Pointers of each pair as in
  * sgm_compute (all host or all device per pair).  Blocking.
  * Each pair's result is bit-identical to sgm_compute of that pair alone.
  * Errors: SGM_EINVAL (n < 0, null pairs, any invalid pair), SGM_ENOMEM,
- * SGM_ECUDA, SGM_EDEVICE.
+ * SGM_ECUDA, SGM_EDEVICE (a kernel rejected a descriptor; the context
+ * stays usable).
  */
 SGM_API int sgm_compute_batch(sgm_ctx *ctx, int n, const sgm_pair *pairs);
 
@@ -203,6 +220,8 @@ SGM_API int sgm_compute_batch(sgm_ctx *ctx, int n, const sgm_pair *pairs);
  * free.  Each result is bit-identical to sgm_compute of that pair alone.
  * The caller keeps left/right/disp_out alive and unmodified until sgm_poll
  * returns something other than SGM_EAGAIN for the ticket.
+ * With an admission bound set (sgm_set_admission_bound) a request whose
+ * estimated wait exceeds it is shed: SGM_EAGAIN, nothing queued, no ticket.
  * Errors: SGM_EINVAL (bad pair or null ticket), SGM_ENOMEM (the pair alone
  * exceeds the memory cap).
  */
@@ -225,9 +244,23 @@ SGM_API int sgm_poll(sgm_ctx *ctx, uint64_t ticket, int64_t timeout_us);
  * request's batch on the GPU (its last copy) minus submit time.  `n_out`
  * must be >= 4.  With n_out >= 8 also: out[4] = batches launched, out[5] =
  * mean pairs per batch, out[6] = most batches in flight at once, out[7] =
- * disparity evaluations (W*H*D) of the completed requests.
+ * disparity evaluations (W*H*D) of the completed requests.  With n_out >= 10
+ * also: out[8] = requests shed by the admission bound, out[9] = the measured
+ * service rate: disparity evaluations per second of time with a served batch
+ * in flight, over the context's life (0 before the first batch finishes).
  */
 SGM_API int sgm_served_stats(sgm_ctx *ctx, double *out, int n_out);
+
+/*
+ * Admission bound of the served form: sgm_submit sheds (SGM_EAGAIN) a
+ * request whose estimated wait exceeds max_wait_us.  The estimate is the
+ * disparity evaluations (W*H*D) queued or running, the new request's
+ * included, over the service rate measured so far (every evaluation served
+ * over the time the GPU had a served batch in flight); before the first
+ * batch has finished nothing is shed.  0 (the default) = no bound.
+ * Errors: SGM_EINVAL (null context, max_wait_us < 0).
+ */
+SGM_API int sgm_set_admission_bound(sgm_ctx *ctx, int64_t max_wait_us);
 
 /*
  * Start a new statistics window for sgm_served_stats (for example after a

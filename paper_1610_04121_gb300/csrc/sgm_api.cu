@@ -1,15 +1,18 @@
 // C ABI of the SGM path (include/sgm.h): context, device work arena, launch
 // sequence and CUDA-graph cache, batched and served execution.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
 #include <mutex>
+#include <set>
 #include <string>
 #include <thread>
 #include <tuple>
@@ -220,10 +223,43 @@ struct Request {
     std::chrono::steady_clock::time_point t_submit;
 };
 
+// ---------------------------------------------------------------------------
+// Batched execution state of one stream (sgm_compute_batch, or one served
+// slot).  A wave of pairs is grouped by (D, path count, sum width, Census
+// type); every stage of a group is one persistent grid over a device work
+// list (sgm_internal.h).  The lists of a wave live in one blob: its pinned
+// host image is filled per wave and copied to the device copy before the
+// wave's graph runs.  The graph, captured once per wave shape (the groups'
+// keys and the sweep grid) and replayed for every wave of that shape, zeroes
+// the lists' counters, runs each group's stages on one of kListBranches
+// concurrent branches, and copies the device status word back to the host.
+// Blob layout: status word at 0, the counters at kBlobCounters, the WorkList
+// headers at kBlobLists, the descriptors and prefix sums from kBlobHead.
+// ---------------------------------------------------------------------------
+constexpr int kListGroups = 16, kListBranches = 4, kListStages = 5, kListCounters = 8;
+constexpr size_t kBlobCounters = 64, kBlobLists = 1024, kBlobListStride = 32, kBlobHead = 4096;
+static_assert(kBlobCounters + 4 * kListGroups * kListCounters <= kBlobLists, "blob counters");
+static_assert(kBlobLists + kBlobListStride * kListGroups * kListStages <= kBlobHead, "blob list headers");
+static_assert(sizeof(WorkList<SweepArgs>) <= kBlobListStride, "work list header");
+// Persistent blocks per SM of the sweep kernels the autotuner chooses among.
+constexpr int kSweepGrids[] = {2, 3, 4, 5};
+constexpr int kDefaultSweepGrid = 4;
+
+struct ListExec {
+    cudaStream_t capture = nullptr;
+    cudaStream_t branch[kListBranches] = {};
+    cudaEvent_t fork = nullptr, join[kListBranches] = {};
+    uint8_t* blob_dev = nullptr;
+    uint8_t* blob_host = nullptr;     // pinned, blob_cap bytes
+    size_t blob_cap = 0;
+    uint32_t* status_host = nullptr;  // pinned: the status word after the last wave
+    std::map<std::pair<std::vector<int>, int>, cudaGraphExec_t> graphs;  // (group keys, sweep grid) -> graph
+};
+
 // Served execution: up to kServeSlots batches in flight, each on its own
 // stream with its own arena from a device-resident pool.
 constexpr int kServeSlots = 2;
-constexpr int kServeMaxPairs = kMaxBatch;
+constexpr int kServeMaxPairs = 64;
 
 struct ServeSlot {
     sgm_ctx* ctx = nullptr;
@@ -236,6 +272,7 @@ struct ServeSlot {
     uint8_t* pinned = nullptr;
     size_t pinned_bytes = 0;
     std::vector<std::tuple<uint8_t*, const uint8_t*, size_t>> out_copies;
+    ListExec exec;
     bool busy = false;          // reserved by the scheduler or running
     bool finished = false;      // set by the stream callback after the batch's last copy
     std::chrono::steady_clock::time_point t_done;
@@ -268,6 +305,18 @@ struct sgm_ctx {
     int forced_sched = -1;
     std::map<std::tuple<int, int, int, int, int, bool>, int> tuned;  // (W, H, D, n_paths, ct62, s8) -> schedule
     cudaEvent_t tune_ev[2] = {};
+    // batched execution: the caller's stream's list state, the SM count, the
+    // sweep grid tuned per wave (its pairs' (W, H, D, n_paths), sorted)
+    ListExec batch_exec;
+    int n_sm = 0;
+    std::map<std::vector<int>, int> list_tuned;
+
+    // test hooks, read at sgm_create: SGM_TEST_FAIL_ALLOC=n fails the n-th
+    // allocation; SGM_TEST_BAD_JOB=n gives n waves one descriptor with a D its
+    // kernel rejects (through the device status word)
+    int fail_alloc_at = 0;
+    std::atomic<int> alloc_count{0};
+    std::atomic<int> bad_job_waves{0};
 
     // served requests
     std::mutex mu;
@@ -287,6 +336,13 @@ struct sgm_ctx {
     uint64_t batches = 0, batched_pairs = 0;
     int in_flight = 0, max_in_flight = 0;
     double served_de = 0.0;
+    // admission bound (sgm_set_admission_bound): the backlog's disparity
+    // evaluations over the measured service rate (all evaluations served over
+    // the time with a batch in flight) estimate a new request's wait
+    int64_t admit_max_us = 0;
+    double backlog_de = 0.0, lifetime_de = 0.0, busy_us = 0.0;
+    std::chrono::steady_clock::time_point busy_since;
+    uint64_t shed = 0;
 };
 
 static thread_local std::string g_noctx_err;
@@ -312,6 +368,21 @@ static int fail(sgm_ctx* ctx, int code, const char* fmt, ...) {
                         cudaGetErrorString(e_), __FILE__, __LINE__);                                          \
     } while (0)
 
+// Every device or pinned-host allocation of a context asks here first: the
+// test hook SGM_TEST_FAIL_ALLOC=n makes the context's n-th allocation fail as
+// if the device were out of memory, allocating nothing.
+static bool injected_alloc_failure(sgm_ctx* ctx) {
+    return ctx->fail_alloc_at > 0 && ctx->alloc_count.fetch_add(1) + 1 == ctx->fail_alloc_at;
+}
+
+static cudaError_t ctx_malloc(sgm_ctx* ctx, void** p, size_t bytes) {
+    return injected_alloc_failure(ctx) ? cudaErrorMemoryAllocation : cudaMalloc(p, bytes);
+}
+
+static cudaError_t ctx_malloc_host(sgm_ctx* ctx, void** p, size_t bytes) {
+    return injected_alloc_failure(ctx) ? cudaErrorMemoryAllocation : cudaMallocHost(p, bytes);
+}
+
 static int ensure_arena(sgm_ctx* ctx, uint8_t** arena, size_t* bytes, size_t need, bool clear_graphs) {
     if (*bytes >= need) return SGM_OK;
     const size_t used_elsewhere = ctx->serve_bytes.load();
@@ -329,7 +400,7 @@ static int ensure_arena(sgm_ctx* ctx, uint8_t** arena, size_t* bytes, size_t nee
         ctx->graphs.clear();
     }
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, need);
+    cudaError_t e = ctx_malloc(ctx, &p, need);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, SGM_ENOMEM, "cudaMalloc(%zu) for the work arena: %s", need, cudaGetErrorString(e));
@@ -718,10 +789,10 @@ static int check_args(sgm_ctx* ctx, const Problem& p, const void* left, const vo
 }
 
 // ---------------------------------------------------------------------------
-// Batched execution: pairs grouped by (D, n_paths); every stage is one launch
-// per group over a job table covering the group's pairs (up to kMaxBatch per
-// launch).  Pairs are packed into waves whose buffers fit the memory budget;
-// each pair has its own region of the arena.
+// Batched execution: pairs grouped by (D, n_paths, sum width, Census type),
+// each group's stages as persistent grids over device work lists, the whole
+// wave one graph launch.  Pairs are packed into waves whose buffers fit the
+// memory budget; each pair has its own region of the arena.
 // ---------------------------------------------------------------------------
 struct BatchItem {
     Problem p;
@@ -730,17 +801,277 @@ struct BatchItem {
     size_t offset;  // of the pair's region in the arena
 };
 
-// Items launched together share D, the path count, the sum storage and the Census type.
+// Items of one group share D, the path count, the sum storage and the Census type.
 static std::tuple<int, int, bool, int> batch_key(const BatchItem& it) {
     return std::make_tuple(it.p.D, it.p.n_paths, s8_for(it.p), it.p.ct62);
 }
 
+static int group_code(const BatchItem& it) {
+    return it.p.D | it.p.n_paths << 9 | (s8_for(it.p) ? 1 : 0) << 13 | it.p.ct62 << 14;
+}
+
 static int launches_per_group(int n_paths) { return 4 + (n_paths == 8 ? 3 : 1); }
 
-// Enqueue the batched path for items[b, e) (one wave, same stream).
-static int enqueue_wave(sgm_ctx* ctx, std::vector<BatchItem>& items, size_t b, size_t e, uint8_t* arena,
-                        cudaStream_t s) {
-    // copy-in of host inputs
+static int list_exec_init(sgm_ctx* ctx, ListExec& x) {
+    CUDA_TRY(ctx, cudaStreamCreateWithFlags(&x.capture, cudaStreamNonBlocking));
+    CUDA_TRY(ctx, cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming));
+    for (int b = 0; b < kListBranches; ++b) {
+        CUDA_TRY(ctx, cudaStreamCreateWithFlags(&x.branch[b], cudaStreamNonBlocking));
+        CUDA_TRY(ctx, cudaEventCreateWithFlags(&x.join[b], cudaEventDisableTiming));
+    }
+    void* q = nullptr;
+    CUDA_TRY(ctx, ctx_malloc_host(ctx, &q, sizeof(uint32_t)));
+    x.status_host = static_cast<uint32_t*>(q);
+    *x.status_host = 0;
+    return SGM_OK;
+}
+
+static void list_exec_clear_graphs(ListExec& x) {
+    for (auto& kv : x.graphs) cudaGraphExecDestroy(kv.second);
+    x.graphs.clear();
+}
+
+static void list_exec_release(ListExec& x) {
+    list_exec_clear_graphs(x);
+    if (x.blob_dev) cudaFree(x.blob_dev);
+    if (x.blob_host) cudaFreeHost(x.blob_host);
+    if (x.status_host) cudaFreeHost(x.status_host);
+    for (int b = 0; b < kListBranches; ++b) {
+        if (x.branch[b]) cudaStreamDestroy(x.branch[b]);
+        if (x.join[b]) cudaEventDestroy(x.join[b]);
+    }
+    if (x.fork) cudaEventDestroy(x.fork);
+    if (x.capture) cudaStreamDestroy(x.capture);
+    x = ListExec{};
+}
+
+// Room for `bytes` of blob (device copy and pinned host image); a new blob
+// moves the lists, so the graphs that point into the old one go.
+static int list_exec_reserve(sgm_ctx* ctx, ListExec& x, size_t bytes) {
+    if (x.blob_cap >= bytes) return SGM_OK;
+    const size_t cap = std::max(bytes, x.blob_cap * 2);
+    list_exec_clear_graphs(x);
+    if (x.blob_dev) CUDA_TRY(ctx, cudaFree(x.blob_dev));
+    if (x.blob_host) CUDA_TRY(ctx, cudaFreeHost(x.blob_host));
+    x.blob_dev = x.blob_host = nullptr;
+    x.blob_cap = 0;
+    void *d = nullptr, *h = nullptr;
+    CUDA_TRY(ctx, ctx_malloc(ctx, &d, cap));
+    x.blob_dev = static_cast<uint8_t*>(d);
+    CUDA_TRY(ctx, ctx_malloc_host(ctx, &h, cap));
+    x.blob_host = static_cast<uint8_t*>(h);
+    x.blob_cap = cap;
+    return SGM_OK;
+}
+
+// The groups of a wave: [first item, end) per group, at most kListGroups
+// (items sorted by batch_key; a longer run of groups goes to the next wave).
+static std::vector<std::pair<size_t, size_t>> wave_groups(const std::vector<BatchItem>& items, size_t b, size_t e) {
+    std::vector<std::pair<size_t, size_t>> g;
+    for (size_t g0 = b; g0 < e;) {
+        size_t g1 = g0;
+        while (g1 < e && batch_key(items[g1]) == batch_key(items[g0])) ++g1;
+        g.emplace_back(g0, g1);
+        g0 = g1;
+    }
+    return g;
+}
+
+// Fill the blob's host image with the lists of a wave's groups; returns its
+// used bytes, or 0 with *rc set on failure.
+static size_t build_lists(sgm_ctx* ctx, ListExec& x, const std::vector<BatchItem>& items,
+                          const std::vector<std::pair<size_t, size_t>>& groups, uint8_t* arena, int* rc) {
+    auto up8 = [](size_t v) { return (v + 7) & ~size_t(7); };
+    size_t need = kBlobHead;
+    for (const auto& g : groups) {
+        const size_t n = g.second - g.first;
+        need += up8(n * sizeof(CensusJob)) + up8(n * sizeof(CostJob)) + 2 * up8(n * sizeof(SweepArgs)) +
+                up8(n * sizeof(MedianJob)) + kListStages * up8((n + 1) * sizeof(uint32_t));
+    }
+    if ((*rc = list_exec_reserve(ctx, x, need)) != SGM_OK) return 0;
+    std::memset(x.blob_host, 0, kBlobHead);
+    size_t off = kBlobHead;
+    auto place = [&](const void* src, size_t bytes) -> const void* {
+        const size_t o = off;
+        std::memcpy(x.blob_host + o, src, bytes);
+        off = up8(o + bytes);
+        return x.blob_dev + o;
+    };
+    auto header = [&](size_t g, int stage, const void* job, const void* start, int n) {
+        WorkList<CensusJob> w{static_cast<const CensusJob*>(job), static_cast<const uint32_t*>(start), n};
+        std::memcpy(x.blob_host + kBlobLists + (g * kListStages + stage) * kBlobListStride, &w, sizeof w);
+    };
+    for (size_t g = 0; g < groups.size(); ++g) {
+        const size_t g0 = groups[g].first, n = groups[g].second - g0;
+        std::vector<CensusJob> cj(n);
+        std::vector<CostJob> mj(n);
+        std::vector<SweepArgs> hj, vj;
+        std::vector<MedianJob> dj(n);
+        std::vector<uint32_t> cs(n + 1, 0), ms(n + 1, 0), hs(n + 1, 0), vs(n + 1, 0), ds(n + 1, 0);
+        std::vector<SweepArgs> sa(n);
+        for (size_t k = 0; k < n; ++k) {
+            const BatchItem& it = items[g0 + k];
+            const Layout l = layout_for(it.p, true);
+            uint8_t* base = arena + it.offset;
+            void* Fb = base + l.Fb;
+            void* Fm = base + l.Fm;
+            cj[k] = CensusJob{it.left, it.right, Fb, Fm, it.p.W, it.p.H};
+            mj[k] = CostJob{Fb, Fm, base + l.rec, l.RB, it.p.W, it.p.H, it.p.D};
+            SweepArgs a{};
+            a.rec = base + l.rec;
+            a.RB = l.RB;
+            a.lx_off = 3 * it.p.D;  // one stored-L_r field, reused pair after pair
+            a.raw = base + l.raw;
+            a.W = it.p.W;
+            a.H = it.p.H;
+            a.D = it.p.D;
+            a.P1x2 = static_cast<uint32_t>(it.p.P1) * 0x10001u;
+            a.P2x2 = static_cast<uint32_t>(it.p.P2) * 0x10001u;
+            a.pair = it.p.n_paths >= 4;
+            a.s8 = s8_for(it.p);
+            sa[k] = a;
+            uint8_t* dst = kernel_accessible(it.out) ? it.out : base + l.out;
+            dj[k] = MedianJob{base + l.raw, dst, it.p.W, it.p.H};
+            cs[k + 1] = cs[k] + census_units(it.p.W, it.p.H);
+            ms[k + 1] = ms[k] + cost_units(it.p.W, it.p.H);
+            ds[k + 1] = ds[k] + median_units(it.p.W, it.p.H);
+        }
+        // the sweeps hand out the longest chains first: rows by width, columns by height
+        std::vector<size_t> oh(n), ov(n);
+        for (size_t k = 0; k < n; ++k) oh[k] = ov[k] = k;
+        std::stable_sort(oh.begin(), oh.end(), [&](size_t i, size_t j) { return sa[i].W > sa[j].W; });
+        std::stable_sort(ov.begin(), ov.end(), [&](size_t i, size_t j) { return sa[i].H > sa[j].H; });
+        for (size_t k = 0; k < n; ++k) {
+            hj.push_back(sa[oh[k]]);
+            vj.push_back(sa[ov[k]]);
+            hs[k + 1] = hs[k] + sweep_units(sa[oh[k]].H, sa[oh[k]].D, sa[oh[k]].pair);
+            vs[k + 1] = vs[k] + sweep_units(sa[ov[k]].W, sa[ov[k]].D, sa[ov[k]].pair);
+        }
+        if (g == 0 && ctx->bad_job_waves.load() > 0) {  // test hook: a descriptor its kernel must reject
+            --ctx->bad_job_waves;
+            hj[0].D += 32;
+        }
+        const int ni = static_cast<int>(n);
+        header(g, 0, place(cj.data(), n * sizeof(CensusJob)), place(cs.data(), (n + 1) * 4), ni);
+        header(g, 1, place(mj.data(), n * sizeof(CostJob)), place(ms.data(), (n + 1) * 4), ni);
+        header(g, 2, place(hj.data(), n * sizeof(SweepArgs)), place(hs.data(), (n + 1) * 4), ni);
+        header(g, 3, place(vj.data(), n * sizeof(SweepArgs)), place(vs.data(), (n + 1) * 4), ni);
+        header(g, 4, place(dj.data(), n * sizeof(MedianJob)), place(ds.data(), (n + 1) * 4), ni);
+    }
+    return off;
+}
+
+// The graph of a wave shape: counters zeroed, each group's stages on a
+// branch, the status word copied back.
+static int list_graph(sgm_ctx* ctx, ListExec& x, const std::vector<int>& keys, int sweep_grid,
+                      cudaGraphExec_t* out) {
+    const auto key = std::make_pair(keys, sweep_grid);
+    auto it = x.graphs.find(key);
+    if (it != x.graphs.end()) {
+        *out = it->second;
+        return SGM_OK;
+    }
+    cudaStream_t c = x.capture;
+    CUDA_TRY(ctx, cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal));
+    auto body = [&]() -> cudaError_t {
+        cudaError_t e;
+        uint32_t* counters = reinterpret_cast<uint32_t*>(x.blob_dev + kBlobCounters);
+        uint32_t* status = reinterpret_cast<uint32_t*>(x.blob_dev);
+        if ((e = cudaMemsetAsync(counters, 0, 4 * kListGroups * kListCounters, c)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(x.fork, c)) != cudaSuccess) return e;
+        const int nb = std::min<int>(kListBranches, static_cast<int>(keys.size()));
+        for (int b = 0; b < nb; ++b)
+            if ((e = cudaStreamWaitEvent(x.branch[b], x.fork, 0)) != cudaSuccess) return e;
+        for (size_t g = 0; g < keys.size(); ++g) {
+            cudaStream_t s = x.branch[g % kListBranches];
+            const int D = keys[g] & 511, n_paths = (keys[g] >> 9) & 15;
+            ListLaunch l{};
+            l.status = status;
+            l.D = D;
+            l.s8 = ((keys[g] >> 13) & 1) != 0;
+            l.ct62 = ((keys[g] >> 14) & 1) != 0;
+            l.pair = n_paths >= 4;
+            auto at = [&](int stage, int counter) {
+                l.list = x.blob_dev + kBlobLists + (g * kListStages + stage) * kBlobListStride;
+                l.next = counters + g * kListCounters + counter;
+            };
+            at(0, 0);
+            l.grid = kCensusListPerSM * ctx->n_sm;
+            if ((e = launch_census_list(l, s)) != cudaSuccess) return e;
+            at(1, 1);
+            l.grid = kCostListPerSM * ctx->n_sm;
+            if ((e = launch_cost_list(l, s)) != cudaSuccess) return e;
+            at(2, 2);
+            l.grid = sweep_grid * ctx->n_sm;
+            if ((e = launch_sweep_h_list(l, s)) != cudaSuccess) return e;
+            const int vrx[3] = {1, -1, 0};
+            const int nv = n_paths == 8 ? 3 : 1;
+            for (int v = 0; v < nv; ++v) {
+                at(3, 3 + v);
+                l.rx = n_paths == 8 ? vrx[v] : 0;
+                if ((e = launch_sweep_v_list(l, s)) != cudaSuccess) return e;
+            }
+            at(4, 6);
+            l.grid = kMedianListPerSM * ctx->n_sm;
+            if ((e = launch_median_list(l, s)) != cudaSuccess) return e;
+        }
+        for (int b = 0; b < nb; ++b) {
+            if ((e = cudaEventRecord(x.join[b], x.branch[b])) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(c, x.join[b], 0)) != cudaSuccess) return e;
+        }
+        return cudaMemcpyAsync(x.status_host, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, c);
+    };
+    const cudaError_t eb = body();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(c, &graph);
+    if (eb != cudaSuccess || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return fail(ctx, SGM_ECUDA, "capturing the batched graph: %s",
+                    cudaGetErrorString(eb != cudaSuccess ? eb : ee));
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return fail(ctx, SGM_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
+    x.graphs.emplace(key, exec);
+    *out = exec;
+    return SGM_OK;
+}
+
+// The kernels a wave's graph launches.
+static int wave_launches(const std::vector<BatchItem>& items, const std::vector<std::pair<size_t, size_t>>& groups) {
+    int n = 0;
+    for (const auto& g : groups) n += launches_per_group(items[g.first].p.n_paths);
+    return n;
+}
+
+// The autotuner's key of a wave: its pairs' (W, H, D, n_paths), sorted.
+static std::vector<int> wave_signature(const std::vector<BatchItem>& items, size_t b, size_t e) {
+    std::vector<int> sig;
+    for (size_t i = b; i < e; ++i) {
+        sig.push_back(items[i].p.W);
+        sig.push_back(items[i].p.H);
+        sig.push_back(items[i].p.D | items[i].p.n_paths << 9);
+    }
+    std::vector<std::array<int, 3>> t(sig.size() / 3);
+    for (size_t i = 0; i < t.size(); ++i) t[i] = {sig[3 * i], sig[3 * i + 1], sig[3 * i + 2]};
+    std::sort(t.begin(), t.end());
+    sig.clear();
+    for (const auto& v : t) sig.insert(sig.end(), v.begin(), v.end());
+    return sig;
+}
+
+// Enqueue the batched path for items[b, e) (one wave) on stream s: copy-in of
+// host inputs, the lists, the wave's graph, copy-out of host outputs.
+// `tune` (the caller's thread of sgm_compute_batch): on the first wave of its
+// signature, time each sweep grid (one warm-up and kTuneReps runs, CUDA
+// events on s) and keep the lowest median; without it (served batches) the
+// default grid runs.
+static int enqueue_wave(sgm_ctx* ctx, ListExec& x, std::vector<BatchItem>& items, size_t b, size_t e,
+                        uint8_t* arena, cudaStream_t s, bool tune) {
+    // the host image may be rewritten only once the previous wave's copy of it is done
+    CUDA_TRY(ctx, cudaStreamSynchronize(s));
     for (size_t i = b; i < e; ++i) {
         BatchItem& it = items[i];
         const Layout l = layout_for(it.p, true);
@@ -755,60 +1086,47 @@ static int enqueue_wave(sgm_ctx* ctx, std::vector<BatchItem>& items, size_t b, s
             it.right = base + l.in_right;
         }
     }
-    // groups of equal (D, n_paths, byte sums) are contiguous (items are sorted)
-    for (size_t g0 = b; g0 < e;) {
-        size_t g1 = g0;
-        while (g1 < e && g1 - g0 < static_cast<size_t>(kMaxBatch) && batch_key(items[g1]) == batch_key(items[g0]))
-            ++g1;
-        const int n = static_cast<int>(g1 - g0), D = items[g0].p.D, n_paths = items[g0].p.n_paths;
-        JobTable<CensusJob> ct{};
-        JobTable<CostJob> mt{};
-        JobTable<SweepArgs> st{};
-        JobTable<MedianJob> dt{};
-        ct.n = mt.n = st.n = dt.n = n;
-        for (int k = 0; k < n; ++k) {
-            const BatchItem& it = items[g0 + k];
-            const Layout l = layout_for(it.p, true);
-            uint8_t* base = arena + it.offset;
-            void* Fb = base + l.Fb;
-            void* Fm = base + l.Fm;
-            ct.job[k] = CensusJob{it.left, it.right, Fb, Fm, it.p.W, it.p.H};
-            mt.job[k] = CostJob{Fb, Fm, base + l.rec, l.RB, it.p.W, it.p.H};
-            SweepArgs a{};
-            a.rec = base + l.rec;
-            a.RB = l.RB;
-            a.lx_off = 3 * it.p.D;  // one stored-L_r field, reused pair after pair
-            a.raw = base + l.raw;
-            a.W = it.p.W;
-            a.H = it.p.H;
-            a.D = it.p.D;
-            a.P1x2 = static_cast<uint32_t>(it.p.P1) * 0x10001u;
-            a.P2x2 = static_cast<uint32_t>(it.p.P2) * 0x10001u;
-            a.pair = it.p.n_paths >= 4;
-            a.s8 = s8_for(it.p);
-            st.job[k] = a;
-            uint8_t* dst = kernel_accessible(it.out) ? it.out : base + l.out;
-            dt.job[k] = MedianJob{base + l.raw, dst, it.p.W, it.p.H};
-        }
-        const bool ct62 = items[g0].p.ct62 != 0;
-        CUDA_TRY(ctx, launch_census_batch(ct, ct62, s));
-        CUDA_TRY(ctx, launch_cost_batch(mt, D, ct62, s));
-        CUDA_TRY(ctx, launch_sweep_h_batch(st, s));
-        const int vrx[3] = {1, -1, 0};
-        const int nv = n_paths == 8 ? 3 : 1;
-        for (int v = 0; v < nv; ++v) {
-            for (int k = 0; k < n; ++k) {
-                st.job[k].rx = (n_paths == 8) ? vrx[v] : 0;
-                st.job[k].wta = (st.job[k].rx == 0) ? 1 : 0;
-                st.job[k].phase = 0;
+    const auto groups = wave_groups(items, b, e);
+    std::vector<int> keys;
+    for (const auto& g : groups) keys.push_back(group_code(items[g.first]));
+    int rc = SGM_OK;
+    const size_t used = build_lists(ctx, x, items, groups, arena, &rc);
+    if (rc != SGM_OK) return rc;
+    CUDA_TRY(ctx, cudaMemcpyAsync(x.blob_dev, x.blob_host, used, cudaMemcpyHostToDevice, s));
+    const int per_wave = wave_launches(items, groups);
+    int grid = kDefaultSweepGrid;  // served batches (the scheduler thread) take the default grid
+    const std::vector<int> sig = tune ? wave_signature(items, b, e) : std::vector<int>{};
+    if (tune && ctx->list_tuned.count(sig)) {
+        grid = ctx->list_tuned[sig];
+    } else if (tune) {
+        float best = 0.0f;
+        for (int cand : kSweepGrids) {
+            cudaGraphExec_t g = nullptr;
+            if ((rc = list_graph(ctx, x, keys, cand, &g)) != SGM_OK) return rc;
+            std::vector<float> ms;
+            for (int r = 0; r <= kTuneReps; ++r) {
+                CUDA_TRY(ctx, cudaEventRecord(ctx->tune_ev[0], s));
+                CUDA_TRY(ctx, cudaGraphLaunch(g, s));
+                CUDA_TRY(ctx, cudaEventRecord(ctx->tune_ev[1], s));
+                CUDA_TRY(ctx, cudaEventSynchronize(ctx->tune_ev[1]));
+                ctx->launches += per_wave;
+                float t = 0.0f;
+                CUDA_TRY(ctx, cudaEventElapsedTime(&t, ctx->tune_ev[0], ctx->tune_ev[1]));
+                if (r > 0) ms.push_back(t);  // run 0 warms up
             }
-            CUDA_TRY(ctx, launch_sweep_v_batch(st, s));
+            std::sort(ms.begin(), ms.end());
+            const float med = ms[ms.size() / 2];
+            if (cand == kSweepGrids[0] || med < best) {
+                best = med;
+                grid = cand;
+            }
         }
-        CUDA_TRY(ctx, launch_median_batch(dt, s));
-        ctx->launches += launches_per_group(n_paths);
-        g0 = g1;
+        ctx->list_tuned[sig] = grid;
     }
-    // copy-out of host outputs
+    cudaGraphExec_t g = nullptr;
+    if ((rc = list_graph(ctx, x, keys, grid, &g)) != SGM_OK) return rc;
+    CUDA_TRY(ctx, cudaGraphLaunch(g, s));
+    ctx->launches += per_wave;
     for (size_t i = b; i < e; ++i) {
         const BatchItem& it = items[i];
         if (!kernel_accessible(it.out)) {
@@ -820,13 +1138,22 @@ static int enqueue_wave(sgm_ctx* ctx, std::vector<BatchItem>& items, size_t b, s
     return SGM_OK;
 }
 
-// Run a batch through one arena: sort by (D, n_paths), pack waves that fit the
-// budget (the context's memory cap, else the device's free memory plus what the
-// arena already holds), grow the arena once per wave.
-static int run_batch(sgm_ctx* ctx, std::vector<BatchItem>& items, uint8_t** arena, size_t* arena_bytes,
-                     bool clear_graphs, cudaStream_t s) {
-    std::stable_sort(items.begin(), items.end(), [](const BatchItem& x, const BatchItem& y) {
-        return batch_key(x) < batch_key(y);
+// After a wave has finished: SGM_EDEVICE if a kernel rejected a descriptor.
+static int wave_status(sgm_ctx* ctx, const ListExec& x) {
+    const uint32_t st = *x.status_host;
+    if (st != 0)
+        return fail(ctx, SGM_EDEVICE, "a batched kernel rejected a work-list descriptor (device status %#x)", st);
+    return SGM_OK;
+}
+
+// Run a batch through one arena: sort by group, pack waves that fit the
+// budget (the context's memory cap, else the device's free memory plus what
+// the arena already holds) and hold at most kListGroups groups, grow the arena
+// once per wave.
+static int run_batch(sgm_ctx* ctx, ListExec& x, std::vector<BatchItem>& items, uint8_t** arena, size_t* arena_bytes,
+                     bool clear_graphs, cudaStream_t s, bool tune) {
+    std::stable_sort(items.begin(), items.end(), [](const BatchItem& a, const BatchItem& c) {
+        return batch_key(a) < batch_key(c);
     });
     size_t free_b = 0, total_b = 0;
     CUDA_TRY(ctx, cudaMemGetInfo(&free_b, &total_b));
@@ -838,9 +1165,12 @@ static int run_batch(sgm_ctx* ctx, std::vector<BatchItem>& items, uint8_t** aren
     size_t b = 0;
     while (b < items.size()) {
         size_t e = b, total = 0;
+        int groups = 0;
         while (e < items.size()) {
             const size_t sz = layout_for(items[e].p, true).total;
-            if (e > b && total + sz > budget) break;
+            const bool new_group = e == b || batch_key(items[e]) != batch_key(items[e - 1]);
+            if (e > b && (total + sz > budget || (new_group && groups == kListGroups))) break;
+            groups += new_group ? 1 : 0;
             items[e].offset = total;
             total += sz;
             ++e;
@@ -848,10 +1178,14 @@ static int run_batch(sgm_ctx* ctx, std::vector<BatchItem>& items, uint8_t** aren
         if (total > budget)
             return fail(ctx, SGM_ENOMEM, "a %dx%d D=%d pair needs %zu bytes, over the memory budget of %zu", items[b].p.W,
                         items[b].p.H, items[b].p.D, total, budget);
-        if (b > 0) CUDA_TRY(ctx, cudaStreamSynchronize(s));  // the previous wave still uses the arena
+        if (b > 0) {  // the previous wave still uses the arena
+            CUDA_TRY(ctx, cudaStreamSynchronize(s));
+            const int rc = wave_status(ctx, x);
+            if (rc != SGM_OK) return rc;
+        }
         int rc = ensure_arena(ctx, arena, arena_bytes, total, clear_graphs);
         if (rc != SGM_OK) return rc;
-        rc = enqueue_wave(ctx, items, b, e, *arena, s);
+        rc = enqueue_wave(ctx, x, items, b, e, *arena, s, tune);
         if (rc != SGM_OK) return rc;
         b = e;
     }
@@ -911,7 +1245,8 @@ static int slot_reserve(sgm_ctx* ctx, ServeSlot& sl, size_t need, size_t budget)
     int rc = slot_release(ctx, sl);
     if (rc != SGM_OK) return rc;
     void* p = nullptr;
-    cudaError_t e = cudaMallocFromPoolAsync(&p, need, ctx->serve_pool, sl.stream);
+    cudaError_t e = injected_alloc_failure(ctx) ? cudaErrorMemoryAllocation
+                                                : cudaMallocFromPoolAsync(&p, need, ctx->serve_pool, sl.stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, SGM_ENOMEM, "served batch arena of %zu bytes: %s", need, cudaGetErrorString(e));
@@ -940,7 +1275,7 @@ static int slot_launch(sgm_ctx* ctx, ServeSlot& sl, size_t budget) {
         sl.pinned = nullptr;
         sl.pinned_bytes = 0;
         void* q = nullptr;
-        CUDA_TRY(ctx, cudaMallocHost(&q, want));
+        CUDA_TRY(ctx, ctx_malloc_host(ctx, &q, want));
         sl.pinned = static_cast<uint8_t*>(q);
         sl.pinned_bytes = want;
     }
@@ -973,21 +1308,48 @@ static int slot_launch(sgm_ctx* ctx, ServeSlot& sl, size_t budget) {
         total += layout_for(it.p, true).total;
     }
     int rc = slot_reserve(ctx, sl, total, budget);
-    if (rc == SGM_OK) rc = enqueue_wave(ctx, items, 0, items.size(), sl.arena, sl.stream);
+    if (rc == SGM_OK) rc = enqueue_wave(ctx, sl.exec, items, 0, items.size(), sl.arena, sl.stream, false);
     if (rc == SGM_OK) CUDA_TRY(ctx, cudaLaunchHostFunc(sl.stream, slot_finished, &sl));
     return rc;
 }
+
+static double request_de(const Request& r) { return static_cast<double>(r.p.W) * r.p.H * r.p.D; }
 
 static void retire(sgm_ctx* ctx, const std::vector<Request>& reqs, int rc,
                    std::chrono::steady_clock::time_point t_done) {
     for (const Request& r : reqs) {
         ctx->done[r.ticket] = rc;
+        ctx->backlog_de = std::max(0.0, ctx->backlog_de - request_de(r));
         if (rc == SGM_OK) {
             ctx->latencies_us.push_back(std::chrono::duration<double, std::micro>(t_done - r.t_submit).count());
-            ctx->served_de += static_cast<double>(r.p.W) * r.p.H * r.p.D;
+            ctx->served_de += request_de(r);
+            ctx->lifetime_de += request_de(r);
         }
         --ctx->pending;
     }
+}
+
+// A batch leaves the GPU (under the context's lock): the busy time ends with the last one.
+static void batch_left(sgm_ctx* ctx) {
+    if (--ctx->in_flight == 0)
+        ctx->busy_us +=
+            std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - ctx->busy_since).count();
+}
+
+// Served disparity evaluations per microsecond of time with a batch in
+// flight, or 0 before any batch has completed (under the context's lock).
+static double service_rate(const sgm_ctx* ctx) {
+    double busy = ctx->busy_us;
+    if (ctx->in_flight > 0)
+        busy += std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - ctx->busy_since).count();
+    return (ctx->lifetime_de > 0.0 && busy > 0.0) ? ctx->lifetime_de / busy : 0.0;
+}
+
+// Estimated wait (us) of a request of `de` disparity evaluations submitted
+// now, or -1 without a measured rate (under the context's lock).
+static double estimated_wait_us(const sgm_ctx* ctx, double de) {
+    const double rate = service_rate(ctx);
+    return rate > 0.0 ? (ctx->backlog_de + de) / rate : -1.0;
 }
 
 static void serve_loop(sgm_ctx* ctx) {
@@ -1014,13 +1376,14 @@ static void serve_loop(sgm_ctx* ctx) {
             cudaError_t e = cudaStreamSynchronize(sl->stream);  // the callback has run: returns at once
             int rc = SGM_OK;
             if (e != cudaSuccess) rc = fail(ctx, SGM_ECUDA, "served batch: %s", cudaGetErrorString(e));
+            if (rc == SGM_OK) rc = wave_status(ctx, sl->exec);
             if (rc == SGM_OK)
                 for (auto& c : sl->out_copies) std::memcpy(std::get<0>(c), std::get<1>(c), std::get<2>(c));
             lk.lock();
             retire(ctx, sl->reqs, rc, sl->t_done);
             sl->reqs.clear();
             sl->busy = sl->finished = false;
-            --ctx->in_flight;
+            batch_left(ctx);
             ctx->cv_done.notify_all();
             continue;
         }
@@ -1044,10 +1407,13 @@ static void serve_loop(sgm_ctx* ctx) {
         int rc = slot_budget(ctx, *sl, &budget);
         lk.lock();
         size_t used = 0;
+        std::set<std::tuple<int, int, bool, int>> keys;
         while (rc == SGM_OK && !ctx->queue.empty() && sl->reqs.size() < static_cast<size_t>(kServeMaxPairs)) {
             const Request& r = ctx->queue.front();
             const size_t sz = layout_for(r.p, true).total;
-            if (used + sz > budget) break;
+            const auto key = batch_key(BatchItem{r.p, nullptr, nullptr, nullptr, 0});
+            if (used + sz > budget || (!keys.count(key) && keys.size() == static_cast<size_t>(kListGroups))) break;
+            keys.insert(key);
             used += sz;
             sl->reqs.push_back(r);
             ctx->queue.pop_front();
@@ -1091,7 +1457,7 @@ static void serve_loop(sgm_ctx* ctx) {
             ctx->cv_done.notify_all();
             continue;
         }
-        ++ctx->in_flight;
+        if (ctx->in_flight++ == 0) ctx->busy_since = std::chrono::steady_clock::now();
         ctx->max_in_flight = std::max(ctx->max_in_flight, ctx->in_flight);
         ++ctx->batches;
         ctx->batched_pairs += sl->reqs.size();
@@ -1103,7 +1469,7 @@ static void serve_loop(sgm_ctx* ctx) {
             retire(ctx, sl->reqs, rc, std::chrono::steady_clock::now());
             sl->reqs.clear();
             sl->busy = sl->finished = false;
-            --ctx->in_flight;
+            batch_left(ctx);
             ctx->cv_done.notify_all();
         }
     }
@@ -1157,6 +1523,22 @@ int sgm_create(sgm_ctx** out, int device, size_t mem_cap_bytes, unsigned flags) 
         sgm_destroy(ctx);
         return fail(nullptr, SGM_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
     }
+    if ((e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) {
+        sgm_destroy(ctx);
+        return fail(nullptr, SGM_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+    }
+    if (const char* v = std::getenv("SGM_TEST_FAIL_ALLOC")) ctx->fail_alloc_at = std::atoi(v);
+    if (const char* v = std::getenv("SGM_TEST_BAD_JOB")) ctx->bad_job_waves = std::atoi(v);
+    {
+        int rc = list_exec_init(ctx, ctx->batch_exec);
+        for (auto& sl : ctx->slots)
+            if (rc == SGM_OK) rc = list_exec_init(ctx, sl.exec);
+        if (rc != SGM_OK) {
+            const std::string why = ctx->err;
+            sgm_destroy(ctx);
+            return fail(nullptr, rc, "%s", why.c_str());
+        }
+    }
     ctx->stream = ctx->own_stream;
     ctx->stage_timing = (flags & SGM_FLAG_STAGE_TIMING) != 0;
     ctx->ct62 = (flags & SGM_FLAG_CENSUS_FULL) ? 1 : 0;
@@ -1190,6 +1572,7 @@ int sgm_destroy(sgm_ctx* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
     if (ctx->arena) cudaFree(ctx->arena);
+    list_exec_release(ctx->batch_exec);
     for (auto& sl : ctx->slots) {
         if (sl.arena) cudaFreeAsync(sl.arena, sl.stream);
         if (sl.pinned) cudaFreeHost(sl.pinned);
@@ -1197,6 +1580,7 @@ int sgm_destroy(sgm_ctx* ctx) {
             cudaStreamSynchronize(sl.stream);
             cudaStreamDestroy(sl.stream);
         }
+        list_exec_release(sl.exec);
     }
     if (ctx->serve_pool) cudaMemPoolDestroy(ctx->serve_pool);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
@@ -1295,10 +1679,10 @@ int sgm_compute_batch(sgm_ctx* ctx, int n, const sgm_pair* pairs) {
         items.push_back(BatchItem{p, q.left, q.right, q.disp_out, 0});
     }
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-    int rc = run_batch(ctx, items, &ctx->arena, &ctx->arena_bytes, true, ctx->stream);
+    int rc = run_batch(ctx, ctx->batch_exec, items, &ctx->arena, &ctx->arena_bytes, true, ctx->stream, true);
     if (rc != SGM_OK) return rc;
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-    return SGM_OK;
+    return wave_status(ctx, ctx->batch_exec);
 }
 
 int sgm_submit(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H, int D, int P1, int P2,
@@ -1310,12 +1694,22 @@ int sgm_submit(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, i
     if (ctx->mem_cap && layout_for(p, true).total + ctx->arena_bytes > ctx->mem_cap)
         return fail(ctx, SGM_ENOMEM, "pair %dx%d D=%d needs more than the context's memory cap", W, H, D);
     std::lock_guard<std::mutex> lk(ctx->mu);
+    const double de = static_cast<double>(W) * H * D;
+    if (ctx->admit_max_us > 0) {
+        const double wait = estimated_wait_us(ctx, de);
+        if (wait > static_cast<double>(ctx->admit_max_us)) {
+            ++ctx->shed;
+            return fail(ctx, SGM_EAGAIN, "estimated wait %.0f us exceeds the admission bound of %lld us", wait,
+                        static_cast<long long>(ctx->admit_max_us));
+        }
+    }
     if (!ctx->worker_started) {
         ctx->worker = std::thread(serve_loop, ctx);
         ctx->worker_started = true;
     }
     Request r{ctx->next_ticket++, p, left, right, disp_out, std::chrono::steady_clock::now()};
     *ticket = r.ticket;
+    ctx->backlog_de += de;
     ctx->queue.push_back(r);
     ctx->outstanding.insert(r.ticket);
     ++ctx->pending;
@@ -1359,6 +1753,18 @@ int sgm_served_stats(sgm_ctx* ctx, double* out, int n_out) {
         out[6] = static_cast<double>(ctx->max_in_flight);
         out[7] = ctx->served_de;
     }
+    if (n_out >= 10) {
+        out[8] = static_cast<double>(ctx->shed);
+        out[9] = service_rate(ctx) * 1e6;
+    }
+    return SGM_OK;
+}
+
+int sgm_set_admission_bound(sgm_ctx* ctx, int64_t max_wait_us) {
+    if (!ctx) return fail(nullptr, SGM_EINVAL, "null context");
+    if (max_wait_us < 0) return fail(ctx, SGM_EINVAL, "negative admission bound %lld", (long long)max_wait_us);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->admit_max_us = max_wait_us;
     return SGM_OK;
 }
 
@@ -1367,6 +1773,7 @@ int sgm_served_reset_stats(sgm_ctx* ctx) {
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->latencies_us.clear();
     ctx->batches = ctx->batched_pairs = 0;
+    ctx->shed = 0;
     ctx->max_in_flight = ctx->in_flight;
     ctx->served_de = 0.0;
     return SGM_OK;

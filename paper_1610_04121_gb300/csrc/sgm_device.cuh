@@ -17,6 +17,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "sgm_internal.h"
+
 namespace sgm {
 
 // "+infinity" in one u16 lane: adding a penalty (<= 224) stays below 0x10000,
@@ -229,18 +231,35 @@ __device__ __forceinline__ uint8_t wta_disparity(uint32_t key) {
     return static_cast<uint8_t>(KEY16 ? key % static_cast<uint32_t>(D) : key & 0xffu);
 }
 
-// Index of the job that owns block b in a job table (start[] ascending).
-template <class Table>
-__device__ __forceinline__ int find_job(const Table& t, int b) {
-    int lo = 0, hi = t.n - 1;
+// The next unit of a work list for this block (job index and unit within
+// the job): thread 0 takes it with an atomic on the list's counter and
+// shares it.  False once the list is exhausted.  Every thread of the block
+// calls it (it synchronises the block, which also orders the reuse of the
+// block's shared memory between units).
+template <class Job>
+__device__ __forceinline__ bool take_unit(const WorkList<Job>& L, uint32_t* next, int& job, int& unit) {
+    __shared__ uint32_t s_unit;
+    if (threadIdx.x == 0) s_unit = atomicAdd(next, 1u);
+    __syncthreads();
+    const uint32_t i = s_unit;
+    __syncthreads();
+    if (L.n <= 0 || i >= L.start[L.n]) return false;
+    int lo = 0, hi = L.n - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (t.start[mid] <= b)
+        if (L.start[mid] <= i)
             lo = mid;
         else
             hi = mid - 1;
     }
-    return lo;
+    job = lo;
+    unit = static_cast<int>(i - L.start[lo]);
+    return true;
+}
+
+// A descriptor the kernel cannot run: recorded in the device status word.
+__device__ __forceinline__ void report_bad_job(uint32_t* status) {
+    if (threadIdx.x == 0) atomicOr(status, 1u);
 }
 
 }  // namespace sgm

@@ -50,13 +50,23 @@ inline bool sum_fits_u8(int n_paths, int P2, int mc_max = 31) {
 }
 
 // ---------------------------------------------------------------------------
-// Batched execution: one launch per stage covers many pairs.  A job table is
-// passed by value as the kernel parameter (up to kMaxBatch jobs); block b
-// belongs to the job p with start[p] <= b < start[p + 1].
+// Batched execution over device work lists.  A stage of a group of pairs (one
+// D, path count, sum width and Census type) is one persistent grid: every
+// block takes the next unit of the stage's list (a Census tile, a cost row
+// segment, a block of sweep lines, a median tile) with an atomic counter
+// until the list is exhausted.  The list lives in device memory: the pairs'
+// descriptors in the list's order (longest chains first) and the prefix sums
+// of their unit counts.  A kernel skips a descriptor whose D is not its own
+// and sets bit 0 of the device status word.
 // ---------------------------------------------------------------------------
-constexpr int kMaxBatch = 64;
+template <class Job>
+struct WorkList {
+    const Job* job;         // [n] descriptors
+    const uint32_t* start;  // [n + 1]: jobs [0, k) hold units [0, start[k])
+    int n;
+};
 
-// Features are uint32 (CSCT) or uint64 (full Census) as the table's ct62 flag says.
+// Features are uint32 (CSCT) or uint64 (full Census) as the launch's ct62 says.
 struct CensusJob {
     const uint8_t *left, *right;
     void *Fb, *Fm;
@@ -65,7 +75,7 @@ struct CensusJob {
 struct CostJob {
     const void *Fb, *Fm;
     uint8_t* rec;  // MC is written at offset 0 of each RB-byte record
-    int RB, W, H;
+    int RB, W, H, D;
 };
 struct MedianJob {
     const uint8_t* raw;
@@ -73,11 +83,15 @@ struct MedianJob {
     int W, H;
 };
 
-template <class Job>
-struct JobTable {
-    int n;
-    int start[kMaxBatch + 1];
-    Job job[kMaxBatch];
+// One stage of a group over its work list.
+struct ListLaunch {
+    const void* list;  // device WorkList<Job> of the stage
+    uint32_t* next;    // the list's unit counter, 0 before the launch
+    uint32_t* status;  // device status word
+    int grid;          // persistent blocks
+    int D;
+    bool ct62, pair, s8;
+    int rx;            // vertical-type sweeps: 0 (vertical, finishing with Eq. 4), +1 / -1 (diagonals)
 };
 
 // Each launcher enqueues one kernel on `stream` and returns the launch error.
@@ -124,13 +138,20 @@ cudaError_t launch_mirror(const uint8_t* left, const uint8_t* right, uint8_t* ml
 // fails.
 cudaError_t launch_post(const uint8_t* rawL, const uint32_t* sub, const uint8_t* rawRm, uint16_t* out16, int W,
                         int H, int D, cudaStream_t stream);
-// Batched forms; every job of a cost or sweep table has the same D (and, for
-// sweeps, the same pair / rx / phase / wta / s8 settings).  `start` is filled in.
-cudaError_t launch_census_batch(JobTable<CensusJob>& t, bool ct62, cudaStream_t stream);
-cudaError_t launch_cost_batch(JobTable<CostJob>& t, int D, bool ct62, cudaStream_t stream);
-cudaError_t launch_median_batch(JobTable<MedianJob>& t, cudaStream_t stream);
-cudaError_t launch_sweep_h_batch(JobTable<SweepArgs>& t, cudaStream_t stream);
-cudaError_t launch_sweep_v_batch(JobTable<SweepArgs>& t, cudaStream_t stream);
+// The work-list kernels: every job of a list has the launch's D (and, for
+// sweeps, its pair / s8 settings; a vertical-type list runs both halves of
+// its pair in one unit, the vertical one finishing with Eq. 4).
+cudaError_t launch_census_list(const ListLaunch& l, cudaStream_t stream);
+cudaError_t launch_cost_list(const ListLaunch& l, cudaStream_t stream);
+cudaError_t launch_sweep_h_list(const ListLaunch& l, cudaStream_t stream);
+cudaError_t launch_sweep_v_list(const ListLaunch& l, cudaStream_t stream);
+cudaError_t launch_median_list(const ListLaunch& l, cudaStream_t stream);
+// Units of one pair in each list; blocks of each list kernel resident per SM.
+int census_units(int W, int H);
+int cost_units(int W, int H);
+int sweep_units(int lines, int D, bool pair);
+int median_units(int W, int H);
+constexpr int kCensusListPerSM = 16, kCostListPerSM = 8, kMedianListPerSM = 8, kSweepListMaxPerSM = 5;
 // Debug: paired costs (offset 0 of RB-byte records) -> natural order [H][W][D].
 cudaError_t launch_unpair_cost(const uint8_t* rec, int RB, uint8_t* out, int W, int H, int D, cudaStream_t stream);
 

@@ -147,22 +147,25 @@ __global__ void __launch_bounds__(kCtT) census_kernel(const uint8_t* __restrict_
 }
 
 template <bool CT>
-__global__ void __launch_bounds__(kCtT) census_batch_kernel(const __grid_constant__ JobTable<CensusJob> t) {
-    const int p = find_job(t, blockIdx.x);
-    const CensusJob& j = t.job[p];
-    const int b = blockIdx.x - t.start[p];
-    const int tx = (j.W + kCtW - 1) / kCtW, ty = (j.H + kCtH - 1) / kCtH;
-    census_body<CT>(j.left, j.right, j.Fb, j.Fm, j.W, j.H, b % tx, (b / tx) % ty, b / (tx * ty));
+__global__ void __launch_bounds__(kCtT) census_list_kernel(const WorkList<CensusJob>* __restrict__ Lp,
+                                                           uint32_t* __restrict__ next, uint32_t* __restrict__ status) {
+    const WorkList<CensusJob> L = *Lp;
+    int p, u;
+    while (take_unit(L, next, p, u)) {
+        const CensusJob j = L.job[p];
+        const int tx = (j.W + kCtW - 1) / kCtW, ty = (j.H + kCtH - 1) / kCtH;
+        census_body<CT>(j.left, j.right, j.Fb, j.Fm, j.W, j.H, u % tx, (u / tx) % ty, u / (tx * ty));
+    }
 }
 
-cudaError_t launch_census_batch(JobTable<CensusJob>& t, bool ct62, cudaStream_t stream) {
-    t.start[0] = 0;
-    for (int i = 0; i < t.n; ++i)
-        t.start[i + 1] = t.start[i] + 2 * ((t.job[i].W + kCtW - 1) / kCtW) * ((t.job[i].H + kCtH - 1) / kCtH);
-    if (ct62)
-        census_batch_kernel<true><<<t.start[t.n], kCtT, 0, stream>>>(t);
+int census_units(int W, int H) { return 2 * ((W + kCtW - 1) / kCtW) * ((H + kCtH - 1) / kCtH); }
+
+cudaError_t launch_census_list(const ListLaunch& l, cudaStream_t stream) {
+    const auto* L = static_cast<const WorkList<CensusJob>*>(l.list);
+    if (l.ct62)
+        census_list_kernel<true><<<l.grid, kCtT, 0, stream>>>(L, l.next, l.status);
     else
-        census_batch_kernel<false><<<t.start[t.n], kCtT, 0, stream>>>(t);
+        census_list_kernel<false><<<l.grid, kCtT, 0, stream>>>(L, l.next, l.status);
     return cudaGetLastError();
 }
 
@@ -272,36 +275,44 @@ __global__ void __launch_bounds__(kMcThreads) cost_kernel(const FT* __restrict__
 }
 
 template <int D, class FT>
-__global__ void __launch_bounds__(kMcThreads) cost_batch_kernel(const __grid_constant__ JobTable<CostJob> t) {
-    const int p = find_job(t, blockIdx.x);
-    const CostJob& j = t.job[p];
-    const int b = blockIdx.x - t.start[p];
-    const int segs = (j.W + kMcSeg - 1) / kMcSeg;
-    cost_body<D, FT>(static_cast<const FT*>(j.Fb), static_cast<const FT*>(j.Fm), j.rec, j.RB, j.W, b % segs,
-                     b / segs);
+__global__ void __launch_bounds__(kMcThreads) cost_list_kernel(const WorkList<CostJob>* __restrict__ Lp,
+                                                               uint32_t* __restrict__ next, uint32_t* __restrict__ status) {
+    const WorkList<CostJob> L = *Lp;
+    int p, u;
+    while (take_unit(L, next, p, u)) {
+        const CostJob j = L.job[p];
+        if (j.D != D) {
+            report_bad_job(status);
+            continue;
+        }
+        const int segs = (j.W + kMcSeg - 1) / kMcSeg;
+        cost_body<D, FT>(static_cast<const FT*>(j.Fb), static_cast<const FT*>(j.Fm), j.rec, j.RB, j.W, u % segs,
+                         u / segs);
+    }
 }
 
+int cost_units(int W, int H) { return ((W + kMcSeg - 1) / kMcSeg) * H; }
+
 template <int D>
-static cudaError_t launch_cost_batch_t(JobTable<CostJob>& t, bool ct62, cudaStream_t s) {
-    t.start[0] = 0;
-    for (int i = 0; i < t.n; ++i) t.start[i + 1] = t.start[i] + ((t.job[i].W + kMcSeg - 1) / kMcSeg) * t.job[i].H;
-    if (ct62)
-        cost_batch_kernel<D, uint64_t><<<t.start[t.n], kMcThreads, 0, s>>>(t);
+static cudaError_t launch_cost_list_t(const ListLaunch& l, cudaStream_t s) {
+    const auto* L = static_cast<const WorkList<CostJob>*>(l.list);
+    if (l.ct62)
+        cost_list_kernel<D, uint64_t><<<l.grid, kMcThreads, 0, s>>>(L, l.next, l.status);
     else
-        cost_batch_kernel<D, uint32_t><<<t.start[t.n], kMcThreads, 0, s>>>(t);
+        cost_list_kernel<D, uint32_t><<<l.grid, kMcThreads, 0, s>>>(L, l.next, l.status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_cost_batch(JobTable<CostJob>& t, int D, bool ct62, cudaStream_t stream) {
-    switch (D) {
-        case 32: return launch_cost_batch_t<32>(t, ct62, stream);
-        case 64: return launch_cost_batch_t<64>(t, ct62, stream);
-        case 96: return launch_cost_batch_t<96>(t, ct62, stream);
-        case 128: return launch_cost_batch_t<128>(t, ct62, stream);
-        case 160: return launch_cost_batch_t<160>(t, ct62, stream);
-        case 192: return launch_cost_batch_t<192>(t, ct62, stream);
-        case 224: return launch_cost_batch_t<224>(t, ct62, stream);
-        case 256: return launch_cost_batch_t<256>(t, ct62, stream);
+cudaError_t launch_cost_list(const ListLaunch& l, cudaStream_t stream) {
+    switch (l.D) {
+        case 32: return launch_cost_list_t<32>(l, stream);
+        case 64: return launch_cost_list_t<64>(l, stream);
+        case 96: return launch_cost_list_t<96>(l, stream);
+        case 128: return launch_cost_list_t<128>(l, stream);
+        case 160: return launch_cost_list_t<160>(l, stream);
+        case 192: return launch_cost_list_t<192>(l, stream);
+        case 224: return launch_cost_list_t<224>(l, stream);
+        case 256: return launch_cost_list_t<256>(l, stream);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -560,19 +571,21 @@ __global__ void __launch_bounds__(kMedW) median_kernel(const uint8_t* __restrict
     median_body(raw, out, W, H, blockIdx.x, blockIdx.y);
 }
 
-__global__ void __launch_bounds__(kMedW) median_batch_kernel(const __grid_constant__ JobTable<MedianJob> t) {
-    const int p = find_job(t, blockIdx.x);
-    const MedianJob& j = t.job[p];
-    const int b = blockIdx.x - t.start[p];
-    const int tx = (j.W + kMedW - 1) / kMedW;
-    median_body(j.raw, j.out, j.W, j.H, b % tx, b / tx);
+__global__ void __launch_bounds__(kMedW) median_list_kernel(const WorkList<MedianJob>* __restrict__ Lp,
+                                                             uint32_t* __restrict__ next) {
+    const WorkList<MedianJob> L = *Lp;
+    int p, u;
+    while (take_unit(L, next, p, u)) {
+        const MedianJob j = L.job[p];
+        const int tx = (j.W + kMedW - 1) / kMedW;
+        median_body(j.raw, j.out, j.W, j.H, u % tx, u / tx);
+    }
 }
 
-cudaError_t launch_median_batch(JobTable<MedianJob>& t, cudaStream_t stream) {
-    t.start[0] = 0;
-    for (int i = 0; i < t.n; ++i)
-        t.start[i + 1] = t.start[i] + ((t.job[i].W + kMedW - 1) / kMedW) * ((t.job[i].H + kMedH - 1) / kMedH);
-    median_batch_kernel<<<t.start[t.n], kMedW, 0, stream>>>(t);
+int median_units(int W, int H) { return ((W + kMedW - 1) / kMedW) * ((H + kMedH - 1) / kMedH); }
+
+cudaError_t launch_median_list(const ListLaunch& l, cudaStream_t stream) {
+    median_list_kernel<<<l.grid, kMedW, 0, stream>>>(static_cast<const WorkList<MedianJob>*>(l.list), l.next);
     return cudaGetLastError();
 }
 

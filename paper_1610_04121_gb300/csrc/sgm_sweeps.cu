@@ -47,14 +47,18 @@ cudaError_t launch_sweep_first4(FirstStageArgs& f, cudaStream_t stream) {
 
 cudaError_t launch_sweep_h2(const SweepArgs& a, cudaStream_t stream) { SGM_DISPATCH_D(sweep_launch_h2, a.D, a, stream) }
 
-cudaError_t launch_sweep_h_batch(JobTable<SweepArgs>& t, cudaStream_t stream) {
-    if (t.n < 1) return cudaSuccess;
-    SGM_DISPATCH_D(sweep_launch_h_batch, t.job[0].D, t, stream)
+cudaError_t launch_sweep_h_list(const ListLaunch& l, cudaStream_t stream) {
+    SGM_DISPATCH_D(sweep_launch_h_list, l.D, l, stream)
 }
 
-cudaError_t launch_sweep_v_batch(JobTable<SweepArgs>& t, cudaStream_t stream) {
-    if (t.n < 1) return cudaSuccess;
-    SGM_DISPATCH_D(sweep_launch_v_batch, t.job[0].D, t, stream)
+cudaError_t launch_sweep_v_list(const ListLaunch& l, cudaStream_t stream) {
+    SGM_DISPATCH_D(sweep_launch_v_list, l.D, l, stream)
+}
+
+int sweep_units(int lines, int D, bool pair) {
+    // lines per block: a path takes G = 32 lanes (D % 64 == 0) or 16, a pair two paths
+    const int G = (D % 64 == 0) ? 32 : 16, per_warp = 32 / G, per = kWarpsPerBlock * per_warp / (pair ? 2 : 1);
+    return (lines + per - 1) / per;
 }
 
 // The paired-line 4-path schedule: n1 steps of each horizontal direction

@@ -614,15 +614,25 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_h_kernel(SweepArgs 
     sweep_h_body<D, PAIR, S8, 0, false, false, POST>(a, blockIdx.x);
 }
 
-// Batched forms: many chains in flight, so more warps per SM (5 blocks) with
-// half the prefetch registers serve better than deep prefetch.
-constexpr int kBatchBlocksPerSM = 5, kBatchPrefetchBudget = 24;
+// Work-list forms (batched pairs): many chains in flight, so more warps per
+// SM (up to kSweepListMaxPerSM blocks) with half the prefetch registers serve
+// better than deep prefetch.  A unit is one block's lines of one pair.
+constexpr int kBatchPrefetchBudget = 24;
 
 template <int D, bool PAIR, bool S8>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, kBatchBlocksPerSM)
-    sweep_h_batch_kernel(const __grid_constant__ JobTable<SweepArgs> t) {
-    const int p = find_job(t, blockIdx.x);
-    sweep_h_body<D, PAIR, S8, 0, false, false, 0, kBatchPrefetchBudget>(t.job[p], blockIdx.x - t.start[p]);
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, kSweepListMaxPerSM)
+    sweep_h_list_kernel(const WorkList<SweepArgs>* __restrict__ Lp, uint32_t* __restrict__ next,
+                        uint32_t* __restrict__ status) {
+    const WorkList<SweepArgs> L = *Lp;
+    int p, u;
+    while (take_unit(L, next, p, u)) {
+        const SweepArgs a = L.job[p];
+        if (a.D != D) {
+            report_bad_job(status);
+            continue;
+        }
+        sweep_h_body<D, PAIR, S8, 0, false, false, 0, kBatchPrefetchBudget>(a, u);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -687,12 +697,21 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) sweep_v_kernel(SweepArgs 
     sweep_v_body<D, RX, PH, WTA, PAIR, S8, DBG, false, POST>(a, blockIdx.x);
 }
 
-// Batched form: both phases in one launch (PH = 0).
+// Work-list form: both phases in one unit (PH = 0).
 template <int D, int RX, bool WTA, bool PAIR, bool S8>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, kBatchBlocksPerSM)
-    sweep_v_batch_kernel(const __grid_constant__ JobTable<SweepArgs> t) {
-    const int p = find_job(t, blockIdx.x);
-    sweep_v_body<D, RX, 0, WTA, PAIR, S8, false, false, 0, kBatchPrefetchBudget>(t.job[p], blockIdx.x - t.start[p]);
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, kSweepListMaxPerSM)
+    sweep_v_list_kernel(const WorkList<SweepArgs>* __restrict__ Lp, uint32_t* __restrict__ next,
+                        uint32_t* __restrict__ status) {
+    const WorkList<SweepArgs> L = *Lp;
+    int p, u;
+    while (take_unit(L, next, p, u)) {
+        const SweepArgs a = L.job[p];
+        if (a.D != D) {
+            report_bad_job(status);
+            continue;
+        }
+        sweep_v_body<D, RX, 0, WTA, PAIR, S8, false, false, 0, kBatchPrefetchBudget>(a, u);
+    }
 }
 
 // The horizontal pair and the vertical-type first halves in one grid: one
@@ -825,35 +844,31 @@ struct SweepD {
         return cudaGetLastError();
     }
 
-    static cudaError_t launch_h_batch(JobTable<SweepArgs>& t, cudaStream_t s) {
-        t.start[0] = 0;
-        for (int i = 0; i < t.n; ++i) t.start[i + 1] = t.start[i] + blocks(t.job[i].H, t.job[i].pair);
-        const dim3 grid(t.start[t.n]), block(32 * kWarpsPerBlock);
-        const SweepArgs& a = t.job[0];
-        if (!a.pair)
-            sweep_h_batch_kernel<D, false, true><<<grid, block, 0, s>>>(t);
-        else if (a.s8)
-            sweep_h_batch_kernel<D, true, true><<<grid, block, 0, s>>>(t);
+    static cudaError_t launch_h_list(const ListLaunch& l, cudaStream_t s) {
+        const auto* L = static_cast<const WorkList<SweepArgs>*>(l.list);
+        const dim3 block(32 * kWarpsPerBlock);
+        if (!l.pair)
+            sweep_h_list_kernel<D, false, true><<<l.grid, block, 0, s>>>(L, l.next, l.status);
+        else if (l.s8)
+            sweep_h_list_kernel<D, true, true><<<l.grid, block, 0, s>>>(L, l.next, l.status);
         else
-            sweep_h_batch_kernel<D, true, false><<<grid, block, 0, s>>>(t);
+            sweep_h_list_kernel<D, true, false><<<l.grid, block, 0, s>>>(L, l.next, l.status);
         return cudaGetLastError();
     }
 
-    static cudaError_t launch_v_batch(JobTable<SweepArgs>& t, cudaStream_t s) {
-        t.start[0] = 0;
-        for (int i = 0; i < t.n; ++i) t.start[i + 1] = t.start[i] + blocks(t.job[i].W, t.job[i].pair);
-        const dim3 grid(t.start[t.n]), block(32 * kWarpsPerBlock);
-        const SweepArgs& a = t.job[0];
-        if (!a.pair)
-            sweep_v_batch_kernel<D, 0, true, false, true><<<grid, block, 0, s>>>(t);
-        else if (a.rx == 0 && a.s8)
-            sweep_v_batch_kernel<D, 0, true, true, true><<<grid, block, 0, s>>>(t);
-        else if (a.rx == 0)
-            sweep_v_batch_kernel<D, 0, true, true, false><<<grid, block, 0, s>>>(t);
-        else if (a.rx > 0)
-            sweep_v_batch_kernel<D, 1, false, true, false><<<grid, block, 0, s>>>(t);
+    static cudaError_t launch_v_list(const ListLaunch& l, cudaStream_t s) {
+        const auto* L = static_cast<const WorkList<SweepArgs>*>(l.list);
+        const dim3 block(32 * kWarpsPerBlock);
+        if (!l.pair)
+            sweep_v_list_kernel<D, 0, true, false, true><<<l.grid, block, 0, s>>>(L, l.next, l.status);
+        else if (l.rx == 0 && l.s8)
+            sweep_v_list_kernel<D, 0, true, true, true><<<l.grid, block, 0, s>>>(L, l.next, l.status);
+        else if (l.rx == 0)
+            sweep_v_list_kernel<D, 0, true, true, false><<<l.grid, block, 0, s>>>(L, l.next, l.status);
+        else if (l.rx > 0)
+            sweep_v_list_kernel<D, 1, false, true, false><<<l.grid, block, 0, s>>>(L, l.next, l.status);
         else
-            sweep_v_batch_kernel<D, -1, false, true, false><<<grid, block, 0, s>>>(t);
+            sweep_v_list_kernel<D, -1, false, true, false><<<l.grid, block, 0, s>>>(L, l.next, l.status);
         return cudaGetLastError();
     }
 
@@ -914,13 +929,13 @@ SGM_INTERNAL cudaError_t sweep_launch_v(const SweepArgs& a, cudaStream_t s);
 template <int D>
 SGM_INTERNAL cudaError_t sweep_launch_first(FirstStageArgs& f, cudaStream_t s);
 template <int D>
-SGM_INTERNAL cudaError_t sweep_launch_h_batch(JobTable<SweepArgs>& t, cudaStream_t s);
+SGM_INTERNAL cudaError_t sweep_launch_h_list(const ListLaunch& l, cudaStream_t s);
 template <int D>
 SGM_INTERNAL cudaError_t sweep_launch_first4(FirstStageArgs& f, cudaStream_t s);
 template <int D>
 SGM_INTERNAL cudaError_t sweep_launch_h2(const SweepArgs& a, cudaStream_t s);
 template <int D>
-SGM_INTERNAL cudaError_t sweep_launch_v_batch(JobTable<SweepArgs>& t, cudaStream_t s);
+SGM_INTERNAL cudaError_t sweep_launch_v_list(const ListLaunch& l, cudaStream_t s);
 
 #define SGM_INSTANTIATE_SWEEPS(D)                                                               \
     template <>                                                                                 \
@@ -940,12 +955,12 @@ SGM_INTERNAL cudaError_t sweep_launch_v_batch(JobTable<SweepArgs>& t, cudaStream
         return SweepD<D>::launch_first(f, s);                                                   \
     }                                                                                           \
     template <>                                                                                 \
-    SGM_INTERNAL cudaError_t sweep_launch_h_batch<D>(JobTable<SweepArgs> & t, cudaStream_t s) { \
-        return SweepD<D>::launch_h_batch(t, s);                                                 \
+    SGM_INTERNAL cudaError_t sweep_launch_h_list<D>(const ListLaunch& l, cudaStream_t s) {      \
+        return SweepD<D>::launch_h_list(l, s);                                                  \
     }                                                                                           \
     template <>                                                                                 \
-    SGM_INTERNAL cudaError_t sweep_launch_v_batch<D>(JobTable<SweepArgs> & t, cudaStream_t s) { \
-        return SweepD<D>::launch_v_batch(t, s);                                                 \
+    SGM_INTERNAL cudaError_t sweep_launch_v_list<D>(const ListLaunch& l, cudaStream_t s) {      \
+        return SweepD<D>::launch_v_list(l, s);                                                  \
     }                                                                                           \
     template <>                                                                                 \
     SGM_INTERNAL cudaError_t sweep_launch_first4<D>(FirstStageArgs & f, cudaStream_t s) {       \

@@ -70,6 +70,7 @@ _sig("sgm_submit", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, ctypes.POINT
 _sig("sgm_poll", _i, [_vp, ctypes.c_uint64, ctypes.c_int64])
 _sig("sgm_served_stats", _i, [_vp, ctypes.POINTER(ctypes.c_double), _i])
 _sig("sgm_served_reset_stats", _i, [_vp])
+_sig("sgm_set_admission_bound", _i, [_vp, ctypes.c_int64])
 _sig("sgm_debug_stages", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp])
 _sig("sgm_kernel_launches", ctypes.c_uint64, [_vp])
 _sig("sgm_stage_times", _i, [_vp, ctypes.POINTER(ctypes.c_float), _i])
@@ -165,11 +166,16 @@ def sgm_compute_batch(ctx, pairs: Sequence[tuple]) -> None:
     _check(ctx, _lib.sgm_compute_batch(ctx, len(pairs), arr))
 
 
-def sgm_submit(ctx, left, right, W, H, D, P1, P2, n_paths, disp_out) -> int:
+def sgm_submit(ctx, left, right, W, H, D, P1, P2, n_paths, disp_out) -> Optional[int]:
+    """The request's ticket, or None when the admission bound shed it (SGM_EAGAIN)."""
     t = ctypes.c_uint64()
-    _check(ctx, _lib.sgm_submit(ctx, addr(left), addr(right), W, H, D, P1, P2, n_paths, addr(disp_out),
-                                ctypes.byref(t)))
-    return t.value
+    rc = _check(ctx, _lib.sgm_submit(ctx, addr(left), addr(right), W, H, D, P1, P2, n_paths, addr(disp_out),
+                                     ctypes.byref(t)), allow=(SGM_OK, SGM_EAGAIN))
+    return t.value if rc == SGM_OK else None
+
+
+def sgm_set_admission_bound(ctx, max_wait_us: int) -> None:
+    _check(ctx, _lib.sgm_set_admission_bound(ctx, max_wait_us))
 
 
 def sgm_poll(ctx, ticket: int, timeout_us: int = -1) -> int:
@@ -178,10 +184,11 @@ def sgm_poll(ctx, ticket: int, timeout_us: int = -1) -> int:
 
 
 def sgm_served_stats(ctx) -> dict:
-    out = (ctypes.c_double * 8)()
-    _check(ctx, _lib.sgm_served_stats(ctx, out, 8))
+    out = (ctypes.c_double * 10)()
+    _check(ctx, _lib.sgm_served_stats(ctx, out, 10))
     return {"completed": int(out[0]), "p50_us": out[1], "p99_us": out[2], "max_us": out[3], "batches": int(out[4]),
-            "mean_batch": out[5], "max_in_flight": int(out[6]), "de": out[7]}
+            "mean_batch": out[5], "max_in_flight": int(out[6]), "de": out[7], "shed": int(out[8]),
+            "service_de_per_s": out[9]}
 
 
 def sgm_served_reset_stats(ctx) -> None:
