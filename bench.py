@@ -42,6 +42,9 @@ SM_MAX_MHZ_GB300 = 2070.0
 OPS_PER_DE_PATH = 8
 L2_FLUSH_BYTES = 256 << 20
 SERVED_RATE_HZ = 2000.0
+SERVED_LINE_SECONDS = 2.5      # the served object of the default line
+SERVED_LINE_BOUND_US = 100000  # its admission bound (estimated wait)
+BATCHED_LINE_STEPS = 5         # timed steps of the batched object of the default line
 SERVED_OUT_RING = 4  # output buffers per pool pair (a pair can be in flight more than once)
 # DRAM bytes (read + write) per launch of a kernel, from the ncu capture summarised
 # under profiles/, with the fingerprint of the kernel sources it was taken on;
@@ -81,6 +84,12 @@ def parse():
                     choices=sorted(synth.WORKLOADS) + ["batch64", "served"])
     ap.add_argument("--duration", type=float, default=10.0, help="served: seconds of Poisson arrivals")
     ap.add_argument("--rate", type=float, default=SERVED_RATE_HZ, help="served: arrivals per second")
+    ap.add_argument("--admission-us", type=float, default=0.0,
+                    help="served: admission bound on the estimated wait (us); 0 = none")
+    ap.add_argument("--no-batched", action="store_true", help="default line: skip the batched object")
+    ap.add_argument("--no-served", action="store_true", help="default line: skip the served object")
+    ap.add_argument("--served-seconds", type=float, default=SERVED_LINE_SECONDS,
+                    help="default line: seconds of Poisson arrivals of the served object")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--post", type=int, default=0,
@@ -459,19 +468,13 @@ def run_inflight_bench(args, w, ws, rank, local):
     return 0
 
 
-def run_batch_bench(args, ws, rank, local):
-    """64 uneven pairs per step through sgm_compute_batch, against the same
-    pairs as plain per-pair launches (sgm_compute_async, one after another)."""
+def measure_batched(args, ws, rank, local, pg, steps, warmup, cpu_sample=False):
+    """64 uneven pairs per step through sgm_compute_batch (persistent per-stage
+    grids over device work lists, one graph per wave), against the same pairs
+    as plain per-pair launches (sgm_compute_async, one after another)."""
     import torch
     from paper_1610_04121_gb300 import sgm
 
-    pg = None
-    if ws > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl")
-        pg = dist
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     recipe = synth.batch_recipe(64)
     pairs = [synth.make_pair(w.spec, synth.BASE_SEED + 3000 + i + 7919 * rank) for i, w in enumerate(recipe)]
@@ -487,9 +490,9 @@ def run_batch_bench(args, ws, rank, local):
     stream = torch.cuda.Stream(dev)
     ctx = sgm.Context(local)
     sgm.sgm_set_stream(ctx.handle, stream)
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(max(warmup, 3)):  # the first call autotunes the sweep grid of the wave
         sgm.sgm_compute_batch(ctx.handle, tuples)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     if pg:
         pg.barrier()
     torch.cuda.synchronize(dev)
@@ -504,9 +507,9 @@ def run_batch_bench(args, ws, rank, local):
             pg.barrier()
     launches = ctx.launches - launches0
     total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), pg, dev)
-    value = job_mdes(ws, args.steps, de, total_ms)
+    value = job_mdes(ws, steps, de, total_ms)
     # the same pairs as plain per-pair launches
-    for t in tuples:  # warm-up: captures one graph per pair
+    for t in tuples:  # warm-up: tunes and captures one graph per pair
         sgm.sgm_compute_async(ctx.handle, t[0], t[1], t[3], t[4], t[5], t[6], t[7], t[8], t[2])
     torch.cuda.synchronize(dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -518,6 +521,7 @@ def run_batch_bench(args, ws, rank, local):
     plain_ms = max_over_ranks(a.elapsed_time(b), pg, dev)
     plain = job_mdes(ws, 1, de, plain_ms)
     # end to end with pinned host buffers
+    sgm.sgm_compute_batch(ctx.handle, host_tuples)
     t0 = time.perf_counter()
     sgm.sgm_compute_batch(ctx.handle, host_tuples)
     dt = max_over_ranks(time.perf_counter() - t0, pg, dev)
@@ -526,9 +530,9 @@ def run_batch_bench(args, ws, rank, local):
     peaks, peak_kind = load_peaks()
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     alg_bytes = sum(3 * t[3] * t[4] + 4 * t[3] * t[4] * t[5] for t in tuples)
-    gbs = alg_bytes / (total_ms / args.steps / 1e3) / 1e9
+    gbs = alg_bytes / (total_ms / steps / 1e3) / 1e9
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if cpu_sample and rank == 0 and ws == 1:
         import oracle
 
         oracle.build()
@@ -539,37 +543,25 @@ def run_batch_bench(args, ws, rank, local):
             n_de += w.spec.W * w.spec.H * w.spec.D
         cpu = {"value": n_de / (time.perf_counter() - t0) / 1e6, "unit": "MDE/s", "cores": 1, "kind": "oracle",
                "sample": f"the {len(small)} 320x240 pairs of the batch, single thread"}
-    if rank == 0:
-        line = {
-            "metric": "MDE/s", "value": value, "unit": "MDE/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u16", "data": "synthetic (seeded stereo_synth batch, resident in HBM)",
-            "config": {"workload": "batch64", "pairs_per_step": len(tuples), "de_per_step": de,
-                       "sizes": "320x240/640x480/1242x375/1920x1080, D 64/128/256, 4 or 8 paths",
-                       "parallelism": f"replicas x{ws}", "l2": "inputs and buffers (~58 GB) exceed L2",
-                       "plain_per_pair_mdes": plain, "batched_over_plain": value / plain},
-            "roofline": {"bound": "hbm", "kernel": "whole batch", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                         "frac": gbs / hbm, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs"},
-            "cpu_baseline": cpu,
-            "e2e": {"value": job_mdes(ws, 1, de, dt * 1e3), "unit": "MDE/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "api": "sgm_compute_batch"},
-            "gpu_launches": launches, "clocks": clk.summary(),
-        }
-        print(json.dumps(line))
     ctx.close()
-    if pg:
-        pg.destroy_process_group()
-    return 0
+    return {
+        "value": value, "unit": "MDE/s", "steps": steps, "ms_per_step": total_ms / steps, "pairs_per_step": len(tuples),
+        "de_per_step": de, "plain_per_pair_mdes": plain, "batched_over_plain": value / plain,
+        "sizes": "320x240/640x480/1242x375/1920x1080, D 64/128/256, 4 or 8 paths (P1 = 7, P2 = 84)",
+        "execution": "sgm_compute_batch: persistent per-stage grids over device work lists, one graph launch "
+                     "per wave, sweep grid autotuned",
+        "l2": "inputs and buffers (~58 GB) exceed L2",
+        "roofline": {"bound": "hbm", "kernel": "whole batch", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                     "frac": gbs / hbm, "traffic": None, "algorithmic_bytes_per_step": alg_bytes,
+                     "peak_source": f"{peak_kind} hbm_gbs"},
+        "e2e": {"value": job_mdes(ws, 1, de, dt * 1e3), "unit": "MDE/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "api": "sgm_compute_batch (pinned host buffers)"},
+        "gpu_launches": launches, "clocks": clk.summary(), "cpu_baseline": cpu,
+    }
 
 
-def run_served_bench(args, ws, rank, local):
-    """Poisson arrivals of mixed pairs (sizes up to 1920x1080, D up to 256, 4
-    or 8 paths) through sgm_submit / sgm_poll with pinned host buffers; the
-    context batches whatever is queued and keeps two batches in flight."""
-    import threading
-
+def run_batch_bench(args, ws, rank, local):
     import torch
-    from paper_1610_04121_gb300 import sgm
 
     pg = None
     if ws > 1:
@@ -578,6 +570,35 @@ def run_served_bench(args, ws, rank, local):
         dist.init_process_group("nccl")
         pg = dist
     torch.cuda.set_device(local)
+    r = measure_batched(args, ws, rank, local, pg, args.steps, args.warmup, cpu_sample=not args.no_cpu_baseline)
+    if rank == 0:
+        line = {
+            "metric": "MDE/s", "value": r["value"], "unit": "MDE/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u16", "data": "synthetic (seeded stereo_synth batch, resident in HBM)",
+            "config": {"workload": "batch64", "pairs_per_step": r["pairs_per_step"], "de_per_step": r["de_per_step"],
+                       "sizes": r["sizes"], "parallelism": f"replicas x{ws}", "l2": r["l2"],
+                       "plain_per_pair_mdes": r["plain_per_pair_mdes"], "batched_over_plain": r["batched_over_plain"]},
+            "roofline": r["roofline"], "cpu_baseline": r["cpu_baseline"], "e2e": r["e2e"],
+            "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
+        }
+        print(json.dumps(line))
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def measure_served(args, ws, rank, local, pg, duration, rate, bound_us):
+    """Poisson arrivals of mixed pairs (sizes up to 1920x1080, D up to 256, 8
+    paths) through sgm_submit / sgm_poll with pinned host buffers; the context
+    batches whatever is queued and keeps two batches in flight.  With
+    bound_us > 0 the admission bound sheds requests whose estimated wait
+    exceeds it."""
+    import threading
+
+    import torch
+    from paper_1610_04121_gb300 import sgm
+
     dev = torch.device("cuda", local)
     # sizes and D as the batch; 8 paths with P1 = 10, P2 = 120 ("up to 1920x1080 with D up to 256 and 8 paths")
     recipe = synth.batch_recipe(64, config=4, paths=(8,), P1=10, P2=120)
@@ -588,18 +609,19 @@ def run_served_bench(args, ws, rank, local):
         pool.append((torch.from_numpy(p.left).pin_memory(), torch.from_numpy(p.right).pin_memory(),
                      torch.empty((SERVED_OUT_RING, H, W), dtype=torch.uint8).pin_memory(), W, H, D, w.P1, w.P2,
                      w.n_paths))
-    arrivals = synth.poisson_arrivals(args.rate, args.duration, synth.BASE_SEED + 4 + 7919 * rank)
+    arrivals = synth.poisson_arrivals(rate, duration, synth.BASE_SEED + 4 + 7919 * rank)
     ctx = sgm.Context(local)
 
     def submit(k, ring):
         L, R, O, W, H, D, P1, P2, npth = pool[k]
         return sgm.sgm_submit(ctx.handle, L, R, W, H, D, P1, P2, npth, O[ring])
 
-    # warm-up: every pool pair once (grows the slot arenas and the kernels' caches)
-    for _ in range(max(1, args.warmup // 3)):
-        for t in [submit(k, 0) for k in range(len(pool))]:
-            sgm.sgm_poll(ctx.handle, t, -1)
+    # warm-up: every pool pair once (grows the slot arenas, measures the service rate)
+    for t in [submit(k, 0) for k in range(len(pool))]:
+        sgm.sgm_poll(ctx.handle, t, -1)
     sgm.sgm_served_reset_stats(ctx.handle)
+    if bound_us > 0:
+        sgm.sgm_set_admission_bound(ctx.handle, int(bound_us))
     launches0 = ctx.launches
     tickets = [None] * len(arrivals)
     submitted = threading.Semaphore(0)
@@ -620,15 +642,18 @@ def run_served_bench(args, ws, rank, local):
         th.start()
         for i in range(len(arrivals)):
             submitted.acquire()
-            sgm.sgm_poll(ctx.handle, tickets[i], -1)
+            if tickets[i] is not None:  # None: shed by the admission bound
+                sgm.sgm_poll(ctx.handle, tickets[i], -1)
         wall = time.perf_counter() - t0
         th.join()
     wall = max_over_ranks(wall, pg, dev)
     st = sgm.sgm_served_stats(ctx.handle)
     launches = ctx.launches - launches0
     n = len(arrivals)
-    de = sum(pool[i % len(pool)][3] * pool[i % len(pool)][4] * pool[i % len(pool)][5] for i in range(n))
-    value = job_mdes(ws, 1, de, wall * 1e3)
+    de_of = lambda i: pool[i % len(pool)][3] * pool[i % len(pool)][4] * pool[i % len(pool)][5]  # noqa: E731
+    offered = sum(de_of(i) for i in range(n))
+    served = sum(de_of(i) for i in range(n) if tickets[i] is not None)
+    value = job_mdes(ws, 1, served, wall * 1e3)
     # the same pool as plain one-pair calls, one after another (the first pass
     # sizes the arena and captures one graph per pair)
     for timed in (False, True):
@@ -639,27 +664,49 @@ def run_served_bench(args, ws, rank, local):
     pool_de = sum(t[3] * t[4] * t[5] for t in pool)
     plain = job_mdes(ws, 1, pool_de, max_over_ranks(plain_s, pg, dev) * 1e3)
     h2d = sum(2 * pool[i % len(pool)][3] * pool[i % len(pool)][4] for i in range(n)) / max(n, 1)
+    ctx.close()
+    return {
+        "value": value, "unit": "MDE/s", "arrival_rate_hz": rate, "duration_s": duration, "requests": n,
+        "admitted": n - st["shed"], "shed": st["shed"], "admission_bound_us": bound_us or None,
+        "offered_mdes": offered / duration / 1e6, "served_mdes": value, "wall_s": wall,
+        "pool": "64 pairs: 320x240/640x480/1242x375/1920x1080, D 64/128/256, 8 paths, P1 = 10, P2 = 120",
+        "plain_per_pair_mdes": plain, "served_over_plain": value / plain if plain else None,
+        "latency_us": {"p50": st["p50_us"], "p99": st["p99_us"], "max": st["max_us"]},
+        "batching": {"batches": st["batches"], "mean_pairs_per_batch": st["mean_batch"],
+                     "max_in_flight": st["max_in_flight"]},
+        "e2e": {"value": value, "unit": "MDE/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d / 2,
+                "api": "sgm_submit / sgm_poll (host buffers, copies inside)"},
+        "gpu_launches": launches, "clocks": clk.summary(),
+    }
+
+
+def run_served_bench(args, ws, rank, local):
+    import torch
+
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+        pg = dist
+    torch.cuda.set_device(local)
+    r = measure_served(args, ws, rank, local, pg, args.duration, args.rate, args.admission_us)
     if rank == 0:
         line = {
-            "metric": "MDE/s", "value": value, "unit": "MDE/s", "n_gpus": ws, "steps": n, "warmup": args.warmup,
-            "ms_per_step": wall * 1e3 / max(n, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "u16", "data": "synthetic (seeded stereo_synth pairs, pinned host buffers)",
-            "config": {"workload": "served", "arrival_rate_hz": args.rate, "duration_s": args.duration,
-                       "requests": n,
-                       "pool": "64 pairs: 320x240/640x480/1242x375/1920x1080, D 64/128/256, 8 paths, P1 = 10, P2 = 120",
-                       "offered_mdes": de / args.duration / 1e6, "step": "one request",
-                       "parallelism": f"replicas x{ws}", "l2": "inputs and buffers far exceed L2",
-                       "plain_per_pair_mdes": plain, "served_over_plain": value / plain if plain else None},
-            "latency_us": {"p50": st["p50_us"], "p99": st["p99_us"], "max": st["max_us"]},
-            "batching": {"batches": st["batches"], "mean_pairs_per_batch": st["mean_batch"],
-                         "max_in_flight": st["max_in_flight"]},
-            "cpu_baseline": None,
-            "e2e": {"value": value, "unit": "MDE/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d / 2,
-                    "api": "sgm_submit / sgm_poll (host buffers, copies inside)"},
-            "gpu_launches": launches, "clocks": clk.summary(),
+            "metric": "MDE/s", "value": r["value"], "unit": "MDE/s", "n_gpus": ws, "steps": r["requests"],
+            "warmup": args.warmup, "ms_per_step": r["wall_s"] * 1e3 / max(r["requests"], 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u16",
+            "data": "synthetic (seeded stereo_synth pairs, pinned host buffers)",
+            "config": {"workload": "served", "arrival_rate_hz": r["arrival_rate_hz"], "duration_s": r["duration_s"],
+                       "requests": r["requests"], "admitted": r["admitted"], "shed": r["shed"],
+                       "admission_bound_us": r["admission_bound_us"], "pool": r["pool"],
+                       "offered_mdes": r["offered_mdes"], "step": "one request", "parallelism": f"replicas x{ws}",
+                       "l2": "inputs and buffers far exceed L2", "plain_per_pair_mdes": r["plain_per_pair_mdes"],
+                       "served_over_plain": r["served_over_plain"]},
+            "latency_us": r["latency_us"], "batching": r["batching"], "cpu_baseline": None, "e2e": r["e2e"],
+            "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
         }
         print(json.dumps(line))
-    ctx.close()
     if pg:
         pg.destroy_process_group()
     return 0
@@ -847,6 +894,16 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_baseline(w, census=oracle_census(args))
 
+    # the batched and served forms of the same metric (64 uneven pairs; a
+    # Poisson stream at 2000 pairs/s under an admission bound)
+    batched = served = None
+    if args.workload == DEFAULT_WORKLOAD and args.census == "csct" and args.schedule < 0:
+        if not args.no_batched:
+            batched = measure_batched(args, ws, rank, local, pg, BATCHED_LINE_STEPS, 3)
+            batched.pop("cpu_baseline", None)
+        if not args.no_served:
+            served = measure_served(args, ws, rank, local, pg, args.served_seconds, args.rate, SERVED_LINE_BOUND_US)
+
     if rank == 0:
         line = {
             "metric": "MDE/s", "value": value, "unit": "MDE/s", "n_gpus": ws, "steps": args.steps,
@@ -861,6 +918,7 @@ def main():
             "stage_timing": f"separate pass of {stage_steps} steps with an event between kernels "
                             "(the events lengthen that pass's frames)",
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "batched": batched, "served": served,
         }
         print(json.dumps(line))
     ctx.close()
