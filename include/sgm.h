@@ -140,7 +140,7 @@ SGM_API int sgm_set_stream(sgm_ctx *ctx, void *cuda_stream);
 SGM_API int sgm_compute(sgm_ctx *ctx, const uint8_t *left, const uint8_t *right, int W, int H, int D, int P1, int P2,
                 int n_paths, uint8_t *disp_out);
 
-/* Post-filter flags of sgm_compute_ex (the post-filters Section 6 of the
+/* Post-filter flags of sgm_compute_ex (the post-filters Section 5 of the
  * paper announces; the paper gives no definition, these are the readings). */
 #define SGM_POST_SUBPIXEL 1u    /* parabola vertex through S(d-1), S(d), S(d+1) at the winner d */
 #define SGM_POST_LR_CHECK 2u    /* left-right consistency check */

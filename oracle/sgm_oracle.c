@@ -35,7 +35,7 @@
  *    against the centre, bit k = s(I(x+i, y+j), I(x, y)) for the k-th
  *    (j, i) of j = -3..3 (outer), i = -4..4 (inner) with (0, 0) skipped:
  *    62 bits, LSB first, 0 wherever the window leaves the image.
- *  - The post-filters the paper announces for later work (Section 6:
+ *  - The post-filters the paper announces for later work (Section 5:
  *    left-right consistency check, sub-pixel disparity, adaptive P2) are
  *    named there without a definition; oracle_sgm_ex states the readings
  *    taken here, each from the standard SGM formulation.
@@ -152,7 +152,7 @@ ORACLE_EXPORT void oracle_cost(const uint32_t *Fb, const uint32_t *Fm, int W, in
 }
 
 /*
- * Adaptive P2 (announced in Section 6; reading): for the step from q to p
+ * Adaptive P2 (announced in Section 5; reading): for the step from q to p
  * the jump penalty is P2(p, q) = max(P1, P2 / (1 + |I_b(p) - I_b(q)|)), integer
  * division, I_b the base image: a large intensity step along the path makes
  * a disparity jump cheaper, never cheaper than P1.
@@ -425,7 +425,7 @@ static long floor_div(long n, long d) {
 }
 
 /*
- * Sub-pixel disparity (announced in Section 6; reading): the vertex of the
+ * Sub-pixel disparity (announced in Section 5; reading): the vertex of the
  * parabola through (d-1, S(d-1)), (d, S(d)), (d+1, S(d+1)) at the winner d
  * of Eq. 4, in 1/16 pixel: 16 d + round(16 * (S(d-1) - S(d+1)) /
  * (2 (S(d-1) + S(d+1) - 2 S(d)))), halves rounded up, i.e.
@@ -514,7 +514,7 @@ static void mirror_rows(const uint8_t *in, int W, int H, uint8_t *out) {
 #define ORACLE_DISP16_INVALID 0xFFFFu
 
 /*
- * The path with the post-filters announced in Section 6, output in 1/16
+ * The path with the post-filters announced in Section 5, output in 1/16
  * pixel (uint16 [H][W]):
  *  1. the left pass (base = left, match = right) gives S and the
  *     winner-take-all disparity d_L (Eq. 4), with adaptive P2 when asked;

@@ -607,7 +607,7 @@ cudaError_t launch_median_quads(const uint8_t* rawq, uint8_t* disp, int W, int H
 }
 
 // ---------------------------------------------------------------------------
-// Post-filters (announced in Section 6; the readings are those of
+// Post-filters (announced in Section 5; the readings are those of
 // sgm_compute_ex in sgm.h).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) mirror_kernel(const uint8_t* __restrict__ left,

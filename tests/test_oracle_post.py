@@ -1,4 +1,4 @@
-"""Pins for the oracle's post-filters (announced in Section 6 of the paper):
+"""Pins for the oracle's post-filters (announced in Section 5 of the paper):
 adaptive P2, the sub-pixel disparity and the left-right consistency check.
 
 Each pin computes the expected value a second way that shares nothing with

@@ -1,7 +1,7 @@
 """Post-filters on the GPU (sgm_compute_ex) vs the oracle, bit-exact.
 
 Sub-pixel disparity, the left-right check and adaptive P2 (the post-filters
-Section 6 announces) are integer arithmetic in the readings both sides
+Section 5 announces) are integer arithmetic in the readings both sides
 implement, so the bar stays bit-exact equality of the uint16 output.
 """
 import numpy as np
