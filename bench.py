@@ -50,13 +50,15 @@ SERVED_OUT_RING = 4  # output buffers per pool pair (a pair can be in flight mor
 # under profiles/, with the fingerprint of the kernel sources it was taken on;
 # reported as null once those sources have changed since the capture.
 MEASURED_TRAFFIC = {
-    ("sgm_640x480_d128_p4", "sweep_v+h1"): (148489984, "491a94ead9f28c1f"),
-    ("sgm_640x480_d128_p4", "sweep_h2"): (119061120, "491a94ead9f28c1f"),
-    ("sgm_1242x375_d128_p8", "sweep_h"): (586146816, "491a94ead9f28c1f"),
-    ("sgm_1242x375_d128_p8", "sweep_diag+"): (311648768, "491a94ead9f28c1f"),
-    ("sgm_1242x375_d128_p8", "sweep_v"): (241617152, "491a94ead9f28c1f"),
+    # the paired schedule's second stage is two kernels side by side: their sum
+    ("sgm_640x480_d128_p4", "pairs_vh"): (119760384, "88d62a9d8634f444"),
+    ("sgm_640x480_d128_p4", "pairs_h_wta"): (79050496 + 78685056, "88d62a9d8634f444"),
+    ("sgm_1242x375_d128_p8", "sweep_h"): (584676352, "88d62a9d8634f444"),
+    ("sgm_1242x375_d128_p8", "sweep_diag+"): (311659392, "88d62a9d8634f444"),
+    ("sgm_1242x375_d128_p8", "sweep_diag-"): (311890048, "88d62a9d8634f444"),
+    ("sgm_1242x375_d128_p8", "sweep_v"): (241657344, "88d62a9d8634f444"),
 }
-KERNEL_SOURCES = ("sgm_sweeps.cuh", "sgm_device.cuh", "sgm_internal.h")
+KERNEL_SOURCES = ("sgm_sweeps.cuh", "sgm_pairs.cuh", "sgm_device.cuh", "sgm_internal.h")
 
 
 def kernel_fingerprint():
