@@ -248,6 +248,9 @@ SGM_API int sgm_poll(sgm_ctx *ctx, uint64_t ticket, int64_t timeout_us);
  * also: out[8] = requests shed by the admission bound, out[9] = the measured
  * service rate: disparity evaluations per second of time with a served batch
  * in flight, over the context's life (0 before the first batch finishes).
+ * With n_out >= 13 also the current state: out[10] = requests queued and not
+ * yet admitted, out[11] = batches in flight, out[12] = device bytes held by
+ * the served slots' arenas (the pool's occupancy).
  */
 SGM_API int sgm_served_stats(sgm_ctx *ctx, double *out, int n_out);
 
@@ -261,6 +264,18 @@ SGM_API int sgm_served_stats(sgm_ctx *ctx, double *out, int n_out);
  * Errors: SGM_EINVAL (null context, max_wait_us < 0).
  */
 SGM_API int sgm_set_admission_bound(sgm_ctx *ctx, int64_t max_wait_us);
+
+/*
+ * The autotuners' results as a JSON file: the 4-path sweep schedule per
+ * (W, H, D, n_paths, Census type, byte sums) key and the batched sweep grid
+ * per set of pair shapes.  sgm_load_tuning merges a saved file into a context
+ * on a device with the same SM count, so that a new process skips the timed
+ * tuning runs.  Nothing else of a context persists.
+ * Errors: SGM_EINVAL (null context or path, a file that cannot be written or
+ * read, is malformed, or was tuned on a device with another SM count).
+ */
+SGM_API int sgm_save_tuning(const sgm_ctx *ctx, const char *path);
+SGM_API int sgm_load_tuning(sgm_ctx *ctx, const char *path);
 
 /*
  * Start a new statistics window for sgm_served_stats (for example after a

@@ -1757,6 +1757,101 @@ int sgm_served_stats(sgm_ctx* ctx, double* out, int n_out) {
         out[8] = static_cast<double>(ctx->shed);
         out[9] = service_rate(ctx) * 1e6;
     }
+    if (n_out >= 13) {
+        out[10] = static_cast<double>(ctx->queue.size());  // queued, not yet admitted
+        out[11] = static_cast<double>(ctx->in_flight);
+        out[12] = static_cast<double>(ctx->serve_bytes.load());  // device bytes of the slots' arenas
+    }
+    return SGM_OK;
+}
+
+// The tuning cache: {"sgm_tuning": 1, "sm_count": N, "schedules": [[W, H, D,
+// n_paths, ct62, s8, schedule], ...], "batch_grids": [[grid, W, H, D | paths
+// << 9, ...], ...]}.  The reader takes the integers of each bracketed list in
+// order.
+int sgm_save_tuning(const sgm_ctx* ctx, const char* path) {
+    if (!ctx || !path) return fail(nullptr, SGM_EINVAL, "null context or path");
+    FILE* f = std::fopen(path, "w");
+    if (!f) return fail(const_cast<sgm_ctx*>(ctx), SGM_EINVAL, "cannot write %s", path);
+    std::fprintf(f, "{\"sgm_tuning\": 1, \"sm_count\": %d, \"schedules\": [", ctx->n_sm);
+    bool first = true;
+    for (const auto& kv : ctx->tuned) {
+        const auto& k = kv.first;
+        std::fprintf(f, "%s[%d, %d, %d, %d, %d, %d, %d]", first ? "" : ", ", std::get<0>(k), std::get<1>(k),
+                     std::get<2>(k), std::get<3>(k), std::get<4>(k), std::get<5>(k) ? 1 : 0, kv.second);
+        first = false;
+    }
+    std::fprintf(f, "], \"batch_grids\": [");
+    first = true;
+    for (const auto& kv : ctx->list_tuned) {
+        std::fprintf(f, "%s[%d", first ? "" : ", ", kv.second);
+        for (int v : kv.first) std::fprintf(f, ", %d", v);
+        std::fprintf(f, "]");
+        first = false;
+    }
+    std::fprintf(f, "]}\n");
+    const bool ok = std::fclose(f) == 0;
+    return ok ? SGM_OK : fail(const_cast<sgm_ctx*>(ctx), SGM_EINVAL, "cannot write %s", path);
+}
+
+// The integer lists inside the outer list that follows `"key":` in text.
+static bool read_lists(const std::string& text, const char* key, std::vector<std::vector<long>>* out) {
+    const std::string k = std::string("\"") + key + "\"";
+    size_t i = text.find(k);
+    if (i == std::string::npos) return false;
+    i = text.find('[', i + k.size());
+    if (i == std::string::npos) return false;
+    int depth = 0;
+    std::vector<long> cur;
+    for (size_t j = i; j < text.size(); ++j) {
+        const char c = text[j];
+        if (c == '[') {
+            ++depth;
+            if (depth == 2) cur.clear();
+            if (depth > 2) return false;
+        } else if (c == ']') {
+            if (depth == 2) out->push_back(cur);
+            if (--depth == 0) return true;
+        } else if (depth == 2 && (c == '-' || (c >= '0' && c <= '9'))) {
+            char* end = nullptr;
+            cur.push_back(std::strtol(text.c_str() + j, &end, 10));
+            j = static_cast<size_t>(end - text.c_str()) - 1;
+        } else if (!(c == ',' || c == ' ' || c == '\n' || c == '\t' || c == '\r')) {
+            return false;
+        }
+    }
+    return false;
+}
+
+int sgm_load_tuning(sgm_ctx* ctx, const char* path) {
+    if (!ctx || !path) return fail(ctx, SGM_EINVAL, "null context or path");
+    FILE* f = std::fopen(path, "r");
+    if (!f) return fail(ctx, SGM_EINVAL, "cannot read %s", path);
+    std::string text;
+    char buf[4096];
+    size_t n;
+    while ((n = std::fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, n);
+    std::fclose(f);
+    const size_t h = text.find("\"sm_count\":");
+    if (text.find("\"sgm_tuning\": 1") == std::string::npos || h == std::string::npos)
+        return fail(ctx, SGM_EINVAL, "%s is not a tuning cache", path);
+    if (std::atoi(text.c_str() + h + 11) != ctx->n_sm)
+        return fail(ctx, SGM_EINVAL, "%s was tuned on a device with another SM count", path);
+    std::vector<std::vector<long>> sched, grids;
+    if (!read_lists(text, "schedules", &sched) || !read_lists(text, "batch_grids", &grids))
+        return fail(ctx, SGM_EINVAL, "%s is malformed", path);
+    for (const auto& v : sched) {
+        if (v.size() != 7 || v[6] < 0 || v[6] > SGM_SCHED_PAIRS)
+            return fail(ctx, SGM_EINVAL, "%s: bad schedule entry", path);
+    }
+    for (const auto& v : grids) {
+        bool known = false;
+        for (int g : kSweepGrids) known |= v.size() >= 4 && v[0] == g;
+        if (!known || (v.size() - 1) % 3 != 0) return fail(ctx, SGM_EINVAL, "%s: bad batch grid entry", path);
+    }
+    for (const auto& v : sched)
+        ctx->tuned[std::make_tuple(int(v[0]), int(v[1]), int(v[2]), int(v[3]), int(v[4]), v[5] != 0)] = int(v[6]);
+    for (const auto& v : grids) ctx->list_tuned[std::vector<int>(v.begin() + 1, v.end())] = int(v[0]);
     return SGM_OK;
 }
 

@@ -71,6 +71,8 @@ _sig("sgm_poll", _i, [_vp, ctypes.c_uint64, ctypes.c_int64])
 _sig("sgm_served_stats", _i, [_vp, ctypes.POINTER(ctypes.c_double), _i])
 _sig("sgm_served_reset_stats", _i, [_vp])
 _sig("sgm_set_admission_bound", _i, [_vp, ctypes.c_int64])
+_sig("sgm_save_tuning", _i, [_vp, ctypes.c_char_p])
+_sig("sgm_load_tuning", _i, [_vp, ctypes.c_char_p])
 _sig("sgm_debug_stages", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp])
 _sig("sgm_kernel_launches", ctypes.c_uint64, [_vp])
 _sig("sgm_stage_times", _i, [_vp, ctypes.POINTER(ctypes.c_float), _i])
@@ -178,17 +180,26 @@ def sgm_set_admission_bound(ctx, max_wait_us: int) -> None:
     _check(ctx, _lib.sgm_set_admission_bound(ctx, max_wait_us))
 
 
+def sgm_save_tuning(ctx, path: str) -> None:
+    _check(ctx, _lib.sgm_save_tuning(ctx, os.fsencode(path)))
+
+
+def sgm_load_tuning(ctx, path: str) -> None:
+    _check(ctx, _lib.sgm_load_tuning(ctx, os.fsencode(path)))
+
+
 def sgm_poll(ctx, ticket: int, timeout_us: int = -1) -> int:
     """Returns SGM_OK, SGM_EAGAIN or SGM_ETIMEDOUT; raises on errors."""
     return _check(ctx, _lib.sgm_poll(ctx, ticket, timeout_us), allow=(SGM_OK, SGM_EAGAIN, SGM_ETIMEDOUT))
 
 
 def sgm_served_stats(ctx) -> dict:
-    out = (ctypes.c_double * 10)()
-    _check(ctx, _lib.sgm_served_stats(ctx, out, 10))
+    out = (ctypes.c_double * 13)()
+    _check(ctx, _lib.sgm_served_stats(ctx, out, 13))
     return {"completed": int(out[0]), "p50_us": out[1], "p99_us": out[2], "max_us": out[3], "batches": int(out[4]),
             "mean_batch": out[5], "max_in_flight": int(out[6]), "de": out[7], "shed": int(out[8]),
-            "service_de_per_s": out[9]}
+            "service_de_per_s": out[9], "queued": int(out[10]), "in_flight": int(out[11]),
+            "pool_bytes": int(out[12])}
 
 
 def sgm_served_reset_stats(ctx) -> None:

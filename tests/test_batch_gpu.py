@@ -197,3 +197,54 @@ def test_admission_bound_sheds_and_admitted_results_stay_exact(sgm):
             sgm.sgm_set_admission_bound(c.handle, -1)
     finally:
         c.close()
+
+
+def test_tuning_cache_round_trip(sgm, tmp_path):
+    p = _pair(160, 96, 64, 1100)
+    ref = oracle.sgm(p.left, p.right, 64, 7, 84, 4)
+    items = _small_mix(1200)
+    groups = {(D, npth, P2) for q, W, H, D, P1, P2, npth in items}
+    per_wave = sum(4 + (3 if npth == 8 else 1) for D, npth, P2 in groups)
+    path = str(tmp_path / "tuning.json")
+    with sgm.Context(0) as c:
+        assert (c.compute(p.left, p.right, 64, 7, 84, 4) == ref).all()  # tunes the 4-path schedule
+        _run(sgm, c, items)  # tunes the batch's sweep grid
+        chosen = sgm.sgm_schedule_for(c.handle, 160, 96, 64, 7, 84, 4)
+        sgm.sgm_save_tuning(c.handle, path)
+    with sgm.Context(0) as c:
+        sgm.sgm_load_tuning(c.handle, path)
+        assert sgm.sgm_schedule_for(c.handle, 160, 96, 64, 7, 84, 4) == chosen
+        before = c.launches
+        assert (c.compute(p.left, p.right, 64, 7, 84, 4) == ref).all()
+        # no timed tuning runs: one path (the paired schedule runs its second
+        # launch as two kernels)
+        assert c.launches - before == (6 if chosen == sgm.SGM_SCHED_PAIRS else 5)
+        before = c.launches
+        refs = [oracle.sgm(q.left, q.right, D, P1, P2, npth) for q, W, H, D, P1, P2, npth in items]
+        for o, r in zip(_run(sgm, c, items), refs):
+            assert (o == r).all()
+        assert c.launches - before == per_wave
+        bad = tmp_path / "bad.json"
+        bad.write_text('{"sgm_tuning": 1, "sm_count": 1, "schedules": [], "batch_grids": []}')
+        with pytest.raises(sgm.SgmError):
+            sgm.sgm_load_tuning(c.handle, str(bad))  # another device
+        bad.write_text('{"sgm_tuning": 1, "sm_count": 152, "schedules": [[1, 2]], "batch_grids": []}')
+        with pytest.raises(sgm.SgmError):
+            sgm.sgm_load_tuning(c.handle, str(bad))
+        with pytest.raises(sgm.SgmError):
+            sgm.sgm_load_tuning(c.handle, str(tmp_path / "missing.json"))
+
+
+def test_served_state_in_stats(sgm):
+    W, H, D = 320, 240, 64
+    p = _pair(W, H, D, 1300)
+    c = sgm.Context(0)
+    try:
+        outs = [np.zeros((H, W), np.uint8) for _ in range(4)]
+        ts = [sgm.sgm_submit(c.handle, p.left, p.right, W, H, D, 7, 84, 4, o) for o in outs]
+        for t in ts:
+            assert sgm.sgm_poll(c.handle, t, -1) == sgm.SGM_OK
+        st = sgm.sgm_served_stats(c.handle)
+        assert st["queued"] == 0 and st["in_flight"] == 0 and st["pool_bytes"] > 0
+    finally:
+        c.close()
