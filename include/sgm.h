@@ -319,6 +319,21 @@ SGM_API int sgm_stage_times(sgm_ctx *ctx, float *ms_out, int n);
 /* Name of stage i of a path with n_paths directions, or NULL. */
 SGM_API const char *sgm_stage_name(int n_paths, int i);
 
+/*
+ * The bounds-checked build (the library compiled with -DSGM_BOUNDS_CHECK,
+ * `python -m paper_1610_04121_gb300.build --bounds-check`): every global
+ * access of the kernels, and the shared-memory feature indices of the cost
+ * kernels, is tested against the extent of its array; a violation records a
+ * site number in a device fault word and skips the access (no trap).  The
+ * synchronous calls (sgm_compute, sgm_compute_ex, sgm_compute_batch,
+ * sgm_debug_stages, and sgm_poll for served requests) then return
+ * SGM_EDEVICE.  sgm_bounds_checked() is 1 in that build, else 0;
+ * sgm_bounds_fault() returns and clears the first recorded site (0: none),
+ * for callers of the asynchronous entry points.
+ */
+SGM_API int sgm_bounds_checked(void);
+SGM_API unsigned sgm_bounds_fault(void);
+
 /* Path count (2, 4 or 8) of the path that sgm_stage_times reports on, or 0
  * when none has been enqueued with SGM_FLAG_STAGE_TIMING. */
 SGM_API int sgm_stage_paths(const sgm_ctx *ctx);

@@ -19,6 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB_NAME = "libsgm_gb300.so"
 LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
+# the bounds-checked build (-DSGM_BOUNDS_CHECK, include/sgm.h), beside the ordinary one
+CHECKED_LIB_PATH = os.path.join(OUT_DIR, "libsgm_gb300_checked.so")
 SOURCES = ["sgm_stages.cu", "sgm_sweeps.cu", "sgm_api.cu"] + [f"sgm_sweeps_d{32 * k}.cu" for k in range(1, 9)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -42,21 +44,23 @@ def _deps():
     return files
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB_PATH):
+def needs_build(lib: str = LIB_PATH) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB_PATH)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(f) > t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile and link if any source is newer than the library; return its path."""
-    if not force and not needs_build():
-        return LIB_PATH
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, bounds_check: bool = False) -> str:
+    """Compile and link if any source is newer than the library; return its path.
+    bounds_check: the bounds-checked build (CHECKED_LIB_PATH)."""
+    lib = CHECKED_LIB_PATH if bounds_check else LIB_PATH
+    if not force and not needs_build(lib):
+        return lib
     nvcc = _nvcc()
-    obj_dir = os.path.join(OUT_DIR, "obj")
+    obj_dir = os.path.join(OUT_DIR, "obj_checked" if bounds_check else "obj")
     os.makedirs(obj_dir, exist_ok=True)
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + (["-DSGM_BOUNDS_CHECK"] if bounds_check else [])
 
     def compile_one(src):
         obj = os.path.join(obj_dir, src.replace(".cu", ".o"))
@@ -73,14 +77,15 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         for _, err in results:
             if err.strip():
                 print(err, file=sys.stderr)
-    tmp = LIB_PATH + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp] + [o for o, _ in results]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv,
+                bounds_check="--bounds-check" in sys.argv))

@@ -21,9 +21,28 @@
 #include <vector>
 
 #include "sgm.h"
+#include "sgm_check.cuh"
 #include "sgm_internal.h"
 
 using namespace sgm;
+
+namespace sgm {
+// The fault words of the bounds-checked build (sgm_check.cuh): one reader per
+// translation unit, registered at load time.
+static std::vector<unsigned (*)()>& bounds_readers() {
+    static std::vector<unsigned (*)()> readers;
+    return readers;
+}
+void register_bounds_reader(unsigned (*reader)()) { bounds_readers().push_back(reader); }
+unsigned take_bounds_fault() {
+    unsigned first = 0;
+    for (auto reader : bounds_readers()) {
+        const unsigned site = reader();
+        if (site != 0 && first == 0) first = site;
+    }
+    return first;
+}
+}  // namespace sgm
 
 namespace {
 
@@ -93,6 +112,7 @@ struct Problem {
     int post = 0;  // 0: the plain path (u8 output); else kPostOut16 | the SGM_POST_* flags of sgm_compute_ex
     int sched = 0;  // 4-path sweep schedule (SGM_SCHED_*)
     int n1 = -1;    // SGM_SCHED_PAIRS: horizontal steps in the first launch (-1: the default)
+    int check_shrink = 0;  // bounds-checked build, test hook (PairsArgs::check_shrink)
 };
 
 // Set on every sgm_compute_ex problem: the post form with uint16 output, even
@@ -316,6 +336,10 @@ struct sgm_ctx {
     // kernel rejects (through the device status word)
     int fail_alloc_at = 0;
     std::atomic<int> alloc_count{0};
+    // bounds-checked build: SGM_TEST_BOUNDS_SHRINK=1 declares the paired
+    // schedule's cube arrays one quad shorter than they are, so that a guard
+    // fires on an access that is in fact in range
+    bool bounds_shrink = false;
     std::atomic<int> bad_job_waves{0};
 
     // served requests
@@ -381,6 +405,18 @@ static cudaError_t ctx_malloc(sgm_ctx* ctx, void** p, size_t bytes) {
 
 static cudaError_t ctx_malloc_host(sgm_ctx* ctx, void** p, size_t bytes) {
     return injected_alloc_failure(ctx) ? cudaErrorMemoryAllocation : cudaMallocHost(p, bytes);
+}
+
+// After a synchronous call in the bounds-checked build: SGM_EDEVICE if a
+// kernel's guard fired (sgm_check.cuh).  Always SGM_OK in the ordinary build.
+static int bounds_status(sgm_ctx* ctx) {
+#ifdef SGM_BOUNDS_CHECK
+    const unsigned site = take_bounds_fault();
+    if (site != 0) return fail(ctx, SGM_EDEVICE, "bounds check: an access out of its array at site %u", site);
+#else
+    (void)ctx;
+#endif
+    return SGM_OK;
 }
 
 static int ensure_arena(sgm_ctx* ctx, uint8_t** arena, size_t* bytes, size_t need, bool clear_graphs) {
@@ -485,6 +521,7 @@ static cudaError_t enqueue_match(const Problem& p, const Layout& l, uint8_t* are
         g.P2x2 = static_cast<uint32_t>(p.P2) * 0x10001u;
         g.s8 = s8_for(p) ? 1 : 0;
         g.mc_max = mc_max(p);
+        g.check_shrink = p.check_shrink;
         if ((e = launch_pairs_stage1(g, s)) != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
         // the horizontal chains (the long pole: enqueued first) and the
@@ -521,6 +558,7 @@ static cudaError_t enqueue_match(const Problem& p, const Layout& l, uint8_t* are
     a.sub = sub;
     uint32_t* states = reinterpret_cast<uint32_t*>(arena + l.state);
     const size_t sw = sweep_state_words(p.W, p.D);
+    a.state_end = states + (p.n_paths == 8 ? 3 * sw : sweep_state_words(std::max(p.W, p.H), p.D));
     // vertical-type pairs: (rx, wta) in the order their second halves run
     const int nv = p.n_paths == 8 ? 3 : 1;
     const int vrx[3] = {1, -1, 0};
@@ -777,6 +815,7 @@ static int enqueue_pair(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const ui
 static Problem make_problem(const sgm_ctx* ctx, int W, int H, int D, int P1, int P2, int n_paths) {
     Problem p{W, H, D, P1, P2, n_paths};
     p.ct62 = ctx ? ctx->ct62 : 0;
+    p.check_shrink = (ctx && ctx->bounds_shrink) ? 4 * D : 0;
     return p;
 }
 
@@ -1377,6 +1416,7 @@ static void serve_loop(sgm_ctx* ctx) {
             int rc = SGM_OK;
             if (e != cudaSuccess) rc = fail(ctx, SGM_ECUDA, "served batch: %s", cudaGetErrorString(e));
             if (rc == SGM_OK) rc = wave_status(ctx, sl->exec);
+            if (rc == SGM_OK) rc = bounds_status(ctx);
             if (rc == SGM_OK)
                 for (auto& c : sl->out_copies) std::memcpy(std::get<0>(c), std::get<1>(c), std::get<2>(c));
             lk.lock();
@@ -1529,6 +1569,9 @@ int sgm_create(sgm_ctx** out, int device, size_t mem_cap_bytes, unsigned flags) 
     }
     if (const char* v = std::getenv("SGM_TEST_FAIL_ALLOC")) ctx->fail_alloc_at = std::atoi(v);
     if (const char* v = std::getenv("SGM_TEST_BAD_JOB")) ctx->bad_job_waves = std::atoi(v);
+#ifdef SGM_BOUNDS_CHECK
+    if (const char* v = std::getenv("SGM_TEST_BOUNDS_SHRINK")) ctx->bounds_shrink = std::atoi(v) != 0;
+#endif
     {
         int rc = list_exec_init(ctx, ctx->batch_exec);
         for (auto& sl : ctx->slots)
@@ -1618,7 +1661,7 @@ int sgm_compute(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, 
     rc = enqueue_pair(ctx, p, ctx->arena, left, right, disp_out, ctx->stream, true);
     if (rc != SGM_OK) return rc;
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-    return SGM_OK;
+    return bounds_status(ctx);
 }
 
 int sgm_compute_ex(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H, int D, int P1, int P2,
@@ -1633,7 +1676,7 @@ int sgm_compute_ex(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int 
     rc = enqueue_pair(ctx, p, ctx->arena, left, right, reinterpret_cast<uint8_t*>(disp16_out), ctx->stream, true);
     if (rc != SGM_OK) return rc;
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-    return SGM_OK;
+    return bounds_status(ctx);
 }
 
 int sgm_compute_async(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H, int D, int P1, int P2,
@@ -1682,7 +1725,8 @@ int sgm_compute_batch(sgm_ctx* ctx, int n, const sgm_pair* pairs) {
     int rc = run_batch(ctx, ctx->batch_exec, items, &ctx->arena, &ctx->arena_bytes, true, ctx->stream, true);
     if (rc != SGM_OK) return rc;
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-    return wave_status(ctx, ctx->batch_exec);
+    rc = wave_status(ctx, ctx->batch_exec);
+    return rc != SGM_OK ? rc : bounds_status(ctx);
 }
 
 int sgm_submit(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H, int D, int P1, int P2,
@@ -1915,7 +1959,7 @@ int sgm_debug_stages(sgm_ctx* ctx, const uint8_t* left, const uint8_t* right, in
     }
     if (disp) CUDA_TRY(ctx, cudaMemcpyAsync(disp, a + l.out, wh, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    return SGM_OK;
+    return bounds_status(ctx);
 }
 
 int sgm_stage_times(sgm_ctx* ctx, float* ms_out, int n) {
@@ -1975,6 +2019,16 @@ const char* sgm_stage_name(int n_paths, int i) {
 }
 
 uint64_t sgm_kernel_launches(const sgm_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
+
+int sgm_bounds_checked(void) {
+#ifdef SGM_BOUNDS_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+unsigned sgm_bounds_fault(void) { return take_bounds_fault(); }
 
 const char* sgm_version(void) { return "sgm-gb300 0.1 (sm_103a)"; }
 

@@ -17,6 +17,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "sgm_check.cuh"
 #include "sgm_internal.h"
 
 namespace sgm {

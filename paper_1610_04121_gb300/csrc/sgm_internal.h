@@ -28,6 +28,7 @@ struct SweepArgs {
     int phase;            // vertical-type pairs: 0 = both phases, 1 = first half of each path
                           // (saves the path state), 2 = second half (restores it)
     uint32_t* state;      // path states between phases 1 and 2 (sweep_state_words)
+    uint32_t* state_end;  // the end of the state array (bounds-checked build)
     int s8;               // S kept as paired bytes instead of u16x2 words
     // Post-filter form of the sweeps (sgm_compute_ex): post = 1 selects it.
     // Every step q -> p then takes its jump penalty from a per-block table
@@ -190,6 +191,7 @@ struct PairsArgs {
     int mc_max;       // largest matching cost: 31 (CSCT) or 62 (full Census)
     int nvb, nhb;     // first launch: vertical / horizontal blocks (64 threads each)
     int nh2, npw;     // second launch: chain blocks; parallel winner-take-all blocks (beside them)
+    int check_shrink; // bounds-checked build, test hook: bytes taken off the declared end of the fields
 };
 // Geometry and block counts for a W x H problem (n1 < 0: the default split).
 PairsArgs pairs_geometry(int W, int H, int D, int n1);

@@ -145,6 +145,40 @@ constexpr int kChainPrefetchRegs = 192, kParItems = 4;
 // walkers are about to read (first launch 51 -> 43 us, second 41 -> 35 us).
 constexpr int kHintMcLoad = kL2Normal, kHintLStore = kL2First, kHintLLoad = kL2First;
 
+// Extents for the bounds-checked build: the field arrays, the quad raw
+// disparity, the chains' state and the debug sums.
+__device__ __forceinline__ const uint8_t* cubes_end(const PairsArgs& a) {
+    return a.rec + kPairsFields * a.FS - a.check_shrink;
+}
+__device__ __forceinline__ size_t state_words(const PairsArgs& a) {
+    return static_cast<size_t>(a.QH) * 2 * 32 * (a.D / 32 + 1);
+}
+
+template <int N, int HINT>
+__device__ __forceinline__ void ldv_checked(const PairsArgs& a, const uint8_t* p, uint32_t (&r)[N], unsigned site) {
+    if (SGM_GUARD(p, 4 * N, a.rec, cubes_end(a), site)) {
+        ldv<N, false, HINT>(p, r);
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) r[i] = 0u;
+    }
+}
+
+template <int N, int HINT>
+__device__ __forceinline__ void stv_checked(const PairsArgs& a, uint8_t* p, const uint32_t (&r)[N], unsigned site) {
+    if (SGM_GUARD(p, 4 * N, a.rec, cubes_end(a), site)) stv<N, HINT>(p, r);
+}
+
+__device__ __forceinline__ void raw_quad_store(const PairsArgs& a, size_t q, uint32_t v, unsigned site) {
+    if (SGM_GUARD_INDEX(static_cast<long long>(q), static_cast<long long>(a.QW) * a.QH, site))
+        reinterpret_cast<uint32_t*>(a.rawq)[q] = v;
+}
+
+__device__ __forceinline__ void sdbg_store(const PairsArgs& a, size_t i, uint32_t v, unsigned site) {
+    if (SGM_GUARD_INDEX(static_cast<long long>(i), static_cast<long long>(a.W) * a.H * a.D, site))
+        a.Sdbg[i] = static_cast<uint16_t>(v);
+}
+
 // 64-bit base + 32-bit record offset in one instruction.
 __device__ __forceinline__ uint8_t* at(uint8_t* base, uint32_t off) {
     uint64_t r;
@@ -339,11 +373,11 @@ __device__ __forceinline__ void walk(Chain2<D / 32>& ch, const PairsArgs& a, con
     // run is never re-read by the same SM (measured: the L1 path made the
     // first launch 1.7x slower)
     auto load = [&](In& in, uint32_t off) {
-        ldv<K, false, kHintMcLoad>(at(bs.mc, off), in.mc);
+        ldv_checked<K, kHintMcLoad>(a, at(bs.mc, off), in.mc, 101);
         if constexpr (MODE == kWta) {
-            ldv<K, false, kHintLLoad>(at(bs.o, off), in.o);
-            ldv<K, false, kHintLLoad>(at(bs.v0, off), in.v0);
-            ldv<K, false, kHintLLoad>(at(bs.v1, off), in.v1);
+            ldv_checked<K, kHintLLoad>(a, at(bs.o, off), in.o, 102);
+            ldv_checked<K, kHintLLoad>(a, at(bs.v0, off), in.v0, 103);
+            ldv_checked<K, kHintLLoad>(a, at(bs.v1, off), in.v1, 104);
         }
     };
     uint32_t dc[K];
@@ -368,7 +402,7 @@ __device__ __forceinline__ void walk(Chain2<D / 32>& ch, const PairsArgs& a, con
                     uint32_t q[K];
 #pragma unroll
                     for (int j = 0; j < K; ++j) q[j] = __byte_perm(first[j], ch.w[j], sel.cq);
-                    stv<K, kHintLStore>(at(bs.out, off_cur), q);
+                    stv_checked<K, kHintLStore>(a, at(bs.out, off_cur), q, 105);
                 }
             } else {  // kWta (horizontal)
                 uint32_t S[K];
@@ -381,16 +415,16 @@ __device__ __forceinline__ void walk(Chain2<D / 32>& ch, const PairsArgs& a, con
 #pragma unroll
                         for (int j = 0; j < K; ++j) {
                             const size_t d = static_cast<size_t>(K * lane + j);
-                            if (y0 < a.H) a.Sdbg[(static_cast<size_t>(y0) * a.W + x) * D + d] = S[j] & 0xffffu;
-                            if (y0 + 1 < a.H) a.Sdbg[(static_cast<size_t>(y0 + 1) * a.W + x) * D + d] = S[j] >> 16;
+                            if (y0 < a.H) sdbg_store(a, (static_cast<size_t>(y0) * a.W + x) * D + d, S[j] & 0xffffu, 106);
+                            if (y0 + 1 < a.H)
+                                sdbg_store(a, (static_cast<size_t>(y0 + 1) * a.W + x) * D + d, S[j] >> 16, 106);
                         }
                     }
                 }
                 if (t == 0) {
                     dfirst = dd;
                 } else if (lane == 0) {
-                    *reinterpret_cast<uint32_t*>(a.rawq + (static_cast<size_t>(wk.r) * a.QW + qc) * 4) =
-                        __byte_perm(dfirst, dd, sel.cq);
+                    raw_quad_store(a, static_cast<size_t>(wk.r) * a.QW + qc, __byte_perm(dfirst, dd, sel.cq), 107);
                 }
             }
         }
@@ -473,9 +507,11 @@ __global__ void __launch_bounds__(64) pairs_stage1_kernel(const __grid_constant_
                         walk_sel(false, right));
         if (a.nh2 > 0) {
             uint32_t* st = state_slot<K>(a, r, warp);
+            if (SGM_GUARD(st, 4 * (K + 1), a.state, a.state + state_words(a), 108)) {
 #pragma unroll
-            for (int j = 0; j < K; ++j) st[j] = ch.w[j];
-            st[K] = ch.mpx2;
+                for (int j = 0; j < K; ++j) st[j] = ch.w[j];
+                st[K] = ch.mpx2;
+            }
         }
     }
 }
@@ -493,9 +529,11 @@ __global__ void __launch_bounds__(64) pairs_chain2_kernel(const __grid_constant_
     ch.init(lane);
     {
         const uint32_t* st = state_slot<K>(a, r, warp);
+        if (SGM_GUARD(st, 4 * (K + 1), a.state, a.state + state_words(a), 109)) {
 #pragma unroll
-        for (int j = 0; j < K; ++j) ch.w[j] = __ldcg(st + j);
-        ch.mpx2 = __ldcg(st + K);
+            for (int j = 0; j < K; ++j) ch.w[j] = __ldcg(st + j);
+            ch.mpx2 = __ldcg(st + K);
+        }
         ch.exchange();
     }
     const uint32_t off0 = static_cast<uint32_t>(r) * a.QW * QB;
@@ -531,10 +569,10 @@ __global__ void __launch_bounds__(64) pairs_par_kernel(const __grid_constant__ P
     for (int n = 0; n < NI; ++n) {
         const int it = min(it0 + n, items - 1);  // past the end: re-read the last quad
         const uint8_t* q = a.rec + (static_cast<size_t>(it / cols) * a.QW + a.b / 2 + it % cols) * a.QB + lb;
-        ldv<K, false, kHintLLoad>(q + kLH0 * a.FS, l0[n]);
-        ldv<K, false, kHintLLoad>(q + kLH1 * a.FS, l1[n]);
-        ldv<K, false, kHintLLoad>(q + kLVT * a.FS, v0[n]);
-        ldv<K, false, kHintLLoad>(q + kLVB * a.FS, v1[n]);
+        ldv_checked<K, kHintLLoad>(a, q + kLH0 * a.FS, l0[n], 110);
+        ldv_checked<K, kHintLLoad>(a, q + kLH1 * a.FS, l1[n], 110);
+        ldv_checked<K, kHintLLoad>(a, q + kLVT * a.FS, v0[n], 110);
+        ldv_checked<K, kHintLLoad>(a, q + kLVB * a.FS, v1[n], 110);
     }
 #pragma unroll
     for (int n = 0; n < NI; ++n) {
@@ -563,15 +601,13 @@ __global__ void __launch_bounds__(64) pairs_par_kernel(const __grid_constant__ P
                         if (x >= a.W) continue;
 #pragma unroll
                         for (int j = 0; j < K; ++j)
-                            a.Sdbg[(static_cast<size_t>(y) * a.W + x) * D + K * lane + j] =
-                                i ? (S[j] >> 16) : (S[j] & 0xffffu);
+                            sdbg_store(a, (static_cast<size_t>(y) * a.W + x) * D + K * lane + j,
+                                       i ? (S[j] >> 16) : (S[j] & 0xffffu), 111);
                     }
                 }
             }
         }
-        if (lane == 0)
-            *reinterpret_cast<uint32_t*>(a.rawq + (static_cast<size_t>(r) * a.QW + qx) * 4) =
-                __byte_perm(dd[0], dd[1], 0x6420u);
+        if (lane == 0) raw_quad_store(a, static_cast<size_t>(r) * a.QW + qx, __byte_perm(dd[0], dd[1], 0x6420u), 112);
     }
 }
 

@@ -98,7 +98,10 @@ __device__ __forceinline__ void census_body(const uint8_t* __restrict__ left, co
 #pragma unroll
             for (int ty = 0; ty < TH; ++ty) {
                 const int gy = y0 - 3 + ty;
-                v[h][ty] = (xin && gy >= 0 && gy < H) ? __ldg(img + (size_t)gy * W + gx) : uint8_t(0);
+                v[h][ty] = (xin && gy >= 0 && gy < H &&
+                            SGM_GUARD_INDEX((long long)gy * W + gx, (long long)W * H, 301))
+                               ? __ldg(img + (size_t)gy * W + gx)
+                               : uint8_t(0);
             }
         }
 #pragma unroll
@@ -135,8 +138,10 @@ __device__ __forceinline__ void census_body(const uint8_t* __restrict__ left, co
             f1 = census_feature(win, r, 1);
         }
         FT* row = F + (size_t)y * W + x;
-        row[0] = (ok0 && yok) ? f0 : FT(0);
-        if (has1) row[1] = (ok1 && yok) ? f1 : FT(0);
+        if (SGM_GUARD_INDEX((long long)y * W + x + (has1 ? 1 : 0), (long long)W * H, 302)) {
+            row[0] = (ok0 && yok) ? f0 : FT(0);
+            if (has1) row[1] = (ok1 && yok) ? f1 : FT(0);
+        }
     }
 }
 
@@ -209,7 +214,7 @@ __device__ __forceinline__ uint32_t bitcount(uint64_t v) { return __popcll(v); }
 // FT: uint32_t (CSCT features) or uint64_t (full Census features).
 template <int D, class FT>
 __device__ __forceinline__ void cost_body(const FT* __restrict__ Fb, const FT* __restrict__ Fm,
-                                          uint8_t* __restrict__ rec, int RB, int W, int seg, int y) {
+                                          uint8_t* __restrict__ rec, int RB, int W, int H, int seg, int y) {
     constexpr int Q = D / 4, half = D / 2, NF = kMcSeg + D;  // words per pixel; staged match features (even)
     __shared__ __align__(16) FT fm[NF];  // fm[k] = F_match(x0 - D + k)
     __shared__ __align__(16) FT fb[kMcSeg];
@@ -247,6 +252,7 @@ __device__ __forceinline__ void cost_body(const FT* __restrict__ Fb, const FT* _
         const int ba = px + D - i0 - 2;  // d = i0 + 1 - p' ... : fm[ba + p + 1] is d = i0 + 1, fm[ba + p + 2] is d = i0
         const int bb = ba - half;
         FT ra[kMcPix + 2], rb[kMcPix + 2], b4[kMcPix];
+        if (!SGM_GUARD_INDEX(bb, NF, 303) || !SGM_GUARD_INDEX(ba + kMcPix + 1, NF, 303)) continue;
 #pragma unroll
         for (int k = 0; k < kMcPix + 2; k += 2) {
             ld2(fm + ba + k, ra[k], ra[k + 1]);
@@ -262,16 +268,17 @@ __device__ __forceinline__ void cost_body(const FT* __restrict__ Fb, const FT* _
             const uint32_t c1 = bitcount(b ^ rb[p + 2]);  // d = i0 + D/2
             const uint32_t c2 = bitcount(b ^ ra[p + 1]);  // d = i0 + 1
             const uint32_t c3 = bitcount(b ^ rb[p + 1]);  // d = i0 + 1 + D/2
-            reinterpret_cast<uint32_t*>(out + (size_t)(px + p) * RB)[wi] =
-                __byte_perm(c0 | (c2 << 16), c1 | (c3 << 16), 0x6240u);  // [c0, c1, c2, c3]
+            if (SGM_GUARD_INDEX(((long long)y * W + x0 + px + p) * RB + 4 * wi + 3, (long long)W * H * RB, 304))
+                reinterpret_cast<uint32_t*>(out + (size_t)(px + p) * RB)[wi] =
+                    __byte_perm(c0 | (c2 << 16), c1 | (c3 << 16), 0x6240u);  // [c0, c1, c2, c3]
         }
     }
 }
 
 template <int D, class FT>
 __global__ void __launch_bounds__(kMcThreads) cost_kernel(const FT* __restrict__ Fb, const FT* __restrict__ Fm,
-                                                          uint8_t* __restrict__ rec, int RB, int W) {
-    cost_body<D, FT>(Fb, Fm, rec, RB, W, blockIdx.x, blockIdx.y);
+                                                          uint8_t* __restrict__ rec, int RB, int W, int H) {
+    cost_body<D, FT>(Fb, Fm, rec, RB, W, H, blockIdx.x, blockIdx.y);
 }
 
 template <int D, class FT>
@@ -286,8 +293,8 @@ __global__ void __launch_bounds__(kMcThreads) cost_list_kernel(const WorkList<Co
             continue;
         }
         const int segs = (j.W + kMcSeg - 1) / kMcSeg;
-        cost_body<D, FT>(static_cast<const FT*>(j.Fb), static_cast<const FT*>(j.Fm), j.rec, j.RB, j.W, u % segs,
-                         u / segs);
+        cost_body<D, FT>(static_cast<const FT*>(j.Fb), static_cast<const FT*>(j.Fm), j.rec, j.RB, j.W, j.H,
+                         u % segs, u / segs);
     }
 }
 
@@ -323,10 +330,10 @@ static cudaError_t launch_cost_t(const void* Fb, const void* Fm, uint8_t* rec, i
     const dim3 grid((W + kMcSeg - 1) / kMcSeg, H);
     if (ct62)
         cost_kernel<D, uint64_t><<<grid, kMcThreads, 0, s>>>(static_cast<const uint64_t*>(Fb),
-                                                             static_cast<const uint64_t*>(Fm), rec, RB, W);
+                                                             static_cast<const uint64_t*>(Fm), rec, RB, W, H);
     else
         cost_kernel<D, uint32_t><<<grid, kMcThreads, 0, s>>>(static_cast<const uint32_t*>(Fb),
-                                                             static_cast<const uint32_t*>(Fm), rec, RB, W);
+                                                             static_cast<const uint32_t*>(Fm), rec, RB, W, H);
     return cudaGetLastError();
 }
 
@@ -412,6 +419,9 @@ __device__ __forceinline__ void cost_quads_body(const FT* __restrict__ Fb, const
             // match features of pixels xl, xl + 1 at d0 .. d0 + kQcDisp - 1:
             // fm[j][xl + i - d + D] = m[kQcDisp + i - e] for d = d0 + e
             const int kb = xl + D - d0 - kQcDisp;  // even
+            if (!SGM_GUARD_INDEX(kb, 2 * kQcSeg + D, 305) || !SGM_GUARD_INDEX(kb + kQcDisp + 1, 2 * kQcSeg + D, 305) ||
+                !SGM_GUARD_INDEX(xl + 1, 2 * kQcSeg, 305))
+                continue;
             FT m[kQcDisp + 2];
 #pragma unroll
             for (int k = 0; k < kQcDisp + 2; k += 2) ld2(&fm[j][kb + k], m[k], m[k + 1]);
@@ -425,6 +435,8 @@ __device__ __forceinline__ void cost_quads_body(const FT* __restrict__ Fb, const
         }
         // one 32-byte store
         uint8_t* dst = mc + ((size_t)qy * QW + qx0 + ql) * QB + 4 * d0;
+        if (!SGM_GUARD_INDEX(((long long)qy * QW + qx0 + ql) * QB + 4 * d0 + 31, (long long)QW * ((H + 1) / 2) * QB, 306))
+            continue;
         asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst), "r"(q[0]), "r"(q[1]),
                      "r"(q[2]), "r"(q[3]), "r"(q[4]), "r"(q[5]), "r"(q[6]), "r"(q[7])
                      : "memory");
@@ -528,7 +540,7 @@ __device__ __forceinline__ int raw_at(const uint8_t* __restrict__ raw, int W, in
     if constexpr (QUAD)
         return __ldg(raw + ((size_t)(y >> 1) * ((W + 1) >> 1) + (x >> 1)) * 4 + (x & 1) + 2 * (y & 1));
     else
-        return __ldg(raw + (size_t)y * W + x);
+        return SGM_GUARD_INDEX(x, W, 307) ? __ldg(raw + (size_t)y * W + x) : 0;
 }
 
 template <bool QUAD = false>
@@ -562,7 +574,7 @@ __device__ __forceinline__ void median_body(const uint8_t* __restrict__ raw, uin
             const int h = min(min(hi[k], hi[k + 1]), hi[k + 2]);
             v = med3(l, m, h);
         }
-        out[(size_t)y * W + x] = static_cast<uint8_t>(v);
+        if (SGM_GUARD_INDEX(x, W, 308)) out[(size_t)y * W + x] = static_cast<uint8_t>(v);
     }
 }
 

@@ -159,12 +159,14 @@ struct LaneBases {
     uint8_t* pairs;
     uint8_t* words;
     uint8_t* lx;
+    const uint8_t *lo, *hi;  // the records' extent (bounds-checked build)
 };
 
 template <int D>
 __device__ __forceinline__ LaneBases lane_bases(const SweepArgs& a, int pl) {
     constexpr int K = PathShape<D>::K;
-    return LaneBases{a.rec + 2 * K * pl, a.rec + D + 4 * K * pl, a.rec + a.lx_off + 2 * K * pl};
+    return LaneBases{a.rec + 2 * K * pl, a.rec + D + 4 * K * pl, a.rec + a.lx_off + 2 * K * pl, a.rec,
+                     a.rec + static_cast<size_t>(a.W) * a.H * a.RB};
 }
 
 // One step's inputs for one lane, loaded from the record at byte offset `off`.
@@ -178,15 +180,38 @@ struct StepIn {
     Regs<M::IN_LO ? PW : 0> lo;
     Regs<M::IN_S ? (S8 ? PW : K) : 0> s;
 
+    template <int N>
+    static __device__ __forceinline__ void zero(uint32_t (&r)[N]) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) r[i] = 0u;
+    }
+
     __device__ __forceinline__ void load(const LaneBases& lb, uint32_t off) {
         const uint8_t* p = at(lb.pairs, off);
-        ldg_pairs<K, true>(p, mc.r);
-        if constexpr (M::IN_LO) ldg_pairs<K, false>(at(lb.lx, off), lo.r);
-        if constexpr (M::IN_S) {
-            if constexpr (S8)
-                ldg_pairs<K, false>(p + D, s.r);
+        if (SGM_GUARD(p, 2 * K, lb.lo, lb.hi, 201))
+            ldg_pairs<K, true>(p, mc.r);
+        else
+            zero(mc.r);
+        if constexpr (M::IN_LO) {
+            const uint8_t* q = at(lb.lx, off);
+            if (SGM_GUARD(q, 2 * K, lb.lo, lb.hi, 202))
+                ldg_pairs<K, false>(q, lo.r);
             else
-                ldg_words<K>(reinterpret_cast<const uint32_t*>(at(lb.words, off)), s.r);
+                zero(lo.r);
+        }
+        if constexpr (M::IN_S) {
+            if constexpr (S8) {
+                if (SGM_GUARD(p + D, 2 * K, lb.lo, lb.hi, 203))
+                    ldg_pairs<K, false>(p + D, s.r);
+                else
+                    zero(s.r);
+            } else {
+                const uint8_t* q = at(lb.words, off);
+                if (SGM_GUARD(q, 4 * K, lb.lo, lb.hi, 203))
+                    ldg_words<K>(reinterpret_cast<const uint32_t*>(q), s.r);
+                else
+                    zero(s.r);
+            }
         }
     }
 };
@@ -378,7 +403,10 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
     // penalty at the chunk's start; step k then takes lane k's penalty with
     // one shuffle.  im_last carries the intensity of the step before the chunk.
     static_assert(PF <= G, "one lane per step of a chunk");
-    auto img_at_step = [&](int i) -> uint32_t { return __ldg(a.img + (i < n_own ? g.pix_at(i) : pix0)); };
+    auto img_at_step = [&](int i) -> uint32_t {
+        const int pix = i < n_own ? g.pix_at(i) : pix0;
+        return SGM_GUARD_INDEX(pix, static_cast<long long>(a.W) * a.H, 214) ? __ldg(a.img + pix) : 0u;
+    };
     uint32_t im_nxt = 0, im_last = 0, p2_lane = 0;
     if constexpr (POST != 0) {
         im_nxt = img_at_step(pl);
@@ -403,14 +431,16 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
         ch.step(mc, a.P1x2, p2x2, L);
         const uint32_t off = Geo::kLinear ? off_cur : static_cast<uint32_t>(cur.pix) * RB;
         if constexpr (M::OUT_LX) {
-            if (active) st_pairs<K>(at(lb.lx, off), pack_pairs<K>(L));
+            if (active && SGM_GUARD(at(lb.lx, off), 2 * K, lb.lo, lb.hi, 204))
+                st_pairs<K>(at(lb.lx, off), pack_pairs<K>(L));
         } else if constexpr (MODE == kSumH && S8) {
             // byte sums: every L_r <= 127 here (sum_fits_u8), so the paired
             // bytes of L and of the stored L_r add without carries
             U8Pairs<K> o = pack_pairs<K>(L);
 #pragma unroll
             for (int q = 0; q < (K + 1) / 2; ++q) o.r[q] += in.lo.r[q];
-            if (active) st_pairs<K>(at(lb.pairs, off) + D, o);
+            if (active && SGM_GUARD(at(lb.pairs, off) + D, 2 * K, lb.lo, lb.hi, 205))
+                st_pairs<K>(at(lb.pairs, off) + D, o);
         } else {
             uint32_t s[K];
 #pragma unroll
@@ -434,15 +464,19 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
             }
             if constexpr (M::OUT_S) {
                 if (active) {
-                    if constexpr (S8)
-                        st_pairs<K>(at(lb.pairs, off) + D, pack_pairs<K>(s));
-                    else
-                        st_words<K>(reinterpret_cast<uint32_t*>(at(lb.words, off)), s);
+                    if constexpr (S8) {
+                        if (SGM_GUARD(at(lb.pairs, off) + D, 2 * K, lb.lo, lb.hi, 206))
+                            st_pairs<K>(at(lb.pairs, off) + D, pack_pairs<K>(s));
+                    } else {
+                        if (SGM_GUARD(at(lb.words, off), 4 * K, lb.lo, lb.hi, 206))
+                            st_words<K>(reinterpret_cast<uint32_t*>(at(lb.words, off)), s);
+                    }
                 }
             }
             if constexpr (M::WTA) {
                 const uint32_t key = ch.path_min(wta_key<K, D, KEY16>(s, dconst));
-                if (active && pl == 0) a.raw[cur.pix] = wta_disparity<D, KEY16>(key);
+                if (active && pl == 0 && SGM_GUARD_INDEX(cur.pix, static_cast<long long>(a.W) * a.H, 207))
+                    a.raw[cur.pix] = wta_disparity<D, KEY16>(key);
                 if constexpr (POST != 0) {
                     if (a.sub) {  // uniform: S at the winner's neighbours for the sub-pixel step
                         const int d = wta_disparity<D, KEY16>(key);
@@ -460,7 +494,8 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
                         const uint32_t sm = s_at(d > 0 ? d - 1 : 0), sp = s_at(d + 1 < D ? d + 1 : d);
                         const uint32_t al = d > 0 ? sm - Sd : 0u;
                         const uint32_t ga = d + 1 < D ? sp - Sd : 0u;
-                        if (active && pl == 0) a.sub[cur.pix] = al | ga << 16;
+                        if (active && pl == 0 && SGM_GUARD_INDEX(cur.pix, static_cast<long long>(a.W) * a.H, 208))
+                            a.sub[cur.pix] = al | ga << 16;
                     }
                 }
                 if (DBG && active) {  // debug: natural-order S
@@ -468,8 +503,11 @@ __device__ __forceinline__ void walk(Chain<PathShape<D>::G, PathShape<D>::K>& ch
 #pragma unroll
                     for (int j = 0; j < K; ++j) {
                         const int i = pl * K + j;
-                        a.Sdbg[p * D + i] = static_cast<uint16_t>(s[j] & 0xffffu);
-                        a.Sdbg[p * D + i + D / 2] = static_cast<uint16_t>(s[j] >> 16);
+                        if (SGM_GUARD_INDEX(static_cast<long long>(p * D + i + D / 2),
+                                            static_cast<long long>(a.W) * a.H * D, 209)) {
+                            a.Sdbg[p * D + i] = static_cast<uint16_t>(s[j] & 0xffffu);
+                            a.Sdbg[p * D + i + D / 2] = static_cast<uint16_t>(s[j] >> 16);
+                        }
                     }
                 }
             }
@@ -586,10 +624,14 @@ __device__ __forceinline__ void sweep_h_body(const SweepArgs& a, int bx) {
                                                            G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
         }
         if constexpr (PH == 1) {
-            save_state(ch, state_slot<D>(a, y, r.dir));
+            uint32_t* st = state_slot<D>(a, y, r.dir);
+            if (SGM_GUARD(st, 4 * (K + 3), a.state, a.state_end, 210)) save_state(ch, st);
             return;
         }
-        if constexpr (PH == 2) load_state(ch, state_slot<D>(a, y, r.dir));
+        if constexpr (PH == 2) {
+            const uint32_t* st = state_slot<D>(a, y, r.dir);
+            if (SGM_GUARD(st, 4 * (K + 3), a.state, a.state_end, 211)) load_state(ch, st);
+        }
         if constexpr (PH == 0) pair_barrier<D>();
         {
             const RowGeo g = in_b ? RowGeo{rowbase, Wm - 1, -1} : RowGeo{rowbase, Wm, 1};
@@ -677,10 +719,14 @@ __device__ __forceinline__ void sweep_v_body(const SweepArgs& a, int bx) {
                                                         G == 16 ? (in_b ? nA : nB) : (in_b ? nB : nA), a, r.pl);
         }
         if constexpr (PH == 1) {
-            save_state(ch, state_slot<D>(a, c, r.dir));
+            uint32_t* st = state_slot<D>(a, c, r.dir);
+            if (SGM_GUARD(st, 4 * (K + 3), a.state, a.state_end, 212)) save_state(ch, st);
             return;
         }
-        if constexpr (PH == 2) load_state(ch, state_slot<D>(a, c, r.dir));
+        if constexpr (PH == 2) {
+            const uint32_t* st = state_slot<D>(a, c, r.dir);
+            if (SGM_GUARD(st, 4 * (K + 3), a.state, a.state_end, 213)) load_state(ch, st);
+        }
         if constexpr (PH != 1) {
             if constexpr (PH == 0) pair_barrier<D>();
             const Geo g = in_b ? Geo{W, H, c, Hm - 1, -1} : Geo{W, H, c, Hm, 1};

@@ -15,7 +15,8 @@ from typing import Iterable, Optional, Sequence
 
 from . import build as _build
 
-LIB_PATH = _build.LIB_PATH
+# SGM_BOUNDS_CHECK=1 in the environment selects the bounds-checked build
+LIB_PATH = _build.CHECKED_LIB_PATH if os.environ.get("SGM_BOUNDS_CHECK") == "1" else _build.LIB_PATH
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
@@ -72,6 +73,8 @@ _sig("sgm_served_stats", _i, [_vp, ctypes.POINTER(ctypes.c_double), _i])
 _sig("sgm_served_reset_stats", _i, [_vp])
 _sig("sgm_set_admission_bound", _i, [_vp, ctypes.c_int64])
 _sig("sgm_save_tuning", _i, [_vp, ctypes.c_char_p])
+_sig("sgm_bounds_checked", _i, [])
+_sig("sgm_bounds_fault", ctypes.c_uint, [])
 _sig("sgm_load_tuning", _i, [_vp, ctypes.c_char_p])
 _sig("sgm_debug_stages", _i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp])
 _sig("sgm_kernel_launches", ctypes.c_uint64, [_vp])
@@ -174,6 +177,14 @@ def sgm_submit(ctx, left, right, W, H, D, P1, P2, n_paths, disp_out) -> Optional
     rc = _check(ctx, _lib.sgm_submit(ctx, addr(left), addr(right), W, H, D, P1, P2, n_paths, addr(disp_out),
                                      ctypes.byref(t)), allow=(SGM_OK, SGM_EAGAIN))
     return t.value if rc == SGM_OK else None
+
+
+def sgm_bounds_checked() -> bool:
+    return _lib.sgm_bounds_checked() == 1
+
+
+def sgm_bounds_fault() -> int:
+    return int(_lib.sgm_bounds_fault())
 
 
 def sgm_set_admission_bound(ctx, max_wait_us: int) -> None:
