@@ -51,12 +51,12 @@ SERVED_OUT_RING = 4  # output buffers per pool pair (a pair can be in flight mor
 # reported as null once those sources have changed since the capture.
 MEASURED_TRAFFIC = {
     # the paired schedule's second stage is two kernels side by side: their sum
-    ("sgm_640x480_d128_p4", "pairs_vh"): (119760384, "88d62a9d8634f444"),
-    ("sgm_640x480_d128_p4", "pairs_h_wta"): (79050496 + 78685056, "88d62a9d8634f444"),
-    ("sgm_1242x375_d128_p8", "sweep_h"): (584676352, "88d62a9d8634f444"),
-    ("sgm_1242x375_d128_p8", "sweep_diag+"): (311659392, "88d62a9d8634f444"),
-    ("sgm_1242x375_d128_p8", "sweep_diag-"): (311890048, "88d62a9d8634f444"),
-    ("sgm_1242x375_d128_p8", "sweep_v"): (241657344, "88d62a9d8634f444"),
+    ("sgm_640x480_d128_p4", "pairs_vh"): (119860608, "95b078de84ceb5af"),
+    ("sgm_640x480_d128_p4", "pairs_h_wta"): (79050752 + 78680320, "95b078de84ceb5af"),
+    ("sgm_1242x375_d128_p8", "sweep_h"): (584803456, "95b078de84ceb5af"),
+    ("sgm_1242x375_d128_p8", "sweep_diag+"): (311627264, "95b078de84ceb5af"),
+    ("sgm_1242x375_d128_p8", "sweep_diag-"): (311867008, "95b078de84ceb5af"),
+    ("sgm_1242x375_d128_p8", "sweep_v"): (241667328, "95b078de84ceb5af"),
 }
 KERNEL_SOURCES = ("sgm_sweeps.cuh", "sgm_pairs.cuh", "sgm_device.cuh", "sgm_internal.h")
 
