@@ -544,7 +544,9 @@ __global__ void __launch_bounds__(64) pairs_chain2_kernel(const __grid_constant_
                     right ? Walk{off0 + n1u * QB, QB, au - n1u, 0, 0, r}
                           : Walk{off0 + (ru - 1) * QB, 0u - QB, ru - bu, 0, 0, r},
                     sel);
-    if (a.a > a.n1) pair_sync();  // the other direction's stores of this launch
+    // when the pair meets in the middle each direction stores columns the other
+    // finishes in this launch (also when a == n1: then only right to left does)
+    if (a.W2 > 2 * a.n1) pair_sync();
     walk<D, kWta, S8, KEY16, DBG, kChainPrefetchRegs>(ch, a, lane_bases<D>(a, kMC, right ? kLH1 : kLH0),
                                                       right ? Walk{off0 + au * QB, QB, a.QW - au, au, 1, r}
                                                             : Walk{off0 + (bu - 1) * QB, 0u - QB, bu, bu - 1, -1, r},

@@ -9,8 +9,9 @@ features, the quad costs in natural order, S, the raw and the final
 disparity.  The shapes cover odd and even sizes (padding rows and columns),
 W <= H (the horizontal pair ends in the first launch), H < W <= 2H (an
 overlap finished in parallel) and W > 2H (the horizontal pair meets in the
-middle in the second launch); the penalties cover byte and u16 sums of the
-vertical pair and 16- and 32-bit winner-take-all keys.
+middle in the second launch, including W2 = 2 H2 + 2, where only the
+right-to-left chain stores columns for the other); the penalties cover byte
+and u16 sums of the vertical pair and 16- and 32-bit winner-take-all keys.
 """
 import numpy as np
 import pytest
@@ -68,7 +69,8 @@ def test_every_D_ragged(ctx, D, P2):
 
 
 @pytest.mark.parametrize("W,H", [(1, 1), (1, 9), (9, 1), (2, 2), (3, 3), (2, 33), (33, 2), (17, 23), (64, 64),
-                                 (100, 3), (101, 51), (200, 31), (31, 200), (130, 66), (131, 67)])
+                                 (100, 3), (101, 51), (200, 31), (31, 200), (130, 66), (131, 67), (134, 66),
+                                 (133, 65)])
 def test_sizes_and_split_geometries(ctx, W, H):
     rng = np.random.default_rng(W * 1000 + H)
     left = rng.integers(0, 256, (H, W), dtype=np.uint8)
