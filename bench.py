@@ -46,17 +46,20 @@ SERVED_LINE_SECONDS = 2.5      # the served object of the default line
 SERVED_LINE_BOUND_US = 100000  # its admission bound (estimated wait)
 BATCHED_LINE_STEPS = 5         # timed steps of the batched object of the default line
 SERVED_OUT_RING = 4  # output buffers per pool pair (a pair can be in flight more than once)
-# DRAM bytes (read + write) per launch of a kernel, from the ncu capture summarised
-# under profiles/, with the fingerprint of the kernel sources it was taken on;
-# reported as null once those sources have changed since the capture.
+# DRAM bytes (read + write) per launch of a kernel, from the ncu captures summarised
+# under profiles/, with the fingerprint of the kernel sources they were taken on;
+# reported as null once those sources have changed since the capture.  The
+# 640x480 frame's figures come from the in-sequence capture (--cache-control
+# none: the L2 flushed once before the frame, as in the timed steps); the
+# 8-path frame's from a capture with ncu's default per-launch cache flush.
 MEASURED_TRAFFIC = {
     # the paired schedule's second stage is two kernels side by side: their sum
-    ("sgm_640x480_d128_p4", "pairs_vh"): (119860608, "95b078de84ceb5af"),
-    ("sgm_640x480_d128_p4", "pairs_h_wta"): (79050752 + 78680320, "95b078de84ceb5af"),
-    ("sgm_1242x375_d128_p8", "sweep_h"): (584803456, "95b078de84ceb5af"),
-    ("sgm_1242x375_d128_p8", "sweep_diag+"): (311627264, "95b078de84ceb5af"),
-    ("sgm_1242x375_d128_p8", "sweep_diag-"): (311867008, "95b078de84ceb5af"),
-    ("sgm_1242x375_d128_p8", "sweep_v"): (241667328, "95b078de84ceb5af"),
+    ("sgm_640x480_d128_p4", "pairs_vh"): (131189248, "f7a7031745fff723"),
+    ("sgm_640x480_d128_p4", "pairs_h_wta"): (59698176 + 73417984, "f7a7031745fff723"),
+    ("sgm_1242x375_d128_p8", "sweep_h"): (585012992, "f7a7031745fff723"),
+    ("sgm_1242x375_d128_p8", "sweep_diag+"): (311625472, "f7a7031745fff723"),
+    ("sgm_1242x375_d128_p8", "sweep_diag-"): (311849088, "f7a7031745fff723"),
+    ("sgm_1242x375_d128_p8", "sweep_v"): (241643136, "f7a7031745fff723"),
 }
 KERNEL_SOURCES = ("sgm_sweeps.cuh", "sgm_pairs.cuh", "sgm_device.cuh", "sgm_internal.h")
 
