@@ -42,6 +42,10 @@ unsigned take_bounds_fault() {
     }
     return first;
 }
+// sgm_stages.cu: copy n bytes src0 -> dst0 and, when src1 is not null,
+// src1 -> dst1 (pinned host buffers to or from the work arena).
+cudaError_t launch_stage(const uint8_t* src0, uint8_t* dst0, const uint8_t* src1, uint8_t* dst1, size_t n,
+                         cudaStream_t stream);
 }  // namespace sgm
 
 namespace {
@@ -784,19 +788,41 @@ static int enqueue_pair(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const ui
                         uint8_t* disp, cudaStream_t s, bool use_graph) {
     const Layout l = layout_for(p);
     const size_t wh = static_cast<size_t>(p.W) * p.H;
-    auto in_place = kernel_accessible;
+    // device buffers are used in place; pinned host buffers are copied by a
+    // staging kernel (each byte crosses the host link once, in wide requests;
+    // the Census tiles would read every image byte several times over the
+    // link); pageable host buffers by cudaMemcpyAsync
+    const cudaMemoryType kl = pointer_kind(left), kr = pointer_kind(right), ko = pointer_kind(disp);
+    auto device_side = [](cudaMemoryType t) { return t == cudaMemoryTypeDevice || t == cudaMemoryTypeManaged; };
     const uint8_t* dl = left;
     const uint8_t* dr = right;
     uint8_t* dout = disp;
-    if (!in_place(left)) {
-        CUDA_TRY(ctx, cudaMemcpyAsync(arena + l.in_left, left, wh, cudaMemcpyHostToDevice, s));
+    const uint8_t* st_src[2] = {nullptr, nullptr};
+    uint8_t* st_dst[2] = {nullptr, nullptr};
+    int n_st = 0;
+    if (!device_side(kl)) {
         dl = arena + l.in_left;
+        if (kl == cudaMemoryTypeHost) {
+            st_src[n_st] = left;
+            st_dst[n_st++] = arena + l.in_left;
+        } else {
+            CUDA_TRY(ctx, cudaMemcpyAsync(arena + l.in_left, left, wh, cudaMemcpyHostToDevice, s));
+        }
     }
-    if (!in_place(right)) {
-        CUDA_TRY(ctx, cudaMemcpyAsync(arena + l.in_right, right, wh, cudaMemcpyHostToDevice, s));
+    if (!device_side(kr)) {
         dr = arena + l.in_right;
+        if (kr == cudaMemoryTypeHost) {
+            st_src[n_st] = right;
+            st_dst[n_st++] = arena + l.in_right;
+        } else {
+            CUDA_TRY(ctx, cudaMemcpyAsync(arena + l.in_right, right, wh, cudaMemcpyHostToDevice, s));
+        }
     }
-    const bool out_staged = !in_place(disp);
+    if (n_st > 0) {
+        CUDA_TRY(ctx, launch_stage(st_src[0], st_dst[0], st_src[1], st_dst[1], wh, s));
+        ctx->launches += 1;
+    }
+    const bool out_staged = !device_side(ko);
     if (out_staged) dout = arena + l.out;
     if (use_graph) {
         Problem q = p;
@@ -807,7 +833,15 @@ static int enqueue_pair(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const ui
     } else {
         CUDA_TRY(ctx, enqueue_path(ctx, p, arena, dl, dr, dout, nullptr, s, false));
     }
-    if (out_staged) CUDA_TRY(ctx, cudaMemcpyAsync(disp, dout, (p.post ? 2 : 1) * wh, cudaMemcpyDeviceToHost, s));
+    if (out_staged) {
+        const size_t ob = (p.post ? 2 : 1) * wh;
+        if (ko == cudaMemoryTypeHost) {
+            CUDA_TRY(ctx, launch_stage(dout, disp, nullptr, nullptr, ob, s));
+            ctx->launches += 1;
+        } else {
+            CUDA_TRY(ctx, cudaMemcpyAsync(disp, dout, ob, cudaMemcpyDeviceToHost, s));
+        }
+    }
     return SGM_OK;
 }
 

@@ -1,5 +1,6 @@
 // Census (Eq. 1), matching cost (Eq. 2) and the 3x3 median (Section 2,
 // stage 4) of the SGM path in arXiv 1610.04121, for sm_103a.
+#include <algorithm>
 #include <type_traits>
 
 #include "sgm_device.cuh"
@@ -615,6 +616,38 @@ __global__ void __launch_bounds__(kMedW) median_quads_kernel(const uint8_t* __re
 cudaError_t launch_median_quads(const uint8_t* rawq, uint8_t* disp, int W, int H, cudaStream_t stream) {
     dim3 grid((W + kMedW - 1) / kMedW, (H + kMedH - 1) / kMedH);
     median_quads_kernel<<<grid, kMedW, 0, stream>>>(rawq, disp, W, H);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Copies between pinned host buffers and the work arena: few wide requests
+// (16 bytes per thread when both sides and the size allow it), so that the
+// host link carries each byte once.  Up to two buffers per launch
+// (blockIdx.y; src[1] may be null).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) stage_kernel(const uint8_t* __restrict__ src0, uint8_t* __restrict__ dst0,
+                                                    const uint8_t* __restrict__ src1, uint8_t* __restrict__ dst1,
+                                                    size_t n) {
+    const uint8_t* src = blockIdx.y ? src1 : src0;
+    uint8_t* dst = blockIdx.y ? dst1 : dst0;
+    if (!src) return;
+    const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+    const size_t t0 = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (n % 16 == 0 && ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0) {
+        const uint4* s4 = reinterpret_cast<const uint4*>(src);
+        uint4* d4 = reinterpret_cast<uint4*>(dst);
+        for (size_t i = t0; i < n / 16; i += stride) d4[i] = s4[i];
+    } else {
+        for (size_t i = t0; i < n; i += stride) dst[i] = src[i];
+    }
+}
+
+cudaError_t launch_stage(const uint8_t* src0, uint8_t* dst0, const uint8_t* src1, uint8_t* dst1, size_t n,
+                         cudaStream_t stream) {
+    if (n == 0) return cudaSuccess;
+    const size_t per = 256 * 16;  // bytes one block moves per pass
+    const unsigned blocks = static_cast<unsigned>(std::min<size_t>(4 * 152, (n + per - 1) / per));
+    stage_kernel<<<dim3(blocks, src1 ? 2 : 1), 256, 0, stream>>>(src0, dst0, src1, dst1, n);
     return cudaGetLastError();
 }
 
