@@ -29,10 +29,9 @@
  *           path takes L_r = MC; the median copies the one-pixel border ring.
  *  Pointers "host or device": the library asks the CUDA runtime which kind a
  *           pointer is.  Host memory may be pageable (copied through the
- *           context's arena with cudaMemcpyAsync) or pinned (copied by a
- *           staging kernel in the single-pair calls, read and written in
- *           place by the kernels in the batched and served forms).  Device
- *           pointers must be on the context's device and are used in place.
+ *           context's arena with cudaMemcpyAsync) or pinned (copied to and
+ *           from the arena by a staging kernel).  Device pointers must be on
+ *           the context's device and are used in place.
  *  Ownership the caller owns every buffer it passes; the library never frees
  *           or keeps a caller pointer beyond the call, except for
  *           sgm_submit (see there).  The library owns its context, its device

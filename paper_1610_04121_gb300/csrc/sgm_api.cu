@@ -464,14 +464,6 @@ static bool is_device_ptr(const void* p) {
     return t == cudaMemoryTypeDevice || t == cudaMemoryTypeManaged;
 }
 
-// Memory the kernels may read or write in place: device memory, and pinned
-// host memory (mapped into the device's address space); pageable host memory
-// goes through copies.
-static bool kernel_accessible(const void* p) {
-    const cudaMemoryType t = pointer_kind(p);
-    return t == cudaMemoryTypeDevice || t == cudaMemoryTypeManaged || t == cudaMemoryTypeHost;
-}
-
 // Kernels per path: census, cost, the first sweep stage (horizontal pair and
 // vertical-type first halves), the second halves of each vertical-type pair
 // (sweep_diag+, sweep_diag-, sweep_v), median; with 2 paths: census, cost,
@@ -1003,7 +995,7 @@ static size_t build_lists(sgm_ctx* ctx, ListExec& x, const std::vector<BatchItem
             a.pair = it.p.n_paths >= 4;
             a.s8 = s8_for(it.p);
             sa[k] = a;
-            uint8_t* dst = kernel_accessible(it.out) ? it.out : base + l.out;
+            uint8_t* dst = is_device_ptr(it.out) ? it.out : base + l.out;
             dj[k] = MedianJob{base + l.raw, dst, it.p.W, it.p.H};
             cs[k + 1] = cs[k] + census_units(it.p.W, it.p.H);
             ms[k + 1] = ms[k] + cost_units(it.p.W, it.p.H);
@@ -1150,13 +1142,27 @@ static int enqueue_wave(sgm_ctx* ctx, ListExec& x, std::vector<BatchItem>& items
         const Layout l = layout_for(it.p, true);
         const size_t wh = static_cast<size_t>(it.p.W) * it.p.H;
         uint8_t* base = arena + it.offset;
-        if (!kernel_accessible(it.left)) {
-            CUDA_TRY(ctx, cudaMemcpyAsync(base + l.in_left, it.left, wh, cudaMemcpyHostToDevice, s));
-            it.left = base + l.in_left;
+        // host images go to the pair's arena region: pinned ones through a
+        // staging kernel (each byte over the host link once), pageable ones
+        // through cudaMemcpyAsync
+        const uint8_t* st_src[2] = {nullptr, nullptr};
+        uint8_t* st_dst[2] = {nullptr, nullptr};
+        int n_st = 0;
+        for (int side = 0; side < 2; ++side) {
+            const uint8_t*& img = side ? it.right : it.left;
+            if (is_device_ptr(img)) continue;
+            uint8_t* dst = base + (side ? l.in_right : l.in_left);
+            if (pointer_kind(img) == cudaMemoryTypeHost) {
+                st_src[n_st] = img;
+                st_dst[n_st++] = dst;
+            } else {
+                CUDA_TRY(ctx, cudaMemcpyAsync(dst, img, wh, cudaMemcpyHostToDevice, s));
+            }
+            img = dst;
         }
-        if (!kernel_accessible(it.right)) {
-            CUDA_TRY(ctx, cudaMemcpyAsync(base + l.in_right, it.right, wh, cudaMemcpyHostToDevice, s));
-            it.right = base + l.in_right;
+        if (n_st > 0) {
+            CUDA_TRY(ctx, launch_stage(st_src[0], st_dst[0], st_src[1], st_dst[1], wh, s));
+            ctx->launches += 1;
         }
     }
     const auto groups = wave_groups(items, b, e);
@@ -1202,10 +1208,15 @@ static int enqueue_wave(sgm_ctx* ctx, ListExec& x, std::vector<BatchItem>& items
     ctx->launches += per_wave;
     for (size_t i = b; i < e; ++i) {
         const BatchItem& it = items[i];
-        if (!kernel_accessible(it.out)) {
+        if (!is_device_ptr(it.out)) {
             const Layout l = layout_for(it.p, true);
-            CUDA_TRY(ctx, cudaMemcpyAsync(it.out, arena + it.offset + l.out,
-                                          static_cast<size_t>(it.p.W) * it.p.H, cudaMemcpyDeviceToHost, s));
+            const size_t wh = static_cast<size_t>(it.p.W) * it.p.H;
+            if (pointer_kind(it.out) == cudaMemoryTypeHost) {
+                CUDA_TRY(ctx, launch_stage(arena + it.offset + l.out, it.out, nullptr, nullptr, wh, s));
+                ctx->launches += 1;
+            } else {
+                CUDA_TRY(ctx, cudaMemcpyAsync(it.out, arena + it.offset + l.out, wh, cudaMemcpyDeviceToHost, s));
+            }
         }
     }
     return SGM_OK;
