@@ -681,9 +681,24 @@ static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, 
 }
 
 // Enqueue through a cached CUDA graph for this problem and these pointers.
+// Pinned host buffers of one call, copied by staging kernels that are part of
+// the call's graph: the images into the arena before the path, the output out
+// of it after.
+struct HostIO {
+    const uint8_t* src[2] = {nullptr, nullptr};  // host images
+    uint8_t* dst[2] = {nullptr, nullptr};        // their arena copies
+    const uint8_t* out_src = nullptr;            // arena output
+    uint8_t* out_dst = nullptr;                  // host output
+    size_t img_bytes = 0, out_bytes = 0;
+    int launches() const { return (src[0] ? 1 : 0) + (out_src ? 1 : 0); }
+};
+
 static int enqueue_graph(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const uint8_t* left, const uint8_t* right,
-                         uint8_t* disp, cudaStream_t s) {
-    GraphKey key{p, left, right, disp, arena};
+                         uint8_t* disp, cudaStream_t s, const HostIO& io = HostIO{}, const void* key_left = nullptr,
+                         const void* key_right = nullptr, const void* key_out = nullptr) {
+    // the key names the caller's buffers (a staged host buffer's arena copy is
+    // the same for every host buffer)
+    GraphKey key{p, key_left ? key_left : left, key_right ? key_right : right, key_out ? key_out : disp, arena};
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
         if (ctx->graphs.size() >= 64) {
@@ -693,9 +708,14 @@ static int enqueue_graph(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const u
         cudaGraph_t g = nullptr;
         CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
         const uint64_t before = ctx->launches.load();
+        cudaError_t e = cudaSuccess;
+        if (io.src[0]) e = launch_stage(io.src[0], io.dst[0], io.src[1], io.dst[1], io.img_bytes, ctx->capture_stream);
         // paths with post-filters are never stage-timed (sgm_stage_times names the plain path's kernels)
-        cudaError_t e = enqueue_path(ctx, p, arena, left, right, disp, nullptr, ctx->capture_stream,
-                                     ctx->stage_timing && !p.post);
+        if (e == cudaSuccess)
+            e = enqueue_path(ctx, p, arena, left, right, disp, nullptr, ctx->capture_stream,
+                             ctx->stage_timing && !p.post);
+        if (e == cudaSuccess && io.out_src)
+            e = launch_stage(io.out_src, io.out_dst, nullptr, nullptr, io.out_bytes, ctx->capture_stream);
         ctx->launches = before;  // captured, not launched
         cudaError_t e2 = cudaStreamEndCapture(ctx->capture_stream, &g);
         if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -710,7 +730,7 @@ static int enqueue_graph(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const u
         it = ctx->graphs.emplace(key, exec).first;
     }
     CUDA_TRY(ctx, cudaGraphLaunch(it->second, s));
-    ctx->launches += launches_per_path(p);
+    ctx->launches += launches_per_path(p) + io.launches();
     ctx->last_stages = (ctx->stage_timing && !p.post) ? stages_per_path(p) : 0;
     ctx->last_n_paths = (ctx->stage_timing && !p.post) ? p.n_paths : 0;
     ctx->last_sched = p.sched;
@@ -780,23 +800,24 @@ static int enqueue_pair(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const ui
                         uint8_t* disp, cudaStream_t s, bool use_graph) {
     const Layout l = layout_for(p);
     const size_t wh = static_cast<size_t>(p.W) * p.H;
-    // device buffers are used in place; pinned host buffers are copied by a
-    // staging kernel (each byte crosses the host link once, in wide requests;
-    // the Census tiles would read every image byte several times over the
-    // link); pageable host buffers by cudaMemcpyAsync
+    // device buffers are used in place; pinned host buffers are copied by
+    // staging kernels (each byte crosses the host link once, in wide
+    // requests; the Census tiles would read every image byte several times
+    // over the link), inside the call's graph; pageable host buffers by
+    // cudaMemcpyAsync before and after it
     const cudaMemoryType kl = pointer_kind(left), kr = pointer_kind(right), ko = pointer_kind(disp);
     auto device_side = [](cudaMemoryType t) { return t == cudaMemoryTypeDevice || t == cudaMemoryTypeManaged; };
     const uint8_t* dl = left;
     const uint8_t* dr = right;
     uint8_t* dout = disp;
-    const uint8_t* st_src[2] = {nullptr, nullptr};
-    uint8_t* st_dst[2] = {nullptr, nullptr};
+    HostIO io;
+    io.img_bytes = wh;
     int n_st = 0;
     if (!device_side(kl)) {
         dl = arena + l.in_left;
         if (kl == cudaMemoryTypeHost) {
-            st_src[n_st] = left;
-            st_dst[n_st++] = arena + l.in_left;
+            io.src[n_st] = left;
+            io.dst[n_st++] = arena + l.in_left;
         } else {
             CUDA_TRY(ctx, cudaMemcpyAsync(arena + l.in_left, left, wh, cudaMemcpyHostToDevice, s));
         }
@@ -804,36 +825,38 @@ static int enqueue_pair(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const ui
     if (!device_side(kr)) {
         dr = arena + l.in_right;
         if (kr == cudaMemoryTypeHost) {
-            st_src[n_st] = right;
-            st_dst[n_st++] = arena + l.in_right;
+            io.src[n_st] = right;
+            io.dst[n_st++] = arena + l.in_right;
         } else {
             CUDA_TRY(ctx, cudaMemcpyAsync(arena + l.in_right, right, wh, cudaMemcpyHostToDevice, s));
         }
     }
-    if (n_st > 0) {
-        CUDA_TRY(ctx, launch_stage(st_src[0], st_dst[0], st_src[1], st_dst[1], wh, s));
-        ctx->launches += 1;
+    const size_t ob = (p.post ? 2 : 1) * wh;
+    if (!device_side(ko)) {
+        dout = arena + l.out;
+        if (ko == cudaMemoryTypeHost) {
+            io.out_src = dout;
+            io.out_dst = disp;
+            io.out_bytes = ob;
+        }
     }
-    const bool out_staged = !device_side(ko);
-    if (out_staged) dout = arena + l.out;
     if (use_graph) {
+        // the tuner's runs read the arena copies before this call's staging
+        // has filled them: their timing does not depend on the values, and
+        // the graph launched below recomputes the result from the staged ones
         Problem q = p;
         int rc = choose_schedule(ctx, q, arena, dl, dr, dout, s);
         if (rc != SGM_OK) return rc;
-        rc = enqueue_graph(ctx, q, arena, dl, dr, dout, s);
+        rc = enqueue_graph(ctx, q, arena, dl, dr, dout, s, io, left, right, disp);
         if (rc != SGM_OK) return rc;
     } else {
+        if (io.src[0]) CUDA_TRY(ctx, launch_stage(io.src[0], io.dst[0], io.src[1], io.dst[1], wh, s));
         CUDA_TRY(ctx, enqueue_path(ctx, p, arena, dl, dr, dout, nullptr, s, false));
+        if (io.out_src) CUDA_TRY(ctx, launch_stage(io.out_src, io.out_dst, nullptr, nullptr, ob, s));
+        ctx->launches += io.launches();
     }
-    if (out_staged) {
-        const size_t ob = (p.post ? 2 : 1) * wh;
-        if (ko == cudaMemoryTypeHost) {
-            CUDA_TRY(ctx, launch_stage(dout, disp, nullptr, nullptr, ob, s));
-            ctx->launches += 1;
-        } else {
-            CUDA_TRY(ctx, cudaMemcpyAsync(disp, dout, ob, cudaMemcpyDeviceToHost, s));
-        }
-    }
+    if (!device_side(ko) && ko != cudaMemoryTypeHost)
+        CUDA_TRY(ctx, cudaMemcpyAsync(disp, dout, ob, cudaMemcpyDeviceToHost, s));
     return SGM_OK;
 }
 
