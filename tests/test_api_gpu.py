@@ -213,12 +213,12 @@ def test_batch_rejects_a_pair_over_the_cap(sgm):
         c.close()
 
 
-def test_pinned_buffers_used_in_place(sgm):
+def test_pinned_buffers_staged(sgm):
     import torch
 
-    # pinned host buffers are read and written in place by the kernels; a
-    # fresh context tunes first, then replays; pageable buffers beside them
-    # are staged through copies
+    # pinned host buffers are copied to and from the context's arena by
+    # staging kernels inside the call's graph; a fresh context tunes first,
+    # then replays; pageable buffers beside them go through cudaMemcpyAsync
     p = _pair(160, 96, 64, seed=41)
     ref = oracle.sgm(p.left, p.right, 64, 7, 84, 4)
     Lp, Rp = torch.from_numpy(p.left).pin_memory(), torch.from_numpy(p.right).pin_memory()
@@ -245,5 +245,48 @@ def test_pinned_buffers_used_in_place(sgm):
             sgm.sgm_compute_ex(c.handle, Lp, Rp, 160, 96, 64, 7, 84, 4,
                                oracle.POST_SUBPIXEL | oracle.POST_LR_CHECK, o16)
             assert (o16.numpy().view(np.uint16) == ref16).all()
+        # the graph is keyed by the caller's buffers: a second pair of pinned
+        # images of the same shape, alternating with the first, gets its own
+        q = _pair(160, 96, 64, seed=43)
+        refq = oracle.sgm(q.left, q.right, 64, 7, 84, 4)
+        Lq, Rq = torch.from_numpy(q.left).pin_memory(), torch.from_numpy(q.right).pin_memory()
+        for k in range(4):
+            l, r, want = (Lp, Rp, ref) if k % 2 == 0 else (Lq, Rq, refq)
+            sgm.sgm_compute(c.handle, l, r, 160, 96, 64, 7, 84, 4, op)
+            assert (op.numpy() == want).all(), k
+        # sizes that are not whole 16-byte pieces (the staging kernel's byte path)
+        for W, H, npth in ((97, 61, 4), (97, 61, 8), (33, 7, 2)):
+            o = _pair(W, H, 64, seed=W + H + npth)
+            refo = oracle.sgm(o.left, o.right, 64, 7, 84, npth)
+            Lo, Ro = torch.from_numpy(o.left).pin_memory(), torch.from_numpy(o.right).pin_memory()
+            oo = torch.full((H, W), 255, dtype=torch.uint8).pin_memory()
+            sgm.sgm_compute(c.handle, Lo, Ro, W, H, 64, 7, 84, npth, oo)
+            assert (oo.numpy() == refo).all(), (W, H, npth)
+    finally:
+        c.close()
+
+
+def test_pinned_buffers_batched_and_served(sgm):
+    import torch
+
+    # the batched and served forms stage pinned host buffers the same way
+    shapes = [(97, 61, 64, 4), (66, 40, 32, 8), (160, 96, 128, 4)]
+    pairs = [_pair(W, H, D, seed=500 + i) for i, (W, H, D, npth) in enumerate(shapes)]
+    refs = [oracle.sgm(q.left, q.right, D, 7, 84, npth) for q, (W, H, D, npth) in zip(pairs, shapes)]
+    pin = [(torch.from_numpy(q.left).pin_memory(), torch.from_numpy(q.right).pin_memory(),
+            torch.full((H, W), 255, dtype=torch.uint8).pin_memory()) for q, (W, H, D, npth) in zip(pairs, shapes)]
+    c = sgm.Context(0)
+    try:
+        sgm.sgm_compute_batch(c.handle, [(l, r, o, W, H, D, 7, 84, npth)
+                                         for (l, r, o), (W, H, D, npth) in zip(pin, shapes)])
+        for (l, r, o), want in zip(pin, refs):
+            assert (o.numpy() == want).all()
+        for (l, r, o), (W, H, D, npth) in zip(pin, shapes):
+            o.fill_(255)
+        ts = [sgm.sgm_submit(c.handle, l, r, W, H, D, 7, 84, npth, o) for (l, r, o), (W, H, D, npth) in zip(pin, shapes)]
+        for t in ts:
+            assert sgm.sgm_poll(c.handle, t, -1) == sgm.SGM_OK
+        for (l, r, o), want in zip(pin, refs):
+            assert (o.numpy() == want).all()
     finally:
         c.close()
