@@ -680,7 +680,6 @@ static cudaError_t enqueue_path(sgm_ctx* ctx, const Problem& p, uint8_t* arena, 
     return cudaSuccess;
 }
 
-// Enqueue through a cached CUDA graph for this problem and these pointers.
 // Pinned host buffers of one call, copied by staging kernels that are part of
 // the call's graph: the images into the arena before the path, the output out
 // of it after.
@@ -693,11 +692,15 @@ struct HostIO {
     int launches() const { return (src[0] ? 1 : 0) + (out_src ? 1 : 0); }
 };
 
+// Enqueue through a cached CUDA graph for this problem and these pointers.
+// The key names the caller's buffers (a staged host buffer's arena copy is the
+// same for every host buffer).  An address that is staged in one call and
+// used in place in another (freed and reused as another kind of memory)
+// reuses the first call's graph, which is correct for either kind: the copies
+// work on device memory, and the kernels can read pinned host memory.
 static int enqueue_graph(sgm_ctx* ctx, const Problem& p, uint8_t* arena, const uint8_t* left, const uint8_t* right,
                          uint8_t* disp, cudaStream_t s, const HostIO& io = HostIO{}, const void* key_left = nullptr,
                          const void* key_right = nullptr, const void* key_out = nullptr) {
-    // the key names the caller's buffers (a staged host buffer's arena copy is
-    // the same for every host buffer)
     GraphKey key{p, key_left ? key_left : left, key_right ? key_right : right, key_out ? key_out : disp, arena};
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {

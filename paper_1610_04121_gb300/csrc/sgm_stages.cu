@@ -645,8 +645,9 @@ __global__ void __launch_bounds__(256) stage_kernel(const uint8_t* __restrict__ 
 cudaError_t launch_stage(const uint8_t* src0, uint8_t* dst0, const uint8_t* src1, uint8_t* dst1, size_t n,
                          cudaStream_t stream) {
     if (n == 0) return cudaSuccess;
-    const size_t per = 256 * 16;  // bytes one block moves per pass
-    const unsigned blocks = static_cast<unsigned>(std::min<size_t>(4 * 152, (n + per - 1) / per));
+    constexpr size_t kPer = 256 * 16;        // bytes one block moves per pass
+    constexpr size_t kMaxBlocks = 4 * 152;   // four per SM of a GB300: enough requests in flight
+    const unsigned blocks = static_cast<unsigned>(std::min<size_t>(kMaxBlocks, (n + kPer - 1) / kPer));
     stage_kernel<<<dim3(blocks, src1 ? 2 : 1), 256, 0, stream>>>(src0, dst0, src1, dst1, n);
     return cudaGetLastError();
 }
